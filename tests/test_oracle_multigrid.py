@@ -1,0 +1,130 @@
+"""Pins of the oracle's multigrid hierarchy: orthonormal aggregation
+prolongators (R = P^H, P^H P = I, Section 3.1), their sparsity, the Galerkin
+definition D_{l+1} = R_l D_l P_l, gamma5-structure of the coarse operators,
+the SAP smoother's defining property, and the telescoping identity of
+eq. mlmc_decomp_trace."""
+import numpy as np
+import pytest
+
+from oracle import multigrid as mg
+from oracle import schwinger as osch
+from oracle.linalg import trace_inverse_dense
+from synthetic import gauge
+
+
+@pytest.fixture(scope="module")
+def hier():
+    U = gauge.links(gauge.field(64, 3.0, 0, sweeps=40))
+    D = osch.dirac_sparse(U, -0.05)
+    return mg.Hierarchy(D, 64, ntv=4, setup_sweeps=3, seed=5)
+
+
+def test_level_rule():
+    assert [mg.default_levels(L) for L in (16, 32, 64, 128, 256, 512, 1024)] == [2, 2, 3, 3, 4, 4, 5]
+
+
+def test_sizes(hier):
+    assert hier.levels == 3
+    assert hier.n == [2 * 64 * 64, 8 * 16 * 16, 8 * 4 * 4]
+
+
+def test_orthonormal_and_aggregate_support(hier):
+    for l, P in enumerate(hier.P):
+        PhP = (P.conj().T @ P).toarray()
+        assert np.abs(PhP - np.eye(P.shape[1])).max() < 1e-13
+        Ls, d = hier.side[l], hier.dof[l]
+        Lc, dc = Ls // 4, hier.dof[l + 1]
+        Pc = P.tocoo()
+        fs = Pc.row // d
+        fk = Pc.row % d
+        cs = Pc.col // dc
+        ck = Pc.col % dc
+        ft, fx = fs // Ls, fs % Ls
+        ct, cx = cs // Lc, cs % Lc
+        assert np.all(ft // 4 == ct) and np.all(fx // 4 == cx)           # aggregate support
+        assert np.all(mg.chirality(fk, d) == mg.chirality(ck, dc))      # chirality blocks
+
+
+@pytest.fixture(scope="module")
+def small3():
+    """A 3-level hierarchy small enough for dense checks (2x2 aggregates)."""
+    U = gauge.links(gauge.field(32, 3.0, 3, sweeps=40))
+    return mg.Hierarchy(osch.dirac_sparse(U, -0.05), 32, levels=3, agg=2, ntv=2,
+                        setup_sweeps=2, seed=1)
+
+
+def test_galerkin_dense(small3):
+    for l in range(small3.levels - 1):
+        P, D = small3.P[l].toarray(), small3.D[l].toarray()
+        assert np.abs(P.conj().T @ D @ P - small3.D[l + 1].toarray()).max() < 1e-13
+
+
+def test_galerkin_on_vectors(hier):
+    rng = np.random.default_rng(2)
+    for l in range(hier.levels - 1):
+        x = rng.standard_normal((hier.n[l + 1], 3)) + 1j * rng.standard_normal((hier.n[l + 1], 3))
+        P = hier.P[l]
+        ref = P.conj().T @ (hier.D[l] @ (P @ x))
+        assert np.abs(hier.D[l + 1] @ x - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_gamma5_coarse(hier):
+    for l in range(hier.levels):
+        g5 = hier.gamma5(l)
+        Dl = hier.D[l]
+        assert abs(g5 @ Dl @ g5 - Dl.conj().T).max() < 1e-13
+        assert np.allclose(g5.diagonal() ** 2, 1.0)
+
+
+def test_coarse_operator_is_nearest_neighbour(hier):
+    Dc = hier.D[1]
+    S = mg.stencil_blocks(Dc, hier.side[1], hier.dof[1])
+    rebuilt = sum(np.abs(S[..., k, :, :]).sum() for k in range(5))
+    assert abs(rebuilt - np.abs(Dc).sum()) < 1e-9 * np.abs(Dc).sum()
+
+
+def test_sap_residual_vanishes_on_updated_colour():
+    L = 16
+    U = gauge.links(gauge.field(L, 3.0, 1, sweeps=30))
+    D = osch.dirac_sparse(U, 0.1)
+    sap = mg.SAP(D, L, 2, 4)
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal(D.shape[0]) + 1j * rng.standard_normal(D.shape[0])
+    x = np.zeros_like(f)
+    for c, (I, inv) in enumerate(sap.sets):
+        r = f - D @ x
+        x[I] += np.einsum("bij,bj->bi", inv, r[I])
+        assert np.abs((f - D @ x)[I]).max() < 1e-12
+    # the class's sweep is exactly these two half steps
+    x2 = sap.sweep(f, np.zeros_like(f))
+    assert np.abs(x2 - x).max() < 1e-14
+    # fixed point: the exact solution is not moved
+    xs = np.linalg.solve(D.toarray(), f)
+    assert np.abs(sap.sweep(f, xs.copy()) - xs).max() < 1e-11
+    # and iterating converges to it
+    y = np.zeros_like(f)
+    for _ in range(60):
+        sap.sweep(f, y)
+    assert np.linalg.norm(y - xs) < 1e-8 * np.linalg.norm(xs)
+
+
+def test_coarse_sap_blocks():
+    U = gauge.links(gauge.field(32, 3.0, 2, sweeps=30))
+    H = mg.Hierarchy(osch.dirac_sparse(U, 0.1), 32, ntv=2, setup_sweeps=1)
+    sap = mg.SAP(H.D[1], H.side[1], H.dof[1], 2)
+    f = np.random.default_rng(1).standard_normal(H.n[1]).astype(complex)
+    x = np.zeros_like(f)
+    I0, inv0 = sap.sets[0]
+    x[I0] += np.einsum("bij,bj->bi", inv0, f[I0])
+    assert np.abs((f - H.D[1] @ x)[I0]).max() < 1e-12
+
+
+def test_telescoping_sum_equals_trace(small3):
+    from oracle.estimators import LevelDifference
+    for form in ("accumulated", "reduced"):
+        ld = LevelDifference(small3, form)
+        # traces of the level differences from their explicit matrices
+        diffs = [complex(np.trace(ld.apply(l, np.eye(ld.vec_size(l))))) for l in range(2)]
+        tL = complex(np.trace(np.linalg.inv(small3.D[2].toarray())))
+        total = sum(diffs) + tL
+        assert abs(total - trace_inverse_dense(small3.D[0].toarray())) < 1e-10 * abs(total)
