@@ -1,0 +1,274 @@
+/*
+ * mgmlmc.h -- C ABI of the GB300 MG-MLMC++ trace-estimation library.
+ *
+ * The library estimates tr(D^{-1}) for the 2D Schwinger Wilson-Dirac operator
+ * with multigrid multilevel Monte Carlo and Hutch++ deflation of every level
+ * difference (Frommer & Nasr Khalil, "MG-MLMC++ as a Variance Reduction Method
+ * for Estimating the Trace of a Matrix Inverse", Lattice 2022).  Every step of
+ * the computation runs in the library's own CUDA kernels (sm_103a).
+ *
+ * Conventions shared by all calls
+ *   Status      every call returns an int: MGMLMC_OK (0) or a negative
+ *               mgmlmc_status; mgmlmc_last_error(ctx) gives a message.
+ *   Memory      vectors and gauge fields are DEVICE pointers owned by the
+ *               caller unless a parameter says "host".  Objects created by the
+ *               library (mgmlmc_ctx, mgmlmc_hier, mgmlmc_sketch) own their
+ *               device memory and are released by their destroy call.
+ *   Stream      all device work of a call is issued on the stream given to
+ *               mgmlmc_ctx_create.  Calls that take decisions on the host
+ *               (set-up, solves, sketches, estimates, anything that writes to
+ *               a host pointer) synchronise that stream before returning;
+ *               schwinger_apply, mg_apply, mg_restrict, mg_prolong, mg_vcycle
+ *               and mgmlmc_rademacher are asynchronous.
+ *   Complex     interleaved (re, im): complex128 for MGMLMC_FP64 and
+ *               MGMLMC_MIXED, complex64 for MGMLMC_FP32.
+ *   Gauge field U[t][x][mu] complex128, mu = 0 the x direction, mu = 1 the t
+ *               direction, L x L sites, U_mu(x) = exp(i theta_mu(x)).
+ *   Vectors     [rhs][site][dof] with site = t * L_l + x (x fastest) and
+ *               dof 0..d_l-1 (d = 2 spins on the fine level, 2 * ntv on coarse
+ *               levels; on coarse levels dof < ntv has chirality +1).
+ *   Levels      0-based: level 0 is the fine operator D_1 of the paper,
+ *               level nlev-1 the coarsest D_L.
+ */
+#ifndef MGMLMC_H
+#define MGMLMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum mgmlmc_status {
+  MGMLMC_OK = 0,
+  MGMLMC_ERR_INVALID_ARG = -1,   /* bad size, null pointer, unsupported shape */
+  MGMLMC_ERR_OOM = -2,           /* device allocation failed */
+  MGMLMC_ERR_NOT_CONVERGED = -3, /* solver hit its iteration limit; results are the last iterate */
+  MGMLMC_ERR_CUDA = -4,          /* a CUDA runtime call or kernel failed */
+  MGMLMC_ERR_TIMEOUT = -5,       /* a bounded device wait ran out */
+  MGMLMC_ERR_NAN = -6,           /* a norm or sample became NaN/Inf */
+  MGMLMC_ERR_NOT_POSDEF = -7     /* CholeskyQR Gram matrix not positive definite (rank-deficient sketch) */
+};
+
+enum mgmlmc_prec {
+  MGMLMC_FP64 = 0,   /* everything in FP64 */
+  MGMLMC_FP32 = 1,   /* everything in FP32 */
+  MGMLMC_MIXED = 2   /* FP64 vectors and true residuals, FP32 inner Krylov + V-cycle */
+};
+
+enum mgmlmc_form {
+  MGMLMC_ACCUMULATED = 0, /* fine-size Rademacher vectors restricted by Rhat_l (Algorithm 2 as printed) */
+  MGMLMC_REDUCED = 1      /* level-size Rademacher vectors (eq. mlmc_dec_trace_reduced) */
+};
+
+enum mgmlmc_policy { MGMLMC_OPTIMAL = 0, MGMLMC_UNIFORM = 1 };
+
+enum mgmlmc_phase { /* streams of the counter-based Rademacher generator */
+  MGMLMC_PHASE_STOCH = 0, MGMLMC_PHASE_SKETCH = 1, MGMLMC_PHASE_TESTVEC = 2, MGMLMC_PHASE_HUTCH = 3
+};
+
+#define MGMLMC_MAX_LEVELS 8
+
+typedef struct mgmlmc_ctx mgmlmc_ctx;
+typedef struct mgmlmc_hier mgmlmc_hier;
+typedef struct mgmlmc_sketch mgmlmc_sketch;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context bound to `cuda_stream` (a cudaStream_t, may be NULL for the
+ * legacy default stream) on the current device.  *out receives the handle. */
+int mgmlmc_ctx_create(void* cuda_stream, mgmlmc_ctx** out);
+void mgmlmc_ctx_destroy(mgmlmc_ctx* ctx);
+/* Message of the last failing call on this context ("" if none).  Owned by ctx. */
+const char* mgmlmc_last_error(const mgmlmc_ctx* ctx);
+/* Number of this library's kernel launches issued on ctx since creation. */
+int64_t mgmlmc_launch_count(const mgmlmc_ctx* ctx);
+int mgmlmc_version(void);
+
+/* ---- operator ----------------------------------------------------------- */
+
+/* y = D x for the fine Schwinger Wilson-Dirac operator (Section 4; the
+ * formula is the standard Wilson form with sigma_1, sigma_2 hops):
+ *   (D x)(s) = (m0+2) x(s) - 1/2 sum_mu [(1-sigma_mu) U_mu(s) x(s+mu)
+ *                                       + (1+sigma_mu) U_mu(s-mu)^* x(s-mu)]
+ * periodic in x, antiperiodic in t.  U: device complex128 [L][L][2].
+ * x, y: device, nrhs vectors of n = 2 L^2 complex, precision `prec`
+ * (MGMLMC_MIXED reads as FP64).  L even, >= 4.  x and y must not alias. */
+int schwinger_apply(mgmlmc_ctx* ctx, const double* U, int L, double m0,
+                    const void* x, void* y, int nrhs, int prec);
+
+/* Fill out[rhs][i] (device complex128, imaginary part 0) with the real
+ * Rademacher stream (seed, level, phase, sample0 + rhs), i = 0..n-1 (the
+ * isotropic vectors of eq. random_props).  Generator: SplitMix64 finaliser
+ * mix64; key = mix64(seed ^ mix64(level<<56 | phase<<48 | sample));
+ * word(i) = mix64(key + 0x9E3779B97F4A7C15 * (i+1)); sign = top bit. */
+int mgmlmc_rademacher(mgmlmc_ctx* ctx, uint64_t seed, int level, int phase,
+                      int64_t sample0, int64_t n, int nrhs, double* out);
+
+/* ---- multigrid hierarchy (Section 3.1; set-up of Section 4) ------------- */
+
+typedef struct {
+  int levels;            /* number of levels, 0 = coarsen while side > 8 and side % (4 agg) == 0 */
+  int agg;               /* aggregate side in sites (4) */
+  int ntv;               /* test vectors per chirality (8): 2 ntv coarse dof per site */
+  int sap_block_fine;    /* SAP block side on level 0 (4) */
+  int sap_block_coarse;  /* SAP block side on coarse levels (2) */
+  int setup_sweeps;      /* SAP sweeps for D v = 0 that smooth each test vector (4) */
+  int pre_smooth;        /* V-cycle SAP sweeps before the coarse correction (1) */
+  int post_smooth;       /* ... and after (1) */
+  uint64_t seed;         /* test-vector stream seed (phase TESTVEC, level l, sample m) */
+} mg_params;
+
+int mg_params_default(mg_params* p);
+
+/* Build the aggregation hierarchy for D(U, m0): per level l < nlev-1 the ntv
+ * complex Rademacher test vectors are smoothed by setup_sweeps SAP sweeps for
+ * D_l v = 0, split by aggregate (agg x agg sites) and chirality, orthonormalised
+ * (QR with real positive diagonal) into P_l; D_{l+1} = P_l^H D_l P_l
+ * (Galerkin, Section 3) is stored as a 5-point block stencil; the coarsest
+ * operator is inverted densely in FP64.  L must be a multiple of 16. */
+int mg_setup(mgmlmc_ctx* ctx, const double* U, int L, double m0,
+             const mg_params* params, mgmlmc_hier** out);
+void mg_destroy(mgmlmc_hier* h);
+int mg_num_levels(const mgmlmc_hier* h);
+/* side, dof per site and n of level l (any pointer may be NULL). */
+int mg_level_info(const mgmlmc_hier* h, int level, int* side, int* dof, int64_t* n);
+/* tr(D_L^{-1}) of the coarsest level (= tau_L of Algorithm 2), host complex128. */
+int mg_coarsest_trace(const mgmlmc_hier* h, double* tau_L);
+
+/* y = D_l x on level l (vectors of n_l, precision prec). */
+int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y, int nrhs, int prec);
+/* xc = P_l^H xf  (level l -> l+1). */
+int mg_restrict(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* xf, void* xc, int nrhs, int prec);
+/* xf = P_l xc  (level l+1 -> l, overwrites xf). */
+int mg_prolong(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* xc, void* xf, int nrhs, int prec);
+/* Copy P_l to host: complex128 [aggregate T*Lc+X][chirality 2][agg*agg*d_l/2][ntv];
+ * row j of a block is local site (jt*agg+jx) times the dof of that chirality. */
+int mg_get_prolongator(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* host_out);
+/* Copy the stencil of level l >= 1 to host: complex128 [site][dir 5][d][d],
+ * dir = self, +x, -x, +t, -t; block (s, dir) = D_l[rows of s, cols of s+dir]. */
+int mg_get_stencil(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* host_out);
+
+/* One V-cycle from level l as an approximate solve x ~ D_l^{-1} b: SAP
+ * pre-smoothing, coarse correction P_l V(l+1)(P_l^H r), SAP post-smoothing;
+ * the coarsest level applies its dense inverse.  prec FP64 or FP32. */
+int mg_vcycle(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* b, void* x, int nrhs, int prec);
+
+/* ---- batched solver ----------------------------------------------------- */
+
+typedef struct {
+  int m;             /* FGMRES restart length (16) */
+  double tol;        /* stop at true relative residual ||b - D x|| / ||b|| <= tol, per rhs (1e-10) */
+  int maxit;         /* total inner iteration limit per solve (2000) */
+  int precond;       /* 1 = V-cycle preconditioner, 0 = none (GMRES) */
+  int prec;          /* mgmlmc_prec */
+  double inner_tol;  /* MIXED: relative reduction of each FP32 inner solve (1e-6) */
+} solve_params;
+
+typedef struct {
+  int iters;          /* inner iterations of the slowest rhs */
+  int outer;          /* FP64 refinement / restart cycles */
+  double max_relres;  /* largest true relative residual at return */
+  int converged;      /* 1 if every rhs reached tol */
+  int64_t total_iters;/* sum of inner iterations over rhs */
+} solve_stats;
+
+int solve_params_default(solve_params* p);
+
+/* Solve D_l x = b for nrhs right-hand sides with flexible GMRES(m),
+ * preconditioned by the V-cycle, each rhs stopping on its own true residual.
+ * b, x: device, complex128 for FP64/MIXED, complex64 for FP32 (x is output,
+ * its input value is ignored).  iters_out: host int[nrhs] or NULL. */
+int fgmres_batched(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* b, void* x,
+                   int nrhs, const solve_params* sp, solve_stats* st, int* iters_out);
+
+/* ---- MG-MLMC level differences (Section 3.1, Algorithm 2) -------------- */
+
+/* y = (D_l^{-1} - P_l D_{l+1}^{-1} P_l^H) zeta on level l (0 <= l < nlev-1):
+ * the level difference of eq. mlmc_dec_trace_reduced; for the accumulated form
+ * of eq. mlmc_decomp_matrix apply it to Rhat_l zeta and prolong.  zeta, y:
+ * device complex128 [nrhs][n_l]; solves to sp->tol. */
+int mlmc_level_sample(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const double* zeta,
+                      double* y, int nrhs, const solve_params* sp, solve_stats* st);
+
+/* out = Rhat_l zeta = P_{l-1}^H ... P_0^H zeta (fine -> level l), FP64. */
+int mg_restrict_to_level(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const double* zeta_fine,
+                         double* out, int nrhs);
+
+/* ---- Hutch++ deflation (Sections 2.4 and 3.2) -------------------------- */
+
+/* Deflation part of Algorithm 2 for level difference l: S = d Rademacher
+ * vectors (phase SKETCH, samples 0..d-1, restricted by Rhat_l in the
+ * accumulated form), k block power sweeps Y = A_l S, Q = qr(Y) (CholeskyQR2 in
+ * FP64, R with real positive diagonal), S = Q; then the low-rank part
+ * tau_lr = sum_i q_i^H A_l q_i.  Q is kept at level size (Q_fine = Phat_l Q).
+ * tau_lr: host complex128.  *out owns Q (n_l x d, FP64). */
+int hutchpp_sketch_qr(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, int d, int k, uint64_t seed,
+                      int form, const solve_params* sp, mgmlmc_sketch** out, double* tau_lr);
+void hutchpp_sketch_destroy(mgmlmc_sketch* s);
+/* Copy Q to a device buffer complex128 [d][n_l]. */
+int hutchpp_sketch_get_q(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, double* q_dev, int* d, int64_t* n);
+
+/* Projected samples of Algorithm 2: tau_r = z_r^H y_r with z_r = zeta_r - Q Q^H zeta_r,
+ * computed as zeta^H y - (Q^H zeta)^H (Q^H y).  zeta, y: device complex128
+ * [nrhs][n_l]; s may be NULL (no deflation: tau = zeta^H y).  tau_out: host
+ * complex128 [nrhs]. */
+int hutchpp_project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double* zeta, const double* y,
+                    int64_t n, int nrhs, double* tau_out);
+
+/* ---- Algorithm 2 end to end --------------------------------------------- */
+
+typedef struct {
+  double eps;                       /* target relative 1-sigma accuracy */
+  int d[MGMLMC_MAX_LEVELS];         /* deflation vectors per level difference (0 = plain MG-MLMC) */
+  int k;                            /* block power sweeps (2) */
+  int nrhs_max;                     /* largest batch of samples per level (256) */
+  int nrhs_first;                   /* first batch per level (32) */
+  int policy;                       /* mgmlmc_policy */
+  int form;                         /* mgmlmc_form */
+  uint64_t seed;
+  double cost[MGMLMC_MAX_LEVELS];   /* C_l per sample (cost_mode 0) */
+  int cost_mode;                    /* 0 = cost[], 1 = counted flops of each sample's solves */
+  int min_samples;                  /* >= 2 */
+  int64_t max_samples;              /* per level */
+  solve_params solve;
+  double* sample_out[MGMLMC_MAX_LEVELS]; /* optional host buffers, complex128 [sample_cap] */
+  int64_t sample_cap;
+} est_params;
+
+typedef struct {
+  double tau[2];                    /* estimate of tr(D^{-1}) = sum_l (tau_l + tau_l^lr) + tau_L */
+  double sigma;                     /* sqrt(sum_l V_l / N_l) */
+  double tau_L[2];
+  int nlev;
+  int64_t N[MGMLMC_MAX_LEVELS];     /* samples used per level difference */
+  int64_t computed[MGMLMC_MAX_LEVELS]; /* samples computed (>= N; batches overshoot) */
+  double mean[MGMLMC_MAX_LEVELS][2];
+  double V[MGMLMC_MAX_LEVELS];
+  double C[MGMLMC_MAX_LEVELS];
+  double tau_lr[MGMLMC_MAX_LEVELS][2];
+  int64_t solves;                   /* linear solves (right-hand sides) issued */
+  int64_t inner_iters;              /* total inner Krylov iterations */
+  int steps;                        /* s at which Algorithm 2 stopped */
+} est_result;
+
+int est_params_default(est_params* p);
+
+/* MG-MLMC++ (Algorithm 2): per level difference the Hutch++ sketch (d_l, k),
+ * tau_L from the coarsest dense inverse, then the stochastic loop.  Samples
+ * are computed in batches on the GPU; the host replays Algorithm 2 sample by
+ * sample (s = 1, 2, ...) on them, so the stopping decisions are those of the
+ * per-sample algorithm and extra batch samples are discarded. */
+int trace_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const est_params* p, est_result* r);
+
+/* The target-accuracy update of Algorithm 2 for one step (host only, no GPU):
+ * active[l] (in/out, 0/1) becomes 0 when V[l]/N[l] <= rho_l^2 with
+ * rho_l^2 = sqrt(C_l V_l)/sum_j sqrt(C_j V_j) (eps |tau|)^2 (optimal) or
+ * (eps |tau|)^2/nd (uniform); nothing changes while some N[j] < 2. */
+int mlmc_update_active(int nd, int* active, const double* V, const int64_t* N, const double* C,
+                       double eps, double tau_abs, int policy, int min_samples);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGMLMC_H */

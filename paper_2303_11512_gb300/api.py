@@ -1,0 +1,299 @@
+"""Python binding of the MG-MLMC++ library: the C-ABI calls under the same
+names, taking torch CUDA tensors (complex128 for FP64/MIXED vectors,
+complex64 for FP32) and returning plain Python/numpy results.
+
+Vectors are [nrhs, n] tensors (row-major, so the C layout [rhs][site][dof]),
+gauge fields [L, L, 2] complex128 tensors on the GPU.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (ACCUMULATED, FP32, FP64, MIXED, OPTIMAL, REDUCED, UNIFORM, EstParams, EstResult,
+                   MgParams, SolveParams, SolveStats, check)
+
+__all__ = ["Context", "Hierarchy", "Sketch", "schwinger_apply", "mgmlmc_rademacher", "mg_setup",
+           "fgmres_batched", "mlmc_level_sample", "mg_restrict_to_level", "hutchpp_sketch_qr",
+           "hutchpp_project", "trace_estimate", "mlmc_update_active", "FP64", "FP32", "MIXED",
+           "ACCUMULATED", "REDUCED", "OPTIMAL", "UNIFORM"]
+
+
+def _ptr(t: torch.Tensor, dtype=None) -> int:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+    return t.data_ptr()
+
+
+def _vec_dtype(prec: int):
+    return torch.complex64 if prec == FP32 else torch.complex128
+
+
+class Context:
+    """Library context bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        lib = _lib.load()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        h = C.c_void_p()
+        check(lib.mgmlmc_ctx_create(C.c_void_p(s.cuda_stream), C.byref(h)))
+        self.ptr = h
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.load().mgmlmc_launch_count(self.ptr))
+
+    def close(self):
+        if self.ptr:
+            _lib.load().mgmlmc_ctx_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def schwinger_apply(ctx: Context, U: torch.Tensor, L: int, m0: float, x: torch.Tensor, y: torch.Tensor,
+                    prec: int = FP64):
+    """y = D x (fine Schwinger operator); x, y [nrhs, 2 L^2]."""
+    dt = _vec_dtype(prec)
+    nrhs = x.shape[0] if x.dim() == 2 else 1
+    check(_lib.load().schwinger_apply(ctx.ptr, _ptr(U, torch.complex128), L, m0, _ptr(x, dt), _ptr(y, dt),
+                                      nrhs, prec), ctx.ptr)
+
+
+def mgmlmc_rademacher(ctx: Context, seed: int, level: int, phase: int, sample0: int, n: int, nrhs: int,
+                      out: torch.Tensor | None = None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
+    check(_lib.load().mgmlmc_rademacher(ctx.ptr, seed, level, phase, sample0, n, nrhs,
+                                        _ptr(out, torch.complex128)), ctx.ptr)
+    return out
+
+
+def mg_params(**kw) -> MgParams:
+    p = MgParams()
+    _lib.load().mg_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def solve_params(**kw) -> SolveParams:
+    p = SolveParams()
+    _lib.load().solve_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Hierarchy:
+    def __init__(self, ctx: Context, handle: C.c_void_p, L: int, m0: float):
+        self.ctx, self.ptr, self.L, self.m0 = ctx, handle, L, m0
+        lib = _lib.load()
+        self.levels = lib.mg_num_levels(handle)
+        self.side, self.dof, self.n = [], [], []
+        for l in range(self.levels):
+            s, d, n = C.c_int(), C.c_int(), C.c_int64()
+            check(lib.mg_level_info(handle, l, C.byref(s), C.byref(d), C.byref(n)))
+            self.side.append(s.value)
+            self.dof.append(d.value)
+            self.n.append(n.value)
+
+    def coarsest_trace(self) -> complex:
+        t = (C.c_double * 2)()
+        check(_lib.load().mg_coarsest_trace(self.ptr, t))
+        return complex(t[0], t[1])
+
+    def apply(self, level: int, x: torch.Tensor, y: torch.Tensor, prec: int = FP64):
+        dt = _vec_dtype(prec)
+        check(_lib.load().mg_apply(self.ctx.ptr, self.ptr, level, _ptr(x, dt), _ptr(y, dt), x.shape[0], prec),
+              self.ctx.ptr)
+
+    def restrict(self, level: int, xf: torch.Tensor, xc: torch.Tensor, prec: int = FP64):
+        dt = _vec_dtype(prec)
+        check(_lib.load().mg_restrict(self.ctx.ptr, self.ptr, level, _ptr(xf, dt), _ptr(xc, dt), xf.shape[0],
+                                      prec), self.ctx.ptr)
+
+    def prolong(self, level: int, xc: torch.Tensor, xf: torch.Tensor, prec: int = FP64):
+        dt = _vec_dtype(prec)
+        check(_lib.load().mg_prolong(self.ctx.ptr, self.ptr, level, _ptr(xc, dt), _ptr(xf, dt), xc.shape[0],
+                                     prec), self.ctx.ptr)
+
+    def vcycle(self, level: int, b: torch.Tensor, x: torch.Tensor, prec: int = FP64):
+        dt = _vec_dtype(prec)
+        check(_lib.load().mg_vcycle(self.ctx.ptr, self.ptr, level, _ptr(b, dt), _ptr(x, dt), b.shape[0], prec),
+              self.ctx.ptr)
+
+    def get_prolongator(self, level: int, agg: int, ntv: int) -> np.ndarray:
+        Lc = self.side[level + 1]
+        bsz = agg * agg * self.dof[level] // 2
+        out = np.empty((Lc * Lc, 2, bsz, ntv), dtype=np.complex128)
+        check(_lib.load().mg_get_prolongator(self.ctx.ptr, self.ptr, level, out.ctypes.data), self.ctx.ptr)
+        return out
+
+    def get_stencil(self, level: int) -> np.ndarray:
+        s, d = self.side[level], self.dof[level]
+        out = np.empty((s * s, 5, d, d), dtype=np.complex128)
+        check(_lib.load().mg_get_stencil(self.ctx.ptr, self.ptr, level, out.ctypes.data), self.ctx.ptr)
+        return out
+
+    def close(self):
+        if self.ptr:
+            _lib.load().mg_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_setup(ctx: Context, U: torch.Tensor, L: int, m0: float, **params) -> Hierarchy:
+    p = mg_params(**params)
+    h = C.c_void_p()
+    check(_lib.load().mg_setup(ctx.ptr, _ptr(U, torch.complex128), L, m0, C.byref(p), C.byref(h)), ctx.ptr)
+    return Hierarchy(ctx, h, L, m0)
+
+
+def _stats(st: SolveStats) -> dict:
+    return dict(iters=st.iters, outer=st.outer, max_relres=st.max_relres, converged=bool(st.converged),
+                total_iters=st.total_iters)
+
+
+def fgmres_batched(ctx: Context, h: Hierarchy, level: int, b: torch.Tensor, x: torch.Tensor,
+                   raise_on_nonconvergence: bool = True, **solve) -> dict:
+    sp = solve_params(**solve)
+    dt = _vec_dtype(sp.prec)
+    st = SolveStats()
+    nrhs = b.shape[0]
+    its = np.zeros(nrhs, dtype=np.int32)
+    rc = _lib.load().fgmres_batched(ctx.ptr, h.ptr, level, _ptr(b, dt), _ptr(x, dt), nrhs, C.byref(sp),
+                                    C.byref(st), its.ctypes.data)
+    if rc != _lib.ERR_NOT_CONVERGED or raise_on_nonconvergence:
+        check(rc, ctx.ptr)
+    d = _stats(st)
+    d["its"] = its
+    return d
+
+
+def mlmc_level_sample(ctx: Context, h: Hierarchy, level: int, zeta: torch.Tensor, y: torch.Tensor,
+                      **solve) -> dict:
+    sp = solve_params(**solve)
+    st = SolveStats()
+    check(_lib.load().mlmc_level_sample(ctx.ptr, h.ptr, level, _ptr(zeta, torch.complex128),
+                                        _ptr(y, torch.complex128), zeta.shape[0], C.byref(sp), C.byref(st)),
+          ctx.ptr)
+    return _stats(st)
+
+
+def mg_restrict_to_level(ctx: Context, h: Hierarchy, level: int, zeta_fine: torch.Tensor,
+                         out: torch.Tensor | None = None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty((zeta_fine.shape[0], h.n[level]), dtype=torch.complex128, device="cuda")
+    check(_lib.load().mg_restrict_to_level(ctx.ptr, h.ptr, level, _ptr(zeta_fine, torch.complex128),
+                                           _ptr(out, torch.complex128), zeta_fine.shape[0]), ctx.ptr)
+    return out
+
+
+class Sketch:
+    def __init__(self, ctx: Context, handle: C.c_void_p):
+        self.ctx, self.ptr = ctx, handle
+        d, n = C.c_int(), C.c_int64()
+        check(_lib.load().hutchpp_sketch_get_q(ctx.ptr, handle, None, C.byref(d), C.byref(n)), ctx.ptr)
+        self.d, self.n = d.value, n.value
+
+    def Q(self) -> torch.Tensor:
+        q = torch.empty((self.d, self.n), dtype=torch.complex128, device="cuda")
+        check(_lib.load().hutchpp_sketch_get_q(self.ctx.ptr, self.ptr, _ptr(q), None, None), self.ctx.ptr)
+        torch.cuda.synchronize()
+        return q
+
+    def close(self):
+        if self.ptr:
+            _lib.load().hutchpp_sketch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hutchpp_sketch_qr(ctx: Context, h: Hierarchy, level: int, d: int, k: int, seed: int,
+                      form: int = ACCUMULATED, **solve):
+    sp = solve_params(**solve)
+    s = C.c_void_p()
+    t = (C.c_double * 2)()
+    check(_lib.load().hutchpp_sketch_qr(ctx.ptr, h.ptr, level, d, k, seed, form, C.byref(sp), C.byref(s), t),
+          ctx.ptr)
+    return Sketch(ctx, s), complex(t[0], t[1])
+
+
+def hutchpp_project(ctx: Context, sketch: Sketch | None, zeta: torch.Tensor, y: torch.Tensor) -> np.ndarray:
+    nrhs, n = zeta.shape
+    out = np.empty(nrhs, dtype=np.complex128)
+    check(_lib.load().hutchpp_project(ctx.ptr, sketch.ptr if sketch else None, _ptr(zeta, torch.complex128),
+                                      _ptr(y, torch.complex128), n, nrhs,
+                                      out.ctypes.data_as(C.POINTER(C.c_double))), ctx.ptr)
+    return out
+
+
+def trace_estimate(ctx: Context, h: Hierarchy, eps: float = 1e-3, d=32, k: int = 2, nrhs_max: int = 256,
+                   nrhs_first: int = 32, policy: int = OPTIMAL, form: int = ACCUMULATED, seed: int = 0,
+                   cost=None, cost_mode: int = 0, min_samples: int = 2, max_samples: int = 1 << 20,
+                   keep_samples: int = 0, **solve) -> dict:
+    p = EstParams()
+    lib = _lib.load()
+    lib.est_params_default(C.byref(p))
+    nd = h.levels - 1
+    dl = [d] * nd if np.isscalar(d) else list(d)
+    for l in range(nd):
+        p.d[l] = int(dl[l])
+        p.cost[l] = float(1.0 if cost is None else cost[l])
+    p.eps, p.k, p.nrhs_max, p.nrhs_first = eps, k, nrhs_max, nrhs_first
+    p.policy, p.form, p.seed, p.cost_mode = policy, form, seed, cost_mode
+    p.min_samples, p.max_samples = min_samples, max_samples
+    p.solve = solve_params(**solve)
+    bufs = []
+    if keep_samples:
+        for l in range(nd):
+            b = np.zeros(2 * keep_samples, dtype=np.float64)
+            bufs.append(b)
+            p.sample_out[l] = b.ctypes.data_as(C.POINTER(C.c_double))
+        p.sample_cap = keep_samples
+    r = EstResult()
+    check(lib.trace_estimate(ctx.ptr, h.ptr, C.byref(p), C.byref(r)), ctx.ptr)
+    out = dict(tau=complex(r.tau[0], r.tau[1]), sigma=r.sigma, tau_L=complex(r.tau_L[0], r.tau_L[1]),
+               N=[r.N[l] for l in range(nd)], computed=[r.computed[l] for l in range(nd)],
+               mean=[complex(r.mean[l][0], r.mean[l][1]) for l in range(nd)],
+               V=[r.V[l] for l in range(nd)], C=[r.C[l] for l in range(nd)],
+               tau_lr=[complex(r.tau_lr[l][0], r.tau_lr[l][1]) for l in range(nd)],
+               solves=r.solves, inner_iters=r.inner_iters, steps=r.steps)
+    if keep_samples:
+        out["samples"] = [bufs[l].view(np.complex128)[: min(keep_samples, out["computed"][l])] for l in range(nd)]
+    return out
+
+
+def mlmc_update_active(active, V, N, C_, eps: float, tau_abs: float, policy: int = OPTIMAL,
+                       min_samples: int = 2):
+    """Host-only stop test of Algorithm 2 (no GPU needed)."""
+    nd = len(active)
+    a = (C.c_int * nd)(*[int(x) for x in active])
+    v = (C.c_double * nd)(*V)
+    n = (C.c_int64 * nd)(*N)
+    c = (C.c_double * nd)(*C_)
+    check(_lib.load().mlmc_update_active(nd, a, v, n, c, eps, tau_abs, policy, min_samples))
+    return [bool(x) for x in a]

@@ -1,0 +1,376 @@
+// extern "C" entry points of libmgmlmc (declared in include/mgmlmc.h).  Each
+// call validates its arguments, binds the launch counter of its context, runs
+// the engine and maps exceptions to status codes.
+#include <cstring>
+
+#include "engine.cuh"
+
+using namespace mg;
+
+namespace {
+
+template <typename F>
+int guarded(mgmlmc_ctx* ctx, F&& f) {
+  if (!ctx) return MGMLMC_ERR_INVALID_ARG;
+  LaunchScope scope(ctx);
+  try {
+    MG_CUDA(cudaSetDevice(ctx->device));
+    f();
+    ctx->err.clear();
+    return MGMLMC_OK;
+  } catch (const Error& e) {
+    ctx->err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    ctx->err = "host allocation failed";
+    return MGMLMC_ERR_OOM;
+  } catch (const std::exception& e) {
+    ctx->err = e.what();
+    return MGMLMC_ERR_CUDA;
+  }
+}
+
+void check_prec(int prec) {
+  MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32 || prec == MGMLMC_MIXED, "unknown precision");
+}
+
+}  // namespace
+
+extern "C" {
+
+int mgmlmc_version(void) { return 100; }
+
+int mgmlmc_ctx_create(void* stream, mgmlmc_ctx** out) {
+  if (!out) return MGMLMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  mgmlmc_ctx* c = new (std::nothrow) mgmlmc_ctx;
+  if (!c) return MGMLMC_ERR_OOM;
+  c->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaMallocHost((void**)&c->pinned, 64) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MGMLMC_ERR_CUDA;
+  }
+  c->pinned_d = reinterpret_cast<double*>(c->pinned + 8);
+  *out = c;
+  return MGMLMC_OK;
+}
+
+void mgmlmc_ctx_destroy(mgmlmc_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+}
+
+const char* mgmlmc_last_error(const mgmlmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t mgmlmc_launch_count(const mgmlmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int schwinger_apply(mgmlmc_ctx* ctx, const double* U, int L, double m0, const void* x, void* y, int nrhs, int prec) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(U && x && y, "null pointer");
+    MG_CHECK_ARG(L >= 4 && L % 2 == 0, "L must be even and >= 4");
+    MG_CHECK_ARG(nrhs >= 0, "nrhs must be >= 0");
+    MG_CHECK_ARG(x != y, "x and y must not alias");
+    check_prec(prec);
+    if (nrhs == 0) return;
+    cudaStream_t st = ctx->stream;
+    DBuf l64(sizeof(double2) * 2 * L * L, st);
+    DBuf l32(prec == MGMLMC_FP32 ? sizeof(float2) * 2 * L * L : 0, st);
+    prepare_links(st, (const double2*)U, L, l64.as<double2>(), prec == MGMLMC_FP32 ? l32.as<float2>() : nullptr);
+    if (prec == MGMLMC_FP32)
+      wilson_apply<float>(st, l32.as<float2>(), (float)(m0 + 2.0), L, (const float2*)x, (float2*)y, nullptr, nrhs,
+                          nullptr);
+    else
+      wilson_apply<double>(st, l64.as<double2>(), m0 + 2.0, L, (const double2*)x, (double2*)y, nullptr, nrhs,
+                           nullptr);
+  });
+}
+
+int mgmlmc_rademacher(mgmlmc_ctx* ctx, uint64_t seed, int level, int phase, int64_t sample0, int64_t n, int nrhs,
+                      double* out) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(out, "null pointer");
+    MG_CHECK_ARG(level >= 0 && level < 256 && phase >= 0 && phase < 256, "level/phase out of range");
+    MG_CHECK_ARG(sample0 >= 0 && n >= 0 && nrhs >= 0, "negative size");
+    if (n == 0 || nrhs == 0) return;
+    rademacher_fill(ctx->stream, seed, level, phase, sample0, (long)n, nrhs, (double2*)out);
+  });
+}
+
+int mg_params_default(mg_params* p) {
+  if (!p) return MGMLMC_ERR_INVALID_ARG;
+  p->levels = 0;
+  p->agg = 4;
+  p->ntv = 8;
+  p->sap_block_fine = 4;
+  p->sap_block_coarse = 2;
+  p->setup_sweeps = 4;
+  p->pre_smooth = 1;
+  p->post_smooth = 1;
+  p->seed = 0;
+  return MGMLMC_OK;
+}
+
+int mg_setup(mgmlmc_ctx* ctx, const double* U, int L, double m0, const mg_params* params, mgmlmc_hier** out) {
+  if (out) *out = nullptr;
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(U && out, "null pointer");
+    MG_CHECK_ARG(L >= 16 && L % 16 == 0, "L must be a multiple of 16");
+    std::unique_ptr<mgmlmc_hier> h(new mgmlmc_hier);
+    h->ctx = ctx;
+    h->L = L;
+    h->m0 = m0;
+    if (params)
+      h->prm = *params;
+    else
+      mg_params_default(&h->prm);
+    build_hierarchy(ctx, h.get(), (const double2*)U);
+    *out = h.release();
+  });
+}
+
+void mg_destroy(mgmlmc_hier* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->ctx->stream);
+  delete h;
+}
+
+int mg_num_levels(const mgmlmc_hier* h) { return h ? h->nlev : MGMLMC_ERR_INVALID_ARG; }
+
+int mg_level_info(const mgmlmc_hier* h, int level, int* side, int* dof, int64_t* n) {
+  if (!h || level < 0 || level >= h->nlev) return MGMLMC_ERR_INVALID_ARG;
+  if (side) *side = h->lv[level].side;
+  if (dof) *dof = h->lv[level].dof;
+  if (n) *n = h->lv[level].n;
+  return MGMLMC_OK;
+}
+
+int mg_coarsest_trace(const mgmlmc_hier* h, double* tau_L) {
+  if (!h || !tau_L) return MGMLMC_ERR_INVALID_ARG;
+  tau_L[0] = h->lv[h->nlev - 1].trace.x;
+  tau_L[1] = h->lv[h->nlev - 1].trace.y;
+  return MGMLMC_OK;
+}
+
+int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y, int nrhs, int prec) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && x && y && x != y, "null or aliased pointer");
+    MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
+    check_prec(prec);
+    if (nrhs <= 0) return;
+    if (prec == MGMLMC_FP32)
+      op_apply<float>(h, level, (const float2*)x, (float2*)y, nullptr, nrhs, nullptr);
+    else
+      op_apply<double>(h, level, (const double2*)x, (double2*)y, nullptr, nrhs, nullptr);
+  });
+}
+
+int mg_restrict(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* xf, void* xc, int nrhs, int prec) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && xf && xc, "null pointer");
+    MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level out of range");
+    check_prec(prec);
+    if (nrhs <= 0) return;
+    if (prec == MGMLMC_FP32)
+      restrict_level<float>(h, level, (const float2*)xf, (float2*)xc, nrhs);
+    else
+      restrict_level<double>(h, level, (const double2*)xf, (double2*)xc, nrhs);
+  });
+}
+
+int mg_prolong(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* xc, void* xf, int nrhs, int prec) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && xf && xc, "null pointer");
+    MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level out of range");
+    check_prec(prec);
+    if (nrhs <= 0) return;
+    if (prec == MGMLMC_FP32)
+      prolong_level<float>(h, level, (const float2*)xc, (float2*)xf, nrhs);
+    else
+      prolong_level<double>(h, level, (const double2*)xc, (double2*)xf, nrhs);
+  });
+}
+
+int mg_get_prolongator(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* host_out) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && host_out, "null pointer");
+    MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level out of range");
+    const LevelData& L = h->lv[level];
+    MG_CUDA(cudaMemcpyAsync(host_out, L.P64.p, L.P64.bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+int mg_get_stencil(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* host_out) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && host_out, "null pointer");
+    MG_CHECK_ARG(level >= 1 && level < h->nlev, "level out of range");
+    const LevelData& L = h->lv[level];
+    MG_CUDA(cudaMemcpyAsync(host_out, L.st64.p, L.st64.bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+int mg_vcycle(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* b, void* x, int nrhs, int prec) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && b && x && b != x, "null or aliased pointer");
+    MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
+    MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32, "V-cycle precision is FP64 or FP32");
+    if (nrhs <= 0) return;
+    if (prec == MGMLMC_FP32)
+      vcycle<float>(h, level, (const float2*)b, (float2*)x, nrhs, nullptr);
+    else
+      vcycle<double>(h, level, (const double2*)b, (double2*)x, nrhs, nullptr);
+  });
+}
+
+int solve_params_default(solve_params* p) {
+  if (!p) return MGMLMC_ERR_INVALID_ARG;
+  p->m = 16;
+  p->tol = 1e-10;
+  p->maxit = 2000;
+  p->precond = 1;
+  p->prec = MGMLMC_MIXED;
+  p->inner_tol = 1e-6;
+  return MGMLMC_OK;
+}
+
+static void fill_stats(const SolveOut& o, solve_stats* st) {
+  if (!st) return;
+  st->iters = o.iters;
+  st->outer = o.outer;
+  st->max_relres = o.max_relres;
+  st->converged = o.converged;
+  st->total_iters = o.total_iters;
+}
+
+int fgmres_batched(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* b, void* x, int nrhs,
+                   const solve_params* sp, solve_stats* st, int* iters_out) {
+  int nc = 0;
+  int rc = guarded(ctx, [&] {
+    MG_CHECK_ARG(h && b && x && sp && b != x, "null or aliased pointer");
+    MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
+    MG_CHECK_ARG(sp->tol > 0 && sp->maxit > 0, "tol and maxit must be positive");
+    check_prec(sp->prec);
+    if (nrhs <= 0) return;
+    SolveOut o = solve(h, level, b, x, nrhs, *sp);
+    fill_stats(o, st);
+    if (iters_out) std::memcpy(iters_out, o.its.data(), sizeof(int) * nrhs);
+    nc = !o.converged;
+  });
+  if (rc == MGMLMC_OK && nc) {
+    ctx->err = "fgmres_batched: not every right-hand side reached tol";
+    return MGMLMC_ERR_NOT_CONVERGED;
+  }
+  return rc;
+}
+
+int mlmc_level_sample(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const double* zeta, double* y, int nrhs,
+                      const solve_params* sp, solve_stats* st) {
+  int nc = 0;
+  int rc = guarded(ctx, [&] {
+    MG_CHECK_ARG(h && zeta && y && sp && (const void*)zeta != (void*)y, "null or aliased pointer");
+    MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level difference out of range");
+    if (nrhs <= 0) return;
+    SolveOut o = level_sample(h, level, (const double2*)zeta, (double2*)y, nrhs, *sp);
+    fill_stats(o, st);
+    nc = !o.converged;
+  });
+  if (rc == MGMLMC_OK && nc) {
+    ctx->err = "mlmc_level_sample: a solve did not reach tol";
+    return MGMLMC_ERR_NOT_CONVERGED;
+  }
+  return rc;
+}
+
+int mg_restrict_to_level(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const double* zeta_fine, double* out, int nrhs) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && zeta_fine && out, "null pointer");
+    MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
+    if (nrhs <= 0) return;
+    restrict_to_level(h, level, (const double2*)zeta_fine, (double2*)out, nrhs);
+  });
+}
+
+int hutchpp_sketch_qr(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, int d, int k, uint64_t seed, int form,
+                      const solve_params* sp, mgmlmc_sketch** out, double* tau_lr) {
+  if (out) *out = nullptr;
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && sp && out && tau_lr, "null pointer");
+    MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level difference out of range");
+    MG_CHECK_ARG(form == MGMLMC_ACCUMULATED || form == MGMLMC_REDUCED, "unknown form");
+    double2 t;
+    *out = sketch_qr(h, level, d, k, seed, form, *sp, &t);
+    tau_lr[0] = t.x;
+    tau_lr[1] = t.y;
+  });
+}
+
+void hutchpp_sketch_destroy(mgmlmc_sketch* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->st);
+  delete s;
+}
+
+int hutchpp_sketch_get_q(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, double* q_dev, int* d, int64_t* n) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(s, "null sketch");
+    if (d) *d = s->d;
+    if (n) *n = s->n;
+    if (q_dev)
+      MG_CUDA(cudaMemcpyAsync(q_dev, s->Q.p, sizeof(double2) * s->n * s->d, cudaMemcpyDeviceToDevice, ctx->stream));
+  });
+}
+
+int hutchpp_project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double* zeta, const double* y, int64_t n, int nrhs,
+                    double* tau_out) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(zeta && y && tau_out, "null pointer");
+    MG_CHECK_ARG(n > 0, "n must be positive");
+    if (nrhs <= 0) return;
+    std::vector<double2> t(nrhs);
+    project(ctx, s, (const double2*)zeta, (const double2*)y, (long)n, nrhs, t.data());
+    std::memcpy(tau_out, t.data(), sizeof(double2) * nrhs);
+  });
+}
+
+int est_params_default(est_params* p) {
+  if (!p) return MGMLMC_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->eps = 1e-3;
+  for (int l = 0; l < MGMLMC_MAX_LEVELS; ++l) {
+    p->d[l] = 32;
+    p->cost[l] = 1.0;
+  }
+  p->k = 2;
+  p->nrhs_max = 256;
+  p->nrhs_first = 32;
+  p->policy = MGMLMC_OPTIMAL;
+  p->form = MGMLMC_ACCUMULATED;
+  p->seed = 0;
+  p->cost_mode = 0;
+  p->min_samples = 2;
+  p->max_samples = 1 << 20;
+  solve_params_default(&p->solve);
+  return MGMLMC_OK;
+}
+
+int trace_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const est_params* p, est_result* r) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && p && r, "null pointer");
+    MG_CHECK_ARG(p->form == MGMLMC_ACCUMULATED || p->form == MGMLMC_REDUCED, "unknown form");
+    estimate(h, *p, r);
+  });
+}
+
+int mlmc_update_active(int nd, int* active, const double* V, const int64_t* N, const double* C, double eps,
+                       double tau_abs, int policy, int min_samples) {
+  if (nd <= 0 || nd > MGMLMC_MAX_LEVELS || !active || !V || !N || !C) return MGMLMC_ERR_INVALID_ARG;
+  update_active(nd, active, V, N, C, eps, tau_abs, policy, min_samples);
+  return MGMLMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,833 @@
+// Host engine: hierarchy set-up, V-cycle, batched flexible GMRES with FP64
+// iterative refinement, MG-MLMC level differences, Hutch++ sketch/projection
+// and the Algorithm 2 driver.  Every arithmetic step is a kernel of ops_*.cu;
+// the host only sequences launches and takes the per-batch decisions.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+#include "engine.cuh"
+
+namespace mg {
+
+thread_local int64_t* g_launch_counter = nullptr;
+
+// ---------------------------------------------------------------- helpers
+template <typename R> static inline const typename CT<R>::T* links_of(const LevelData& L) {
+  if constexpr (sizeof(R) == 8) return L.links64.as<double2>(); else return L.links32.as<float2>();
+}
+template <typename R> static inline const typename CT<R>::T* st_of(const LevelData& L) {
+  if constexpr (sizeof(R) == 8) return L.st64.as<double2>(); else return L.st32.as<float2>();
+}
+template <typename R> static inline const typename CT<R>::T* sapinv_of(const LevelData& L) {
+  if constexpr (sizeof(R) == 8) return L.sapinv64.as<double2>(); else return L.sapinv32.as<float2>();
+}
+template <typename R> static inline const typename CT<R>::T* P_of(const LevelData& L) {
+  if constexpr (sizeof(R) == 8) return L.P64.as<double2>(); else return L.P32.as<float2>();
+}
+template <typename R> static inline const typename CT<R>::T* inv_of(const LevelData& L) {
+  if constexpr (sizeof(R) == 8) return L.inv64.as<double2>(); else return L.inv32.as<float2>();
+}
+
+static void to_fp32(cudaStream_t st, const DBuf& src, DBuf& dst, size_t count) {
+  dst.alloc(count * sizeof(float2), st);
+  vconvert<float2, double2>(st, src.as<double2>(), dst.as<float2>(), (long)count, 1, nullptr, nullptr);
+}
+
+static int read_flag(mgmlmc_ctx* ctx, const int* dflag) {
+  MG_CUDA(cudaMemcpyAsync(ctx->pinned, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  MG_CUDA(cudaStreamSynchronize(ctx->stream));
+  return ctx->pinned[0];
+}
+
+static int default_levels(int L, int agg) {
+  int lv = 1, side = L;
+  while (side > 8 && side % (4 * agg) == 0) {
+    side /= agg;
+    ++lv;
+  }
+  return lv;
+}
+
+// ---------------------------------------------------------------- operator pieces
+template <typename R>
+void op_apply(mgmlmc_hier* h, int l, const typename CT<R>::T* x, typename CT<R>::T* y, const typename CT<R>::T* b,
+              int nrhs, const int* active) {
+  const LevelData& L = h->lv[l];
+  cudaStream_t st = h->ctx->stream;
+  if (l == 0)
+    wilson_apply<R>(st, links_of<R>(L), (R)L.diag, L.side, x, y, b, nrhs, active);
+  else
+    coarse_apply<R>(st, st_of<R>(L), L.side, L.dof, x, y, b, nrhs, active);
+}
+
+template <typename R>
+static void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>::T* x, int nrhs,
+                      const int* active) {
+  const LevelData& L = h->lv[l];
+  cudaStream_t st = h->ctx->stream;
+  for (int color = 0; color < 2; ++color) {
+    if (l == 0)
+      sap_half_fine<R>(st, links_of<R>(L), (R)L.diag, L.side, L.sap_bs, sapinv_of<R>(L), f, x, color, nrhs, active);
+    else
+      sap_half_coarse<R>(st, st_of<R>(L), L.side, L.dof, L.sap_bs, sapinv_of<R>(L), f, x, color, nrhs, active);
+  }
+}
+
+template <typename R>
+void restrict_level(mgmlmc_hier* h, int l, const typename CT<R>::T* xf, typename CT<R>::T* xc, int nrhs) {
+  const LevelData& L = h->lv[l];
+  restrict_op<R>(h->ctx->stream, P_of<R>(L), L.side, L.dof, h->prm.agg, h->prm.ntv, xf, xc, nrhs, nullptr);
+}
+template <typename R>
+void prolong_level(mgmlmc_hier* h, int l, const typename CT<R>::T* xc, typename CT<R>::T* xf, int nrhs) {
+  const LevelData& L = h->lv[l];
+  prolong_op<R>(h->ctx->stream, P_of<R>(L), L.side, L.dof, h->prm.agg, h->prm.ntv, xc, xf, false, nrhs, nullptr);
+}
+
+template <typename R>
+void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T* e, int nrhs, const int* active) {
+  typedef typename CT<R>::T C;
+  cudaStream_t st = h->ctx->stream;
+  const LevelData& L = h->lv[l];
+  if (l == h->nlev - 1) {
+    dense_apply<R>(st, inv_of<R>(L), (int)L.n, r, e, nrhs, active);
+    return;
+  }
+  const LevelData& Lc = h->lv[l + 1];
+  const int pr = sizeof(R) == 8;
+  C* res = (C*)h->work(pr ? "vc_res64" : "vc_res32", l, sizeof(C) * L.n * nrhs);
+  C* rc = (C*)h->work(pr ? "vc_rc64" : "vc_rc32", l, sizeof(C) * Lc.n * nrhs);
+  C* ec = (C*)h->work(pr ? "vc_ec64" : "vc_ec32", l, sizeof(C) * Lc.n * nrhs);
+  vzero<C>(st, e, L.n, nrhs);
+  for (int s = 0; s < h->prm.pre_smooth; ++s) sap_sweep<R>(h, l, r, e, nrhs, active);
+  op_apply<R>(h, l, e, res, r, nrhs, active);  // res = r - D e
+  restrict_op<R>(st, P_of<R>(L), L.side, L.dof, h->prm.agg, h->prm.ntv, res, rc, nrhs, active);
+  vcycle<R>(h, l + 1, rc, ec, nrhs, active);
+  prolong_op<R>(st, P_of<R>(L), L.side, L.dof, h->prm.agg, h->prm.ntv, ec, e, true, nrhs, active);
+  for (int s = 0; s < h->prm.post_smooth; ++s) sap_sweep<R>(h, l, r, e, nrhs, active);
+}
+
+template void op_apply<float>(mgmlmc_hier*, int, const float2*, float2*, const float2*, int, const int*);
+template void op_apply<double>(mgmlmc_hier*, int, const double2*, double2*, const double2*, int, const int*);
+template void vcycle<float>(mgmlmc_hier*, int, const float2*, float2*, int, const int*);
+template void vcycle<double>(mgmlmc_hier*, int, const double2*, double2*, int, const int*);
+template void restrict_level<float>(mgmlmc_hier*, int, const float2*, float2*, int);
+template void restrict_level<double>(mgmlmc_hier*, int, const double2*, double2*, int);
+template void prolong_level<float>(mgmlmc_hier*, int, const float2*, float2*, int);
+template void prolong_level<double>(mgmlmc_hier*, int, const double2*, double2*, int);
+
+// ---------------------------------------------------------------- hierarchy set-up
+void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U) {
+  cudaStream_t st = ctx->stream;
+  const mg_params& p = h->prm;
+  const int L = h->L;
+  MG_CHECK_ARG(p.agg >= 2 && p.ntv >= 1 && 2 * p.ntv <= 32 && 256 % (2 * p.ntv) == 0,
+               "mg_params: agg >= 2, 2*ntv must divide 256 and be <= 32");
+  h->nlev = p.levels > 0 ? p.levels : default_levels(L, p.agg);
+  MG_CHECK_ARG(h->nlev >= 2 && h->nlev <= MGMLMC_MAX_LEVELS, "need 2..8 levels");
+  h->lv.clear();
+  h->lv.resize(h->nlev);
+  {
+    int side = L;
+    for (int l = 0; l < h->nlev; ++l) {
+      LevelData& lv = h->lv[l];
+      lv.side = side;
+      lv.dof = l == 0 ? 2 : 2 * p.ntv;
+      lv.n = (long)side * side * lv.dof;
+      if (l < h->nlev - 1) {
+        const int bs = l == 0 ? p.sap_block_fine : p.sap_block_coarse;
+        MG_CHECK_ARG(side % p.agg == 0 && side / p.agg >= 4, "every coarse side must be >= 4 and divide evenly");
+        MG_CHECK_ARG(bs >= 1 && side % bs == 0 && (side / bs) % 2 == 0, "SAP block must tile the level in an even grid");
+        MG_CHECK_ARG(bs * bs * lv.dof <= 64, "SAP block dimension limited to 64");
+        lv.sap_bs = bs;
+        lv.sap_bd = bs * bs * lv.dof;
+        side /= p.agg;
+      }
+    }
+  }
+  int* dfail;
+  DBuf failbuf(sizeof(int) * 4, st);
+  dfail = failbuf.as<int>();
+  MG_CUDA(cudaMemsetAsync(dfail, 0, sizeof(int) * 4, st));
+
+  LevelData& l0 = h->lv[0];
+  l0.diag = h->m0 + 2.0;
+  l0.links64.alloc(sizeof(double2) * 2 * L * L, st);
+  l0.links32.alloc(sizeof(float2) * 2 * L * L, st);
+  prepare_links(st, U, L, l0.links64.as<double2>(), l0.links32.as<float2>());
+
+  for (int l = 0; l + 1 < h->nlev; ++l) {
+    LevelData& lv = h->lv[l];
+    LevelData& lc = h->lv[l + 1];
+    const int Ls = lv.side, d = lv.dof, bs = lv.sap_bs, bd = lv.sap_bd;
+    const long n = lv.n;
+    // SAP block inverses
+    const int nb = (Ls / bs) * (Ls / bs);
+    lv.sapinv64.alloc(sizeof(double2) * (size_t)nb * bd * bd, st);
+    if (l == 0)
+      fine_block_matrices(st, lv.links64.as<double2>(), lv.diag, Ls, bs, lv.sapinv64.as<double2>());
+    else
+      coarse_block_matrices(st, lv.st64.as<double2>(), Ls, d, bs, lv.sapinv64.as<double2>());
+    invert_small_batched(st, lv.sapinv64.as<double2>(), nb, bd, dfail + 0);
+    to_fp32(st, lv.sapinv64, lv.sapinv32, (size_t)nb * bd * bd);
+    // test vectors: complex Rademacher, smoothed by SAP sweeps for D v = 0
+    const int ntv = p.ntv;
+    DBuf V(sizeof(double2) * n * ntv, st), f0(sizeof(double2) * n * ntv, st);
+    complex_rademacher_fill(st, p.seed, l, MGMLMC_PHASE_TESTVEC, 0, n, ntv, V.as<double2>());
+    vzero<double2>(st, f0.as<double2>(), n, ntv);
+    for (int s = 0; s < p.setup_sweeps; ++s) sap_sweep<double>(h, l, f0.as<double2>(), V.as<double2>(), ntv, nullptr);
+    f0.release();
+    // prolongator: per (aggregate, chirality) orthonormal blocks
+    const int Lc = Ls / p.agg, dc = 2 * ntv;
+    const int bsz = p.agg * p.agg * d / 2;
+    const size_t pcount = (size_t)Lc * Lc * 2 * bsz * ntv;
+    lv.P64.alloc(sizeof(double2) * pcount, st);
+    gather_tv_blocks(st, V.as<double2>(), Ls, d, p.agg, ntv, lv.P64.as<double2>());
+    V.release();
+    orthonormalise_blocks(st, lv.P64.as<double2>(), Lc * Lc * 2, bsz, ntv, dfail + 1);
+    to_fp32(st, lv.P64, lv.P32, pcount);
+    // Galerkin D_{l+1} = P^H D_l P by colour probing (16 colours x dc probes)
+    const int np = 16 * dc;
+    const long nc = (long)Lc * Lc * dc;
+    {
+      DBuf probes(sizeof(double2) * n * np, st), imgs(sizeof(double2) * n * np, st);
+      make_probes(st, lv.P64.as<double2>(), Ls, d, p.agg, ntv, probes.as<double2>());
+      op_apply<double>(h, l, probes.as<double2>(), imgs.as<double2>(), nullptr, np, nullptr);
+      probes.release();
+      DBuf cimgs(sizeof(double2) * nc * np, st);
+      restrict_op<double>(st, lv.P64.as<double2>(), Ls, d, p.agg, ntv, imgs.as<double2>(), cimgs.as<double2>(), np,
+                          nullptr);
+      imgs.release();
+      const size_t scount = (size_t)Lc * Lc * 5 * dc * dc;
+      lc.st64.alloc(sizeof(double2) * scount, st);
+      extract_stencil(st, cimgs.as<double2>(), Lc, dc, lc.st64.as<double2>());
+      to_fp32(st, lc.st64, lc.st32, scount);
+    }
+  }
+  // coarsest level: dense FP64 inverse and its trace (tau_L of Algorithm 2)
+  {
+    LevelData& lc = h->lv[h->nlev - 1];
+    const int n = (int)lc.n;
+    MG_CHECK_ARG(n <= 8192, "coarsest level too large for the dense inverse");
+    lc.inv64.alloc(sizeof(double2) * (size_t)n * n, st);
+    dense_from_stencil(st, lc.st64.as<double2>(), lc.side, lc.dof, lc.inv64.as<double2>());
+    DBuf piv(sizeof(int) * n, st), work(sizeof(double2) * n, st), tr(sizeof(double2), st);
+    invert_large(st, lc.inv64.as<double2>(), n, piv.as<int>(), work.as<double2>(), dfail + 2);
+    to_fp32(st, lc.inv64, lc.inv32, (size_t)n * n);
+    trace_dense(st, lc.inv64.as<double2>(), n, tr.as<double2>());
+    MG_CUDA(cudaMemcpyAsync(&lc.trace, tr.p, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+  }
+  int fl[4];
+  MG_CUDA(cudaMemcpyAsync(fl, dfail, sizeof(fl), cudaMemcpyDeviceToHost, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+  if (fl[0]) throw Error(MGMLMC_ERR_NAN, "singular SAP block");
+  if (fl[1]) throw Error(MGMLMC_ERR_NAN, "test-vector block of zero norm");
+  if (fl[2]) throw Error(MGMLMC_ERR_NAN, "singular coarsest operator");
+}
+
+// ---------------------------------------------------------------- FGMRES
+// Per-rhs bookkeeping kernels of the batched flexible GMRES(m).
+__global__ void k_gm_init(const double* __restrict__ bn2, const int* __restrict__ act_in, int* act, double* bnorm,
+                          int* its, double* relres, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const double b = sqrt(bn2[r]);
+  bnorm[r] = b;
+  act[r] = (b > 0.0) && (act_in ? act_in[r] : 1);
+  relres[r] = 0.0;
+  its[r] = 0;
+}
+
+__global__ void k_gm_cycle(const double* __restrict__ beta2, int* act, int* cact, int* iact, int* kvec,
+                           double* beta, double2* g, const double* __restrict__ bnorm, const int* __restrict__ its,
+                           double* relres, double tol, int maxit, int m, int nrhs, int* count) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  kvec[r] = 0;
+  if (!act[r]) { cact[r] = 0; iact[r] = 0; return; }
+  const double b = sqrt(beta2[r]);
+  beta[r] = b;
+  relres[r] = b / bnorm[r];
+  const bool nanb = !(b == b) || isinf(b);
+  if (b <= tol * bnorm[r] || its[r] >= maxit || nanb || b == 0.0) {
+    act[r] = 0; cact[r] = 0; iact[r] = 0;
+    if (nanb) relres[r] = b;
+    return;
+  }
+  cact[r] = 1;
+  iact[r] = 1;
+  g[r] = make_double2(b, 0);
+  for (int i = 1; i <= m; ++i) g[(size_t)i * nrhs + r] = make_double2(0, 0);
+  atomicAdd(count, 1);
+}
+
+__global__ void k_gm_arnoldi(int j, int m, int nrhs, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                             const double* __restrict__ hn2, double* hn, double2* H, double* cs, double2* sn,
+                             double2* g, int* iact, int* kvec, int* its, const double* __restrict__ bnorm,
+                             double tol, int maxit, int* count) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs || !iact[r]) return;
+  double2 col[65];
+  for (int i = 0; i <= j; ++i) col[i] = cadd(h1[(size_t)i * nrhs + r], h2[(size_t)i * nrhs + r]);
+  const double hh = sqrt(hn2[r]);
+  col[j + 1] = make_double2(hh, 0);
+  for (int i = 0; i < j; ++i) {
+    const double c = cs[(size_t)i * nrhs + r];
+    const double2 s = sn[(size_t)i * nrhs + r];
+    const double2 a = col[i], b = col[i + 1];
+    col[i] = cadd(cscale(a, c), cmul(s, b));
+    col[i + 1] = csub(cscale(b, c), cmulc(s, a));
+  }
+  // new rotation zeroing col[j+1]
+  const double2 a = col[j], b = col[j + 1];
+  const double na = sqrt(a.x * a.x + a.y * a.y), nb = sqrt(b.x * b.x + b.y * b.y);
+  double c;
+  double2 s, rr;
+  if (na == 0.0) {
+    c = 0.0; s = make_double2(1, 0); rr = b;
+  } else {
+    const double t = sqrt(na * na + nb * nb);
+    const double2 ph = make_double2(a.x / na, a.y / na);
+    c = na / t;
+    s = cscale(cmul(ph, cconj(b)), 1.0 / t);
+    rr = cscale(ph, t);
+  }
+  cs[(size_t)j * nrhs + r] = c;
+  sn[(size_t)j * nrhs + r] = s;
+  col[j] = rr;
+  for (int i = 0; i <= j; ++i) H[((size_t)i * m + j) * nrhs + r] = col[i];
+  const double2 gj = g[(size_t)j * nrhs + r];
+  g[(size_t)(j + 1) * nrhs + r] = cneg(cmulc(s, gj));
+  g[(size_t)j * nrhs + r] = cscale(gj, c);
+  const double2 gn = g[(size_t)(j + 1) * nrhs + r];
+  const double res = sqrt(gn.x * gn.x + gn.y * gn.y);
+  its[r] += 1;
+  kvec[r] = j + 1;
+  hn[r] = hh;
+  if (res <= tol * bnorm[r] || its[r] >= maxit || hh == 0.0 || j + 1 == m || !(res == res)) {
+    iact[r] = 0;
+  } else {
+    atomicAdd(count, 1);
+  }
+}
+
+__global__ void k_gm_trisolve(int m, int nrhs, const double2* __restrict__ H, const double2* __restrict__ g,
+                              const int* __restrict__ kvec, const int* __restrict__ cact, double2* y) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const int k = cact[r] ? kvec[r] : 0;
+  for (int i = m - 1; i >= 0; --i) {
+    if (i >= k) { y[(size_t)i * nrhs + r] = make_double2(0, 0); continue; }
+    double2 s = g[(size_t)i * nrhs + r];
+    for (int q = i + 1; q < k; ++q) s = csub(s, cmul(H[((size_t)i * m + q) * nrhs + r], y[(size_t)q * nrhs + r]));
+    const double2 d = H[((size_t)i * m + i) * nrhs + r];
+    const double dn = d.x * d.x + d.y * d.y;
+    y[(size_t)i * nrhs + r] = dn > 0 ? cscale(cmulc(d, s), 1.0 / dn) : make_double2(0, 0);
+  }
+}
+
+template <typename R>
+struct GmState {
+  typedef typename CT<R>::T C;
+  C *V, *Z;
+  int *act, *cact, *iact, *kvec, *its, *count;
+  double *bnorm, *beta, *beta2, *hn, *hn2, *cs, *relres;
+  double2 *g, *H, *sn, *h1, *h2, *y;
+  void* red;
+};
+
+template <typename R>
+static GmState<R> gm_state(mgmlmc_hier* h, int l, int nrhs, int m) {
+  typedef typename CT<R>::T C;
+  GmState<R> s;
+  const long n = h->lv[l].n;
+  const char* tg = sizeof(R) == 8 ? "gm64" : "gm32";
+  char* b = (char*)h->work(std::string(tg) + "_V", l, sizeof(C) * n * nrhs * (m + 1));
+  s.V = (C*)b;
+  s.Z = (C*)h->work(std::string(tg) + "_Z", l, sizeof(C) * n * nrhs * m);
+  size_t ints = (size_t)nrhs * 6 + 8;
+  int* ip = (int*)h->work(std::string(tg) + "_i", l, sizeof(int) * ints);
+  s.act = ip; s.cact = ip + nrhs; s.iact = ip + 2 * nrhs; s.kvec = ip + 3 * nrhs; s.its = ip + 4 * nrhs;
+  s.count = ip + 6 * nrhs;
+  double* dp = (double*)h->work(std::string(tg) + "_d", l, sizeof(double) * (size_t)nrhs * (7 + m));
+  s.bnorm = dp; s.beta = dp + nrhs; s.beta2 = dp + 2 * nrhs; s.hn = dp + 3 * nrhs; s.hn2 = dp + 4 * nrhs;
+  s.relres = dp + 5 * nrhs; s.cs = dp + 7 * nrhs;
+  double2* cp = (double2*)h->work(std::string(tg) + "_c", l,
+                                  sizeof(double2) * (size_t)nrhs * ((m + 1) + (size_t)(m + 1) * m + m + 2 * (m + 1) + m));
+  s.g = cp; cp += (size_t)(m + 1) * nrhs;
+  s.H = cp; cp += (size_t)(m + 1) * m * nrhs;
+  s.sn = cp; cp += (size_t)m * nrhs;
+  s.h1 = cp; cp += (size_t)(m + 1) * nrhs;
+  s.h2 = cp; cp += (size_t)(m + 1) * nrhs;
+  s.y = cp;
+  s.red = h->work(std::string(tg) + "_r", l, reduce_work_bytes(n, nrhs, m + 1));
+  return s;
+}
+
+// Batched flexible GMRES(m), x0 = 0, each rhs stops at ||b - D x|| <= tol ||b||
+// (true residual, checked at every restart) or after maxit inner iterations.
+// Per-rhs iteration counts are added to its_acc (device, may be null).
+template <typename R>
+static void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<R>::T* x, int nrhs, int m,
+                        double tol, int maxit, bool precond, const int* act_in, int* its_acc, double* relres_out,
+                        int* cycles_out) {
+  typedef typename CT<R>::T C;
+  mgmlmc_ctx* ctx = h->ctx;
+  cudaStream_t st = ctx->stream;
+  const long n = h->lv[l].n;
+  MG_CHECK_ARG(m >= 1 && m <= 64, "FGMRES restart length must be 1..64");
+  GmState<R> s = gm_state<R>(h, l, nrhs, m);
+  const long vs = n * nrhs;
+  const unsigned nb = cdiv(nrhs, 64);
+  vnorm2<C>(st, b, n, nrhs, s.beta2, s.red, act_in);
+  MG_LAUNCH(k_gm_init, nb, 64, 0, st, s.beta2, act_in, s.act, s.bnorm, s.its, s.relres, nrhs);
+  vzero<C>(st, x, n, nrhs);
+  int cycles = 0;
+  for (;; ++cycles) {
+    if (cycles == 0)
+      vcopy<C>(st, b, s.V, n, nrhs);
+    else
+      op_apply<R>(h, l, x, s.V, b, nrhs, s.act);  // V0 = b - D x
+    vnorm2<C>(st, s.V, n, nrhs, s.beta2, s.red, s.act);
+    MG_CUDA(cudaMemsetAsync(s.count, 0, sizeof(int), st));
+    MG_LAUNCH(k_gm_cycle, nb, 64, 0, st, s.beta2, s.act, s.cact, s.iact, s.kvec, s.beta, s.g, s.bnorm, s.its,
+              s.relres, tol, maxit, m, nrhs, s.count);
+    if (read_flag(ctx, s.count) == 0) break;
+    vscale_inv<C>(st, s.beta, s.V, s.V, n, nrhs, s.cact);
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      C* Vj = s.V + (size_t)j * vs;
+      C* Vj1 = s.V + (size_t)(j + 1) * vs;
+      C* Zj = s.Z + (size_t)j * vs;
+      if (precond)
+        vcycle<R>(h, l, Vj, Zj, nrhs, s.iact);
+      else
+        vcopy<C>(st, Vj, Zj, n, nrhs);
+      op_apply<R>(h, l, Zj, Vj1, nullptr, nrhs, s.iact);
+      vmultidot<C>(st, s.V, vs, j + 1, Vj1, n, nrhs, s.h1, s.red, s.iact);
+      vgs_update<C>(st, s.V, vs, j + 1, s.h1, Vj1, n, nrhs, s.iact);
+      vmultidot<C>(st, s.V, vs, j + 1, Vj1, n, nrhs, s.h2, s.red, s.iact);
+      vgs_update<C>(st, s.V, vs, j + 1, s.h2, Vj1, n, nrhs, s.iact);
+      vnorm2<C>(st, Vj1, n, nrhs, s.hn2, s.red, s.iact);
+      MG_CUDA(cudaMemsetAsync(s.count, 0, sizeof(int), st));
+      MG_LAUNCH(k_gm_arnoldi, nb, 64, 0, st, j, m, nrhs, s.h1, s.h2, s.hn2, s.hn, s.H, s.cs, s.sn, s.g, s.iact,
+                s.kvec, s.its, s.bnorm, tol, maxit, s.count);
+      jdone = j + 1;
+      vscale_inv<C>(st, s.hn, Vj1, Vj1, n, nrhs, s.iact);
+      if (read_flag(ctx, s.count) == 0) break;
+    }
+    MG_LAUNCH(k_gm_trisolve, nb, 64, 0, st, m, nrhs, s.H, s.g, s.kvec, s.cact, s.y);
+    vcombine<C>(st, s.Z, vs, jdone, s.y, x, n, nrhs, s.cact);
+  }
+  if (its_acc) {
+    // its_acc += its
+    std::vector<int> a(nrhs), b2(nrhs);
+    MG_CUDA(cudaMemcpyAsync(a.data(), s.its, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaMemcpyAsync(b2.data(), its_acc, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < nrhs; ++r) b2[r] += a[r];
+    MG_CUDA(cudaMemcpyAsync(its_acc, b2.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+  }
+  if (relres_out) MG_CUDA(cudaMemcpyAsync(relres_out, s.relres, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, st));
+  if (cycles_out) *cycles_out = cycles;
+}
+
+__global__ void k_mixed_check(const double* __restrict__ rn2, const double* __restrict__ bn2, int* act,
+                              double* scale, double* relres, double tol, int nrhs, int* count) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const double rn = sqrt(rn2[r]), bn = sqrt(bn2[r]);
+  scale[r] = rn;
+  if (!act[r]) return;
+  relres[r] = bn > 0 ? rn / bn : 0.0;
+  if (!(rn > tol * bn) || !(rn == rn)) {
+    act[r] = 0;
+    if (!(rn == rn)) relres[r] = rn;
+    return;
+  }
+  atomicAdd(count, 1);
+}
+
+__global__ void k_init_act(const double* __restrict__ bn2, int* act, double* relres, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  act[r] = bn2[r] > 0.0;
+  relres[r] = 0.0;
+}
+
+static SolveOut finish_out(mgmlmc_ctx* ctx, const int* its_dev, const double* relres_dev, int nrhs, double tol,
+                           int cycles) {
+  SolveOut o;
+  o.its.resize(nrhs);
+  std::vector<double> rr(nrhs);
+  MG_CUDA(cudaMemcpyAsync(o.its.data(), its_dev, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  MG_CUDA(cudaMemcpyAsync(rr.data(), relres_dev, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  MG_CUDA(cudaStreamSynchronize(ctx->stream));
+  o.outer = cycles;
+  for (int r = 0; r < nrhs; ++r) {
+    o.iters = std::max(o.iters, o.its[r]);
+    o.total_iters += o.its[r];
+    if (!(rr[r] == rr[r])) {
+      o.max_relres = rr[r];
+      o.converged = 0;
+      continue;
+    }
+    o.max_relres = std::max(o.max_relres, rr[r]);
+    if (rr[r] > tol) o.converged = 0;
+  }
+  return o;
+}
+
+SolveOut solve(mgmlmc_hier* h, int l, const void* b, void* x, int nrhs, const solve_params& sp) {
+  mgmlmc_ctx* ctx = h->ctx;
+  cudaStream_t st = ctx->stream;
+  const long n = h->lv[l].n;
+  MG_CHECK_ARG(l >= 0 && l < h->nlev, "level out of range");
+  if (l == h->nlev - 1) {  // coarsest: dense inverse, exact up to rounding
+    if (sp.prec == MGMLMC_FP32)
+      dense_apply<float>(st, h->lv[l].inv32.as<float2>(), (int)n, (const float2*)b, (float2*)x, nrhs, nullptr);
+    else
+      dense_apply<double>(st, h->lv[l].inv64.as<double2>(), (int)n, (const double2*)b, (double2*)x, nrhs, nullptr);
+    SolveOut o;
+    o.its.assign(nrhs, 0);
+    return o;
+  }
+  int* its = (int*)h->work("sv_its", l, sizeof(int) * nrhs);
+  double* relres = (double*)h->work("sv_rr", l, sizeof(double) * nrhs);
+  MG_CUDA(cudaMemsetAsync(its, 0, sizeof(int) * nrhs, st));
+  const bool pc = sp.precond != 0;
+  if (sp.prec == MGMLMC_FP64) {
+    int cyc = 0;
+    fgmres_core<double>(h, l, (const double2*)b, (double2*)x, nrhs, sp.m, sp.tol, sp.maxit, pc, nullptr, its, relres,
+                        &cyc);
+    return finish_out(ctx, its, relres, nrhs, sp.tol, cyc);
+  }
+  if (sp.prec == MGMLMC_FP32) {
+    int cyc = 0;
+    fgmres_core<float>(h, l, (const float2*)b, (float2*)x, nrhs, sp.m, sp.tol, sp.maxit, pc, nullptr, its, relres,
+                       &cyc);
+    return finish_out(ctx, its, relres, nrhs, sp.tol, cyc);
+  }
+  // MIXED: FP64 outer iterative refinement on the true residual, FP32 inner FGMRES
+  MG_CHECK_ARG(sp.prec == MGMLMC_MIXED, "unknown precision");
+  const double2* b64 = (const double2*)b;
+  double2* x64 = (double2*)x;
+  double2* r64 = (double2*)h->work("mx_r", l, sizeof(double2) * n * nrhs);
+  float2* r32 = (float2*)h->work("mx_r32", l, sizeof(float2) * n * nrhs);
+  float2* e32 = (float2*)h->work("mx_e32", l, sizeof(float2) * n * nrhs);
+  double* dd = (double*)h->work("mx_d", l, sizeof(double) * 3 * nrhs);
+  double *bn2 = dd, *rn2 = dd + nrhs, *scale = dd + 2 * nrhs;
+  int* ip = (int*)h->work("mx_i", l, sizeof(int) * (nrhs + 2));
+  int *act = ip, *count = ip + nrhs;
+  void* red = h->work("mx_red", l, reduce_work_bytes(n, nrhs, 1));
+  const unsigned nb = cdiv(nrhs, 64);
+  vnorm2<double2>(st, b64, n, nrhs, bn2, red, nullptr);
+  MG_LAUNCH(k_init_act, nb, 64, 0, st, bn2, act, relres, nrhs);
+  vzero<double2>(st, x64, n, nrhs);
+  const int max_outer = 30;
+  int outer = 0, used = 0;
+  for (;; ++outer) {
+    if (outer == 0)
+      vcopy<double2>(st, b64, r64, n, nrhs);
+    else
+      op_apply<double>(h, l, x64, r64, b64, nrhs, act);
+    vnorm2<double2>(st, r64, n, nrhs, rn2, red, act);
+    MG_CUDA(cudaMemsetAsync(count, 0, sizeof(int), st));
+    MG_LAUNCH(k_mixed_check, nb, 64, 0, st, rn2, bn2, act, scale, relres, sp.tol, nrhs, count);
+    if (read_flag(ctx, count) == 0 || outer >= max_outer || used >= sp.maxit) break;
+    vconvert<float2, double2>(st, r64, r32, n, nrhs, scale, act);
+    const int inner_max = std::min(sp.maxit - used, std::max(sp.m * 4, 8));
+    int cyc = 0;
+    fgmres_core<float>(h, l, r32, e32, nrhs, sp.m, sp.inner_tol, inner_max, pc, act, its, nullptr, &cyc);
+    used += inner_max;
+    vaccum_mixed<float>(st, scale, e32, x64, n, nrhs, act);
+  }
+  return finish_out(ctx, its, relres, nrhs, sp.tol, outer);
+}
+
+// ---------------------------------------------------------------- MG-MLMC level differences
+SolveOut level_sample(mgmlmc_hier* h, int l, const double2* zeta, double2* y, int nrhs, const solve_params& sp) {
+  MG_CHECK_ARG(l >= 0 && l + 1 < h->nlev, "level difference index out of range");
+  cudaStream_t st = h->ctx->stream;
+  const long n = h->lv[l].n, nc = h->lv[l + 1].n;
+  solve_params s2 = sp;
+  if (s2.prec == MGMLMC_FP32) s2.prec = MGMLMC_MIXED;  // samples are FP64 vectors
+  double2* x1 = (double2*)h->work("ls_x1", l, sizeof(double2) * n * nrhs);
+  double2* zc = (double2*)h->work("ls_zc", l, sizeof(double2) * nc * nrhs);
+  double2* x2 = (double2*)h->work("ls_x2", l, sizeof(double2) * nc * nrhs);
+  SolveOut o1 = solve(h, l, zeta, x1, nrhs, s2);
+  restrict_level<double>(h, l, zeta, zc, nrhs);
+  SolveOut o2 = solve(h, l + 1, zc, x2, nrhs, s2);
+  prolong_level<double>(h, l, x2, y, nrhs);
+  vsub_from(st, x1, y, n, nrhs);  // y = x1 - P x2
+  SolveOut o = o1;
+  o.converged = o1.converged && o2.converged;
+  o.max_relres = std::max(o1.max_relres, o2.max_relres);
+  o.iters = std::max(o1.iters, o2.iters);
+  o.total_iters = o1.total_iters + o2.total_iters;
+  // per-rhs cost proxy: iterations weighted by the nnz of each level's operator
+  return o;
+}
+
+void restrict_to_level(mgmlmc_hier* h, int l, const double2* zfine, double2* out, int nrhs) {
+  cudaStream_t st = h->ctx->stream;
+  if (l == 0) {
+    vcopy<double2>(st, zfine, out, h->lv[0].n, nrhs);
+    return;
+  }
+  const double2* src = zfine;
+  for (int k = 0; k < l; ++k) {
+    double2* dst = (k == l - 1) ? out
+                                : (double2*)h->work((k & 1) ? "rt_b" : "rt_a", 0, sizeof(double2) * h->lv[k + 1].n * nrhs);
+    restrict_level<double>(h, k, src, dst, nrhs);
+    src = dst;
+  }
+}
+
+void make_level_vectors(mgmlmc_hier* h, int l, int form, uint64_t seed, int phase, int64_t sample0, int nrhs,
+                        double2* out) {
+  cudaStream_t st = h->ctx->stream;
+  if (form == MGMLMC_REDUCED || l == 0) {
+    rademacher_fill(st, seed, l, phase, sample0, h->lv[l].n, nrhs, out);
+    return;
+  }
+  double2* zf = (double2*)h->work("mlv_fine", 0, sizeof(double2) * h->lv[0].n * nrhs);
+  rademacher_fill(st, seed, l, phase, sample0, h->lv[0].n, nrhs, zf);
+  restrict_to_level(h, l, zf, out, nrhs);
+}
+
+// ---------------------------------------------------------------- Hutch++
+static void cholesky_qr2(mgmlmc_hier* h, double2* Y, int d, long n) {
+  cudaStream_t st = h->ctx->stream;
+  void* work = h->work("cq_work", 0, gram_work_bytes(d, n));
+  double2* G = (double2*)h->work("cq_G", 0, sizeof(double2) * d * d * 2);
+  double2* Rinv = G + d * d;
+  int* fail = (int*)h->work("cq_fail", 0, sizeof(int));
+  MG_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), st));
+  for (int pass = 0; pass < 2; ++pass) {
+    gram(st, Y, d, n, G, work);
+    chol_inv_upper(st, G, d, Rinv, fail);
+    right_mul_upper(st, Y, d, n, Rinv);
+  }
+  if (read_flag(h->ctx, fail)) throw Error(MGMLMC_ERR_NOT_POSDEF, "CholeskyQR2: Gram matrix not positive definite");
+}
+
+mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int form, const solve_params& sp,
+                         double2* tau_lr) {
+  MG_CHECK_ARG(d >= 1 && d <= 32, "sketch size d must be 1..32");
+  MG_CHECK_ARG(k >= 1, "at least one power sweep");
+  cudaStream_t st = h->ctx->stream;
+  const long n = h->lv[l].n;
+  std::unique_ptr<mgmlmc_sketch> sk(new mgmlmc_sketch);
+  sk->level = l; sk->d = d; sk->n = n; sk->st = st;
+  sk->Q.alloc(sizeof(double2) * n * d, st);
+  double2* S = sk->Q.as<double2>();
+  double2* Y = (double2*)h->work("sk_Y", l, sizeof(double2) * n * d);
+  make_level_vectors(h, l, form, seed, MGMLMC_PHASE_SKETCH, 0, d, S);
+  for (int it = 0; it < k; ++it) {
+    SolveOut o = level_sample(h, l, S, Y, d, sp);
+    if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "sketch solves did not converge");
+    cholesky_qr2(h, Y, d, n);
+    vcopy<double2>(st, Y, S, n, d);
+  }
+  SolveOut o = level_sample(h, l, S, Y, d, sp);
+  if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "low-rank solves did not converge");
+  double2* dots = (double2*)h->work("sk_dots", l, sizeof(double2) * d);
+  void* red = h->work("sk_red", l, reduce_work_bytes(n, d, 1));
+  vdot<double2>(st, S, Y, n, d, dots, red, nullptr);
+  std::vector<double2> hd(d);
+  MG_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double2) * d, cudaMemcpyDeviceToHost, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+  double2 t = make_double2(0, 0);
+  for (int i = 0; i < d; ++i) t = cadd(t, hd[i]);
+  *tau_lr = t;
+  return sk.release();
+}
+
+void project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double2* zeta, const double2* y, long n, int nrhs,
+             double2* tau_host) {
+  cudaStream_t st = ctx->stream;
+  const int d = s ? s->d : 0;
+  DBuf a(sizeof(double2) * nrhs, st);
+  DBuf red(reduce_work_bytes(n, nrhs, 1), st);
+  vdot<double2>(st, zeta, y, n, nrhs, a.as<double2>(), red.p, nullptr);
+  std::vector<double2> ha(nrhs), hc, hg;
+  if (d > 0) {
+    MG_CHECK_ARG(s->n == n, "sketch and vectors differ in size");
+    DBuf c(sizeof(double2) * d * nrhs * 2, st);
+    DBuf w(proj_work_bytes(d, n, nrhs), st);
+    proj_coeffs(st, s->Q.as<double2>(), d, zeta, n, nrhs, c.as<double2>(), w.p);
+    proj_coeffs(st, s->Q.as<double2>(), d, y, n, nrhs, c.as<double2>() + (size_t)d * nrhs, w.p);
+    hc.resize((size_t)d * nrhs * 2);
+    MG_CUDA(cudaMemcpyAsync(hc.data(), c.p, sizeof(double2) * hc.size(), cudaMemcpyDeviceToHost, st));
+  }
+  MG_CUDA(cudaMemcpyAsync(ha.data(), a.p, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+  for (int r = 0; r < nrhs; ++r) {
+    double2 t = ha[r];
+    for (int i = 0; i < d; ++i) t = csub(t, cmulc(hc[(size_t)i * nrhs + r], hc[(size_t)(d + i) * nrhs + r]));
+    tau_host[r] = t;
+  }
+}
+
+// ---------------------------------------------------------------- Algorithm 2
+int update_active(int nd, int* active, const double* V, const int64_t* N, const double* C, double eps,
+                  double tau_abs, int policy, int min_samples) {
+  for (int j = 0; j < nd; ++j)
+    if (N[j] < 2) return 0;
+  double denom = 0;
+  for (int j = 0; j < nd; ++j) denom += std::sqrt(C[j] * V[j]);
+  const double t2 = (eps * tau_abs) * (eps * tau_abs);
+  int changed = 0;
+  for (int l = 0; l < nd; ++l) {
+    if (!active[l] || N[l] < min_samples) continue;
+    double rho2;
+    if (policy == MGMLMC_UNIFORM)
+      rho2 = t2 / nd;
+    else
+      rho2 = (denom > 0 ? std::sqrt(C[l] * V[l]) / denom : 1.0 / nd) * t2;
+    if (V[l] / (double)N[l] <= rho2) {
+      active[l] = 0;
+      changed = 1;
+    }
+  }
+  return changed;
+}
+
+struct LevelStats {  // Welford on real and imaginary parts
+  int64_t N = 0;
+  double mr = 0, mi = 0, sr = 0, si = 0, csum = 0;
+  void add(double2 t, double c) {
+    ++N;
+    const double dr = t.x - mr, di = t.y - mi;
+    mr += dr / N;
+    mi += di / N;
+    sr += dr * (t.x - mr);
+    si += di * (t.y - mi);
+    csum += c;
+  }
+  double var() const { return N >= 2 ? (sr + si) / (N - 1) : NAN; }
+  double cost() const { return N ? csum / N : 0; }
+};
+
+void estimate(mgmlmc_hier* h, const est_params& p, est_result* res) {
+  mgmlmc_ctx* ctx = h->ctx;
+  cudaStream_t st = ctx->stream;
+  const int nd = h->nlev - 1;
+  MG_CHECK_ARG(p.eps > 0, "eps must be positive");
+  MG_CHECK_ARG(p.nrhs_max >= 1 && p.nrhs_first >= 1, "batch sizes must be positive");
+  MG_CHECK_ARG(p.min_samples >= 2, "min_samples must be >= 2");
+  std::memset(res, 0, sizeof(*res));
+  res->nlev = h->nlev;
+  std::vector<std::unique_ptr<mgmlmc_sketch>> sk(nd);
+  std::vector<double2> tau_lr(nd, make_double2(0, 0));
+  for (int l = 0; l < nd; ++l) {
+    if (p.d[l] > 0) {
+      sk[l].reset(sketch_qr(h, l, p.d[l], p.k, p.seed, p.form, p.solve, &tau_lr[l]));
+      res->solves += (int64_t)2 * p.d[l] * (p.k + 1);
+    }
+  }
+  const double2 tauL = h->lv[h->nlev - 1].trace;
+  std::vector<std::vector<double2>> samp(nd);
+  std::vector<std::vector<double>> scost(nd);
+  std::vector<LevelStats> stats(nd);
+  std::vector<int> active(nd, 1);
+  int64_t s = 0;
+  const int64_t maxs = p.max_samples > 0 ? p.max_samples : (int64_t)1 << 40;
+  auto run_batch = [&](int l, int nb) {
+    const long n = h->lv[l].n;
+    double2* z = (double2*)h->work("est_z", l, sizeof(double2) * n * nb);
+    double2* y = (double2*)h->work("est_y", l, sizeof(double2) * n * nb);
+    const int64_t s0 = (int64_t)samp[l].size();
+    make_level_vectors(h, l, p.form, p.seed, MGMLMC_PHASE_STOCH, s0, nb, z);
+    SolveOut o = level_sample(h, l, z, y, nb, p.solve);
+    if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "sample solves did not converge");
+    std::vector<double2> t(nb);
+    project(ctx, sk[l].get(), z, y, n, nb, t.data());
+    const double nnz_l = (double)h->lv[l].n * (l == 0 ? 9.0 : 5.0 * h->lv[l].dof);
+    for (int r = 0; r < nb; ++r) {
+      samp[l].push_back(t[r]);
+      scost[l].push_back(p.cost_mode == 1 ? (double)(o.its[r] + 1) * nnz_l : p.cost[l]);
+    }
+    res->solves += 2 * nb;
+    res->inner_iters += o.total_iters;
+  };
+  auto batch_size = [&](int l) -> int {
+    if (samp[l].empty()) return p.nrhs_first;
+    // predicted samples from the current variances: V_l / rho_l^2
+    bool ok = true;
+    double denom = 0;
+    for (int j = 0; j < nd; ++j) {
+      if (stats[j].N < 2) ok = false; else denom += std::sqrt(stats[j].cost() * stats[j].var());
+    }
+    double tr;
+    double tre = tauL.x, tim = tauL.y;
+    for (int j = 0; j < nd; ++j) { tre += stats[j].mr + tau_lr[j].x; tim += stats[j].mi + tau_lr[j].y; }
+    tr = std::hypot(tre, tim);
+    int64_t want = p.nrhs_first;
+    if (ok && denom > 0 && tr > 0) {
+      const double rho2 = (p.policy == MGMLMC_UNIFORM ? 1.0 / nd
+                                                       : std::sqrt(stats[l].cost() * stats[l].var()) / denom) *
+                          (p.eps * tr) * (p.eps * tr);
+      const double need = stats[l].var() / rho2;
+      want = (int64_t)std::ceil(1.15 * need) - (int64_t)samp[l].size() + 1;
+    }
+    want = std::max<int64_t>(want, 8);
+    want = ((want + 7) / 8) * 8;
+    want = std::min<int64_t>(want, p.nrhs_max);
+    want = std::min<int64_t>(want, maxs - (int64_t)samp[l].size());
+    return (int)std::max<int64_t>(1, want);
+  };
+  while (s < maxs) {
+    bool any = false;
+    for (int l = 0; l < nd; ++l) any |= active[l] != 0;
+    if (!any) break;
+    for (int l = 0; l < nd; ++l)
+      if (active[l] && (int64_t)samp[l].size() <= s) run_batch(l, batch_size(l));
+    ++s;
+    for (int l = 0; l < nd; ++l)
+      if (active[l]) stats[l].add(samp[l][s - 1], scost[l][s - 1]);
+    double tre = tauL.x, tim = tauL.y;
+    for (int l = 0; l < nd; ++l) { tre += stats[l].mr + tau_lr[l].x; tim += stats[l].mi + tau_lr[l].y; }
+    std::vector<double> V(nd), C(nd);
+    std::vector<int64_t> N(nd);
+    for (int l = 0; l < nd; ++l) { V[l] = stats[l].var(); C[l] = stats[l].cost(); N[l] = stats[l].N; }
+    update_active(nd, active.data(), V.data(), N.data(), C.data(), p.eps, std::hypot(tre, tim), p.policy,
+                  p.min_samples);
+  }
+  double tre = tauL.x, tim = tauL.y, var = 0;
+  for (int l = 0; l < nd; ++l) {
+    const LevelStats& S = stats[l];
+    res->N[l] = S.N;
+    res->computed[l] = (int64_t)samp[l].size();
+    res->mean[l][0] = S.mr;
+    res->mean[l][1] = S.mi;
+    res->V[l] = S.var();
+    res->C[l] = S.cost();
+    res->tau_lr[l][0] = tau_lr[l].x;
+    res->tau_lr[l][1] = tau_lr[l].y;
+    tre += S.mr + tau_lr[l].x;
+    tim += S.mi + tau_lr[l].y;
+    if (S.N >= 2) var += S.var() / S.N;
+    if (p.sample_out[l]) {
+      const int64_t cnt = std::min<int64_t>(p.sample_cap, (int64_t)samp[l].size());
+      for (int64_t i = 0; i < cnt; ++i) {
+        p.sample_out[l][2 * i] = samp[l][i].x;
+        p.sample_out[l][2 * i + 1] = samp[l][i].y;
+      }
+    }
+  }
+  res->tau[0] = tre;
+  res->tau[1] = tim;
+  res->tau_L[0] = tauL.x;
+  res->tau_L[1] = tauL.y;
+  res->sigma = std::sqrt(var);
+  res->steps = (int)s;
+  (void)st;
+}
+
+}  // namespace mg

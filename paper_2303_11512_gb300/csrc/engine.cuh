@@ -1,0 +1,108 @@
+// Host-side engine: context, multigrid hierarchy, V-cycle, batched FGMRES,
+// MG-MLMC level differences, Hutch++ sketches and the Algorithm 2 driver.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ops.cuh"
+
+struct mgmlmc_ctx {
+  cudaStream_t stream = 0;
+  int device = 0;
+  std::string err;
+  int64_t launches = 0;
+  int* pinned = nullptr;  // small pinned host buffer for flags
+  double* pinned_d = nullptr;
+};
+
+namespace mg {
+
+struct LevelData {
+  int side = 0, dof = 0;
+  long n = 0;
+  // fine level
+  DBuf links64, links32;
+  double diag = 0;
+  // coarse levels (and the coarsest, for mg_apply)
+  DBuf st64, st32;
+  // SAP smoother (all but the coarsest)
+  int sap_bs = 0, sap_bd = 0;
+  DBuf sapinv64, sapinv32;
+  // prolongator to the next coarser level
+  DBuf P64, P32;
+  // coarsest level: dense inverse
+  DBuf inv64, inv32;
+  double2 trace = make_double2(0, 0);
+};
+
+}  // namespace mg
+
+struct mgmlmc_hier {
+  mgmlmc_ctx* ctx = nullptr;
+  int L = 0;
+  double m0 = 0;
+  mg_params prm;
+  int nlev = 0;
+  std::vector<mg::LevelData> lv;
+  std::map<std::tuple<std::string, int>, mg::DBuf> ws;  // workspaces
+  void* work(const std::string& tag, int level, size_t bytes) {
+    auto& b = ws[std::make_tuple(tag, level)];
+    b.ensure(bytes, ctx->stream);
+    return b.p;
+  }
+};
+
+struct mgmlmc_sketch {
+  int level = 0, d = 0;
+  long n = 0;
+  mg::DBuf Q;  // [d][n] complex128
+  cudaStream_t st = 0;
+};
+
+namespace mg {
+
+// RAII binding of the launch counter to a context
+struct LaunchScope {
+  LaunchScope(mgmlmc_ctx* c) { g_launch_counter = &c->launches; }
+  ~LaunchScope() { g_launch_counter = nullptr; }
+};
+
+void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U);
+
+template <typename R>
+void op_apply(mgmlmc_hier* h, int l, const typename CT<R>::T* x, typename CT<R>::T* y, const typename CT<R>::T* b,
+              int nrhs, const int* active);
+template <typename R>
+void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T* e, int nrhs, const int* active);
+template <typename R>
+void restrict_level(mgmlmc_hier* h, int l, const typename CT<R>::T* xf, typename CT<R>::T* xc, int nrhs);
+template <typename R>
+void prolong_level(mgmlmc_hier* h, int l, const typename CT<R>::T* xc, typename CT<R>::T* xf, int nrhs);
+
+struct SolveOut {
+  int iters = 0, outer = 0, converged = 1;
+  double max_relres = 0;
+  int64_t total_iters = 0;
+  std::vector<int> its;  // per rhs
+};
+// b, x device vectors in the precision implied by sp.prec (FP64 for MIXED)
+SolveOut solve(mgmlmc_hier* h, int l, const void* b, void* x, int nrhs, const solve_params& sp);
+// y = (D_l^{-1} - P_l D_{l+1}^{-1} P_l^H) zeta, FP64 vectors
+SolveOut level_sample(mgmlmc_hier* h, int l, const double2* zeta, double2* y, int nrhs, const solve_params& sp);
+void restrict_to_level(mgmlmc_hier* h, int l, const double2* zfine, double2* out, int nrhs);
+// fills zeta (level-l vectors, FP64) for samples sample0.. of level difference l
+void make_level_vectors(mgmlmc_hier* h, int l, int form, uint64_t seed, int phase, int64_t sample0, int nrhs,
+                        double2* out);
+mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int form, const solve_params& sp,
+                         double2* tau_lr);
+void project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double2* zeta, const double2* y, long n, int nrhs,
+             double2* tau_host);
+void estimate(mgmlmc_hier* h, const est_params& p, est_result* r);
+int update_active(int nd, int* active, const double* V, const int64_t* N, const double* C, double eps,
+                  double tau_abs, int policy, int min_samples);
+
+}  // namespace mg

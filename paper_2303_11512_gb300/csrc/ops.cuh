@@ -1,0 +1,130 @@
+// Host-side launchers of the library's CUDA kernels.  All vectors use the
+// canonical layout [rhs][site][dof] with complex entries (float2 / double2).
+// `active` (device int[nrhs] or nullptr) masks right-hand sides: kernels skip
+// every rhs whose flag is 0.
+#pragma once
+
+#include "common.cuh"
+
+namespace mg {
+
+// ---------------------------------------------------------------- fine level
+// links out[site][mu] = -1/2 * eta * U_mu(site); eta = -1 on the t links of the
+// last time slice (antiperiodic fermion boundary folded into the link).
+void prepare_links(cudaStream_t st, const double2* U, int L, double2* l64, float2* l32);
+// y = D x, or y = b - D x when b != nullptr.
+template <typename R>
+void wilson_apply(cudaStream_t st, const typename CT<R>::T* links, R diag, int L,
+                  const typename CT<R>::T* x, typename CT<R>::T* y, const typename CT<R>::T* b,
+                  int nrhs, const int* active);
+// dense diagonal blocks D_BB (bs x bs sites, 2 dof) of the fine operator: out[block][bd][bd]
+void fine_block_matrices(cudaStream_t st, const double2* l64, double diag, int L, int bs, double2* out);
+
+// ---------------------------------------------------------------- coarse levels
+template <typename R>
+void coarse_apply(cudaStream_t st, const typename CT<R>::T* stencil, int Ls, int d,
+                  const typename CT<R>::T* x, typename CT<R>::T* y, const typename CT<R>::T* b,
+                  int nrhs, const int* active);
+void coarse_block_matrices(cudaStream_t st, const double2* stencil, int Ls, int d, int bs, double2* out);
+
+// ---------------------------------------------------------------- SAP
+// one colour half-sweep: x_B += inv_B (f - D x)_B on the blocks of colour `color`.
+template <typename R>
+void sap_half_fine(cudaStream_t st, const typename CT<R>::T* links, R diag, int L, int bs,
+                   const typename CT<R>::T* inv, const typename CT<R>::T* f, typename CT<R>::T* x,
+                   int color, int nrhs, const int* active);
+template <typename R>
+void sap_half_coarse(cudaStream_t st, const typename CT<R>::T* stencil, int Ls, int d, int bs,
+                     const typename CT<R>::T* inv, const typename CT<R>::T* f, typename CT<R>::T* x,
+                     int color, int nrhs, const int* active);
+
+// ---------------------------------------------------------------- transfer
+// P layout: [aggregate][chirality 2][bsz = agg*agg*d/2][ntv]
+template <typename R>
+void restrict_op(cudaStream_t st, const typename CT<R>::T* P, int Ls, int d, int agg, int ntv,
+                 const typename CT<R>::T* xf, typename CT<R>::T* xc, int nrhs, const int* active);
+template <typename R>
+void prolong_op(cudaStream_t st, const typename CT<R>::T* P, int Ls, int d, int agg, int ntv,
+                const typename CT<R>::T* xc, typename CT<R>::T* xf, bool add, int nrhs,
+                const int* active);
+// gather test-vector blocks from V[m][n] into P layout
+void gather_tv_blocks(cudaStream_t st, const double2* V, int Ls, int d, int agg, int ntv, double2* P);
+// orthonormalise every (aggregate, chirality) block of P (bsz x ntv): QR with real positive diag
+void orthonormalise_blocks(cudaStream_t st, double2* P, int nblocks, int bsz, int ntv, int* fail);
+// Galerkin probing: probes[p][n_l] = P e_{colour kappa, coarse dof j}, p = kappa * dc + j
+void make_probes(cudaStream_t st, const double2* P, int Ls, int d, int agg, int ntv, double2* probes);
+// scatter restricted probe images into the coarse stencil [site][5][dc][dc]
+void extract_stencil(cudaStream_t st, const double2* imgs, int Lc, int dc, double2* stencil);
+
+// ---------------------------------------------------------------- dense (coarsest)
+void dense_from_stencil(cudaStream_t st, const double2* stencil, int Ls, int d, double2* A);
+// batched in-place Gauss-Jordan inverse with partial pivoting (one CTA per matrix, bd <= 64)
+void invert_small_batched(cudaStream_t st, double2* A, int nmat, int bd, int* fail);
+// in-place inverse of one n x n matrix (large n); work: n complex
+void invert_large(cudaStream_t st, double2* A, int n, int* piv, double2* work, int* fail);
+template <typename R>
+void dense_apply(cudaStream_t st, const typename CT<R>::T* A, int n, const typename CT<R>::T* x,
+                 typename CT<R>::T* y, int nrhs, const int* active);
+void trace_dense(cudaStream_t st, const double2* A, int n, double2* out);
+
+// ---------------------------------------------------------------- BLAS-1 (per rhs)
+template <typename C> void vzero(cudaStream_t st, C* x, long n, int nrhs);
+template <typename Cd, typename Cs>
+void vconvert(cudaStream_t st, const Cs* x, Cd* y, long n, int nrhs, const double* scale /*per rhs or null*/,
+              const int* active);
+// y = a * x + y  (a per rhs, double2 on device; sign: +1 or -1 multiplies a)
+template <typename C>
+void vaxpy(cudaStream_t st, const double2* a, double sign, const C* x, C* y, long n, int nrhs, const int* active);
+// y = x * (1 / s[rhs]) where s is a double (norm)
+template <typename C>
+void vscale_inv(cudaStream_t st, const double* s, const C* x, C* y, long n, int nrhs, const int* active);
+template <typename C> void vcopy(cudaStream_t st, const C* x, C* y, long n, int nrhs);
+// x (FP64) += scale[rhs] * e (R)
+template <typename R>
+void vaccum_mixed(cudaStream_t st, const double* scale, const typename CT<R>::T* e, double2* x, long n,
+                  int nrhs, const int* active);
+// y = x - y  (FP64)
+void vsub_from(cudaStream_t st, const double2* x, double2* y, long n, int nrhs);
+
+// reductions: out[rhs] (double / double2) on device; work = partial buffer
+size_t reduce_work_bytes(long n, int nrhs, int nvec);
+template <typename C>
+void vnorm2(cudaStream_t st, const C* x, long n, int nrhs, double* out, void* work, const int* active);
+template <typename C>
+void vdot(cudaStream_t st, const C* x, const C* y, long n, int nrhs, double2* out, void* work, const int* active);
+// h[i * nrhs + rhs] = V_i^H w for i < k; V_i = V + i * vstride
+template <typename C>
+void vmultidot(cudaStream_t st, const C* V, long vstride, int k, const C* w, long n, int nrhs, double2* h,
+               void* work, const int* active);
+// w -= sum_i h[i][rhs] V_i
+template <typename C>
+void vgs_update(cudaStream_t st, const C* V, long vstride, int k, const double2* h, C* w, long n, int nrhs,
+                const int* active);
+// x += sum_i y[i][rhs] Z_i
+template <typename C>
+void vcombine(cudaStream_t st, const C* Z, long zstride, int k, const double2* y, C* x, long n, int nrhs,
+              const int* active);
+
+// ---------------------------------------------------------------- RNG
+void rademacher_fill(cudaStream_t st, uint64_t seed, int level, int phase, int64_t sample0, long n,
+                     int nrhs, double2* out);
+void complex_rademacher_fill(cudaStream_t st, uint64_t seed, int level, int phase, int64_t sample0, long n,
+                             int nrhs, double2* out);
+
+// ---------------------------------------------------------------- Hutch++ (FP64)
+// G = Y^H Y, Y = [d][n]; out d x d (row-major, G[i][j] = y_i^H y_j)
+void gram(cudaStream_t st, const double2* Y, int d, long n, double2* G, void* work);
+size_t gram_work_bytes(int d, long n);
+// Cholesky G = R^H R, then Rinv = R^{-1} (upper); fail != 0 if not positive definite
+void chol_inv_upper(cudaStream_t st, const double2* G, int d, double2* Rinv, int* fail);
+// Y <- Y Rinv (in place, Rinv upper triangular)
+void right_mul_upper(cudaStream_t st, double2* Y, int d, long n, const double2* Rinv);
+// c[i][rhs] = Q_i^H x_rhs, Q = [d][n], x = [nrhs][n]
+void proj_coeffs(cudaStream_t st, const double2* Q, int d, const double2* x, long n, int nrhs, double2* c,
+                 void* work);
+size_t proj_work_bytes(int d, long n, int nrhs);
+
+// ---------------------------------------------------------------- misc
+void fill_int(cudaStream_t st, int* p, int v, int n);
+
+}  // namespace mg

@@ -1,0 +1,488 @@
+// Coarse-level kernels: 5-point block stencil apply, SAP block matrices and
+// smoother on coarse levels, aggregation restriction/prolongation (R = P^H,
+// Section 3.1), the per-aggregate orthonormalisation of the test vectors and
+// the Galerkin construction D_{l+1} = P_l^H D_l P_l by colour probing.
+//
+// Stencil layout: st[site][dir][i][j], dir = 0 self, 1 +x, 2 -x, 3 +t, 4 -t;
+// (D x)(s)_i = sum_dir sum_j st[s][dir][i][j] x(s + dir)_j, periodic (the
+// fermion boundary sign is already inside the Galerkin blocks).
+#include "ops.cuh"
+
+namespace mg {
+
+__device__ __forceinline__ int nbr_site(int s, int dir, int Ls) {
+  const int t = s / Ls, x = s - t * Ls;
+  switch (dir) {
+    case 1: return t * Ls + (x + 1 == Ls ? 0 : x + 1);
+    case 2: return t * Ls + (x == 0 ? Ls - 1 : x - 1);
+    case 3: return (t + 1 == Ls ? 0 : t + 1) * Ls + x;
+    case 4: return (t == 0 ? Ls - 1 : t - 1) * Ls + x;
+    default: return s;
+  }
+}
+
+// ---- coarse stencil apply -----------------------------------------------------
+template <typename R, bool RES>
+__global__ void __launch_bounds__(256) k_coarse_apply(const typename CT<R>::T* __restrict__ st, int Ls, int d,
+                                                      const typename CT<R>::T* __restrict__ x,
+                                                      typename CT<R>::T* __restrict__ y,
+                                                      const typename CT<R>::T* __restrict__ b, int nrhs,
+                                                      const int* __restrict__ active) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sst = reinterpret_cast<C*>(smem_raw);  // [dir][j][i] (transposed)
+  const int G = blockDim.x / d;
+  C* sx = sst + 5 * d * d;                  // [g][dir][j]
+  const int s = blockIdx.x;
+  const int dd = d * d;
+  const C* S = st + (size_t)s * 5 * dd;
+  for (int e = threadIdx.x; e < 5 * dd; e += blockDim.x) {
+    const int dir = e / dd, r = e % dd, i = r / d, j = r % d;
+    sst[dir * dd + j * d + i] = S[e];
+  }
+  int nb[5];
+#pragma unroll
+  for (int dir = 0; dir < 5; ++dir) nb[dir] = nbr_site(s, dir, Ls);
+  const size_t n = (size_t)Ls * Ls * d;
+  const int g = threadIdx.x / d, i = threadIdx.x % d;
+  for (int r0 = 0; r0 < nrhs; r0 += G) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < G * 5 * d; q += blockDim.x) {
+      const int gg = q / (5 * d), rem = q % (5 * d), dir = rem / d, j = rem % d;
+      const int rhs = r0 + gg;
+      if (rhs < nrhs) sx[q] = __ldg(x + rhs * n + (size_t)nb[dir] * d + j);
+    }
+    __syncthreads();
+    const int rhs = r0 + g;
+    if (g < G && rhs < nrhs && !(active && !active[rhs])) {
+      C acc = czero<C>();
+      for (int dir = 0; dir < 5; ++dir) {
+        const C* a = sst + dir * dd + i;
+        const C* v = sx + (g * 5 + dir) * d;
+#pragma unroll 4
+        for (int j = 0; j < d; ++j) acc = cfma(a[j * d], v[j], acc);
+      }
+      const size_t o = rhs * n + (size_t)s * d + i;
+      y[o] = RES ? csub(b[o], acc) : acc;
+    }
+  }
+}
+
+template <typename R>
+void coarse_apply(cudaStream_t stm, const typename CT<R>::T* st, int Ls, int d, const typename CT<R>::T* x,
+                  typename CT<R>::T* y, const typename CT<R>::T* b, int nrhs, const int* active) {
+  typedef typename CT<R>::T C;
+  MG_CHECK_ARG(d <= 64 && 256 % d == 0, "coarse dof must divide 256");
+  const int G = 256 / d;
+  size_t sm = sizeof(C) * (5 * d * d + G * 5 * d);
+  static bool attr_set[2][2] = {{false, false}, {false, false}};
+  const int ri = sizeof(R) == 8;
+  if (b) {
+    if (!attr_set[ri][1]) {
+      MG_CUDA(cudaFuncSetAttribute(k_coarse_apply<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr_set[ri][1] = true;
+    }
+    MG_LAUNCH((k_coarse_apply<R, true>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
+  } else {
+    if (!attr_set[ri][0]) {
+      MG_CUDA(cudaFuncSetAttribute(k_coarse_apply<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr_set[ri][0] = true;
+    }
+    MG_LAUNCH((k_coarse_apply<R, false>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
+  }
+}
+template void coarse_apply<float>(cudaStream_t, const float2*, int, int, const float2*, float2*, const float2*,
+                                  int, const int*);
+template void coarse_apply<double>(cudaStream_t, const double2*, int, int, const double2*, double2*,
+                                   const double2*, int, const int*);
+
+// ---- SAP on coarse levels --------------------------------------------------------
+// Block (BT, BX) of bs x bs sites, local index (jt * bs + jx) * d + k.
+__global__ void k_coarse_blocks(const double2* __restrict__ st, int Ls, int d, int bs, double2* __restrict__ out) {
+  const int nbx = Ls / bs;
+  const int blk = blockIdx.x;
+  const int BT = blk / nbx, BX = blk % nbx;
+  const int ns = bs * bs, bd = ns * d, dd = d * d;
+  double2* A = out + (size_t)blk * bd * bd;
+  for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) A[e] = make_double2(0, 0);
+  __syncthreads();
+  for (int j = 0; j < ns; ++j) {
+    const int s = (BT * bs + j / bs) * Ls + BX * bs + j % bs;
+    for (int dir = 0; dir < 5; ++dir) {
+      const int nbs = nbr_site(s, dir, Ls);
+      const int nt = nbs / Ls, nx = nbs % Ls;
+      if (nt / bs != BT || nx / bs != BX) continue;
+      const int jj = (nt % bs) * bs + nx % bs;
+      const double2* S = st + ((size_t)s * 5 + dir) * dd;
+      for (int e = threadIdx.x; e < dd; e += blockDim.x) {
+        const int i = e / d, k = e % d;
+        double2* a = A + (size_t)(j * d + i) * bd + jj * d + k;
+        *a = cadd(*a, S[e]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+void coarse_block_matrices(cudaStream_t stm, const double2* st, int Ls, int d, int bs, double2* out) {
+  const int nb = (Ls / bs) * (Ls / bs);
+  MG_LAUNCH(k_coarse_blocks, nb, 256, 0, stm, st, Ls, d, bs, out);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_sap_coarse(const typename CT<R>::T* __restrict__ st, int Ls, int d, int bs,
+                                                    const typename CT<R>::T* __restrict__ inv,
+                                                    const typename CT<R>::T* __restrict__ f,
+                                                    typename CT<R>::T* __restrict__ x, int color, int nrhs,
+                                                    const int* __restrict__ active) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ns = bs * bs, bd = ns * d, dd = d * d;
+  const int G = max(1, (int)blockDim.x / bd);
+  C* sinv = reinterpret_cast<C*>(smem_raw);     // [bd][bd]
+  C* sst = sinv + bd * bd;                      // [j][dir][k'][k] transposed stencil of block sites
+  C* sres = sst + ns * 5 * dd;                  // [g][bd]
+  const int nbx = Ls / bs, half = nbx / 2;
+  const int kb = blockIdx.x;
+  const int BT = kb / half;
+  const int BX = 2 * (kb % half) + ((BT + color) & 1);
+  const int blk = BT * nbx + BX;
+  const C* I = inv + (size_t)blk * bd * bd;
+  for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) sinv[e] = I[e];
+  for (int e = threadIdx.x; e < ns * 5 * dd; e += blockDim.x) {
+    const int j = e / (5 * dd), r = e % (5 * dd), dir = r / dd, q = r % dd, i = q / d, k = q % d;
+    const int s = (BT * bs + j / bs) * Ls + BX * bs + j % bs;
+    sst[(j * 5 + dir) * dd + k * d + i] = st[((size_t)s * 5 + dir) * dd + q];
+  }
+  const size_t n = (size_t)Ls * Ls * d;
+  for (int r0 = 0; r0 < nrhs; r0 += G) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < G * bd; q += blockDim.x) {
+      const int g = q / bd, i = q % bd, j = i / d, k = i % d;
+      const int rhs = r0 + g;
+      if (rhs < nrhs && !(active && !active[rhs])) {
+        const int s = (BT * bs + j / bs) * Ls + BX * bs + j % bs;
+        const C* X = x + rhs * n;
+        C acc = __ldg(f + rhs * n + (size_t)s * d + k);
+        for (int dir = 0; dir < 5; ++dir) {
+          const C* xv = X + (size_t)nbr_site(s, dir, Ls) * d;
+          const C* a = sst + (j * 5 + dir) * dd + k;
+          for (int kk = 0; kk < d; ++kk) acc = csub(acc, cmul(a[kk * d], xv[kk]));
+        }
+        sres[g * bd + i] = acc;
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < G * bd; q += blockDim.x) {
+      const int g = q / bd, i = q % bd, j = i / d, k = i % d;
+      const int rhs = r0 + g;
+      if (rhs < nrhs && !(active && !active[rhs])) {
+        C acc = czero<C>();
+        for (int jj = 0; jj < bd; ++jj) acc = cfma(sinv[i * bd + jj], sres[g * bd + jj], acc);
+        const int s = (BT * bs + j / bs) * Ls + BX * bs + j % bs;
+        C* px = x + rhs * n + (size_t)s * d + k;
+        *px = cadd(*px, acc);
+      }
+    }
+  }
+}
+
+template <typename R>
+void sap_half_coarse(cudaStream_t stm, const typename CT<R>::T* st, int Ls, int d, int bs,
+                     const typename CT<R>::T* inv, const typename CT<R>::T* f, typename CT<R>::T* x, int color,
+                     int nrhs, const int* active) {
+  typedef typename CT<R>::T C;
+  const int ns = bs * bs, bd = ns * d;
+  const int G = std::max(1, 256 / bd);
+  size_t sm = sizeof(C) * ((size_t)bd * bd + (size_t)ns * 5 * d * d + (size_t)G * bd);
+  MG_CHECK_ARG(sm <= 220 * 1024, "coarse SAP block too large for shared memory");
+  static bool attr[2] = {false, false};
+  const int ri = sizeof(R) == 8;
+  if (!attr[ri]) {
+    MG_CUDA(cudaFuncSetAttribute(k_sap_coarse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    attr[ri] = true;
+  }
+  const int nb = (Ls / bs) * (Ls / bs) / 2;
+  MG_LAUNCH(k_sap_coarse<R>, nb, 256, sm, stm, st, Ls, d, bs, inv, f, x, color, nrhs, active);
+}
+template void sap_half_coarse<float>(cudaStream_t, const float2*, int, int, int, const float2*, const float2*,
+                                     float2*, int, int, const int*);
+template void sap_half_coarse<double>(cudaStream_t, const double2*, int, int, int, const double2*,
+                                      const double2*, double2*, int, int, const int*);
+
+// ---- restriction / prolongation ---------------------------------------------------
+// Aggregate (T, X) of agg x agg sites; block of chirality c has rows
+// j = js * hd + k' (js = jt * agg + jx local site, hd = d / 2 dof per chirality)
+// mapping to fine dof (site(js)) * d + c * hd + k'.
+template <typename R>
+__global__ void __launch_bounds__(256) k_restrict(const typename CT<R>::T* __restrict__ P, int Ls, int d, int agg,
+                                                  int ntv, const typename CT<R>::T* __restrict__ xf,
+                                                  typename CT<R>::T* __restrict__ xc, int nrhs,
+                                                  const int* __restrict__ active) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int hd = d / 2, na = agg * agg, bsz = na * hd, dc = 2 * ntv, fa = na * d;
+  const int G = max(1, (int)blockDim.x / dc);
+  C* sP = reinterpret_cast<C*>(smem_raw);  // [c][j][m]
+  C* sx = sP + 2 * bsz * ntv;              // [g][js * d + k]
+  const int Lc = Ls / agg;
+  const int a = blockIdx.x, T = a / Lc, X = a % Lc;
+  const C* Pa = P + (size_t)a * 2 * bsz * ntv;
+  for (int e = threadIdx.x; e < 2 * bsz * ntv; e += blockDim.x) sP[e] = Pa[e];
+  const size_t n = (size_t)Ls * Ls * d, nc = (size_t)Lc * Lc * dc;
+  for (int r0 = 0; r0 < nrhs; r0 += G) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < G * fa; q += blockDim.x) {
+      const int g = q / fa, rem = q % fa, js = rem / d, k = rem % d;
+      const int rhs = r0 + g;
+      if (rhs < nrhs) {
+        const size_t site = (size_t)(agg * T + js / agg) * Ls + agg * X + js % agg;
+        sx[q] = __ldg(xf + rhs * n + site * d + k);
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < G * dc; q += blockDim.x) {
+      const int g = q / dc, o = q % dc, c = o / ntv, m = o % ntv;
+      const int rhs = r0 + g;
+      if (rhs < nrhs && !(active && !active[rhs])) {
+        C acc = czero<C>();
+        const C* pc = sP + (size_t)c * bsz * ntv + m;
+        const C* xv = sx + g * fa + c * hd;
+        for (int j = 0; j < bsz; ++j) acc = cfmac(pc[j * ntv], xv[(j / hd) * d + j % hd], acc);
+        xc[rhs * nc + (size_t)a * dc + o] = acc;
+      }
+    }
+  }
+}
+
+template <typename R, bool ADD>
+__global__ void __launch_bounds__(256) k_prolong(const typename CT<R>::T* __restrict__ P, int Ls, int d, int agg,
+                                                 int ntv, const typename CT<R>::T* __restrict__ xc,
+                                                 typename CT<R>::T* __restrict__ xf, int nrhs,
+                                                 const int* __restrict__ active) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int hd = d / 2, na = agg * agg, bsz = na * hd, dc = 2 * ntv, fa = na * d;
+  const int G = max(1, (int)blockDim.x / fa);
+  C* sP = reinterpret_cast<C*>(smem_raw);  // [c][m][j] (transposed)
+  C* sc = sP + 2 * bsz * ntv;              // [g][dc]
+  const int Lc = Ls / agg;
+  const int a = blockIdx.x, T = a / Lc, X = a % Lc;
+  const C* Pa = P + (size_t)a * 2 * bsz * ntv;
+  for (int e = threadIdx.x; e < 2 * bsz * ntv; e += blockDim.x) {
+    const int c = e / (bsz * ntv), r = e % (bsz * ntv), j = r / ntv, m = r % ntv;
+    sP[(c * ntv + m) * bsz + j] = Pa[e];
+  }
+  const size_t n = (size_t)Ls * Ls * d, nc = (size_t)Lc * Lc * dc;
+  for (int r0 = 0; r0 < nrhs; r0 += G) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < G * dc; q += blockDim.x) {
+      const int g = q / dc, o = q % dc;
+      const int rhs = r0 + g;
+      if (rhs < nrhs) sc[q] = __ldg(xc + rhs * nc + (size_t)a * dc + o);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < G * fa; q += blockDim.x) {
+      const int g = q / fa, rem = q % fa, js = rem / d, k = rem % d;
+      const int rhs = r0 + g;
+      if (rhs < nrhs && !(active && !active[rhs])) {
+        const int c = k / hd, kp = k % hd, j = js * hd + kp;
+        C acc = czero<C>();
+        const C* pc = sP + (size_t)c * ntv * bsz + j;
+        const C* cv = sc + g * dc + c * ntv;
+        for (int m = 0; m < ntv; ++m) acc = cfma(pc[m * bsz], cv[m], acc);
+        const size_t site = (size_t)(agg * T + js / agg) * Ls + agg * X + js % agg;
+        C* p = xf + rhs * n + site * d + k;
+        *p = ADD ? cadd(*p, acc) : acc;
+      }
+    }
+  }
+}
+
+template <typename K>
+static void set_smem_attr(K kernel, bool& done) {
+  if (!done) {
+    MG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    done = true;
+  }
+}
+
+template <typename R>
+void restrict_op(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, int agg, int ntv,
+                 const typename CT<R>::T* xf, typename CT<R>::T* xc, int nrhs, const int* active) {
+  typedef typename CT<R>::T C;
+  const int na = agg * agg, bsz = na * d / 2, dc = 2 * ntv;
+  const int G = std::max(1, 256 / dc);
+  size_t sm = sizeof(C) * ((size_t)2 * bsz * ntv + (size_t)G * na * d);
+  static bool done[2] = {false, false};
+  set_smem_attr(k_restrict<R>, done[sizeof(R) == 8]);
+  const int Lc = Ls / agg;
+  MG_LAUNCH(k_restrict<R>, Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs, active);
+}
+
+template <typename R>
+void prolong_op(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, int agg, int ntv,
+                const typename CT<R>::T* xc, typename CT<R>::T* xf, bool add, int nrhs, const int* active) {
+  typedef typename CT<R>::T C;
+  const int na = agg * agg, bsz = na * d / 2, dc = 2 * ntv, fa = na * d;
+  const int G = std::max(1, 256 / fa);
+  size_t sm = sizeof(C) * ((size_t)2 * bsz * ntv + (size_t)G * dc);
+  static bool done[2][2] = {{false, false}, {false, false}};
+  const int Lc = Ls / agg;
+  if (add) {
+    set_smem_attr(k_prolong<R, true>, done[sizeof(R) == 8][1]);
+    MG_LAUNCH((k_prolong<R, true>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active);
+  } else {
+    set_smem_attr(k_prolong<R, false>, done[sizeof(R) == 8][0]);
+    MG_LAUNCH((k_prolong<R, false>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active);
+  }
+}
+template void restrict_op<float>(cudaStream_t, const float2*, int, int, int, int, const float2*, float2*, int,
+                                 const int*);
+template void restrict_op<double>(cudaStream_t, const double2*, int, int, int, int, const double2*, double2*, int,
+                                  const int*);
+template void prolong_op<float>(cudaStream_t, const float2*, int, int, int, int, const float2*, float2*, bool, int,
+                                const int*);
+template void prolong_op<double>(cudaStream_t, const double2*, int, int, int, int, const double2*, double2*, bool,
+                                 int, const int*);
+
+// ---- test vectors -> prolongator blocks --------------------------------------------
+__global__ void k_gather_tv(const double2* __restrict__ V, int Ls, int d, int agg, int ntv, double2* __restrict__ P) {
+  const int hd = d / 2, na = agg * agg, bsz = na * hd;
+  const int Lc = Ls / agg;
+  const size_t total = (size_t)Lc * Lc * 2 * bsz * ntv;
+  const size_t n = (size_t)Ls * Ls * d;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int m = e % ntv;
+    const size_t r = e / ntv;
+    const int j = r % bsz;
+    const size_t r2 = r / bsz;
+    const int c = r2 % 2;
+    const int a = (int)(r2 / 2), T = a / Lc, X = a % Lc;
+    const int js = j / hd, kp = j % hd;
+    const size_t site = (size_t)(agg * T + js / agg) * Ls + agg * X + js % agg;
+    P[e] = V[m * n + site * d + c * hd + kp];
+  }
+}
+
+void gather_tv_blocks(cudaStream_t stm, const double2* V, int Ls, int d, int agg, int ntv, double2* P) {
+  MG_LAUNCH(k_gather_tv, 1024, 256, 0, stm, V, Ls, d, agg, ntv, P);
+}
+
+// Modified Gram-Schmidt with one re-orthogonalisation pass, one warp per block:
+// Q has orthonormal columns and R a real positive diagonal (the QR normalisation
+// of the oracle), FP64.
+__global__ void k_orthonormalise(double2* __restrict__ P, int nblocks, int bsz, int ntv, int* fail) {
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (w >= nblocks) return;
+  double2* B = P + (size_t)w * bsz * ntv;  // B[j][m]
+  for (int m = 0; m < ntv; ++m) {
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = 0; i < m; ++i) {
+        double2 acc = make_double2(0, 0);
+        for (int j = lane; j < bsz; j += 32) acc = cfmac(B[j * ntv + i], B[j * ntv + m], acc);
+        for (int o = 16; o; o >>= 1) {
+          acc.x += __shfl_xor_sync(0xffffffff, acc.x, o);
+          acc.y += __shfl_xor_sync(0xffffffff, acc.y, o);
+        }
+        for (int j = lane; j < bsz; j += 32) B[j * ntv + m] = csub(B[j * ntv + m], cmul(B[j * ntv + i], acc));
+        __syncwarp();
+      }
+    }
+    double nr = 0;
+    for (int j = lane; j < bsz; j += 32) {
+      double2 v = B[j * ntv + m];
+      nr += v.x * v.x + v.y * v.y;
+    }
+    for (int o = 16; o; o >>= 1) nr += __shfl_xor_sync(0xffffffff, nr, o);
+    if (!(nr > 0.0)) {
+      if (lane == 0) atomicExch(fail, 1);
+      return;
+    }
+    const double inv = 1.0 / sqrt(nr);
+    for (int j = lane; j < bsz; j += 32) B[j * ntv + m] = cscale(B[j * ntv + m], inv);
+    __syncwarp();
+  }
+}
+
+void orthonormalise_blocks(cudaStream_t stm, double2* P, int nblocks, int bsz, int ntv, int* fail) {
+  MG_LAUNCH(k_orthonormalise, cdiv(nblocks, 4), 128, 0, stm, P, nblocks, bsz, ntv, fail);
+}
+
+// ---- Galerkin probing -------------------------------------------------------------
+// 16 aggregate colours (X mod 4) + 4 (T mod 4): the five aggregates B, B +- x,
+// B +- t always carry distinct colours, so the restricted image of probe
+// (kappa, j) at coarse site B holds exactly column j of D_c[B, B + dir] for the
+// dir with colour(B + dir) = kappa.
+__device__ __forceinline__ int agg_colour(int T, int X) { return (X & 3) + 4 * (T & 3); }
+
+__global__ void k_make_probes(const double2* __restrict__ P, int Ls, int d, int agg, int ntv,
+                              double2* __restrict__ probes) {
+  const int hd = d / 2, na = agg * agg, bsz = na * hd, dc = 2 * ntv;
+  const int Lc = Ls / agg;
+  const size_t n = (size_t)Ls * Ls * d;
+  const int p = blockIdx.y;
+  const int kappa = p / dc, jc = p % dc, cj = jc / ntv, m = jc % ntv;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t site = q / d;
+    const int k = q % d;
+    const int t = site / Ls, x = site % Ls;
+    const int T = t / agg, X = x / agg;
+    const int c = k / hd;
+    double2 v = make_double2(0, 0);
+    if (c == cj && agg_colour(T, X) == kappa) {
+      const int js = (t % agg) * agg + x % agg;
+      const int j = js * hd + (k % hd);
+      v = P[(((size_t)(T * Lc + X) * 2 + c) * bsz + j) * ntv + m];
+    }
+    probes[(size_t)p * n + q] = v;
+  }
+}
+
+void make_probes(cudaStream_t stm, const double2* P, int Ls, int d, int agg, int ntv, double2* probes) {
+  dim3 grid(256, 16 * 2 * ntv);
+  MG_LAUNCH(k_make_probes, grid, 256, 0, stm, P, Ls, d, agg, ntv, probes);
+}
+
+__global__ void k_extract_stencil(const double2* __restrict__ imgs, int Lc, int dc, double2* __restrict__ stencil) {
+  const size_t nc = (size_t)Lc * Lc * dc;
+  const size_t total = (size_t)Lc * Lc * 5 * dc * dc;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int j = e % dc;
+    const int i = (e / dc) % dc;
+    const int dir = (e / ((size_t)dc * dc)) % 5;
+    const int s = (int)(e / ((size_t)5 * dc * dc));
+    const int nb = nbr_site(s, dir, Lc);
+    const int kappa = agg_colour(nb / Lc, nb % Lc);
+    stencil[e] = imgs[(size_t)(kappa * dc + j) * nc + (size_t)s * dc + i];
+  }
+}
+
+void extract_stencil(cudaStream_t stm, const double2* imgs, int Lc, int dc, double2* stencil) {
+  MG_LAUNCH(k_extract_stencil, 1024, 256, 0, stm, imgs, Lc, dc, stencil);
+}
+
+// ---- coarsest level as a dense matrix -------------------------------------------------
+__global__ void k_dense_from_stencil(const double2* __restrict__ st, int Ls, int d, double2* __restrict__ A) {
+  const int nsite = Ls * Ls;
+  const size_t N = (size_t)nsite * d;
+  const size_t total = (size_t)nsite * d * d;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int j = e % d, i = (e / d) % d, s = (int)(e / ((size_t)d * d));
+    for (int dir = 0; dir < 5; ++dir) {
+      const int nb = nbr_site(s, dir, Ls);
+      double2* a = A + ((size_t)s * d + i) * N + (size_t)nb * d + j;
+      *a = cadd(*a, st[((size_t)s * 5 + dir) * d * d + i * d + j]);
+    }
+  }
+}
+
+void dense_from_stencil(cudaStream_t stm, const double2* st, int Ls, int d, double2* A) {
+  const size_t N = (size_t)Ls * Ls * d;
+  MG_CUDA(cudaMemsetAsync(A, 0, N * N * sizeof(double2), stm));
+  // one thread per (site, i, j): the five neighbour columns are distinct for Ls >= 3
+  MG_LAUNCH(k_dense_from_stencil, 512, 256, 0, stm, st, Ls, d, A);
+}
+
+}  // namespace mg

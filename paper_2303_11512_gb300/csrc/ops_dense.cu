@@ -1,0 +1,433 @@
+// Dense FP64 kernels: Gauss-Jordan inverses (SAP blocks, the coarsest level of
+// Algorithm 2 whose trace is tau_L), the coarsest-level inverse apply, and the
+// Hutch++ pieces of Algorithm 2: the Gram matrix and Cholesky factor of
+// CholeskyQR2 and the projection coefficients Q^H x.
+#include "ops.cuh"
+
+namespace mg {
+
+namespace {
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
+  return v;
+}
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 crecip(double2 a) {
+  const double s = 1.0 / cabs2(a);
+  return make_double2(a.x * s, -a.y * s);
+}
+}  // namespace
+
+// ---- batched small inverse (one CTA per matrix) ------------------------------------------------
+__global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, int bd, int* fail) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* sf = A + bd * bd;
+  int* perm = reinterpret_cast<int*>(sf + bd);
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  double2* G = Ag + (size_t)blockIdx.x * bd * bd;
+  for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) A[e] = G[e];
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int k = 0; k < bd; ++k) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + threadIdx.x; i < bd; i += 32) {
+        double v = cabs2(A[i * bd + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffff, best, o);
+        int oi = __shfl_xor_sync(0xffffffff, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) {
+        s_p = bi;
+        perm[k] = bi;
+        if (!(best > 0.0)) s_bad = 1;
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int p = s_p;
+    if (p != k)
+      for (int j = threadIdx.x; j < bd; j += blockDim.x) {
+        double2 t = A[k * bd + j];
+        A[k * bd + j] = A[p * bd + j];
+        A[p * bd + j] = t;
+      }
+    __syncthreads();
+    const double2 a = crecip(A[k * bd + k]);
+    __syncthreads();
+    for (int j = threadIdx.x; j < bd; j += blockDim.x) {
+      double2 v = (j == k) ? make_double2(1, 0) : A[k * bd + j];
+      A[k * bd + j] = cmul(v, a);
+    }
+    for (int i = threadIdx.x; i < bd; i += blockDim.x) sf[i] = (i == k) ? make_double2(0, 0) : A[i * bd + k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < bd; i += blockDim.x)
+      if (i != k) A[i * bd + k] = make_double2(0, 0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) {
+      const int i = e / bd, j = e % bd;
+      if (i != k) A[e] = csub(A[e], cmul(sf[i], A[k * bd + j]));
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (threadIdx.x == 0) atomicExch(fail, 1);
+    return;
+  }
+  for (int k = bd - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < bd; i += blockDim.x) {
+        double2 t = A[i * bd + k];
+        A[i * bd + k] = A[i * bd + p];
+        A[i * bd + p] = t;
+      }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) G[e] = A[e];
+}
+
+void invert_small_batched(cudaStream_t st, double2* A, int nmat, int bd, int* fail) {
+  MG_CHECK_ARG(bd <= 64, "small inverse limited to 64 x 64");
+  size_t sm = sizeof(double2) * ((size_t)bd * bd + bd) + sizeof(int) * bd + 16;
+  static bool done = false;
+  if (!done) {
+    MG_CUDA(cudaFuncSetAttribute(k_invert_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    done = true;
+  }
+  MG_LAUNCH(k_invert_small, nmat, 256, sm, st, A, bd, fail);
+}
+
+// ---- large in-place inverse, one pivot step per pair of launches ------------------------------
+__global__ void __launch_bounds__(1024) k_gj_pivot(double2* __restrict__ A, int n, int k, int* piv,
+                                                   double2* __restrict__ f, int* fail) {
+  __shared__ double sb[32];
+  __shared__ int si[32];
+  __shared__ int s_p;
+  double best = -1.0;
+  int bi = k;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    double v = cabs2(A[(size_t)i * n + k]);
+    if (v > best) { best = v; bi = i; }
+  }
+  for (int o = 16; o; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffff, best, o);
+    int oi = __shfl_xor_sync(0xffffffff, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sb[w] = best; si[w] = bi; }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    best = l < nw ? sb[l] : -1.0;
+    bi = l < nw ? si[l] : k;
+    for (int o = 16; o; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffff, best, o);
+      int oi = __shfl_xor_sync(0xffffffff, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (l == 0) {
+      s_p = bi;
+      piv[k] = bi;
+      if (!(best > 0.0)) atomicExch(fail, 1);
+    }
+  }
+  __syncthreads();
+  const int p = s_p;
+  if (p != k)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double2 t = A[(size_t)k * n + j];
+      A[(size_t)k * n + j] = A[(size_t)p * n + j];
+      A[(size_t)p * n + j] = t;
+    }
+  __syncthreads();
+  const double2 a = crecip(A[(size_t)k * n + k]);
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double2 v = (j == k) ? make_double2(1, 0) : A[(size_t)k * n + j];
+    A[(size_t)k * n + j] = cmul(v, a);
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (i == k) {
+      f[i] = make_double2(0, 0);
+    } else {
+      f[i] = A[(size_t)i * n + k];
+      A[(size_t)i * n + k] = make_double2(0, 0);
+    }
+  }
+}
+
+__global__ void k_gj_elim(double2* __restrict__ A, int n, int k, const double2* __restrict__ f) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= n || i == k) return;
+  const double2 fi = f[i];
+  if (fi.x == 0.0 && fi.y == 0.0) return;
+  A[(size_t)i * n + j] = csub(A[(size_t)i * n + j], cmul(fi, A[(size_t)k * n + j]));
+}
+
+__global__ void k_gj_unscramble(double2* __restrict__ A, int n, const int* __restrict__ piv) {
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double2 t = A[(size_t)i * n + k];
+        A[(size_t)i * n + k] = A[(size_t)i * n + p];
+        A[(size_t)i * n + p] = t;
+      }
+    __syncthreads();
+  }
+}
+
+void invert_large(cudaStream_t st, double2* A, int n, int* piv, double2* work, int* fail) {
+  for (int k = 0; k < n; ++k) {
+    MG_LAUNCH(k_gj_pivot, 1, 1024, 0, st, A, n, k, piv, work, fail);
+    MG_LAUNCH(k_gj_elim, dim3(cdiv(n, 256), n), 256, 0, st, A, n, k, work);
+  }
+  MG_LAUNCH(k_gj_unscramble, 1, 1024, 0, st, A, n, piv);
+}
+
+// ---- y = A x for the coarsest level (n x n dense, nrhs columns) --------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_dense_apply(const typename CT<R>::T* __restrict__ A, int n,
+                                                     const typename CT<R>::T* __restrict__ x,
+                                                     typename CT<R>::T* __restrict__ y, int nrhs,
+                                                     const int* __restrict__ active) {
+  typedef typename CT<R>::T C;
+  __shared__ C As[16][17];
+  __shared__ C Xs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = blockIdx.x * 16 + tx;   // row of A
+  const int r = blockIdx.y * 16 + ty;   // rhs
+  C acc = czero<C>();
+  for (int j0 = 0; j0 < n; j0 += 16) {
+    {
+      const int ii = blockIdx.x * 16 + ty, jj = j0 + tx;
+      As[ty][tx] = (ii < n && jj < n) ? A[(size_t)ii * n + jj] : czero<C>();
+      const int rr = blockIdx.y * 16 + ty;
+      Xs[ty][tx] = (rr < nrhs && jj < n) ? x[(size_t)rr * n + jj] : czero<C>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc = cfma(As[tx][q], Xs[ty][q], acc);
+    __syncthreads();
+  }
+  if (i < n && r < nrhs && !(active && !active[r])) y[(size_t)r * n + i] = acc;
+}
+
+template <typename R>
+void dense_apply(cudaStream_t st, const typename CT<R>::T* A, int n, const typename CT<R>::T* x,
+                 typename CT<R>::T* y, int nrhs, const int* active) {
+  dim3 grid(cdiv(n, 16), cdiv(nrhs, 16));
+  MG_LAUNCH(k_dense_apply<R>, grid, 256, 0, st, A, n, x, y, nrhs, active);
+}
+template void dense_apply<float>(cudaStream_t, const float2*, int, const float2*, float2*, int, const int*);
+template void dense_apply<double>(cudaStream_t, const double2*, int, const double2*, double2*, int, const int*);
+
+__global__ void k_trace(const double2* __restrict__ A, int n, double2* out) {
+  __shared__ double sr[32], si[32];
+  double re = 0, im = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    re += A[(size_t)i * n + i].x;
+    im += A[(size_t)i * n + i].y;
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sr[w] = re; si[w] = im; }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    re = l < nw ? sr[l] : 0;
+    im = l < nw ? si[l] : 0;
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (l == 0) *out = make_double2(re, im);
+  }
+}
+void trace_dense(cudaStream_t st, const double2* A, int n, double2* out) {
+  MG_LAUNCH(k_trace, 1, 1024, 0, st, A, n, out);
+}
+
+// ---- CholeskyQR2 pieces ---------------------------------------------------------------------------
+namespace {
+constexpr int GCH = 32;     // rows per shared-memory chunk
+constexpr int GBLK = 128;   // blocks (partials)
+}
+
+size_t gram_work_bytes(int d, long n) {
+  (void)n;
+  return sizeof(double2) * (size_t)GBLK * d * d;
+}
+
+__global__ void __launch_bounds__(1024) k_gram_part(const double2* __restrict__ Y, int d, long n,
+                                                    double2* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* Ys = reinterpret_cast<double2*>(smem_raw);  // [GCH][d]
+  const int tid = threadIdx.x;
+  const int i = tid / d, j = tid % d;
+  const bool on = tid < d * d;
+  double2 acc = make_double2(0, 0);
+  for (long e0 = (long)blockIdx.x * GCH; e0 < n; e0 += (long)gridDim.x * GCH) {
+    __syncthreads();
+    for (int q = tid; q < GCH * d; q += blockDim.x) {
+      const int c = q / GCH, e = q % GCH;
+      Ys[e * d + c] = (e0 + e < n) ? Y[(size_t)c * n + e0 + e] : make_double2(0, 0);
+    }
+    __syncthreads();
+    if (on)
+#pragma unroll 8
+      for (int e = 0; e < GCH; ++e) acc = cfmac(Ys[e * d + i], Ys[e * d + j], acc);
+  }
+  if (on) part[((size_t)blockIdx.x * d + i) * d + j] = acc;
+}
+
+__global__ void k_gram_final(const double2* __restrict__ part, int d, int nb, double2* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d * d) return;
+  double2 s = make_double2(0, 0);
+  for (int b = 0; b < nb; ++b) s = cadd(s, part[(size_t)b * d * d + e]);
+  G[e] = s;
+}
+
+void gram(cudaStream_t st, const double2* Y, int d, long n, double2* G, void* work) {
+  MG_CHECK_ARG(d <= 32, "sketch size d limited to 32");
+  const int nb = (int)std::min<long>(GBLK, cdiv(n, GCH));
+  double2* part = reinterpret_cast<double2*>(work);
+  MG_LAUNCH(k_gram_part, nb, 1024, sizeof(double2) * GCH * d, st, Y, d, n, part);
+  MG_LAUNCH(k_gram_final, cdiv(d * d, 256), 256, 0, st, part, d, nb, G);
+}
+
+// G = R^H R (R upper, real positive diagonal), Rinv = R^{-1}.
+__global__ void k_chol_inv(const double2* __restrict__ Gg, int d, double2* __restrict__ Rinv, int* fail) {
+  __shared__ double2 R[32 * 32];
+  __shared__ double2 X[32 * 32];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < d * d; e += blockDim.x) { R[e] = Gg[e]; X[e] = make_double2(0, 0); }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < d; ++k) {
+    if (tid == 0) {
+      double s = R[k * d + k].x;
+      for (int i = 0; i < k; ++i) s -= cabs2(R[i * d + k]);
+      if (!(s > 0.0)) bad = 1;
+      R[k * d + k] = make_double2(sqrt(fmax(s, 1e-300)), 0);
+    }
+    __syncthreads();
+    const double rkk = R[k * d + k].x;
+    for (int j = k + 1 + tid; j < d; j += blockDim.x) {
+      double2 s = R[k * d + j];
+      for (int i = 0; i < k; ++i) s = csub(s, cmulc(R[i * d + k], R[i * d + j]));
+      R[k * d + j] = cscale(s, 1.0 / rkk);
+    }
+    __syncthreads();
+  }
+  // upper-triangular inverse, column j per thread
+  for (int j = tid; j < d; j += blockDim.x) {
+    X[j * d + j] = make_double2(1.0 / R[j * d + j].x, 0);
+    for (int i = j - 1; i >= 0; --i) {
+      double2 s = make_double2(0, 0);
+      for (int m = i + 1; m <= j; ++m) s = cfma(R[i * d + m], X[m * d + j], s);
+      X[i * d + j] = cscale(cneg(s), 1.0 / R[i * d + i].x);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < d * d; e += blockDim.x) Rinv[e] = X[e];
+  if (tid == 0 && bad) atomicExch(fail, 1);
+}
+
+void chol_inv_upper(cudaStream_t st, const double2* G, int d, double2* Rinv, int* fail) {
+  MG_CHECK_ARG(d <= 32, "sketch size d limited to 32");
+  MG_LAUNCH(k_chol_inv, 1, 128, 0, st, G, d, Rinv, fail);
+}
+
+__global__ void k_right_mul_upper(double2* __restrict__ Y, int d, long n, const double2* __restrict__ Rinv) {
+  __shared__ double2 Rs[32 * 32];
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) Rs[e] = Rinv[e];
+  __syncthreads();
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    double2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < d) v[i] = Y[(size_t)i * n + e];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j < d) {
+        double2 s = make_double2(0, 0);
+#pragma unroll
+        for (int i = 0; i <= j; ++i) s = cfma(v[i], Rs[i * d + j], s);
+        Y[(size_t)j * n + e] = s;
+      }
+    }
+  }
+}
+
+void right_mul_upper(cudaStream_t st, double2* Y, int d, long n, const double2* Rinv) {
+  MG_CHECK_ARG(d <= 32, "sketch size d limited to 32");
+  MG_LAUNCH(k_right_mul_upper, std::min<long>(cdiv(n, 128), 2048), 128, 0, st, Y, d, n, Rinv);
+}
+
+// ---- projection coefficients c[i][r] = Q_i^H x_r -----------------------------------------------------
+namespace {
+constexpr int PCH = 64;    // rows per chunk
+constexpr int PRG = 8;     // rhs per block
+constexpr int PBLK = 96;   // chunks (partials)
+}
+
+size_t proj_work_bytes(int d, long n, int nrhs) {
+  (void)n;
+  return sizeof(double2) * (size_t)PBLK * d * nrhs;
+}
+
+__global__ void __launch_bounds__(256) k_proj_part(const double2* __restrict__ Q, int d, const double2* __restrict__ x,
+                                                   long n, int nrhs, double2* __restrict__ part) {
+  __shared__ double2 Qs[PCH * 33];
+  __shared__ double2 Xs[PRG * PCH];
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.y * PRG;
+  const int i = tid % 32, g = tid / 32;  // 32 x 8 threads
+  double2 acc = make_double2(0, 0);
+  for (long e0 = (long)blockIdx.x * PCH; e0 < n; e0 += (long)gridDim.x * PCH) {
+    __syncthreads();
+    for (int q = tid; q < d * PCH; q += blockDim.x) {
+      const int c = q / PCH, e = q % PCH;
+      Qs[e * 33 + c] = (e0 + e < n) ? Q[(size_t)c * n + e0 + e] : make_double2(0, 0);
+    }
+    for (int q = tid; q < PRG * PCH; q += blockDim.x) {
+      const int rr = q / PCH, e = q % PCH;
+      Xs[q] = (r0 + rr < nrhs && e0 + e < n) ? x[(size_t)(r0 + rr) * n + e0 + e] : make_double2(0, 0);
+    }
+    __syncthreads();
+    if (i < d)
+#pragma unroll 8
+      for (int e = 0; e < PCH; ++e) acc = cfmac(Qs[e * 33 + i], Xs[g * PCH + e], acc);
+  }
+  if (i < d && r0 + g < nrhs) part[((size_t)blockIdx.x * d + i) * nrhs + r0 + g] = acc;
+}
+
+__global__ void k_proj_final(const double2* __restrict__ part, int cnt, int nb, double2* __restrict__ c) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= cnt) return;
+  double2 s = make_double2(0, 0);
+  for (int b = 0; b < nb; ++b) s = cadd(s, part[(size_t)b * cnt + e]);
+  c[e] = s;
+}
+
+void proj_coeffs(cudaStream_t st, const double2* Q, int d, const double2* x, long n, int nrhs, double2* c, void* work) {
+  MG_CHECK_ARG(d <= 32, "sketch size d limited to 32");
+  const int nb = (int)std::min<long>(PBLK, cdiv(n, PCH));
+  double2* part = reinterpret_cast<double2*>(work);
+  MG_LAUNCH(k_proj_part, dim3(nb, cdiv(nrhs, PRG)), 256, 0, st, Q, d, x, n, nrhs, part);
+  MG_LAUNCH(k_proj_final, cdiv((long)d * nrhs, 256), 256, 0, st, part, d * nrhs, nb, c);
+}
+
+}  // namespace mg
