@@ -84,6 +84,15 @@ const char* mgmlmc_last_error(const mgmlmc_ctx* ctx);
 /* Number of this library's kernel launches issued on ctx since creation. */
 int64_t mgmlmc_launch_count(const mgmlmc_ctx* ctx);
 int mgmlmc_version(void);
+/* Kernel timer (measurement, not part of the paper's method): while on, every
+ * launch of a kernel whose name contains `filter` (NULL or "" = all) is
+ * bracketed by CUDA events on the context's stream together with its
+ * algorithmic bytes and flops (counted over the right-hand sides still
+ * iterating).  The report resolves the events and writes one line per kernel
+ * "name\tlaunches\tms\tbytes\tflops\n" into buf (host, len bytes), then clears
+ * the records. */
+int mgmlmc_timing_enable(mgmlmc_ctx* ctx, int on, const char* filter);
+int mgmlmc_timing_report(mgmlmc_ctx* ctx, char* buf, int64_t len);
 
 /* ---- operator ----------------------------------------------------------- */
 

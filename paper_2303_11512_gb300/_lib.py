@@ -63,6 +63,8 @@ SIGNATURES = {
     "mgmlmc_ctx_destroy": (None, [vp]),
     "mgmlmc_last_error": (C.c_char_p, [vp]),
     "mgmlmc_launch_count": (C.c_int64, [vp]),
+    "mgmlmc_timing_enable": (ip, [vp, ip, C.c_char_p]),
+    "mgmlmc_timing_report": (ip, [vp, C.c_char_p, C.c_int64]),
     "schwinger_apply": (ip, [vp, vp, ip, C.c_double, vp, vp, ip, ip]),
     "mgmlmc_rademacher": (ip, [vp, C.c_uint64, ip, ip, C.c_int64, C.c_int64, ip, vp]),
     "mg_params_default": (ip, [C.POINTER(MgParams)]),

@@ -51,6 +51,20 @@ class Context:
     def launches(self) -> int:
         return int(_lib.load().mgmlmc_launch_count(self.ptr))
 
+    def timing(self, on: bool = True, filter: str | None = None):
+        """Bracket launches of kernels whose name contains `filter` with CUDA events."""
+        check(_lib.load().mgmlmc_timing_enable(self.ptr, int(on), filter.encode() if filter else None))
+
+    def timing_report(self) -> dict:
+        """{kernel: dict(launches, ms, bytes, flops)} for the launches recorded since the last report."""
+        buf = C.create_string_buffer(1 << 16)
+        check(_lib.load().mgmlmc_timing_report(self.ptr, buf, len(buf)), self.ptr)
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, n, ms, by, fl = line.split("\t")
+            out[name] = dict(launches=int(n), ms=float(ms), bytes=float(by), flops=float(fl))
+        return out
+
     def close(self):
         if self.ptr:
             _lib.load().mgmlmc_ctx_destroy(self.ptr)

@@ -68,11 +68,49 @@ const char* mgmlmc_last_error(const mgmlmc_ctx* ctx) { return ctx ? ctx->err.c_s
 
 int64_t mgmlmc_launch_count(const mgmlmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int mgmlmc_timing_enable(mgmlmc_ctx* ctx, int on, const char* filter) {
+  if (!ctx) return MGMLMC_ERR_INVALID_ARG;
+  ctx->timer.on = on != 0;
+  ctx->timer.filter = filter ? filter : "";
+  return MGMLMC_OK;
+}
+
+int mgmlmc_timing_report(mgmlmc_ctx* ctx, char* buf, int64_t len) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(buf && len > 0, "null buffer");
+    struct Agg { int64_t n = 0; double ms = 0, bytes = 0, flops = 0; };
+    std::map<std::string, Agg> agg;
+    for (auto& r : ctx->timer.recs) {
+      MG_CUDA(cudaEventSynchronize(r.b));
+      float ms = 0;
+      MG_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      Agg& a = agg[r.name];
+      a.n += 1;
+      a.ms += ms;
+      a.bytes += r.bytes;
+      a.flops += r.flops;
+      ctx->timer.pool.push_back(r.a);
+      ctx->timer.pool.push_back(r.b);
+    }
+    ctx->timer.recs.clear();
+    std::string out;
+    char line[512];
+    for (auto& kv : agg) {
+      std::snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.6e\t%.6e\n", kv.first.c_str(), (long long)kv.second.n,
+                    kv.second.ms, kv.second.bytes, kv.second.flops);
+      out += line;
+    }
+    MG_CHECK_ARG((int64_t)out.size() < len, "report buffer too small");
+    std::memcpy(buf, out.c_str(), out.size() + 1);
+  });
+}
+
 int schwinger_apply(mgmlmc_ctx* ctx, const double* U, int L, double m0, const void* x, void* y, int nrhs, int prec) {
   return guarded(ctx, [&] {
+    MG_CHECK_ARG(nrhs >= 0, "nrhs must be >= 0");
+    if (nrhs == 0) return;
     MG_CHECK_ARG(U && x && y, "null pointer");
     MG_CHECK_ARG(L >= 4 && L % 2 == 0, "L must be even and >= 4");
-    MG_CHECK_ARG(nrhs >= 0, "nrhs must be >= 0");
     MG_CHECK_ARG(x != y, "x and y must not alias");
     check_prec(prec);
     if (nrhs == 0) return;
@@ -121,6 +159,7 @@ int mg_setup(mgmlmc_ctx* ctx, const double* U, int L, double m0, const mg_params
     MG_CHECK_ARG(L >= 16 && L % 16 == 0, "L must be a multiple of 16");
     std::unique_ptr<mgmlmc_hier> h(new mgmlmc_hier);
     h->ctx = ctx;
+    h->stream = ctx->stream;
     h->L = L;
     h->m0 = m0;
     if (params)
@@ -134,7 +173,7 @@ int mg_setup(mgmlmc_ctx* ctx, const double* U, int L, double m0, const mg_params
 
 void mg_destroy(mgmlmc_hier* h) {
   if (!h) return;
-  cudaStreamSynchronize(h->ctx->stream);
+  cudaStreamSynchronize(h->stream);
   delete h;
 }
 
@@ -158,6 +197,7 @@ int mg_coarsest_trace(const mgmlmc_hier* h, double* tau_L) {
 int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y, int nrhs, int prec) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && x && y && x != y, "null or aliased pointer");
+    const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
     check_prec(prec);
     if (nrhs <= 0) return;
@@ -171,6 +211,7 @@ int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y,
 int mg_restrict(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* xf, void* xc, int nrhs, int prec) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && xf && xc, "null pointer");
+    const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level out of range");
     check_prec(prec);
     if (nrhs <= 0) return;
@@ -184,6 +225,7 @@ int mg_restrict(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* xf, void
 int mg_prolong(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* xc, void* xf, int nrhs, int prec) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && xf && xc, "null pointer");
+    const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level out of range");
     check_prec(prec);
     if (nrhs <= 0) return;
@@ -217,6 +259,7 @@ int mg_get_stencil(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* hos
 int mg_vcycle(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* b, void* x, int nrhs, int prec) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && b && x && b != x, "null or aliased pointer");
+    const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
     MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32, "V-cycle precision is FP64 or FP32");
     if (nrhs <= 0) return;
@@ -252,6 +295,7 @@ int fgmres_batched(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* b, vo
   int nc = 0;
   int rc = guarded(ctx, [&] {
     MG_CHECK_ARG(h && b && x && sp && b != x, "null or aliased pointer");
+    const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
     MG_CHECK_ARG(sp->tol > 0 && sp->maxit > 0, "tol and maxit must be positive");
     check_prec(sp->prec);
@@ -273,6 +317,7 @@ int mlmc_level_sample(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const double* 
   int nc = 0;
   int rc = guarded(ctx, [&] {
     MG_CHECK_ARG(h && zeta && y && sp && (const void*)zeta != (void*)y, "null or aliased pointer");
+    const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level difference out of range");
     if (nrhs <= 0) return;
     SolveOut o = level_sample(h, level, (const double2*)zeta, (double2*)y, nrhs, *sp);
@@ -289,6 +334,7 @@ int mlmc_level_sample(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const double* 
 int mg_restrict_to_level(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const double* zeta_fine, double* out, int nrhs) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && zeta_fine && out, "null pointer");
+    const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
     if (nrhs <= 0) return;
     restrict_to_level(h, level, (const double2*)zeta_fine, (double2*)out, nrhs);
@@ -300,6 +346,7 @@ int hutchpp_sketch_qr(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, int d, int k, 
   if (out) *out = nullptr;
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && sp && out && tau_lr, "null pointer");
+    const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level difference out of range");
     MG_CHECK_ARG(form == MGMLMC_ACCUMULATED || form == MGMLMC_REDUCED, "unknown form");
     double2 t;
@@ -361,6 +408,7 @@ int est_params_default(est_params* p) {
 int trace_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const est_params* p, est_result* r) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && p && r, "null pointer");
+    const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(p->form == MGMLMC_ACCUMULATED || p->form == MGMLMC_REDUCED, "unknown form");
     estimate(h, *p, r);
   });

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <cstring>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -35,13 +36,56 @@ struct Error : public std::runtime_error {
   } while (0)
 
 // launch bookkeeping: every kernel launch of the library goes through MG_LAUNCH
+// (counted per context) or MG_LAUNCH_W, which also carries the launch's
+// algorithmic bytes and flops for the optional per-kernel event timer.
 extern thread_local int64_t* g_launch_counter;
-#define MG_LAUNCH(kernel, grid, block, smem, stream, ...)                          \
+// Per-kernel CUDA-event timer (enabled per context for kernels whose name
+// contains a filter string); records are resolved when the report is read.
+struct KTimer {
+  bool on = false;
+  std::string filter;
+  struct Rec {
+    const char* name;
+    double bytes, flops;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    MG_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  bool want(const char* name) const { return on && (filter.empty() || std::strstr(name, filter.c_str())); }
+};
+extern thread_local KTimer* g_timer;
+// number of right-hand sides still iterating (host hint for byte accounting), -1 = all
+extern thread_local int g_nact_hint;
+inline double act_rhs(int nrhs) { return (g_nact_hint >= 0 && g_nact_hint < nrhs) ? g_nact_hint : nrhs; }
+
+#define MG_LAUNCH_W(bytes, flops, kernel, grid, block, smem, stream, ...)          \
   do {                                                                             \
-    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                    \
-    MG_CUDA(cudaGetLastError());                                                   \
+    ::mg::KTimer* t_ = ::mg::g_timer;                                              \
+    if (t_ && t_->want(#kernel)) {                                                 \
+      cudaEvent_t a_ = t_->get(), b_ = t_->get();                                  \
+      MG_CUDA(cudaEventRecord(a_, (stream)));                                      \
+      kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
+      MG_CUDA(cudaGetLastError());                                                 \
+      MG_CUDA(cudaEventRecord(b_, (stream)));                                      \
+      t_->recs.push_back({#kernel, (double)(bytes), (double)(flops), a_, b_});     \
+    } else {                                                                       \
+      kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
+      MG_CUDA(cudaGetLastError());                                                 \
+    }                                                                              \
     if (::mg::g_launch_counter) ++*::mg::g_launch_counter;                         \
   } while (0)
+#define MG_LAUNCH(kernel, grid, block, smem, stream, ...) \
+  MG_LAUNCH_W(0, 0, kernel, grid, block, smem, stream, __VA_ARGS__)
 
 // ---------------------------------------------------------------- complex
 template <typename R> struct CT;

@@ -12,6 +12,8 @@
 namespace mg {
 
 thread_local int64_t* g_launch_counter = nullptr;
+thread_local KTimer* g_timer = nullptr;
+thread_local int g_nact_hint = -1;
 
 // ---------------------------------------------------------------- helpers
 template <typename R> static inline const typename CT<R>::T* links_of(const LevelData& L) {
@@ -395,7 +397,9 @@ static void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typen
     MG_CUDA(cudaMemsetAsync(s.count, 0, sizeof(int), st));
     MG_LAUNCH(k_gm_cycle, nb, 64, 0, st, s.beta2, s.act, s.cact, s.iact, s.kvec, s.beta, s.g, s.bnorm, s.its,
               s.relres, tol, maxit, m, nrhs, s.count);
-    if (read_flag(ctx, s.count) == 0) break;
+    const int nstart = read_flag(ctx, s.count);
+    if (nstart == 0) break;
+    g_nact_hint = nstart;
     vscale_inv<C>(st, s.beta, s.V, s.V, n, nrhs, s.cact);
     int jdone = 0;
     for (int j = 0; j < m; ++j) {
@@ -417,11 +421,16 @@ static void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typen
                 s.kvec, s.its, s.bnorm, tol, maxit, s.count);
       jdone = j + 1;
       vscale_inv<C>(st, s.hn, Vj1, Vj1, n, nrhs, s.iact);
-      if (read_flag(ctx, s.count) == 0) break;
+      const int nit = read_flag(ctx, s.count);
+      if (nit == 0) break;
+      g_nact_hint = nit;
     }
+    g_nact_hint = nstart;
     MG_LAUNCH(k_gm_trisolve, nb, 64, 0, st, m, nrhs, s.H, s.g, s.kvec, s.cact, s.y);
     vcombine<C>(st, s.Z, vs, jdone, s.y, x, n, nrhs, s.cact);
+    g_nact_hint = -1;
   }
+  g_nact_hint = -1;
   if (its_acc) {
     // its_acc += its
     std::vector<int> a(nrhs), b2(nrhs);
@@ -538,14 +547,18 @@ SolveOut solve(mgmlmc_hier* h, int l, const void* b, void* x, int nrhs, const so
     vnorm2<double2>(st, r64, n, nrhs, rn2, red, act);
     MG_CUDA(cudaMemsetAsync(count, 0, sizeof(int), st));
     MG_LAUNCH(k_mixed_check, nb, 64, 0, st, rn2, bn2, act, scale, relres, sp.tol, nrhs, count);
-    if (read_flag(ctx, count) == 0 || outer >= max_outer || used >= sp.maxit) break;
+    const int nout = read_flag(ctx, count);
+    if (nout == 0 || outer >= max_outer || used >= sp.maxit) break;
+    g_nact_hint = nout;
     vconvert<float2, double2>(st, r64, r32, n, nrhs, scale, act);
     const int inner_max = std::min(sp.maxit - used, std::max(sp.m * 4, 8));
     int cyc = 0;
     fgmres_core<float>(h, l, r32, e32, nrhs, sp.m, sp.inner_tol, inner_max, pc, act, its, nullptr, &cyc);
     used += inner_max;
     vaccum_mixed<float>(st, scale, e32, x64, n, nrhs, act);
+    g_nact_hint = nout;  // the next true residual covers the rhs active in this pass
   }
+  g_nact_hint = -1;
   return finish_out(ctx, its, relres, nrhs, sp.tol, outer);
 }
 

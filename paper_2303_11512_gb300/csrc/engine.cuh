@@ -17,6 +17,7 @@ struct mgmlmc_ctx {
   int64_t launches = 0;
   int* pinned = nullptr;  // small pinned host buffer for flags
   double* pinned_d = nullptr;
+  mg::KTimer timer;
 };
 
 namespace mg {
@@ -42,7 +43,8 @@ struct LevelData {
 }  // namespace mg
 
 struct mgmlmc_hier {
-  mgmlmc_ctx* ctx = nullptr;
+  mgmlmc_ctx* ctx = nullptr;   // context of the most recent call (set by every entry point)
+  cudaStream_t stream = 0;     // stream the hierarchy's memory is ordered on
   int L = 0;
   double m0 = 0;
   mg_params prm;
@@ -51,7 +53,7 @@ struct mgmlmc_hier {
   std::map<std::tuple<std::string, int>, mg::DBuf> ws;  // workspaces
   void* work(const std::string& tag, int level, size_t bytes) {
     auto& b = ws[std::make_tuple(tag, level)];
-    b.ensure(bytes, ctx->stream);
+    b.ensure(bytes, stream);
     return b.p;
   }
 };
@@ -67,8 +69,16 @@ namespace mg {
 
 // RAII binding of the launch counter to a context
 struct LaunchScope {
-  LaunchScope(mgmlmc_ctx* c) { g_launch_counter = &c->launches; }
-  ~LaunchScope() { g_launch_counter = nullptr; }
+  LaunchScope(mgmlmc_ctx* c) {
+    g_launch_counter = &c->launches;
+    g_timer = c->timer.on ? &c->timer : nullptr;
+    g_nact_hint = -1;
+  }
+  ~LaunchScope() {
+    g_launch_counter = nullptr;
+    g_timer = nullptr;
+    g_nact_hint = -1;
+  }
 };
 
 void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U);

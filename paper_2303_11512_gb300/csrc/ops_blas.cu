@@ -73,7 +73,8 @@ __global__ void k_finalize_real(const double* __restrict__ part, int nrhs, doubl
 template <typename C>
 void vnorm2(cudaStream_t st, const C* x, long n, int nrhs, double* out, void* work, const int* active) {
   double* part = reinterpret_cast<double*>(work);
-  MG_LAUNCH(k_norm2_part<C>, dim3(RBLK, nrhs), RT, 0, st, x, n, part, active);
+  MG_LAUNCH_W(act_rhs(nrhs) * n * sizeof(C), act_rhs(nrhs) * n * 4.0, k_norm2_part<C>, dim3(RBLK, nrhs), RT, 0, st,
+              x, n, part, active);
   MG_LAUNCH(k_finalize_real, cdiv(nrhs, 4), 128, 0, st, part, nrhs, out);
 }
 template void vnorm2<float2>(cudaStream_t, const float2*, long, int, double*, void*, const int*);
@@ -132,7 +133,8 @@ template <typename C>
 void vmultidot(cudaStream_t st, const C* V, long vstride, int k, const C* w, long n, int nrhs, double2* h,
                void* work, const int* active) {
   double2* part = reinterpret_cast<double2*>(work);
-  MG_LAUNCH(k_multidot_part<C>, dim3(RBLK, nrhs), RT, 0, st, V, vstride, k, w, n, part, active);
+  MG_LAUNCH_W(act_rhs(nrhs) * n * sizeof(C) * (k + 1.0), act_rhs(nrhs) * n * 8.0 * k, k_multidot_part<C>,
+              dim3(RBLK, nrhs), RT, 0, st, V, vstride, k, w, n, part, active);
   MG_LAUNCH(k_finalize_cplx, cdiv((long)k * nrhs, 4), 128, 0, st, part, k * nrhs, h);
 }
 template void vmultidot<float2>(cudaStream_t, const float2*, long, int, const float2*, long, int, double2*, void*,
@@ -178,13 +180,15 @@ template <typename C>
 void vgs_update(cudaStream_t st, const C* V, long vstride, int k, const double2* h, C* w, long n, int nrhs,
                 const int* active) {
   MG_CHECK_ARG(k <= 64, "at most 64 basis vectors");
-  MG_LAUNCH((k_lincomb<C, true>), dim3(ew_blocks(n), nrhs), 256, 0, st, V, vstride, k, h, w, n, active);
+  MG_LAUNCH_W(act_rhs(nrhs) * n * sizeof(C) * (k + 2.0), act_rhs(nrhs) * n * 8.0 * k, (k_lincomb<C, true>),
+              dim3(ew_blocks(n), nrhs), 256, 0, st, V, vstride, k, h, w, n, active);
 }
 template <typename C>
 void vcombine(cudaStream_t st, const C* Z, long zstride, int k, const double2* y, C* x, long n, int nrhs,
               const int* active) {
   MG_CHECK_ARG(k <= 64, "at most 64 basis vectors");
-  MG_LAUNCH((k_lincomb<C, false>), dim3(ew_blocks(n), nrhs), 256, 0, st, Z, zstride, k, y, x, n, active);
+  MG_LAUNCH_W(act_rhs(nrhs) * n * sizeof(C) * (k + 2.0), act_rhs(nrhs) * n * 8.0 * k, (k_lincomb<C, false>),
+              dim3(ew_blocks(n), nrhs), 256, 0, st, Z, zstride, k, y, x, n, active);
 }
 template void vgs_update<float2>(cudaStream_t, const float2*, long, int, const double2*, float2*, long, int, const int*);
 template void vgs_update<double2>(cudaStream_t, const double2*, long, int, const double2*, double2*, long, int,

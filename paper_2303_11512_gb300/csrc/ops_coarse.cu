@@ -77,18 +77,21 @@ void coarse_apply(cudaStream_t stm, const typename CT<R>::T* st, int Ls, int d, 
   size_t sm = sizeof(C) * (5 * d * d + G * 5 * d);
   static bool attr_set[2][2] = {{false, false}, {false, false}};
   const int ri = sizeof(R) == 8;
+  const double ns = (double)Ls * Ls, cs = sizeof(C), ar = act_rhs(nrhs);
+  const double bytes = ar * ns * d * cs * (b ? 3 : 2) + ns * 5.0 * d * d * cs;
+  const double flops = ar * ns * 8.0 * 5.0 * d * d;
   if (b) {
     if (!attr_set[ri][1]) {
       MG_CUDA(cudaFuncSetAttribute(k_coarse_apply<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
       attr_set[ri][1] = true;
     }
-    MG_LAUNCH((k_coarse_apply<R, true>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
+    MG_LAUNCH_W(bytes, flops, (k_coarse_apply<R, true>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
   } else {
     if (!attr_set[ri][0]) {
       MG_CUDA(cudaFuncSetAttribute(k_coarse_apply<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
       attr_set[ri][0] = true;
     }
-    MG_LAUNCH((k_coarse_apply<R, false>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
+    MG_LAUNCH_W(bytes, flops, (k_coarse_apply<R, false>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
   }
 }
 template void coarse_apply<float>(cudaStream_t, const float2*, int, int, const float2*, float2*, const float2*,
@@ -203,7 +206,10 @@ void sap_half_coarse(cudaStream_t stm, const typename CT<R>::T* st, int Ls, int 
     attr[ri] = true;
   }
   const int nb = (Ls / bs) * (Ls / bs) / 2;
-  MG_LAUNCH(k_sap_coarse<R>, nb, 256, sm, stm, st, Ls, d, bs, inv, f, x, color, nrhs, active);
+  const double cs = sizeof(C), ar = act_rhs(nrhs);
+  const double bytes = nb * (ar * 3.0 * bd * cs + ((double)bd * bd + ns * 5.0 * d * d) * cs);
+  const double flops = nb * ar * (8.0 * bd * 5.0 * d + 8.0 * bd * bd);
+  MG_LAUNCH_W(bytes, flops, k_sap_coarse<R>, nb, 256, sm, stm, st, Ls, d, bs, inv, f, x, color, nrhs, active);
 }
 template void sap_half_coarse<float>(cudaStream_t, const float2*, int, int, int, const float2*, const float2*,
                                      float2*, int, int, const int*);
@@ -317,7 +323,10 @@ void restrict_op(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, in
   static bool done[2] = {false, false};
   set_smem_attr(k_restrict<R>, done[sizeof(R) == 8]);
   const int Lc = Ls / agg;
-  MG_LAUNCH(k_restrict<R>, Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs, active);
+  const double nag = (double)Lc * Lc, cs = sizeof(C), ar = act_rhs(nrhs);
+  const double bytes = nag * (ar * (na * d + dc) * cs + 2.0 * bsz * ntv * cs);
+  const double flops = nag * ar * 8.0 * 2.0 * bsz * ntv;
+  MG_LAUNCH_W(bytes, flops, k_restrict<R>, Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs, active);
 }
 
 template <typename R>
@@ -329,12 +338,15 @@ void prolong_op(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, int
   size_t sm = sizeof(C) * ((size_t)2 * bsz * ntv + (size_t)G * dc);
   static bool done[2][2] = {{false, false}, {false, false}};
   const int Lc = Ls / agg;
+  const double nag = (double)Lc * Lc, cs = sizeof(C), ar = act_rhs(nrhs);
+  const double bytes = nag * (ar * ((add ? 2.0 : 1.0) * fa + dc) * cs + 2.0 * bsz * ntv * cs);
+  const double flops = nag * ar * 8.0 * 2.0 * bsz * ntv;
   if (add) {
     set_smem_attr(k_prolong<R, true>, done[sizeof(R) == 8][1]);
-    MG_LAUNCH((k_prolong<R, true>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active);
+    MG_LAUNCH_W(bytes, flops, (k_prolong<R, true>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active);
   } else {
     set_smem_attr(k_prolong<R, false>, done[sizeof(R) == 8][0]);
-    MG_LAUNCH((k_prolong<R, false>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active);
+    MG_LAUNCH_W(bytes, flops, (k_prolong<R, false>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active);
   }
 }
 template void restrict_op<float>(cudaStream_t, const float2*, int, int, int, int, const float2*, float2*, int,

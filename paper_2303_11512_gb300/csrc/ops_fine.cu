@@ -124,10 +124,14 @@ void wilson_apply(cudaStream_t st, const typename CT<R>::T* links, R diag, int L
                   typename CT<R>::T* y, const typename CT<R>::T* b, int nrhs, const int* active) {
   if (nrhs <= 0) return;
   dim3 grid(cdiv((long)L * L, 256), nrhs);
+  // algorithmic traffic: x read + y written once per site and rhs (+ b), links once per launch
+  const double V = (double)L * L, sp = 2.0 * sizeof(typename CT<R>::T), ar = act_rhs(nrhs);
+  const double bytes = ar * V * sp * (b ? 3 : 2) + V * sp;
+  const double flops = ar * V * (b ? 56.0 : 52.0);
   if (b)
-    MG_LAUNCH((k_wilson<R, true>), grid, 256, 0, st, links, diag, L, x, y, b, active);
+    MG_LAUNCH_W(bytes, flops, (k_wilson<R, true>), grid, 256, 0, st, links, diag, L, x, y, b, active);
   else
-    MG_LAUNCH((k_wilson<R, false>), grid, 256, 0, st, links, diag, L, x, y, b, active);
+    MG_LAUNCH_W(bytes, flops, (k_wilson<R, false>), grid, 256, 0, st, links, diag, L, x, y, b, active);
 }
 template void wilson_apply<float>(cudaStream_t, const float2*, float, int, const float2*, float2*, const float2*,
                                   int, const int*);
@@ -255,10 +259,14 @@ void sap_half_fine(cudaStream_t st, const typename CT<R>::T* links, R diag, int 
                    int nrhs, const int* active) {
   MG_CHECK_ARG(bs == 4 || bs == 2, "fine SAP block side must be 2 or 4");
   const int nb = (L / bs) * (L / bs) / 2;
+  // per block and rhs: x, f read and x written on the block (bd complex each); inverse once per block
+  const double bd = 2.0 * bs * bs, cs = sizeof(typename CT<R>::T), ar = act_rhs(nrhs);
+  const double bytes = nb * (ar * 3 * bd * cs + bd * bd * cs);
+  const double flops = nb * ar * (bs * bs * 56.0 + 8.0 * bd * bd);
   if (bs == 4)
-    MG_LAUNCH((k_sap_fine<R, 4>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs, active);
+    MG_LAUNCH_W(bytes, flops, (k_sap_fine<R, 4>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs, active);
   else
-    MG_LAUNCH((k_sap_fine<R, 2>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs, active);
+    MG_LAUNCH_W(bytes, flops, (k_sap_fine<R, 2>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs, active);
 }
 template void sap_half_fine<float>(cudaStream_t, const float2*, float, int, int, const float2*, const float2*,
                                    float2*, int, int, const int*);

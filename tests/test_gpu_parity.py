@@ -31,6 +31,9 @@ def api():
 def ctx(api):
     c = api.Context()
     yield c
+    for h, _ in _HIER.values():
+        h.close()
+    _HIER.clear()
     c.close()
 
 
