@@ -1,0 +1,349 @@
+"""Benchmark: time to a 1e-3 relative (1 sigma) MG-MLMC++ estimate of tr(D^{-1}).
+
+One step = the whole hot path on one synthetic gauge field already resident
+in HBM: multigrid set-up (test vectors, aggregation, Galerkin stencils,
+coarsest inverse), the Hutch++ sketches of every level difference and the
+stochastic loop of Algorithm 2 until the relative accuracy eps is reached.
+Workload (default): L = 512 (n = 524288), beta = 5, m0 tuned so that the
+smallest |eigenvalue| of D is ~1e-3, 4 levels (512 -> 128 -> 32 -> 8), 4x4
+aggregates, 8 test vectors per chirality, d = 32, k = 2, up to 256 rhs per
+batch, eps = 1e-3, mixed precision (FP32 inner FGMRES + V-cycle, FP64 true
+residual refinement to 1e-10, FP64 sketch/projection/statistics).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample instead.  Multi-GPU runs are independent replicas (one field
+per rank, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(L=512, beta=5.0, seed=0, ntv=8, d=32, k=2, eps=1e-3, nrhs_max=256, nrhs_first=32,
+                bootstrap=2, bootstrap_its=6, kcycle_its=0, pre_smooth=1, post_smooth=1)
+FALLBACK_M0 = {512: -0.07, 128: -0.1199}
+
+
+def mass_for(L: int, beta: float, seed: int) -> float:
+    path = os.path.join(ROOT, "tests", "golden", "masses.json")
+    try:
+        data = json.load(open(path))
+        return float(data["L%d_beta%g_seed%d" % (L, beta, seed)]["m0"])
+    except Exception:
+        return FALLBACK_M0.get(L, -0.05)
+
+
+def peaks() -> dict:
+    p = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, src="fallback")
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        p.update(hbm_gbs=float(m["hbm_gbs"]), bf16_tflops=float(m["bf16_tflops"]),
+                 bf16_tflops_sustained=float(m.get("bf16_tflops_sustained", m["bf16_tflops"])), src="measured")
+    except Exception:
+        pass
+    # CUDA-core peaks from unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes x 2 flops,
+    # FP64 at the nominal 1.25 TFLOP/s of the part
+    p["fp32_alu_tflops"] = 152 * 128 * 2 * 2.070e9 / 1e12
+    p["fp64_alu_tflops"] = 1.25
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for i, nm in enumerate(names):
+                    if r[3 + i].lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return dict(sm_mhz=med, sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ CPU oracle (reference arm / cpu_baseline)
+def oracle_sample(L_sample: int = 64, eps: float = 1e-3, seed: int = 0):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: the same
+    MG-MLMC++ (Algorithm 2, direct solves) on an L_sample^2 lattice of the same
+    beta, d, k and eps."""
+    from oracle import estimators as oest
+    from oracle import multigrid as omg
+    from oracle import schwinger as osch
+    from synthetic import gauge
+    W = WORKLOAD
+    U = gauge.links(gauge.field(L_sample, W["beta"], seed))
+    t0 = time.perf_counter()
+    D = osch.dirac_sparse(U, mass_for(512, W["beta"], 0))
+    H = omg.Hierarchy(D, L_sample, ntv=W["ntv"], seed=seed)
+    ld = oest.LevelDifference(H)
+    r = oest.mgmlmc_pp(ld, eps, min(W["d"], 16), W["k"], seed=seed)
+    return time.perf_counter() - t0, r
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, r = oracle_sample(args.ref_L, args.ref_eps)
+        if i >= args.warmup:
+            times.append(dt)
+    v = sum(times) / len(times)
+    cores = os.cpu_count()
+    line = dict(impl="reference", metric="time_to_eps_s", value=v, unit="s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * v, higher_is_better=False, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload="CPU oracle MG-MLMC++ (direct sparse-LU solves), L=%d, beta=%g, eps=%g: a "
+                            "bounded sample of the L=512 workload" % (args.ref_L, WORKLOAD["beta"], args.ref_eps)),
+                cpu_baseline=dict(value=v, unit="s", cores=cores, kind="oracle",
+                                  sample="full Algorithm 2 with direct solves on L=%d, eps=%g" % (args.ref_L,
+                                                                                                  args.ref_eps)),
+                e2e=dict(value=v, unit="s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=WORKLOAD["L"])
+    ap.add_argument("--eps", type=float, default=WORKLOAD["eps"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ref-L", type=int, default=64)
+    ap.add_argument("--ref-eps", type=float, default=1e-3)
+    ap.add_argument("--timing-filter", default="")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2303_11512_gb300 import api
+    from paper_2303_11512_gb300.estimator import TraceEstimator
+    from synthetic import gauge
+
+    W = dict(WORKLOAD)
+    W["L"], W["eps"] = args.L, args.eps
+    L = W["L"]
+    seed = W["seed"] + rank
+    m0 = mass_for(L, W["beta"], W["seed"])
+    U_host = gauge.links(gauge.field(L, W["beta"], seed))
+    U = torch.from_numpy(U_host).cuda()
+    mgp = dict(ntv=W["ntv"], bootstrap=W["bootstrap"], bootstrap_its=W["bootstrap_its"],
+               kcycle_its=W["kcycle_its"], pre_smooth=W["pre_smooth"], post_smooth=W["post_smooth"])
+    estp = dict(eps=W["eps"], d=W["d"], k=W["k"], nrhs_max=W["nrhs_max"], nrhs_first=W["nrhs_first"], cost_mode=1,
+                seed=0)
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(stream)
+
+    def step(prec=api.MIXED):
+        h = api.mg_setup(ctx, U, L, m0, **mgp)
+        r = api.trace_estimate(ctx, h, prec=prec, **estp)
+        h.close()
+        return r
+
+    for _ in range(args.warmup):
+        res = step()
+    # timed region: device-resident field, CUDA events on the library's stream
+    clocks = ClockSampler(local)
+    ctx.timing(True, args.timing_filter or None)
+    launches0 = ctx.launches
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    results = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ctx.timing(False)
+    launches = ctx.launches - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    rpt = ctx.timing_report()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ms / 1e3
+
+    # dominant kernel -> roofline
+    P = peaks()
+    dom, info = max(rpt.items(), key=lambda kv: kv[1]["ms"])
+    tot_ms = sum(v["ms"] for v in rpt.values())
+    avg_ms = info["ms"] / info["launches"]
+    bytes_l = info["bytes"] / info["launches"]
+    flops_l = info["flops"] / info["launches"]
+    ai = flops_l / max(bytes_l, 1.0)
+    fp64 = "double" in dom
+    alu_peak = P["fp64_alu_tflops"] if fp64 else P["fp32_alu_tflops"]
+    ridge = alu_peak * 1e12 / (P["hbm_gbs"] * 1e9)
+    if ai <= ridge:
+        roof = dict(bound="hbm", achieved=bytes_l / (avg_ms * 1e-3) / 1e9, peak=P["hbm_gbs"], unit="GB/s")
+    else:
+        roof = dict(bound="alu", achieved=flops_l / (avg_ms * 1e-3) / 1e12, peak=alu_peak, unit="TFLOP/s")
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update(kernel=dom, launches=info["launches"], avg_launch_ms=avg_ms, share=info["ms"] / max(tot_ms, 1e-9),
+                bytes_per_launch=bytes_l, flops_per_launch=flops_l, peak_src=P["src"], traffic=None)
+    kernels = {k: dict(launches=v["launches"], ms=round(v["ms"], 3), share=round(v["ms"] / max(tot_ms, 1e-9), 4),
+                       gbs=round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                       tflops=round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 3))
+               for k, v in sorted(rpt.items(), key=lambda kv: -kv[1]["ms"])[:12]}
+
+    # fine stencil alone in the workload's launch shape (FP32, 256 rhs): HBM GB/s
+    n = 2 * L * L
+    xs = torch.randn((W["nrhs_max"], n), dtype=torch.complex64, device="cuda")
+    ys = torch.empty_like(xs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        api.schwinger_apply(ctx, U, L, m0, xs, ys, api.FP32)
+    ts = []
+    for _ in range(10):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        api.schwinger_apply(ctx, U, L, m0, xs, ys, api.FP32)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ts.sort()
+    st_bytes = W["nrhs_max"] * L * L * 32 + L * L * 16
+    stencil = dict(gbs=st_bytes / (ts[len(ts) // 2] * 1e-3) / 1e9, ms=ts[len(ts) // 2], nrhs=W["nrhs_max"],
+                   frac_hbm=st_bytes / (ts[len(ts) // 2] * 1e-3) / 1e9 / P["hbm_gbs"])
+    del xs, ys, flush
+
+    # end to end through the public API: host gauge field, H2D + set-up + estimate + result D2H
+    U_pin = torch.from_numpy(U_host).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_t = []
+    for _ in range(max(1, args.steps)):
+        t1 = time.perf_counter()
+        est = TraceEstimator(U_pin.numpy(), L, m0, ctx=ctx, **mgp)
+        r_e2e = est.run(**estp)
+        est.close()
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t1)
+    e2e = dict(value=sum(e2e_t) / len(e2e_t), unit="s", h2d_bytes_per_step=int(U_host.nbytes),
+               d2h_bytes_per_step=int(16 * 2))
+
+    # plain FP64 batched MG form of the same estimator (the comparator of the metric)
+    fp64_s = None
+    if not args.no_fp64:
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r64 = step(api.FP64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64_s = a.elapsed_time(b) / 1e3
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+        dt, rcpu = oracle_sample(args.ref_L, args.ref_eps)
+        cpu = dict(value=dt, unit="s", cores=os.cpu_count(), kind="oracle",
+                   sample="the same MG-MLMC++ (Algorithm 2, direct sparse-LU solves, FP64) on an L=%d lattice "
+                          "(beta %g, eps %g): the L=512 oracle needs a ~1 min sparse LU per level, beyond the "
+                          "bounded budget" % (args.ref_L, W["beta"], args.ref_eps))
+
+    r = results[-1]
+    if rank == 0:
+        line = dict(
+            metric="time_to_eps_s", value=value, unit="s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=ms, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32+f64",
+            data="synthetic",
+            config=dict(workload="MG-MLMC++ tr(D^-1), 2D Schwinger Wilson-Dirac, L=%d, beta=%g, m0=%.6f, %d levels, "
+                        "ntv=%d/chirality, d=%d, k=%d, nrhs<=%d, eps=%g, mixed FP32/FP64, solver tol 1e-10"
+                        % (L, W["beta"], m0, r and len(r["N"]) + 1, W["ntv"], W["d"], W["k"], W["nrhs_max"],
+                           W["eps"]),
+                        l2="inputs larger than L2 (fine vectors 0.5-2 GB per batch); stencil timing flushes L2",
+                        bootstrap=W["bootstrap"], kcycle_its=W["kcycle_its"]),
+            roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches // max(1, args.steps)),
+            clocks=clk, fp64_reference_s=fp64_s,
+            speedup_vs_fp64=(fp64_s / value) if fp64_s else None,
+            stencil_fp32=stencil,
+            estimate=dict(tau=[r["tau"].real, r["tau"].imag], sigma=r["sigma"], rel_sigma=r["sigma"] / abs(r["tau"]),
+                          N=r["N"], computed=r["computed"], solves=r["solves"], inner_iters=r["inner_iters"]),
+            kernels=kernels)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -126,6 +126,15 @@ typedef struct {
   int pre_smooth;        /* V-cycle SAP sweeps before the coarse correction (1) */
   int post_smooth;       /* ... and after (1) */
   uint64_t seed;         /* test-vector stream seed (phase TESTVEC, level l, sample m) */
+  int bootstrap;         /* bootstrap rounds after the initial set-up (0): each replaces the test
+                            vectors of every level by bootstrap_its FGMRES iterations on D_l v_new = v
+                            preconditioned by the current hierarchy, then rebuilds P_l and D_{l+1}
+                            (the adaptive part of the DD-alpha-AMG set-up; with 0 the hierarchy is
+                            the deterministic one the CPU oracle reproduces) */
+  int bootstrap_its;     /* (6) */
+  int kcycle_its;        /* 0 = V-cycle; k > 0 = K-cycle: the coarse correction of levels below the
+                            first runs k FGMRES iterations preconditioned by the next V/K-cycle (0) */
+  double kcycle_tol;     /* relative residual at which a K-cycle stops early (0.1) */
 } mg_params;
 
 int mg_params_default(mg_params* p);

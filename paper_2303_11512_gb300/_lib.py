@@ -23,7 +23,8 @@ PHASE_STOCH, PHASE_SKETCH, PHASE_TESTVEC, PHASE_HUTCH = 0, 1, 2, 3
 class MgParams(C.Structure):
     _fields_ = [("levels", C.c_int), ("agg", C.c_int), ("ntv", C.c_int), ("sap_block_fine", C.c_int),
                 ("sap_block_coarse", C.c_int), ("setup_sweeps", C.c_int), ("pre_smooth", C.c_int),
-                ("post_smooth", C.c_int), ("seed", C.c_uint64)]
+                ("post_smooth", C.c_int), ("seed", C.c_uint64), ("bootstrap", C.c_int),
+                ("bootstrap_its", C.c_int), ("kcycle_its", C.c_int), ("kcycle_tol", C.c_double)]
 
 
 class SolveParams(C.Structure):

@@ -149,6 +149,10 @@ int mg_params_default(mg_params* p) {
   p->pre_smooth = 1;
   p->post_smooth = 1;
   p->seed = 0;
+  p->bootstrap = 0;
+  p->bootstrap_its = 6;
+  p->kcycle_its = 0;
+  p->kcycle_tol = 0.1;
   return MGMLMC_OK;
 }
 

@@ -32,24 +32,10 @@ template <typename R> static inline const typename CT<R>::T* inv_of(const LevelD
   if constexpr (sizeof(R) == 8) return L.inv64.as<double2>(); else return L.inv32.as<float2>();
 }
 
-static void to_fp32(cudaStream_t st, const DBuf& src, DBuf& dst, size_t count) {
-  dst.alloc(count * sizeof(float2), st);
-  vconvert<float2, double2>(st, src.as<double2>(), dst.as<float2>(), (long)count, 1, nullptr, nullptr);
-}
-
 static int read_flag(mgmlmc_ctx* ctx, const int* dflag) {
   MG_CUDA(cudaMemcpyAsync(ctx->pinned, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   MG_CUDA(cudaStreamSynchronize(ctx->stream));
   return ctx->pinned[0];
-}
-
-static int default_levels(int L, int agg) {
-  int lv = 1, side = L;
-  while (side > 8 && side % (4 * agg) == 0) {
-    side /= agg;
-    ++lv;
-  }
-  return lv;
 }
 
 // ---------------------------------------------------------------- operator pieces
@@ -65,8 +51,8 @@ void op_apply(mgmlmc_hier* h, int l, const typename CT<R>::T* x, typename CT<R>:
 }
 
 template <typename R>
-static void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>::T* x, int nrhs,
-                      const int* active) {
+void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>::T* x, int nrhs,
+               const int* active) {
   const LevelData& L = h->lv[l];
   cudaStream_t st = h->ctx->stream;
   for (int color = 0; color < 2; ++color) {
@@ -106,11 +92,17 @@ void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T
   for (int s = 0; s < h->prm.pre_smooth; ++s) sap_sweep<R>(h, l, r, e, nrhs, active);
   op_apply<R>(h, l, e, res, r, nrhs, active);  // res = r - D e
   restrict_op<R>(st, P_of<R>(L), L.side, L.dof, h->prm.agg, h->prm.ntv, res, rc, nrhs, active);
-  vcycle<R>(h, l + 1, rc, ec, nrhs, active);
+  if (h->prm.kcycle_its > 0 && l + 1 < h->nlev - 1)  // K-cycle: a few FGMRES steps on level l+1
+    fgmres_core<R>(h, l + 1, rc, ec, nrhs, h->prm.kcycle_its, h->prm.kcycle_tol, h->prm.kcycle_its, true, active,
+                   nullptr, nullptr, nullptr);
+  else
+    vcycle<R>(h, l + 1, rc, ec, nrhs, active);
   prolong_op<R>(st, P_of<R>(L), L.side, L.dof, h->prm.agg, h->prm.ntv, ec, e, true, nrhs, active);
   for (int s = 0; s < h->prm.post_smooth; ++s) sap_sweep<R>(h, l, r, e, nrhs, active);
 }
 
+template void sap_sweep<float>(mgmlmc_hier*, int, const float2*, float2*, int, const int*);
+template void sap_sweep<double>(mgmlmc_hier*, int, const double2*, double2*, int, const int*);
 template void op_apply<float>(mgmlmc_hier*, int, const float2*, float2*, const float2*, int, const int*);
 template void op_apply<double>(mgmlmc_hier*, int, const double2*, double2*, const double2*, int, const int*);
 template void vcycle<float>(mgmlmc_hier*, int, const float2*, float2*, int, const int*);
@@ -119,116 +111,6 @@ template void restrict_level<float>(mgmlmc_hier*, int, const float2*, float2*, i
 template void restrict_level<double>(mgmlmc_hier*, int, const double2*, double2*, int);
 template void prolong_level<float>(mgmlmc_hier*, int, const float2*, float2*, int);
 template void prolong_level<double>(mgmlmc_hier*, int, const double2*, double2*, int);
-
-// ---------------------------------------------------------------- hierarchy set-up
-void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U) {
-  cudaStream_t st = ctx->stream;
-  const mg_params& p = h->prm;
-  const int L = h->L;
-  MG_CHECK_ARG(p.agg >= 2 && p.ntv >= 1 && 2 * p.ntv <= 32 && 256 % (2 * p.ntv) == 0,
-               "mg_params: agg >= 2, 2*ntv must divide 256 and be <= 32");
-  h->nlev = p.levels > 0 ? p.levels : default_levels(L, p.agg);
-  MG_CHECK_ARG(h->nlev >= 2 && h->nlev <= MGMLMC_MAX_LEVELS, "need 2..8 levels");
-  h->lv.clear();
-  h->lv.resize(h->nlev);
-  {
-    int side = L;
-    for (int l = 0; l < h->nlev; ++l) {
-      LevelData& lv = h->lv[l];
-      lv.side = side;
-      lv.dof = l == 0 ? 2 : 2 * p.ntv;
-      lv.n = (long)side * side * lv.dof;
-      if (l < h->nlev - 1) {
-        const int bs = l == 0 ? p.sap_block_fine : p.sap_block_coarse;
-        MG_CHECK_ARG(side % p.agg == 0 && side / p.agg >= 4, "every coarse side must be >= 4 and divide evenly");
-        MG_CHECK_ARG(bs >= 1 && side % bs == 0 && (side / bs) % 2 == 0, "SAP block must tile the level in an even grid");
-        MG_CHECK_ARG(bs * bs * lv.dof <= 64, "SAP block dimension limited to 64");
-        lv.sap_bs = bs;
-        lv.sap_bd = bs * bs * lv.dof;
-        side /= p.agg;
-      }
-    }
-  }
-  int* dfail;
-  DBuf failbuf(sizeof(int) * 4, st);
-  dfail = failbuf.as<int>();
-  MG_CUDA(cudaMemsetAsync(dfail, 0, sizeof(int) * 4, st));
-
-  LevelData& l0 = h->lv[0];
-  l0.diag = h->m0 + 2.0;
-  l0.links64.alloc(sizeof(double2) * 2 * L * L, st);
-  l0.links32.alloc(sizeof(float2) * 2 * L * L, st);
-  prepare_links(st, U, L, l0.links64.as<double2>(), l0.links32.as<float2>());
-
-  for (int l = 0; l + 1 < h->nlev; ++l) {
-    LevelData& lv = h->lv[l];
-    LevelData& lc = h->lv[l + 1];
-    const int Ls = lv.side, d = lv.dof, bs = lv.sap_bs, bd = lv.sap_bd;
-    const long n = lv.n;
-    // SAP block inverses
-    const int nb = (Ls / bs) * (Ls / bs);
-    lv.sapinv64.alloc(sizeof(double2) * (size_t)nb * bd * bd, st);
-    if (l == 0)
-      fine_block_matrices(st, lv.links64.as<double2>(), lv.diag, Ls, bs, lv.sapinv64.as<double2>());
-    else
-      coarse_block_matrices(st, lv.st64.as<double2>(), Ls, d, bs, lv.sapinv64.as<double2>());
-    invert_small_batched(st, lv.sapinv64.as<double2>(), nb, bd, dfail + 0);
-    to_fp32(st, lv.sapinv64, lv.sapinv32, (size_t)nb * bd * bd);
-    // test vectors: complex Rademacher, smoothed by SAP sweeps for D v = 0
-    const int ntv = p.ntv;
-    DBuf V(sizeof(double2) * n * ntv, st), f0(sizeof(double2) * n * ntv, st);
-    complex_rademacher_fill(st, p.seed, l, MGMLMC_PHASE_TESTVEC, 0, n, ntv, V.as<double2>());
-    vzero<double2>(st, f0.as<double2>(), n, ntv);
-    for (int s = 0; s < p.setup_sweeps; ++s) sap_sweep<double>(h, l, f0.as<double2>(), V.as<double2>(), ntv, nullptr);
-    f0.release();
-    // prolongator: per (aggregate, chirality) orthonormal blocks
-    const int Lc = Ls / p.agg, dc = 2 * ntv;
-    const int bsz = p.agg * p.agg * d / 2;
-    const size_t pcount = (size_t)Lc * Lc * 2 * bsz * ntv;
-    lv.P64.alloc(sizeof(double2) * pcount, st);
-    gather_tv_blocks(st, V.as<double2>(), Ls, d, p.agg, ntv, lv.P64.as<double2>());
-    V.release();
-    orthonormalise_blocks(st, lv.P64.as<double2>(), Lc * Lc * 2, bsz, ntv, dfail + 1);
-    to_fp32(st, lv.P64, lv.P32, pcount);
-    // Galerkin D_{l+1} = P^H D_l P by colour probing (16 colours x dc probes)
-    const int np = 16 * dc;
-    const long nc = (long)Lc * Lc * dc;
-    {
-      DBuf probes(sizeof(double2) * n * np, st), imgs(sizeof(double2) * n * np, st);
-      make_probes(st, lv.P64.as<double2>(), Ls, d, p.agg, ntv, probes.as<double2>());
-      op_apply<double>(h, l, probes.as<double2>(), imgs.as<double2>(), nullptr, np, nullptr);
-      probes.release();
-      DBuf cimgs(sizeof(double2) * nc * np, st);
-      restrict_op<double>(st, lv.P64.as<double2>(), Ls, d, p.agg, ntv, imgs.as<double2>(), cimgs.as<double2>(), np,
-                          nullptr);
-      imgs.release();
-      const size_t scount = (size_t)Lc * Lc * 5 * dc * dc;
-      lc.st64.alloc(sizeof(double2) * scount, st);
-      extract_stencil(st, cimgs.as<double2>(), Lc, dc, lc.st64.as<double2>());
-      to_fp32(st, lc.st64, lc.st32, scount);
-    }
-  }
-  // coarsest level: dense FP64 inverse and its trace (tau_L of Algorithm 2)
-  {
-    LevelData& lc = h->lv[h->nlev - 1];
-    const int n = (int)lc.n;
-    MG_CHECK_ARG(n <= 8192, "coarsest level too large for the dense inverse");
-    lc.inv64.alloc(sizeof(double2) * (size_t)n * n, st);
-    dense_from_stencil(st, lc.st64.as<double2>(), lc.side, lc.dof, lc.inv64.as<double2>());
-    DBuf piv(sizeof(int) * n, st), work(sizeof(double2) * n, st), tr(sizeof(double2), st);
-    invert_large(st, lc.inv64.as<double2>(), n, piv.as<int>(), work.as<double2>(), dfail + 2);
-    to_fp32(st, lc.inv64, lc.inv32, (size_t)n * n);
-    trace_dense(st, lc.inv64.as<double2>(), n, tr.as<double2>());
-    MG_CUDA(cudaMemcpyAsync(&lc.trace, tr.p, sizeof(double2), cudaMemcpyDeviceToHost, st));
-    MG_CUDA(cudaStreamSynchronize(st));
-  }
-  int fl[4];
-  MG_CUDA(cudaMemcpyAsync(fl, dfail, sizeof(fl), cudaMemcpyDeviceToHost, st));
-  MG_CUDA(cudaStreamSynchronize(st));
-  if (fl[0]) throw Error(MGMLMC_ERR_NAN, "singular SAP block");
-  if (fl[1]) throw Error(MGMLMC_ERR_NAN, "test-vector block of zero norm");
-  if (fl[2]) throw Error(MGMLMC_ERR_NAN, "singular coarsest operator");
-}
 
 // ---------------------------------------------------------------- FGMRES
 // Per-rhs bookkeeping kernels of the batched flexible GMRES(m).
@@ -373,10 +255,14 @@ static GmState<R> gm_state(mgmlmc_hier* h, int l, int nrhs, int m) {
 // (true residual, checked at every restart) or after maxit inner iterations.
 // Per-rhs iteration counts are added to its_acc (device, may be null).
 template <typename R>
-static void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<R>::T* x, int nrhs, int m,
-                        double tol, int maxit, bool precond, const int* act_in, int* its_acc, double* relres_out,
-                        int* cycles_out) {
+void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<R>::T* x, int nrhs, int m,
+                 double tol, int maxit, bool precond, const int* act_in, int* its_acc, double* relres_out,
+                 int* cycles_out) {
   typedef typename CT<R>::T C;
+  struct HintGuard {  // nested solves (K-cycle, bootstrap) restore the caller's hint
+    int saved = g_nact_hint;
+    ~HintGuard() { g_nact_hint = saved; }
+  } hint_guard;
   mgmlmc_ctx* ctx = h->ctx;
   cudaStream_t st = ctx->stream;
   const long n = h->lv[l].n;
@@ -444,6 +330,10 @@ static void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typen
   if (relres_out) MG_CUDA(cudaMemcpyAsync(relres_out, s.relres, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, st));
   if (cycles_out) *cycles_out = cycles;
 }
+template void fgmres_core<float>(mgmlmc_hier*, int, const float2*, float2*, int, int, double, int, bool, const int*,
+                                 int*, double*, int*);
+template void fgmres_core<double>(mgmlmc_hier*, int, const double2*, double2*, int, int, double, int, bool,
+                                  const int*, int*, double*, int*);
 
 __global__ void k_mixed_check(const double* __restrict__ rn2, const double* __restrict__ bn2, int* act,
                               double* scale, double* relres, double tol, int nrhs, int* count) {

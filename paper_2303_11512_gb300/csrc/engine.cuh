@@ -33,7 +33,8 @@ struct LevelData {
   // SAP smoother (all but the coarsest)
   int sap_bs = 0, sap_bd = 0;
   DBuf sapinv64, sapinv32;
-  // prolongator to the next coarser level
+  // test vectors (ntv x n, FP64) and the prolongator to the next coarser level
+  DBuf tv;
   DBuf P64, P32;
   // coarsest level: dense inverse
   DBuf inv64, inv32;
@@ -82,6 +83,15 @@ struct LaunchScope {
 };
 
 void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U);
+
+// One SAP sweep (colour 0 then 1) for D_l x = f.
+template <typename R>
+void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>::T* x, int nrhs, const int* active);
+// Batched flexible GMRES(m) in precision R, x0 = 0; see engine.cu.
+template <typename R>
+void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<R>::T* x, int nrhs, int m,
+                 double tol, int maxit, bool precond, const int* act_in, int* its_acc, double* relres_out,
+                 int* cycles_out);
 
 template <typename R>
 void op_apply(mgmlmc_hier* h, int l, const typename CT<R>::T* x, typename CT<R>::T* y, const typename CT<R>::T* b,

@@ -85,6 +85,8 @@ void vaccum_mixed(cudaStream_t st, const double* scale, const typename CT<R>::T*
                   int nrhs, const int* active);
 // y = x - y  (FP64)
 void vsub_from(cudaStream_t st, const double2* x, double2* y, long n, int nrhs);
+// v[i] = sqrt(v[i])
+void sqrt_inplace(cudaStream_t st, double* v, int n);
 
 // reductions: out[rhs] (double / double2) on device; work = partial buffer
 size_t reduce_work_bytes(long n, int nrhs, int nvec);

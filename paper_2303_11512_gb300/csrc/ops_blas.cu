@@ -307,6 +307,12 @@ void vsub_from(cudaStream_t st, const double2* x, double2* y, long n, int nrhs) 
   MG_LAUNCH(k_sub_from, 1024, 256, 0, st, x, y, (size_t)n * nrhs);
 }
 
+__global__ void k_sqrt(double* v, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = sqrt(v[i]);
+}
+void sqrt_inplace(cudaStream_t st, double* v, int n) { MG_LAUNCH(k_sqrt, cdiv(n, 256), 256, 0, st, v, n); }
+
 __global__ void k_fill_int(int* p, int v, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;

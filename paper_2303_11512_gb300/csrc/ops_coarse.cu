@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(256) k_sap_coarse(const typename CT<R>::T* __r
   const int BX = 2 * (kb % half) + ((BT + color) & 1);
   const int blk = BT * nbx + BX;
   const C* I = inv + (size_t)blk * bd * bd;
-  for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) sinv[e] = I[e];
+  // transposed, sinv[j * bd + i] = inv[i][j]: threads of a warp differ in i
+  for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) sinv[(e % bd) * bd + e / bd] = I[e];
   for (int e = threadIdx.x; e < ns * 5 * dd; e += blockDim.x) {
     const int j = e / (5 * dd), r = e % (5 * dd), dir = r / dd, q = r % dd, i = q / d, k = q % d;
     const int s = (BT * bs + j / bs) * Ls + BX * bs + j % bs;
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) k_sap_coarse(const typename CT<R>::T* __r
       const int rhs = r0 + g;
       if (rhs < nrhs && !(active && !active[rhs])) {
         C acc = czero<C>();
-        for (int jj = 0; jj < bd; ++jj) acc = cfma(sinv[i * bd + jj], sres[g * bd + jj], acc);
+        for (int jj = 0; jj < bd; ++jj) acc = cfma(sinv[jj * bd + i], sres[g * bd + jj], acc);
         const int s = (BT * bs + j / bs) * Ls + BX * bs + j % bs;
         C* px = x + rhs * n + (size_t)s * d + k;
         *px = cadd(*px, acc);

@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(256) k_sap_fine(const typename CT<R>::T* __res
   typedef typename CT<R>::T C;
   constexpr int NS = BS * BS;      // sites per block
   constexpr int BD = 2 * NS;       // dof per block
-  constexpr int G = 256 / BD;      // rhs per group
-  __shared__ C sinv[BD * BD];
+  constexpr int G = 256 / NS;      // rhs per group (one thread per site and rhs in the residual phase)
+  __shared__ C sinv[BD * BD];      // transposed: sinv[j * BD + i] = inv[i][j] (conflict-free over i)
   __shared__ C sres[G * BD];
   const int nbx = L / BS;
   const int half = nbx / 2;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) k_sap_fine(const typename CT<R>::T* __res
   const int BX = 2 * (k % half) + ((BT + color) & 1);
   const int blk = BT * nbx + BX;
   const C* I = inv + (size_t)blk * BD * BD;
-  for (int e = threadIdx.x; e < BD * BD; e += blockDim.x) sinv[e] = I[e];
+  for (int e = threadIdx.x; e < BD * BD; e += blockDim.x) sinv[(e % BD) * BD + e / BD] = I[e];
   const int V = L * L;
   const size_t n = 2 * (size_t)V;
   for (int r0 = 0; r0 < nrhs; r0 += G) {
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) k_sap_fine(const typename CT<R>::T* __res
       if (rhs < nrhs && !(active && !active[rhs])) {
         C acc = czero<C>();
 #pragma unroll 8
-        for (int j = 0; j < BD; ++j) acc = cfma(sinv[i * BD + j], sres[g * BD + j], acc);
+        for (int j = 0; j < BD; ++j) acc = cfma(sinv[j * BD + i], sres[g * BD + j], acc);
         const int js = i >> 1;
         const int s = (BT * BS + js / BS) * L + BX * BS + (js % BS);
         C* px = x + rhs * n + 2 * s + (i & 1);

@@ -1,0 +1,183 @@
+// Multigrid set-up (Section 3.1 / Section 4): SAP block inverses, test
+// vectors, orthonormal aggregation prolongators, Galerkin coarse stencils by
+// colour probing, the coarsest dense inverse (its trace is tau_L of
+// Algorithm 2), and the optional bootstrap rounds.
+#include <algorithm>
+
+#include "engine.cuh"
+
+namespace mg {
+
+static void to_fp32(cudaStream_t st, const DBuf& src, DBuf& dst, size_t count) {
+  dst.alloc(count * sizeof(float2), st);
+  vconvert<float2, double2>(st, src.as<double2>(), dst.as<float2>(), (long)count, 1, nullptr, nullptr);
+}
+
+static int default_levels(int L, int agg) {
+  int lv = 1, side = L;
+  while (side > 8 && side % (4 * agg) == 0) {
+    side /= agg;
+    ++lv;
+  }
+  return lv;
+}
+
+// SAP block inverses of level l (FP64 master and FP32 copy)
+static void build_sap(mgmlmc_hier* h, int l, int* dfail) {
+  cudaStream_t st = h->stream;
+  LevelData& lv = h->lv[l];
+  const int Ls = lv.side, d = lv.dof, bs = lv.sap_bs, bd = lv.sap_bd;
+  const int nb = (Ls / bs) * (Ls / bs);
+  lv.sapinv64.alloc(sizeof(double2) * (size_t)nb * bd * bd, st);
+  if (l == 0)
+    fine_block_matrices(st, lv.links64.as<double2>(), lv.diag, Ls, bs, lv.sapinv64.as<double2>());
+  else
+    coarse_block_matrices(st, lv.st64.as<double2>(), Ls, d, bs, lv.sapinv64.as<double2>());
+  invert_small_batched(st, lv.sapinv64.as<double2>(), nb, bd, dfail);
+  to_fp32(st, lv.sapinv64, lv.sapinv32, (size_t)nb * bd * bd);
+}
+
+// dense FP64 inverse of the coarsest level and its trace
+static void build_coarsest(mgmlmc_hier* h, int* dfail) {
+  cudaStream_t st = h->stream;
+  LevelData& lc = h->lv[h->nlev - 1];
+  const int n = (int)lc.n;
+  MG_CHECK_ARG(n <= 8192, "coarsest level too large for the dense inverse");
+  lc.inv64.alloc(sizeof(double2) * (size_t)n * n, st);
+  dense_from_stencil(st, lc.st64.as<double2>(), lc.side, lc.dof, lc.inv64.as<double2>());
+  DBuf piv(sizeof(int) * n, st), work(sizeof(double2) * n, st), tr(sizeof(double2), st);
+  invert_large(st, lc.inv64.as<double2>(), n, piv.as<int>(), work.as<double2>(), dfail);
+  to_fp32(st, lc.inv64, lc.inv32, (size_t)n * n);
+  trace_dense(st, lc.inv64.as<double2>(), n, tr.as<double2>());
+  MG_CUDA(cudaMemcpyAsync(&lc.trace, tr.p, sizeof(double2), cudaMemcpyDeviceToHost, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+}
+
+// P_l from the level-l test vectors lv.tv (ntv x n_l, FP64), D_{l+1} = P^H D_l P,
+// then the smoother (or dense inverse) of level l+1.
+static void build_from_tv(mgmlmc_hier* h, int l, int* dfail) {
+  cudaStream_t st = h->stream;
+  const mg_params& p = h->prm;
+  LevelData& lv = h->lv[l];
+  LevelData& lc = h->lv[l + 1];
+  const int Ls = lv.side, d = lv.dof, ntv = p.ntv;
+  const long n = lv.n;
+  const int Lc = Ls / p.agg, dc = 2 * ntv;
+  const int bsz = p.agg * p.agg * d / 2;
+  const size_t pcount = (size_t)Lc * Lc * 2 * bsz * ntv;
+  lv.P64.alloc(sizeof(double2) * pcount, st);
+  gather_tv_blocks(st, lv.tv.as<double2>(), Ls, d, p.agg, ntv, lv.P64.as<double2>());
+  orthonormalise_blocks(st, lv.P64.as<double2>(), Lc * Lc * 2, bsz, ntv, dfail + 1);
+  to_fp32(st, lv.P64, lv.P32, pcount);
+  // Galerkin by colour probing: 16 aggregate colours x dc probe vectors
+  const int np = 16 * dc;
+  const long nc = (long)Lc * Lc * dc;
+  {
+    DBuf probes(sizeof(double2) * n * np, st), imgs(sizeof(double2) * n * np, st);
+    make_probes(st, lv.P64.as<double2>(), Ls, d, p.agg, ntv, probes.as<double2>());
+    op_apply<double>(h, l, probes.as<double2>(), imgs.as<double2>(), nullptr, np, nullptr);
+    probes.release();
+    DBuf cimgs(sizeof(double2) * nc * np, st);
+    restrict_op<double>(st, lv.P64.as<double2>(), Ls, d, p.agg, ntv, imgs.as<double2>(), cimgs.as<double2>(), np,
+                        nullptr);
+    imgs.release();
+    const size_t scount = (size_t)Lc * Lc * 5 * dc * dc;
+    lc.st64.alloc(sizeof(double2) * scount, st);
+    extract_stencil(st, cimgs.as<double2>(), Lc, dc, lc.st64.as<double2>());
+    to_fp32(st, lc.st64, lc.st32, scount);
+  }
+  if (l + 1 < h->nlev - 1)
+    build_sap(h, l + 1, dfail + 0);
+  else
+    build_coarsest(h, dfail + 2);
+}
+
+static void check_fail(mgmlmc_hier* h, const int* dfail) {
+  int fl[4];
+  MG_CUDA(cudaMemcpyAsync(fl, dfail, sizeof(fl), cudaMemcpyDeviceToHost, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  if (fl[0]) throw Error(MGMLMC_ERR_NAN, "singular SAP block");
+  if (fl[1]) throw Error(MGMLMC_ERR_NAN, "test-vector block of zero norm");
+  if (fl[2]) throw Error(MGMLMC_ERR_NAN, "singular coarsest operator");
+}
+
+void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U) {
+  cudaStream_t st = h->stream;
+  const mg_params& p = h->prm;
+  const int L = h->L;
+  MG_CHECK_ARG(p.agg >= 2 && p.ntv >= 1 && 2 * p.ntv <= 32 && 256 % (2 * p.ntv) == 0,
+               "mg_params: agg >= 2, 2*ntv must divide 256 and be <= 32");
+  MG_CHECK_ARG(p.setup_sweeps >= 0 && p.pre_smooth >= 0 && p.post_smooth >= 0 && p.bootstrap >= 0 &&
+                   p.kcycle_its >= 0 && p.kcycle_its <= 64 && p.bootstrap_its >= 1 && p.bootstrap_its <= 64,
+               "mg_params: negative or too large iteration counts");
+  h->nlev = p.levels > 0 ? p.levels : default_levels(L, p.agg);
+  MG_CHECK_ARG(h->nlev >= 2 && h->nlev <= MGMLMC_MAX_LEVELS, "need 2..8 levels");
+  h->lv.clear();
+  h->lv.resize(h->nlev);
+  {
+    int side = L;
+    for (int l = 0; l < h->nlev; ++l) {
+      LevelData& lv = h->lv[l];
+      lv.side = side;
+      lv.dof = l == 0 ? 2 : 2 * p.ntv;
+      lv.n = (long)side * side * lv.dof;
+      if (l < h->nlev - 1) {
+        const int bs = l == 0 ? p.sap_block_fine : p.sap_block_coarse;
+        MG_CHECK_ARG(side % p.agg == 0 && side / p.agg >= 4, "every coarse side must be >= 4 and divide evenly");
+        MG_CHECK_ARG(bs >= 1 && side % bs == 0 && (side / bs) % 2 == 0,
+                     "SAP block must tile the level in an even grid");
+        MG_CHECK_ARG(bs * bs * lv.dof <= 64, "SAP block dimension limited to 64");
+        lv.sap_bs = bs;
+        lv.sap_bd = bs * bs * lv.dof;
+        side /= p.agg;
+      }
+    }
+  }
+  DBuf failbuf(sizeof(int) * 4, st);
+  int* dfail = failbuf.as<int>();
+  MG_CUDA(cudaMemsetAsync(dfail, 0, sizeof(int) * 4, st));
+
+  LevelData& l0 = h->lv[0];
+  l0.diag = h->m0 + 2.0;
+  l0.links64.alloc(sizeof(double2) * 2 * L * L, st);
+  l0.links32.alloc(sizeof(float2) * 2 * L * L, st);
+  prepare_links(st, U, L, l0.links64.as<double2>(), l0.links32.as<float2>());
+  build_sap(h, 0, dfail + 0);
+
+  // initial phase: complex Rademacher test vectors smoothed by SAP sweeps for D_l v = 0
+  const int ntv = p.ntv;
+  for (int l = 0; l + 1 < h->nlev; ++l) {
+    LevelData& lv = h->lv[l];
+    const long n = lv.n;
+    lv.tv.alloc(sizeof(double2) * n * ntv, st);
+    complex_rademacher_fill(st, p.seed, l, MGMLMC_PHASE_TESTVEC, 0, n, ntv, lv.tv.as<double2>());
+    {
+      DBuf f0(sizeof(double2) * n * ntv, st);
+      vzero<double2>(st, f0.as<double2>(), n, ntv);
+      for (int s = 0; s < p.setup_sweeps; ++s) sap_sweep<double>(h, l, f0.as<double2>(), lv.tv.as<double2>(), ntv, nullptr);
+    }
+    build_from_tv(h, l, dfail);
+  }
+  check_fail(h, dfail);
+
+  // bootstrap rounds: inverse iteration with the current hierarchy as approximate inverse
+  for (int it = 0; it < p.bootstrap; ++it) {
+    for (int l = 0; l + 1 < h->nlev; ++l) {
+      LevelData& lv = h->lv[l];
+      const long n = lv.n;
+      DBuf b32(sizeof(float2) * n * ntv, st), x32(sizeof(float2) * n * ntv, st), nrm(sizeof(double) * ntv, st);
+      DBuf red(reduce_work_bytes(n, ntv, 1), st);
+      vnorm2<double2>(st, lv.tv.as<double2>(), n, ntv, nrm.as<double>(), red.p, nullptr);
+      sqrt_inplace(st, nrm.as<double>(), ntv);
+      vconvert<float2, double2>(st, lv.tv.as<double2>(), b32.as<float2>(), n, ntv, nrm.as<double>(), nullptr);
+      fgmres_core<float>(h, l, b32.as<float2>(), x32.as<float2>(), ntv, p.bootstrap_its, 1e-30, p.bootstrap_its, true,
+                         nullptr, nullptr, nullptr, nullptr);
+      vconvert<double2, float2>(st, x32.as<float2>(), lv.tv.as<double2>(), n, ntv, nullptr, nullptr);
+      build_from_tv(h, l, dfail);
+    }
+    check_fail(h, dfail);
+  }
+  (void)ctx;
+}
+
+}  // namespace mg
