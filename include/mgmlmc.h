@@ -234,6 +234,29 @@ int hutchpp_sketch_get_q(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, double* q_dev,
 int hutchpp_project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double* zeta, const double* y,
                     int64_t n, int nrhs, double* tau_out);
 
+/* Same projected samples as hutchpp_project, for callers that cannot allocate
+ * device memory when they need them: a host framework that has reserved the
+ * whole GPU for its own caching allocator, or a latency-critical loop that
+ * forbids cudaMalloc/cudaFree (they synchronise the device) after start-up.
+ * The paper has no counterpart; this is a deployment variant of the call above.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine, and
+ * no context is needed.  Partial sums go to a fixed file-scope device array of
+ * about 4.3 MB that every GPU loading the library holds until exit; the first
+ * call on a device (with that device current) looks up the array's device
+ * address once, so make that first call before any stream capture.  Every call
+ * overwrites the slots it later reads (no state carries over), but all calls
+ * share the one array: calls that overlap on the GPU (other streams, other host
+ * threads) race and give wrong results.
+ *   stream   cudaStream_t for the two launches (asynchronous; NULL = legacy default)
+ *   Q        device complex128 [d][n] (may be NULL when d == 0), d <= 32
+ *   zeta, y  device complex128 [nrhs][n], nrhs <= 256
+ *   tau_out  DEVICE complex128 [nrhs]: tau_r = zeta_r^H y_r - (Q^H zeta_r)^H (Q^H y_r)
+ * Returns MGMLMC_ERR_INVALID_ARG for nrhs > 256, d > 32, negative sizes or null
+ * pointers (nothing is launched), MGMLMC_ERR_CUDA if the address lookup or a
+ * launch fails, MGMLMC_OK otherwise (nrhs == 0 is a no-op). */
+int hutchpp_project_noalloc(void* stream, const double* Q, int d, const double* zeta, const double* y,
+                            int64_t n, int nrhs, double* tau_out);
+
 /* ---- Algorithm 2 end to end --------------------------------------------- */
 
 typedef struct {

@@ -88,6 +88,7 @@ SIGNATURES = {
     "hutchpp_sketch_destroy": (None, [vp]),
     "hutchpp_sketch_get_q": (ip, [vp, vp, vp, C.POINTER(ip), C.POINTER(C.c_int64)]),
     "hutchpp_project": (ip, [vp, vp, vp, vp, C.c_int64, ip, dp]),
+    "hutchpp_project_noalloc": (ip, [vp, vp, ip, vp, vp, C.c_int64, ip, vp]),
     "est_params_default": (ip, [C.POINTER(EstParams)]),
     "trace_estimate": (ip, [vp, vp, C.POINTER(EstParams), C.POINTER(EstResult)]),
     "mlmc_update_active": (ip, [ip, C.POINTER(ip), dp, C.POINTER(C.c_int64), dp, C.c_double, C.c_double, ip, ip]),

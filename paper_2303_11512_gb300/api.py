@@ -265,6 +265,18 @@ def hutchpp_project(ctx: Context, sketch: Sketch | None, zeta: torch.Tensor, y: 
     return out
 
 
+def hutchpp_project_noalloc(Q: torch.Tensor | None, zeta: torch.Tensor, y: torch.Tensor,
+                            tau_out: torch.Tensor, stream: torch.cuda.Stream | None = None):
+    """Projected samples into the device tensor `tau_out` ([nrhs] complex128) without any
+    device allocation inside the library (for callers that cannot allocate; see the header)."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    nrhs, n = zeta.shape
+    d = 0 if Q is None else Q.shape[0]
+    check(_lib.load().hutchpp_project_noalloc(C.c_void_p(s.cuda_stream), _ptr(Q, torch.complex128) if d else None,
+                                              d, _ptr(zeta, torch.complex128), _ptr(y, torch.complex128), n, nrhs,
+                                              _ptr(tau_out, torch.complex128)))
+
+
 def trace_estimate(ctx: Context, h: Hierarchy, eps: float = 1e-3, d=32, k: int = 2, nrhs_max: int = 256,
                    nrhs_first: int = 32, policy: int = OPTIMAL, form: int = ACCUMULATED, seed: int = 0,
                    cost=None, cost_mode: int = 0, min_samples: int = 2, max_samples: int = 1 << 20,
