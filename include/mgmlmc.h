@@ -180,7 +180,7 @@ typedef struct {
   int maxit;         /* total inner iteration limit per solve (2000) */
   int precond;       /* 1 = V-cycle preconditioner, 0 = none (GMRES) */
   int prec;          /* mgmlmc_prec */
-  double inner_tol;  /* MIXED: relative reduction of each FP32 inner solve (1e-6) */
+  double inner_tol;  /* MIXED: relative reduction of each FP32 inner solve (1e-5; FP32 arithmetic floors near 1e-6) */
 } solve_params;
 
 typedef struct {

@@ -84,7 +84,14 @@ int mgmlmc_timing_report(mgmlmc_ctx* ctx, char* buf, int64_t len) {
       MG_CUDA(cudaEventSynchronize(r.b));
       float ms = 0;
       MG_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
-      Agg& a = agg[r.name];
+      std::string key = r.name;
+      const char* w = std::strstr(r.where, "[with ");
+      if (w) {  // append the launcher's template arguments, e.g. "[with R = float]"
+        const char* e = std::strchr(w, ']');
+        key += " ";
+        key.append(w + 6, e ? (size_t)(e - w - 6) : std::strlen(w + 6));
+      }
+      Agg& a = agg[key];
       a.n += 1;
       a.ms += ms;
       a.bytes += r.bytes;
@@ -281,7 +288,7 @@ int solve_params_default(solve_params* p) {
   p->maxit = 2000;
   p->precond = 1;
   p->prec = MGMLMC_MIXED;
-  p->inner_tol = 1e-6;
+  p->inner_tol = 1e-5;
   return MGMLMC_OK;
 }
 

@@ -46,6 +46,7 @@ struct KTimer {
   std::string filter;
   struct Rec {
     const char* name;
+    const char* where;  // launching function (its template arguments name the precision)
     double bytes, flops;
     cudaEvent_t a, b;
   };
@@ -77,7 +78,7 @@ inline double act_rhs(int nrhs) { return (g_nact_hint >= 0 && g_nact_hint < nrhs
       kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
       MG_CUDA(cudaGetLastError());                                                 \
       MG_CUDA(cudaEventRecord(b_, (stream)));                                      \
-      t_->recs.push_back({#kernel, (double)(bytes), (double)(flops), a_, b_});     \
+      t_->recs.push_back({#kernel, __PRETTY_FUNCTION__, (double)(bytes), (double)(flops), a_, b_}); \
     } else {                                                                       \
       kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
       MG_CUDA(cudaGetLastError());                                                 \
