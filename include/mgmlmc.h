@@ -53,7 +53,8 @@ enum mgmlmc_status {
 enum mgmlmc_prec {
   MGMLMC_FP64 = 0,   /* everything in FP64 */
   MGMLMC_FP32 = 1,   /* everything in FP32 */
-  MGMLMC_MIXED = 2   /* FP64 vectors and true residuals, FP32 inner Krylov + V-cycle */
+  MGMLMC_MIXED = 2,  /* FP64 vectors and true residuals, FP32 inner Krylov + V-cycle */
+  MGMLMC_TF32 = 3    /* FP32 vectors, TF32 tensor-core products (mg_apply / mg_smooth on coarse levels) */
 };
 
 enum mgmlmc_form {
@@ -135,6 +136,8 @@ typedef struct {
   int kcycle_its;        /* 0 = V-cycle; k > 0 = K-cycle: the coarse correction of levels below the
                             first runs k FGMRES iterations preconditioned by the next V/K-cycle (0) */
   double kcycle_tol;     /* relative residual at which a K-cycle stops early (0.1) */
+  int tensor_cores;      /* 1: inside the FP32 V-cycle, coarse levels with 16 dof per site run their
+                            SAP sweeps and residuals as TF32 tcgen05 GEMMs over the rhs (1) */
 } mg_params;
 
 int mg_params_default(mg_params* p);
@@ -166,6 +169,17 @@ int mg_get_prolongator(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double*
 /* Copy the stencil of level l >= 1 to host: complex128 [site][dir 5][d][d],
  * dir = self, +x, -x, +t, -t; block (s, dir) = D_l[rows of s, cols of s+dir]. */
 int mg_get_stencil(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* host_out);
+
+/* `sweeps` SAP sweeps for D_l x = f (the multigrid smoother): per sweep the
+ * colour-0 blocks, then the colour-1 blocks, x_B += D_BB^{-1} (f - D_l x)_B
+ * (block side sap_block_fine on level 0, sap_block_coarse above).  x is read
+ * and updated in place.  prec FP64, FP32, or TF32 (tensor cores, coarse levels
+ * with 16 dof only). */
+int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x, int nrhs, int prec, int sweeps);
+
+/* MGMLMC_ERR_TIMEOUT if a tensor-core kernel of this hierarchy ran out of a
+ * bounded wait (it then stopped early and freed its tensor memory), else OK. */
+int mg_tc_status(mgmlmc_ctx* ctx, mgmlmc_hier* h);
 
 /* One V-cycle from level l as an approximate solve x ~ D_l^{-1} b: SAP
  * pre-smoothing, coarse correction P_l V(l+1)(P_l^H r), SAP post-smoothing;

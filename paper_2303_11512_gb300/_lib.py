@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libmgmlmc.so")
 
 MAX_LEVELS = 8
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_NAN, ERR_NOT_POSDEF = 0, -1, -2, -3, -4, -5, -6, -7
-FP64, FP32, MIXED = 0, 1, 2
+FP64, FP32, MIXED, TF32 = 0, 1, 2, 3
 ACCUMULATED, REDUCED = 0, 1
 OPTIMAL, UNIFORM = 0, 1
 PHASE_STOCH, PHASE_SKETCH, PHASE_TESTVEC, PHASE_HUTCH = 0, 1, 2, 3
@@ -24,7 +24,8 @@ class MgParams(C.Structure):
     _fields_ = [("levels", C.c_int), ("agg", C.c_int), ("ntv", C.c_int), ("sap_block_fine", C.c_int),
                 ("sap_block_coarse", C.c_int), ("setup_sweeps", C.c_int), ("pre_smooth", C.c_int),
                 ("post_smooth", C.c_int), ("seed", C.c_uint64), ("bootstrap", C.c_int),
-                ("bootstrap_its", C.c_int), ("kcycle_its", C.c_int), ("kcycle_tol", C.c_double)]
+                ("bootstrap_its", C.c_int), ("kcycle_its", C.c_int), ("kcycle_tol", C.c_double),
+                ("tensor_cores", C.c_int)]
 
 
 class SolveParams(C.Structure):
@@ -80,6 +81,8 @@ SIGNATURES = {
     "mg_get_prolongator": (ip, [vp, vp, ip, vp]),
     "mg_get_stencil": (ip, [vp, vp, ip, vp]),
     "mg_vcycle": (ip, [vp, vp, ip, vp, vp, ip, ip]),
+    "mg_smooth": (ip, [vp, vp, ip, vp, vp, ip, ip, ip]),
+    "mg_tc_status": (ip, [vp, vp]),
     "solve_params_default": (ip, [C.POINTER(SolveParams)]),
     "fgmres_batched": (ip, [vp, vp, ip, vp, vp, ip, C.POINTER(SolveParams), C.POINTER(SolveStats), vp]),
     "mlmc_level_sample": (ip, [vp, vp, ip, vp, vp, ip, C.POINTER(SolveParams), C.POINTER(SolveStats)]),

@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (ACCUMULATED, FP32, FP64, MIXED, OPTIMAL, REDUCED, UNIFORM, EstParams, EstResult,
+from ._lib import (ACCUMULATED, FP32, FP64, MIXED, OPTIMAL, REDUCED, TF32, UNIFORM, EstParams, EstResult,
                    MgParams, SolveParams, SolveStats, check)
 
 __all__ = ["Context", "Hierarchy", "Sketch", "schwinger_apply", "mgmlmc_rademacher", "mg_setup",
@@ -33,7 +33,7 @@ def _ptr(t: torch.Tensor, dtype=None) -> int:
 
 
 def _vec_dtype(prec: int):
-    return torch.complex64 if prec == FP32 else torch.complex128
+    return torch.complex64 if prec in (FP32, TF32) else torch.complex128
 
 
 class Context:
@@ -143,6 +143,15 @@ class Hierarchy:
         dt = _vec_dtype(prec)
         check(_lib.load().mg_prolong(self.ctx.ptr, self.ptr, level, _ptr(xc, dt), _ptr(xf, dt), xc.shape[0],
                                      prec), self.ctx.ptr)
+
+    def smooth(self, level: int, f: torch.Tensor, x: torch.Tensor, prec: int = FP64, sweeps: int = 1):
+        """SAP sweeps for D_l x = f, x updated in place (prec FP64, FP32 or TF32)."""
+        dt = _vec_dtype(prec)
+        check(_lib.load().mg_smooth(self.ctx.ptr, self.ptr, level, _ptr(f, dt), _ptr(x, dt), f.shape[0], prec,
+                                    sweeps), self.ctx.ptr)
+
+    def tc_status(self) -> int:
+        return _lib.load().mg_tc_status(self.ctx.ptr, self.ptr)
 
     def vcycle(self, level: int, b: torch.Tensor, x: torch.Tensor, prec: int = FP64):
         dt = _vec_dtype(prec)

@@ -160,6 +160,7 @@ int mg_params_default(mg_params* p) {
   p->bootstrap_its = 6;
   p->kcycle_its = 0;
   p->kcycle_tol = 0.1;
+  p->tensor_cores = 1;
   return MGMLMC_OK;
 }
 
@@ -210,13 +211,54 @@ int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y,
     MG_CHECK_ARG(h && x && y && x != y, "null or aliased pointer");
     const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
-    check_prec(prec);
+    MG_CHECK_ARG(prec == MGMLMC_TF32 ? h->use_tc(level) : true, "TF32 apply needs a coarse level with 16 dof");
+    if (prec != MGMLMC_TF32) check_prec(prec);
     if (nrhs <= 0) return;
-    if (prec == MGMLMC_FP32)
+    if (prec == MGMLMC_TF32)
+      tc_stencil_apply(ctx->stream, h->lv[level].tcW.as<float>(), h->lv[level].side, (const float2*)x, (float2*)y,
+                       nullptr, nrhs, nullptr, h->tc_err.as<int>());
+    else if (prec == MGMLMC_FP32)
       op_apply<float>(h, level, (const float2*)x, (float2*)y, nullptr, nrhs, nullptr);
     else
       op_apply<double>(h, level, (const double2*)x, (double2*)y, nullptr, nrhs, nullptr);
   });
+}
+
+int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x, int nrhs, int prec, int sweeps) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && f && x && f != x, "null or aliased pointer");
+    h->ctx = ctx;
+    MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "the coarsest level has no smoother");
+    MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32 || prec == MGMLMC_TF32, "FP64, FP32 or TF32");
+    MG_CHECK_ARG(prec != MGMLMC_TF32 || (h->use_tc(level) && h->lv[level].tcInv[0].p),
+                 "TF32 smoothing needs a coarse level with 16 dof and 2x2 SAP blocks");
+    MG_CHECK_ARG(sweeps >= 0, "sweeps must be >= 0");
+    if (nrhs <= 0) return;
+    const int saved = h->prm.tensor_cores;
+    h->prm.tensor_cores = prec == MGMLMC_TF32;
+    try {
+      for (int s = 0; s < sweeps; ++s) {
+        if (prec == MGMLMC_FP64)
+          sap_sweep<double>(h, level, (const double2*)f, (double2*)x, nrhs, nullptr);
+        else
+          sap_sweep<float>(h, level, (const float2*)f, (float2*)x, nrhs, nullptr);
+      }
+    } catch (...) {
+      h->prm.tensor_cores = saved;
+      throw;
+    }
+    h->prm.tensor_cores = saved;
+  });
+}
+
+int mg_tc_status(mgmlmc_ctx* ctx, mgmlmc_hier* h) {
+  int flag = 0;
+  int rc = guarded(ctx, [&] {
+    MG_CHECK_ARG(h, "null hierarchy");
+    MG_CUDA(cudaMemcpyAsync(&flag, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+  return rc != MGMLMC_OK ? rc : (flag ? MGMLMC_ERR_TIMEOUT : MGMLMC_OK);
 }
 
 int mg_restrict(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* xf, void* xc, int nrhs, int prec) {

@@ -55,6 +55,15 @@ void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>
                const int* active) {
   const LevelData& L = h->lv[l];
   cudaStream_t st = h->ctx->stream;
+  if constexpr (sizeof(R) == 4) {
+    if (h->use_tc(l) && L.sap_bs == 2 && L.tcInv[0].p) {
+      float2* res = (float2*)h->work("tc_res", l, sizeof(float2) * L.n * nrhs);
+      for (int color = 0; color < 2; ++color)
+        tc_sap_half(st, L.tcW.as<float>(), L.tcInv[color].as<float>(), L.side, f, x, res, color, nrhs, active,
+                    h->tc_err.as<int>());
+      return;
+    }
+  }
   for (int color = 0; color < 2; ++color) {
     if (l == 0)
       sap_half_fine<R>(st, links_of<R>(L), (R)L.diag, L.side, L.sap_bs, sapinv_of<R>(L), f, x, color, nrhs, active);
@@ -90,7 +99,14 @@ void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T
   C* ec = (C*)h->work(pr ? "vc_ec64" : "vc_ec32", l, sizeof(C) * Lc.n * nrhs);
   vzero<C>(st, e, L.n, nrhs);
   for (int s = 0; s < h->prm.pre_smooth; ++s) sap_sweep<R>(h, l, r, e, nrhs, active);
-  op_apply<R>(h, l, e, res, r, nrhs, active);  // res = r - D e
+  bool done = false;
+  if constexpr (sizeof(R) == 4) {
+    if (h->use_tc(l)) {  // res = r - D e on the tensor cores (preconditioner accuracy)
+      tc_stencil_apply(st, L.tcW.as<float>(), L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
+      done = true;
+    }
+  }
+  if (!done) op_apply<R>(h, l, e, res, r, nrhs, active);  // res = r - D e
   restrict_op<R>(st, P_of<R>(L), L.side, L.dof, h->prm.agg, h->prm.ntv, res, rc, nrhs, active);
   if (h->prm.kcycle_its > 0 && l + 1 < h->nlev - 1)  // K-cycle: a few FGMRES steps on level l+1
     fgmres_core<R>(h, l + 1, rc, ec, nrhs, h->prm.kcycle_its, h->prm.kcycle_tol, h->prm.kcycle_its, true, active,
@@ -359,13 +375,16 @@ __global__ void k_init_act(const double* __restrict__ bn2, int* act, double* rel
 }
 
 static SolveOut finish_out(mgmlmc_ctx* ctx, const int* its_dev, const double* relres_dev, int nrhs, double tol,
-                           int cycles) {
+                           int cycles, const int* tc_err = nullptr) {
   SolveOut o;
   o.its.resize(nrhs);
   std::vector<double> rr(nrhs);
+  int tcflag = 0;
   MG_CUDA(cudaMemcpyAsync(o.its.data(), its_dev, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
   MG_CUDA(cudaMemcpyAsync(rr.data(), relres_dev, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  if (tc_err) MG_CUDA(cudaMemcpyAsync(&tcflag, tc_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   MG_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (tcflag) throw Error(MGMLMC_ERR_TIMEOUT, "a tensor-core kernel ran out of its bounded wait");
   o.outer = cycles;
   for (int r = 0; r < nrhs; ++r) {
     o.iters = std::max(o.iters, o.its[r]);
@@ -403,13 +422,13 @@ SolveOut solve(mgmlmc_hier* h, int l, const void* b, void* x, int nrhs, const so
     int cyc = 0;
     fgmres_core<double>(h, l, (const double2*)b, (double2*)x, nrhs, sp.m, sp.tol, sp.maxit, pc, nullptr, its, relres,
                         &cyc);
-    return finish_out(ctx, its, relres, nrhs, sp.tol, cyc);
+    return finish_out(ctx, its, relres, nrhs, sp.tol, cyc, h->tc_err.as<int>());
   }
   if (sp.prec == MGMLMC_FP32) {
     int cyc = 0;
     fgmres_core<float>(h, l, (const float2*)b, (float2*)x, nrhs, sp.m, sp.tol, sp.maxit, pc, nullptr, its, relres,
                        &cyc);
-    return finish_out(ctx, its, relres, nrhs, sp.tol, cyc);
+    return finish_out(ctx, its, relres, nrhs, sp.tol, cyc, h->tc_err.as<int>());
   }
   // MIXED: FP64 outer iterative refinement on the true residual, FP32 inner FGMRES
   MG_CHECK_ARG(sp.prec == MGMLMC_MIXED, "unknown precision");
@@ -449,7 +468,7 @@ SolveOut solve(mgmlmc_hier* h, int l, const void* b, void* x, int nrhs, const so
     g_nact_hint = nout;  // the next true residual covers the rhs active in this pass
   }
   g_nact_hint = -1;
-  return finish_out(ctx, its, relres, nrhs, sp.tol, outer);
+  return finish_out(ctx, its, relres, nrhs, sp.tol, outer, h->tc_err.as<int>());
 }
 
 // ---------------------------------------------------------------- MG-MLMC level differences

@@ -1,0 +1,424 @@
+// Coarse-level block operators on the 5th-generation tensor cores (tcgen05).
+//
+// On a coarse level every site carries d = 16 complex dof and the operator
+// (Galerkin stencil, SAP block inverse) is a small dense complex matrix per
+// site or block applied to all right-hand sides at once: with the rhs on the
+// M dimension that is a batched GEMM  Y^T[rhs, n] = sum_k X^T[rhs, k] E[n, k]
+// with the complex matrix embedded as a real one (E[2i+a][2j+b] =
+// [[Re, -Im], [Im, Re]]), and FP32 data read directly as TF32.
+//
+//   mode 0 (stencil):   per site s, K = 5 chunks (x at s, s+x, s-x, s+t, s-t),
+//                       N = 32:   y = D x   or   y = b - D x
+//   mode 1 (SAP block): per 2x2 block B of one colour, K = 4 chunks (its sites),
+//                       N = 128:  x_B += inv_B r_B
+//
+// Data movement: the rhs x 32-float slab of one site is one TMA box (128 rhs
+// rows x 128 B, 128-byte swizzle) straight from the canonical [rhs][site][dof]
+// vector; weights are stored pre-swizzled and fetched with one bulk copy per
+// chunk.  One thread issues the MMAs (M = 128, K = 8 per instruction) into a
+// TMEM accumulator; four warps read it back with tcgen05.ld (row = rhs =
+// lane) for the epilogue.  Every wait on an mbarrier is bounded: on expiry the
+// kernel records an error code, stops, waits (bounded) for its own copies and
+// frees its TMEM.
+#include <cuda.h>
+
+#include "ops.cuh"
+
+namespace mg {
+namespace {
+
+constexpr int TC_M = 128;          // rhs per tile (MMA M)
+constexpr int TC_CHUNK = 32;       // floats per site slab (16 complex)
+constexpr int TC_SLAB = TC_M * TC_CHUNK * 4;  // bytes of one A chunk (16 KB)
+constexpr long TC_SPIN = 1L << 26; // bounded waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  for (long it = 0; it < TC_SPIN; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;            // descriptor version of tcgen05
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+// instruction descriptor: D f32, A/B tf32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 lanes x 32 consecutive 32-bit TMEM columns -> 32 registers per thread
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int nbr_site_tc(int s, int dir, int Ls) {
+  const int t = s / Ls, x = s - t * Ls;
+  switch (dir) {
+    case 1: return t * Ls + (x + 1 == Ls ? 0 : x + 1);
+    case 2: return t * Ls + (x == 0 ? Ls - 1 : x - 1);
+    case 3: return (t + 1 == Ls ? 0 : t + 1) * Ls + x;
+    case 4: return (t == 0 ? Ls - 1 : t - 1) * Ls + x;
+    default: return s;
+  }
+}
+// site of local index j (0..3) of the k-th 2x2 block of colour `color`
+__device__ __forceinline__ int block_site(int k, int j, int Ls, int color) {
+  const int nbx = Ls / 2, half = nbx / 2;
+  const int BT = k / half;
+  const int BX = 2 * (k % half) + ((BT + color) & 1);
+  return (2 * BT + (j >> 1)) * Ls + 2 * BX + (j & 1);
+}
+
+// MODE 0: KC = 5, N = 32, two pipeline stages.  MODE 1: KC = 4, N = 128, one stage.
+template <int MODE>
+struct TcCfg;
+template <>
+struct TcCfg<0> {
+  static constexpr int KC = 5, N = 32, STAGES = 2, NCOL = 32;
+};
+template <>
+struct TcCfg<1> {
+  static constexpr int KC = 4, N = 128, STAGES = 1, NCOL = 128;
+};
+template <int MODE>
+constexpr int tc_stage_bytes() {
+  return TcCfg<MODE>::KC * (TC_SLAB + TcCfg<MODE>::N * 128);
+}
+template <int MODE>
+constexpr int tc_smem_bytes() {
+  return TcCfg<MODE>::STAGES * tc_stage_bytes<MODE>() + 1024 /* alignment slack */ + 64;
+}
+
+// items: MODE 0 with bmode = 0: every site; bmode = 1: the 4 sites of every colour-`color` 2x2 block.
+//        MODE 1: every colour-`color` 2x2 block.
+template <int MODE>
+__global__ void __launch_bounds__(128, 1)
+    k_tc(const __grid_constant__ CUtensorMap amap, const float* __restrict__ W, float* __restrict__ out,
+         const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs,
+         const int* __restrict__ active, int* err) {
+  typedef TcCfg<MODE> CF;
+  constexpr int KC = CF::KC, N = CF::N, ST = CF::STAGES;
+  constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
+  constexpr uint32_t STAGE_TX = (uint32_t)tc_stage_bytes<MODE>();
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t tma_bar[2];
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t s_taddr;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rhs0 = blockIdx.y * TC_M;
+  const long ncf = (long)Ls * Ls * TC_CHUNK;  // floats per rhs row
+  auto sA = [&](int st, int kc) { return base + st * tc_stage_bytes<MODE>() + kc * TC_SLAB; };
+  auto sB = [&](int st, int kc) { return base + st * tc_stage_bytes<MODE>() + KC * TC_SLAB + kc * N * 128; };
+  auto site_of = [&](int item, int kc) -> int {
+    if (MODE == 1) return block_site(item, kc, Ls, color);
+    const int s = bmode ? block_site(item >> 2, item & 3, Ls, color) : item;
+    return nbr_site_tc(s, kc, Ls);
+  };
+  auto w_of = [&](int item, int kc) -> const float* {
+    if (MODE == 1) return W + ((size_t)item * KC + kc) * N * TC_CHUNK;
+    const int s = bmode ? block_site(item >> 2, item & 3, Ls, color) : item;
+    return W + ((size_t)s * KC + kc) * N * TC_CHUNK;
+  };
+  auto issue = [&](int item, int st) {
+    mbar_expect_tx(&tma_bar[st], STAGE_TX);
+    for (int kc = 0; kc < KC; ++kc) {
+      tma_load_2d(sA(st, kc), &amap, site_of(item, kc) * TC_CHUNK, rhs0, &tma_bar[st]);
+      bulk_load(sB(st, kc), w_of(item, kc), N * 128, &tma_bar[st]);
+    }
+  };
+
+  if (tid == 0) {
+    mbar_init(&tma_bar[0], 1);
+    mbar_init(&tma_bar[1], 1);
+    mbar_init(&mma_bar, 1);
+    s_bad = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                 "r"((uint32_t)CF::NCOL)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = s_taddr;
+
+  int n_my = 0;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) ++n_my;
+  uint32_t tph[2] = {0u, 0u}, mph = 0u;
+  int pending = -1;  // stage with loads in flight not yet waited for (thread 0)
+  if (tid == 0 && n_my > 0) {
+    issue(blockIdx.x, 0);
+    pending = 0;
+  }
+  for (int i = 0; i < n_my; ++i) {
+    const int item = blockIdx.x + i * gridDim.x;
+    const int st = (ST == 2) ? (i & 1) : 0;
+    if (tid == 0) {
+      if (ST == 2 && i + 1 < n_my) issue(item + gridDim.x, st ^ 1);
+      bool ok = mbar_wait(&tma_bar[st], tph[st]);
+      tph[st] ^= 1u;
+      pending = (ST == 2 && i + 1 < n_my) ? (st ^ 1) : -1;
+      if (!ok) {
+        atomicExch(err, 1);
+        s_bad = 1;
+      } else {
+        tc_fence_after();
+        for (int kc = 0; kc < KC; ++kc) {
+          const uint64_t ad = sw128_desc(smem_u32(sA(st, kc)));
+          const uint64_t bd = sw128_desc(smem_u32(sB(st, kc)));
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4)  // K = 8 tf32 = 32 B per instruction
+            mma_tf32(taddr, ad + 2 * k4, bd + 2 * k4, IDESC, (kc | k4) != 0);
+        }
+        mma_commit(&mma_bar);
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    if (!mbar_wait(&mma_bar, mph)) {
+      atomicExch(err, 2);
+      s_bad = 1;
+    }
+    mph ^= 1u;
+    tc_fence_after();
+    const int row = warp * 32 + lane;
+    const int rhs = rhs0 + row;
+    const bool on = !s_bad && rhs < nrhs && !(active && !active[rhs]);
+    float v[32];
+    if (MODE == 0) {
+      tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), v);
+      if (on) {
+        const int s = bmode ? block_site(item >> 2, item & 3, Ls, color) : item;
+        float4* o = reinterpret_cast<float4*>(out + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
+        if (bvec) {
+          const float4* b = reinterpret_cast<const float4*>(bvec + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float4 bb = b[q];
+            o[q] = make_float4(bb.x - v[4 * q], bb.y - v[4 * q + 1], bb.z - v[4 * q + 2], bb.w - v[4 * q + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < 4; ++j) {
+        tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * j), v);
+        if (on) {
+          const int s = block_site(item, j, Ls, color);
+          float4* o = reinterpret_cast<float4*>(out + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float4 a = o[q];
+            o[q] = make_float4(a.x + v[4 * q], a.y + v[4 * q + 1], a.z + v[4 * q + 2], a.w + v[4 * q + 3]);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (s_bad) break;
+  }
+  // on an early stop, wait (bounded) for this CTA's copies still in flight
+  if (tid == 0 && pending >= 0) mbar_wait(&tma_bar[pending], tph[pending]);
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"((uint32_t)CF::NCOL)
+                 : "memory");
+  }
+}
+
+// real embedding of a complex d x d matrix block into the swizzled K-major B image:
+// element (n, k) of an N x 32 tile sits at n * 32 + (((k >> 2) ^ (n & 7)) << 2) + (k & 3)
+__device__ __forceinline__ int sw_index(int n, int k) { return n * 32 + ((((k >> 2) ^ (n & 7)) << 2) | (k & 3)); }
+
+__global__ void k_tc_stencil_weights(const float2* __restrict__ st, int nsite, float* __restrict__ W) {
+  // st[site][dir][16][16] complex -> W[site][dir][32 x 32] tf32
+  const size_t total = (size_t)nsite * 5 * 32 * 32;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = e % 32, n = (e / 32) % 32;
+    const size_t sd = e / 1024;  // site * 5 + dir
+    const int i = n >> 1, a = n & 1, j = k >> 1, b = k & 1;
+    const float2 z = st[sd * 256 + i * 16 + j];
+    const float v = (a == b) ? z.x : (a == 1 ? z.y : -z.y);
+    W[sd * 1024 + sw_index(n, k)] = v;
+  }
+}
+
+__global__ void k_tc_blockinv_weights(const float2* __restrict__ inv, int Ls, int color, int nblk, float* __restrict__ W) {
+  // colour-`color` blocks only, in their item order: inv[block][64][64] -> W[item][kc 4][128 x 32]
+  const size_t total = (size_t)nblk * 4 * 128 * 32;
+  const int nbx = Ls / 2, half = nbx / 2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int kk = e % 32, n = (e / 32) % 128, kc = (e / 4096) % 4;
+    const int item = (int)(e / 16384);
+    const int BT = item / half, BX = 2 * (item % half) + ((BT + color) & 1);
+    const int blk = BT * nbx + BX;
+    const int kg = kc * 32 + kk;  // real input index 2 * (16 * site_j + dof) + b
+    const int i = n >> 1, a = n & 1, j = kg >> 1, b = kg & 1;
+    const float2 z = inv[(size_t)blk * 4096 + i * 64 + j];
+    const float v = (a == b) ? z.x : (a == 1 ? z.y : -z.y);
+    W[((size_t)item * 4 + kc) * 4096 + sw_index(n, kk)] = v;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    MG_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) throw Error(MGMLMC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D view [nrhs rows][nsite * 32 floats] of a coarse FP32 vector; box 32 floats x 128 rows
+CUtensorMap make_map(const float2* v, int nsite, int nrhs) {
+  MG_CHECK_ARG(((uintptr_t)v & 15) == 0, "tensor-core operand must be 16-byte aligned");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)nsite * TC_CHUNK, (cuuint64_t)nrhs};
+  cuuint64_t strides[1] = {(cuuint64_t)nsite * TC_CHUNK * 4};
+  cuuint32_t box[2] = {TC_CHUNK, TC_M};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)v, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(MGMLMC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+template <int MODE>
+void launch_tc(cudaStream_t st, const CUtensorMap& m, const float* W, float* out, const float* b, int Ls, int nitems,
+               int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops) {
+  static bool attr = false;
+  const int sm = tc_smem_bytes<MODE>();
+  if (!attr) {
+    MG_CUDA(cudaFuncSetAttribute(k_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    attr = true;
+  }
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = (nrhs + TC_M - 1) / TC_M;
+  const int gx = std::max(1, std::min(nitems, (nsm + tiles - 1) / tiles));
+  dim3 grid(gx, tiles);
+  MG_LAUNCH_W(bytes, flops, k_tc<MODE>, grid, 128, sm, st, m, W, out, b, Ls, nitems, bmode, color, nrhs, active, err);
+}
+
+}  // namespace
+
+size_t tc_stencil_weight_floats(int nsite) { return (size_t)nsite * 5 * 1024; }
+size_t tc_blockinv_weight_floats(int Ls) { return (size_t)(Ls / 2) * (Ls / 2) / 2 * 4 * 4096; }
+
+void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, float* W) {
+  MG_LAUNCH(k_tc_stencil_weights, 1024, 256, 0, st, st32, nsite, W);
+}
+void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color, float* W) {
+  const int nblk = (Ls / 2) * (Ls / 2) / 2;
+  MG_LAUNCH(k_tc_blockinv_weights, 1024, 256, 0, st, inv32, Ls, color, nblk, W);
+}
+
+void tc_stencil_apply(cudaStream_t st, const float* W, int Ls, const float2* x, float2* y, const float2* b, int nrhs,
+                      const int* active, int* err) {
+  if (nrhs <= 0) return;
+  const int ns = Ls * Ls;
+  CUtensorMap m = make_map(x, ns, nrhs);
+  const double ar = act_rhs(nrhs);
+  const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + ns * 5.0 * 4096;
+  const double flops = ar * ns * 2.0 * 32 * 160;
+  launch_tc<0>(st, m, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
+}
+
+void tc_sap_half(cudaStream_t st, const float* Wst, const float* Winv, int Ls, const float2* f, float2* x,
+                 float2* res, int color, int nrhs, const int* active, int* err) {
+  if (nrhs <= 0) return;
+  const int ns = Ls * Ls, nblk = ns / 8;
+  const double ar = act_rhs(nrhs);
+  {  // residual on the sites of the colour's blocks
+    CUtensorMap m = make_map(x, ns, nrhs);
+    const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 4096;
+    const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
+    launch_tc<0>(st, m, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes, flops);
+  }
+  {  // x_B += inv_B r_B
+    CUtensorMap m = make_map(res, ns, nrhs);
+    const double bytes = ar * (ns / 2) * 128.0 * 3 + nblk * 65536.0;
+    const double flops = ar * nblk * 2.0 * 128 * 128;
+    launch_tc<1>(st, m, Winv, (float*)x, nullptr, Ls, nblk, 0, color, nrhs, active, err, bytes, flops);
+  }
+}
+
+}  // namespace mg

@@ -177,6 +177,38 @@ def test_level_operators_and_transfers(api, ctx):
             assert relerr(xf.cpu().numpy(), (P @ v.T).T) < 1e-12
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+def test_smoother_parity(api, ctx, prec):
+    """SAP sweeps (the smoother of the V-cycle) against the oracle's SAP on the same level operator."""
+    h, H = hierarchies(api, ctx, 64)
+    tol = {"fp64": 1e-12, "fp32": 2e-5, "tf32": 5e-3}[prec]
+    for l in range(H.levels - 1):
+        if prec == "tf32" and l == 0:
+            continue  # tensor-core smoother runs on coarse levels
+        f = rand_vecs(H.n[l], 3, 40 + l)
+        x0 = rand_vecs(H.n[l], 3, 50 + l)
+        sap = omg.SAP(H.D[l], H.side[l], H.dof[l], 4 if l == 0 else 2)
+        ref = sap.sweep(f.T.copy(), sap.sweep(f.T.copy(), x0.T.copy())).T
+        dt = np.complex128 if prec == "fp64" else np.complex64
+        xd = cuda(x0.astype(dt))
+        h.smooth(l, cuda(f.astype(dt)), xd, {"fp64": api.FP64, "fp32": api.FP32, "tf32": api.TF32}[prec], 2)
+        assert relerr(xd.cpu().numpy(), ref) < tol
+    assert h.tc_status() == 0
+
+
+def test_tensor_core_stencil(api, ctx):
+    """TF32 tcgen05 coarse stencil against the oracle's Galerkin operator; ragged rhs counts."""
+    h, H = hierarchies(api, ctx, 64)
+    for l in range(1, H.levels):
+        for nrhs in (1, 37, 130):
+            x = rand_vecs(H.n[l], nrhs, 60 + nrhs)
+            ref = (H.D[l] @ x.T).T
+            y = torch.zeros((nrhs, H.n[l]), dtype=torch.complex64, device="cuda")
+            h.apply(l, cuda(x.astype(np.complex64)), y, api.TF32)
+            assert relerr(y.cpu().numpy(), ref) < 5e-3
+    assert h.tc_status() == 0
+
+
 # ---------------------------------------------------------------- solver
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 @pytest.mark.parametrize("level", [0, 1])
