@@ -30,7 +30,8 @@ namespace {
 constexpr int TC_M = 128;          // rhs per tile (MMA M)
 constexpr int TC_CHUNK = 32;       // floats per site slab (16 complex)
 constexpr int TC_SLAB = TC_M * TC_CHUNK * 4;  // bytes of one A chunk (16 KB)
-constexpr long TC_SPIN = 1L << 26; // bounded waits
+constexpr long TC_SPIN = 1L << 26; // bounded waits: poll count ...
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // ... and wall time (2 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -40,7 +41,14 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ uint64_t gtimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: gives up after TC_WAIT_NS of wall time (or TC_SPIN polls)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  const uint64_t t0 = gtimer_ns();
   for (long it = 0; it < TC_SPIN; ++it) {
     uint32_t done;
     asm volatile(
@@ -49,6 +57,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
         : "r"(smem_u32(bar)), "r"(phase)
         : "memory");
     if (done) return true;
+    if ((it & 255) == 255 && gtimer_ns() - t0 > TC_WAIT_NS) break;
   }
   return false;
 }
@@ -165,6 +174,10 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ uint32_t s_taddr;
   __shared__ int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ int s_skip;
+  if (tid == 0) s_skip = *(volatile int*)err;  // an earlier launch gave up: do nothing until the host sees it
+  __syncthreads();
+  if (s_skip) return;
   const int rhs0 = blockIdx.y * TC_M;
   const long ncf = (long)Ls * Ls * TC_CHUNK;  // floats per rhs row
   auto sA = [&](int st, int kc) { return base + st * tc_stage_bytes<MODE>() + kc * TC_SLAB; };
@@ -218,6 +231,10 @@ __global__ void __launch_bounds__(128, 1)
     const int item = blockIdx.x + i * gridDim.x;
     const int st = (ST == 2) ? (i & 1) : 0;
     if (tid == 0) {
+      if (ST == 1 && i > 0) {  // one stage: this item's loads start once the previous item is done
+        issue(item, 0);
+        pending = 0;
+      }
       if (ST == 2 && i + 1 < n_my) issue(item + gridDim.x, st ^ 1);
       bool ok = mbar_wait(&tma_bar[st], tph[st]);
       tph[st] ^= 1u;
