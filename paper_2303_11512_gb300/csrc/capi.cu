@@ -215,7 +215,7 @@ int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y,
     if (prec != MGMLMC_TF32) check_prec(prec);
     if (nrhs <= 0) return;
     if (prec == MGMLMC_TF32)
-      tc_stencil_apply(ctx->stream, h->lv[level].st32.as<float2>(), h->lv[level].side, (const float2*)x, (float2*)y,
+      tc_stencil_apply(ctx->stream, h->lv[level].tcW.as<float>(), h->lv[level].side, (const float2*)x, (float2*)y,
                        nullptr, nrhs, nullptr, h->tc_err.as<int>());
     else if (prec == MGMLMC_FP32)
       op_apply<float>(h, level, (const float2*)x, (float2*)y, nullptr, nrhs, nullptr);
@@ -230,7 +230,7 @@ int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x
     h->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "the coarsest level has no smoother");
     MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32 || prec == MGMLMC_TF32, "FP64, FP32 or TF32");
-    MG_CHECK_ARG(prec != MGMLMC_TF32 || (level >= 1 && h->lv[level].dof == 16 && h->lv[level].sap_bs == 2),
+    MG_CHECK_ARG(prec != MGMLMC_TF32 || (h->use_tc(level) && h->lv[level].tcInv[0].p),
                  "TF32 smoothing needs a coarse level with 16 dof and 2x2 SAP blocks");
     MG_CHECK_ARG(sweeps >= 0, "sweeps must be >= 0");
     if (nrhs <= 0) return;

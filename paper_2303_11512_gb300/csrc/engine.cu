@@ -56,10 +56,10 @@ void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>
   const LevelData& L = h->lv[l];
   cudaStream_t st = h->ctx->stream;
   if constexpr (sizeof(R) == 4) {
-    if (h->use_tc(l) && L.sap_bs == 2 && L.sapinv32.p) {
+    if (h->use_tc(l) && L.sap_bs == 2 && L.tcInv[0].p) {
       float2* res = (float2*)h->work("tc_res", l, sizeof(float2) * L.n * nrhs);
       for (int color = 0; color < 2; ++color)
-        tc_sap_half(st, L.st32.as<float2>(), L.sapinv32.as<float2>(), L.side, f, x, res, color, nrhs, active,
+        tc_sap_half(st, L.tcW.as<float>(), L.tcInv[color].as<float>(), L.side, f, x, res, color, nrhs, active,
                     h->tc_err.as<int>());
       return;
     }
@@ -102,7 +102,7 @@ void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T
   bool done = false;
   if constexpr (sizeof(R) == 4) {
     if (h->use_tc(l)) {  // res = r - D e on the tensor cores (preconditioner accuracy)
-      tc_stencil_apply(st, L.st32.as<float2>(), L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
+      tc_stencil_apply(st, L.tcW.as<float>(), L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
       done = true;
     }
   }

@@ -36,6 +36,8 @@ struct LevelData {
   // test vectors (ntv x n, FP64) and the prolongator to the next coarser level
   DBuf tv;
   DBuf P64, P32;
+  // tensor-core images (coarse levels with 16 dof): stencil and per-colour SAP block inverses
+  DBuf tcW, tcInv[2];
   // coarsest level: dense inverse
   DBuf inv64, inv32;
   double2 trace = make_double2(0, 0);
@@ -54,7 +56,7 @@ struct mgmlmc_hier {
   std::map<std::tuple<std::string, int>, mg::DBuf> ws;  // workspaces
   mg::DBuf tc_err;  // device int: set by a tensor-core kernel whose bounded wait expired
   bool use_tc(int l) const {
-    return prm.tensor_cores && l >= 1 && l < nlev && lv[l].dof == 16 && lv[l].st32.p != nullptr;
+    return prm.tensor_cores && l >= 1 && l < nlev && lv[l].dof == 16 && lv[l].tcW.p != nullptr;
   }
   void* work(const std::string& tag, int level, size_t bytes) {
     auto& b = ws[std::make_tuple(tag, level)];

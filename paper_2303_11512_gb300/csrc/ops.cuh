@@ -127,12 +127,16 @@ void proj_coeffs(cudaStream_t st, const double2* Q, int d, const double2* x, lon
 size_t proj_work_bytes(int d, long n, int nrhs);
 
 // ---------------------------------------------------------------- tensor cores (coarse levels, d = 16)
-// Weights are the FP32 complex stencil [site][5][16][16] and SAP inverses [block][64][64].
+// pre-swizzled TF32 weights: stencil [site][dir 5][32 x 32]; SAP block inverses of one colour [item][4][128 x 32]
+size_t tc_stencil_weight_floats(int nsite);
+size_t tc_blockinv_weight_floats(int Ls);
+void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, float* W);
+void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color, float* W);
 // y = D x (b == nullptr) or y = b - D x, FP32 vectors, TF32 products
-void tc_stencil_apply(cudaStream_t st, const float2* stencil, int Ls, const float2* x, float2* y, const float2* b,
-                      int nrhs, const int* active, int* err);
+void tc_stencil_apply(cudaStream_t st, const float* W, int Ls, const float2* x, float2* y, const float2* b, int nrhs,
+                      const int* active, int* err);
 // one SAP colour half sweep with 2x2-site blocks: res = f - D x on the colour's sites, x_B += inv_B res_B
-void tc_sap_half(cudaStream_t st, const float2* stencil, const float2* inv, int Ls, const float2* f, float2* x,
+void tc_sap_half(cudaStream_t st, const float* Wst, const float* Winv, int Ls, const float2* f, float2* x,
                  float2* res, int color, int nrhs, const int* active, int* err);
 
 // ---------------------------------------------------------------- misc

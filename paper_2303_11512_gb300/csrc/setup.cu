@@ -35,6 +35,12 @@ static void build_sap(mgmlmc_hier* h, int l, int* dfail) {
     coarse_block_matrices(st, lv.st64.as<double2>(), Ls, d, bs, lv.sapinv64.as<double2>());
   invert_small_batched(st, lv.sapinv64.as<double2>(), nb, bd, dfail);
   to_fp32(st, lv.sapinv64, lv.sapinv32, (size_t)nb * bd * bd);
+  if (h->prm.tensor_cores && l >= 1 && d == 16 && bs == 2) {
+    for (int c = 0; c < 2; ++c) {
+      lv.tcInv[c].alloc(sizeof(float) * tc_blockinv_weight_floats(Ls), st);
+      tc_blockinv_weights(st, lv.sapinv32.as<float2>(), Ls, c, lv.tcInv[c].as<float>());
+    }
+  }
 }
 
 // dense FP64 inverse of the coarsest level and its trace
@@ -85,6 +91,10 @@ static void build_from_tv(mgmlmc_hier* h, int l, int* dfail) {
     lc.st64.alloc(sizeof(double2) * scount, st);
     extract_stencil(st, cimgs.as<double2>(), Lc, dc, lc.st64.as<double2>());
     to_fp32(st, lc.st64, lc.st32, scount);
+    if (p.tensor_cores && dc == 16) {
+      lc.tcW.alloc(sizeof(float) * tc_stencil_weight_floats(Lc * Lc), st);
+      tc_stencil_weights(st, lc.st32.as<float2>(), Lc * Lc, lc.tcW.as<float>());
+    }
   }
   if (l + 1 < h->nlev - 1)
     build_sap(h, l + 1, dfail + 0);

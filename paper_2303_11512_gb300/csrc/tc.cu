@@ -12,11 +12,11 @@
 //   mode 1 (SAP block): per 2x2 block B of one colour, K = 4 chunks (its sites),
 //                       N = 128:  x_B += inv_B r_B
 //
-// Data movement: the rhs x 32-float slab of one site is one TMA box (up to 128
-// rhs rows x 128 B, 128-byte swizzle) straight from the canonical [rhs][site][dof]
-// vector; the FP32 complex weights of the item arrive with one bulk copy and
-// are expanded in shared memory into the real-embedded, swizzled B tiles.
-// One thread issues the MMAs (M = 128, K = 8 per instruction) into a
+// Data movement: the rhs x 32-float slab of one site is one TMA box (the launch's
+// rhs count rounded up to 8, at most 128 rows, x 128 B, 128-byte swizzle) straight
+// from the canonical [rhs][site][dof] vector; MMA rows beyond the box are never
+// stored.  Weights are stored pre-swizzled and fetched with one bulk copy per
+// chunk.  One thread issues the MMAs (M = 128, K = 8 per instruction) into a
 // TMEM accumulator; four warps read it back with tcgen05.ld (row = rhs =
 // lane) for the epilogue.  Every wait on an mbarrier is bounded: on expiry the
 // kernel records an error code, stops, waits (bounded) for its own copies and
@@ -137,40 +137,31 @@ __device__ __forceinline__ int block_site(int k, int j, int Ls, int color) {
   return (2 * BT + (j >> 1)) * Ls + 2 * BX + (j & 1);
 }
 
-// element (n, k) of an N x 32 K-major tile with 128-byte swizzle (16-byte chunks XOR row % 8)
-__device__ __forceinline__ int sw_index(int n, int k) { return n * 32 + ((((k >> 2) ^ (n & 7)) << 2) | (k & 3)); }
-
-// MODE 0: KC = 5 site slabs, N = 32, two pipeline stages, complex weights 5 x 16 x 16 per site.
-// MODE 1: KC = 4 site slabs, N = 128, one stage, complex weights 64 x 64 per block.
+// MODE 0: KC = 5, N = 32, two pipeline stages.  MODE 1: KC = 4, N = 128, one stage.
 template <int MODE>
 struct TcCfg;
 template <>
 struct TcCfg<0> {
-  static constexpr int KC = 5, N = 32, STAGES = 2, NCOL = 32, WC_BYTES = 5 * 16 * 16 * 8;
+  static constexpr int KC = 5, N = 32, STAGES = 2, NCOL = 32;
 };
 template <>
 struct TcCfg<1> {
-  static constexpr int KC = 4, N = 128, STAGES = 1, NCOL = 128, WC_BYTES = 64 * 64 * 8;
+  static constexpr int KC = 4, N = 128, STAGES = 1, NCOL = 128;
 };
-// stage: A slabs (KC x 128 rows x 128 B) | B tiles (KC x N x 128 B) | staged complex weights
 template <int MODE>
 constexpr int tc_stage_bytes() {
-  return TcCfg<MODE>::KC * (TC_SLAB + TcCfg<MODE>::N * 128) + TcCfg<MODE>::WC_BYTES;
+  return TcCfg<MODE>::KC * (TC_SLAB + TcCfg<MODE>::N * 128);
 }
 template <int MODE>
 constexpr int tc_smem_bytes() {
-  return TcCfg<MODE>::STAGES * tc_stage_bytes<MODE>() + 1024 /* alignment slack */;
+  return TcCfg<MODE>::STAGES * tc_stage_bytes<MODE>() + 1024 /* alignment slack */ + 64;
 }
 
 // items: MODE 0 with bmode = 0: every site; bmode = 1: the 4 sites of every colour-`color` 2x2 block.
 //        MODE 1: every colour-`color` 2x2 block.
-// Wc: MODE 0 the FP32 coarse stencil [site][dir][16][16]; MODE 1 the FP32 SAP inverses [block][64][64].
-// The complex weights are fetched with one bulk copy per item and expanded in shared memory into the
-// real-embedded, swizzled B tiles (half the bytes of a stored TF32 image).  The A boxes have `rows`
-// rhs rows (the launch's rhs count rounded up to 8, at most 128); MMA rows beyond them are never stored.
 template <int MODE>
 __global__ void __launch_bounds__(128, 1)
-    k_tc(const __grid_constant__ CUtensorMap amap, const float2* __restrict__ Wc, float* __restrict__ out,
+    k_tc(const __grid_constant__ CUtensorMap amap, const float* __restrict__ W, float* __restrict__ out,
          const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int rows,
          const int* __restrict__ active, int* err) {
   typedef TcCfg<MODE> CF;
@@ -181,35 +172,32 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ __align__(8) uint64_t tma_bar[2];
   __shared__ __align__(8) uint64_t mma_bar;
   __shared__ uint32_t s_taddr;
-  __shared__ int s_bad, s_skip;
+  __shared__ int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ int s_skip;
   if (tid == 0) s_skip = *(volatile int*)err;  // an earlier launch gave up: do nothing until the host sees it
   __syncthreads();
   if (s_skip) return;
   const int rhs0 = blockIdx.y * TC_M;
   const long ncf = (long)Ls * Ls * TC_CHUNK;  // floats per rhs row
-  const uint32_t stage_tx = (uint32_t)(KC * rows * 128 + CF::WC_BYTES);
+  const uint32_t stage_tx = (uint32_t)(KC * (rows * 128 + N * 128));
   auto sA = [&](int st, int kc) { return base + st * tc_stage_bytes<MODE>() + kc * TC_SLAB; };
-  auto sB = [&](int st, int kc) {
-    return reinterpret_cast<float*>(base + st * tc_stage_bytes<MODE>() + KC * TC_SLAB + kc * N * 128);
+  auto sB = [&](int st, int kc) { return base + st * tc_stage_bytes<MODE>() + KC * TC_SLAB + kc * N * 128; };
+  auto site_of = [&](int item, int kc) -> int {
+    if (MODE == 1) return block_site(item, kc, Ls, color);
+    const int s = bmode ? block_site(item >> 2, item & 3, Ls, color) : item;
+    return nbr_site_tc(s, kc, Ls);
   };
-  auto sW = [&](int st) {
-    return reinterpret_cast<const float2*>(base + st * tc_stage_bytes<MODE>() + KC * (TC_SLAB + N * 128));
+  auto w_of = [&](int item, int kc) -> const float* {
+    if (MODE == 1) return W + ((size_t)item * KC + kc) * N * TC_CHUNK;
+    const int s = bmode ? block_site(item >> 2, item & 3, Ls, color) : item;
+    return W + ((size_t)s * KC + kc) * N * TC_CHUNK;
   };
-  auto center = [&](int item) -> int { return bmode ? block_site(item >> 2, item & 3, Ls, color) : item; };
   auto issue = [&](int item, int st) {
     mbar_expect_tx(&tma_bar[st], stage_tx);
-    const float2* w;
-    if (MODE == 1) {
-      const int nbx = Ls / 2, half = nbx / 2, BT = item / half, BX = 2 * (item % half) + ((BT + color) & 1);
-      w = Wc + (size_t)(BT * nbx + BX) * 4096;
-    } else {
-      w = Wc + (size_t)center(item) * 5 * 256;
-    }
-    bulk_load((void*)sW(st), w, CF::WC_BYTES, &tma_bar[st]);
     for (int kc = 0; kc < KC; ++kc) {
-      const int site = (MODE == 1) ? block_site(item, kc, Ls, color) : nbr_site_tc(center(item), kc, Ls);
-      tma_load_2d(sA(st, kc), &amap, site * TC_CHUNK, rhs0, &tma_bar[st]);
+      tma_load_2d(sA(st, kc), &amap, site_of(item, kc) * TC_CHUNK, rhs0, &tma_bar[st]);
+      bulk_load(sB(st, kc), w_of(item, kc), N * 128, &tma_bar[st]);
     }
   };
 
@@ -235,7 +223,7 @@ __global__ void __launch_bounds__(128, 1)
   int n_my = 0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) ++n_my;
   uint32_t tph[2] = {0u, 0u}, mph = 0u;
-  int pending = -1;  // stage with loads in flight not yet completed (thread 0's view)
+  int pending = -1;  // stage with loads in flight not yet waited for (thread 0)
   if (tid == 0 && n_my > 0) {
     issue(blockIdx.x, 0);
     pending = 0;
@@ -249,47 +237,26 @@ __global__ void __launch_bounds__(128, 1)
         pending = 0;
       }
       if (ST == 2 && i + 1 < n_my) issue(item + gridDim.x, st ^ 1);
+      bool ok = mbar_wait(&tma_bar[st], tph[st]);
+      tph[st] ^= 1u;
+      pending = (ST == 2 && i + 1 < n_my) ? (st ^ 1) : -1;
+      if (!ok) {
+        atomicExch(err, 1);
+        s_bad = 1;
+      } else {
+        tc_fence_after();
+        for (int kc = 0; kc < KC; ++kc) {
+          const uint64_t ad = sw128_desc(smem_u32(sA(st, kc)));
+          const uint64_t bd = sw128_desc(smem_u32(sB(st, kc)));
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4)  // K = 8 tf32 = 32 B per instruction
+            mma_tf32(taddr, ad + 2 * k4, bd + 2 * k4, IDESC, (kc | k4) != 0);
+        }
+        mma_commit(&mma_bar);
+      }
     }
-    if (!mbar_wait(&tma_bar[st], tph[st])) {
-      atomicExch(err, 1);
-      s_bad = 1;
-    }
-    tph[st] ^= 1u;
-    if (tid == 0) pending = (ST == 2 && i + 1 < n_my) ? (st ^ 1) : -1;
     __syncthreads();
     if (s_bad) break;
-    // expand the complex weights into the real-embedded swizzled B tiles
-    {
-      const float2* wc = sW(st);
-      if (MODE == 0) {
-        for (int e = tid; e < 5 * 1024; e += blockDim.x) {
-          const int dir = e >> 10, n = (e >> 5) & 31, k = e & 31;
-          const float2 z = wc[dir * 256 + (n >> 1) * 16 + (k >> 1)];
-          const int a = n & 1, b = k & 1;
-          sB(st, dir)[sw_index(n, k)] = (a == b) ? z.x : (a ? z.y : -z.y);
-        }
-      } else {
-        for (int e = tid; e < 4 * 4096; e += blockDim.x) {
-          const int kc = e >> 12, n = (e >> 5) & 127, kk = e & 31, kg = kc * 32 + kk;
-          const float2 z = wc[(n >> 1) * 64 + (kg >> 1)];
-          const int a = n & 1, b = kg & 1;
-          sB(st, kc)[sw_index(n, kk)] = (a == b) ? z.x : (a ? z.y : -z.y);
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-    }
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      for (int kc = 0; kc < KC; ++kc) {
-        const uint64_t ad = sw128_desc(smem_u32(sA(st, kc)));
-        const uint64_t bd = sw128_desc(smem_u32(sB(st, kc)));
-#pragma unroll
-        for (int k4 = 0; k4 < 4; ++k4)  // K = 8 tf32 = 32 B per instruction
-          mma_tf32(taddr, ad + 2 * k4, bd + 2 * k4, IDESC, (kc | k4) != 0);
-      }
-      mma_commit(&mma_bar);
-    }
     if (!mbar_wait(&mma_bar, mph)) {
       atomicExch(err, 2);
       s_bad = 1;
@@ -303,7 +270,7 @@ __global__ void __launch_bounds__(128, 1)
     if (MODE == 0) {
       tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), v);
       if (on) {
-        const int s = center(item);
+        const int s = bmode ? block_site(item >> 2, item & 3, Ls, color) : item;
         float4* o = reinterpret_cast<float4*>(out + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
         if (bvec) {
           const float4* b = reinterpret_cast<const float4*>(bvec + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
@@ -346,6 +313,40 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// real embedding of a complex d x d matrix block into the swizzled K-major B image:
+// element (n, k) of an N x 32 tile sits at n * 32 + (((k >> 2) ^ (n & 7)) << 2) + (k & 3)
+__device__ __forceinline__ int sw_index(int n, int k) { return n * 32 + ((((k >> 2) ^ (n & 7)) << 2) | (k & 3)); }
+
+__global__ void k_tc_stencil_weights(const float2* __restrict__ st, int nsite, float* __restrict__ W) {
+  // st[site][dir][16][16] complex -> W[site][dir][32 x 32] tf32
+  const size_t total = (size_t)nsite * 5 * 32 * 32;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = e % 32, n = (e / 32) % 32;
+    const size_t sd = e / 1024;  // site * 5 + dir
+    const int i = n >> 1, a = n & 1, j = k >> 1, b = k & 1;
+    const float2 z = st[sd * 256 + i * 16 + j];
+    const float v = (a == b) ? z.x : (a == 1 ? z.y : -z.y);
+    W[sd * 1024 + sw_index(n, k)] = v;
+  }
+}
+
+__global__ void k_tc_blockinv_weights(const float2* __restrict__ inv, int Ls, int color, int nblk, float* __restrict__ W) {
+  // colour-`color` blocks only, in their item order: inv[block][64][64] -> W[item][kc 4][128 x 32]
+  const size_t total = (size_t)nblk * 4 * 128 * 32;
+  const int nbx = Ls / 2, half = nbx / 2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int kk = e % 32, n = (e / 32) % 128, kc = (e / 4096) % 4;
+    const int item = (int)(e / 16384);
+    const int BT = item / half, BX = 2 * (item % half) + ((BT + color) & 1);
+    const int blk = BT * nbx + BX;
+    const int kg = kc * 32 + kk;  // real input index 2 * (16 * site_j + dof) + b
+    const int i = n >> 1, a = n & 1, j = kg >> 1, b = kg & 1;
+    const float2 z = inv[(size_t)blk * 4096 + i * 64 + j];
+    const float v = (a == b) ? z.x : (a == 1 ? z.y : -z.y);
+    W[((size_t)item * 4 + kc) * 4096 + sw_index(n, kk)] = v;
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -380,8 +381,8 @@ CUtensorMap make_map(const float2* v, int nsite, int nrhs) {
 }
 
 template <int MODE>
-void launch_tc(cudaStream_t st, const CUtensorMap& m, const float2* Wc, float* out, const float* b, int Ls,
-               int nitems, int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops) {
+void launch_tc(cudaStream_t st, const CUtensorMap& m, const float* W, float* out, const float* b, int Ls, int nitems,
+               int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops) {
   static bool attr = false;
   const int sm = tc_smem_bytes<MODE>();
   if (!attr) {
@@ -394,38 +395,49 @@ void launch_tc(cudaStream_t st, const CUtensorMap& m, const float2* Wc, float* o
   const int tiles = (nrhs + TC_M - 1) / TC_M;
   const int gx = std::max(1, std::min(nitems, (nsm + tiles - 1) / tiles));
   dim3 grid(gx, tiles);
-  MG_LAUNCH_W(bytes, flops, k_tc<MODE>, grid, 128, sm, st, m, Wc, out, b, Ls, nitems, bmode, color, nrhs,
+  MG_LAUNCH_W(bytes, flops, k_tc<MODE>, grid, 128, sm, st, m, W, out, b, Ls, nitems, bmode, color, nrhs,
               box_rows(nrhs), active, err);
 }
 
 }  // namespace
 
-void tc_stencil_apply(cudaStream_t st, const float2* Wc, int Ls, const float2* x, float2* y, const float2* b,
-                      int nrhs, const int* active, int* err) {
+size_t tc_stencil_weight_floats(int nsite) { return (size_t)nsite * 5 * 1024; }
+size_t tc_blockinv_weight_floats(int Ls) { return (size_t)(Ls / 2) * (Ls / 2) / 2 * 4 * 4096; }
+
+void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, float* W) {
+  MG_LAUNCH(k_tc_stencil_weights, 1024, 256, 0, st, st32, nsite, W);
+}
+void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color, float* W) {
+  const int nblk = (Ls / 2) * (Ls / 2) / 2;
+  MG_LAUNCH(k_tc_blockinv_weights, 1024, 256, 0, st, inv32, Ls, color, nblk, W);
+}
+
+void tc_stencil_apply(cudaStream_t st, const float* W, int Ls, const float2* x, float2* y, const float2* b, int nrhs,
+                      const int* active, int* err) {
   if (nrhs <= 0) return;
   const int ns = Ls * Ls;
   CUtensorMap m = make_map(x, ns, nrhs);
   const double ar = act_rhs(nrhs);
-  const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + ns * 5.0 * 2048;
-  const double flops = ar * ns * 8.0 * 5 * 256;
-  launch_tc<0>(st, m, Wc, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
+  const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + ns * 5.0 * 4096;
+  const double flops = ar * ns * 2.0 * 32 * 160;
+  launch_tc<0>(st, m, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
 }
 
-void tc_sap_half(cudaStream_t st, const float2* Wst, const float2* Winv, int Ls, const float2* f, float2* x,
+void tc_sap_half(cudaStream_t st, const float* Wst, const float* Winv, int Ls, const float2* f, float2* x,
                  float2* res, int color, int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
   const int ns = Ls * Ls, nblk = ns / 8;
   const double ar = act_rhs(nrhs);
   {  // residual on the sites of the colour's blocks
     CUtensorMap m = make_map(x, ns, nrhs);
-    const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 2048;
-    const double flops = ar * (ns / 2) * 8.0 * 5 * 256;
+    const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 4096;
+    const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
     launch_tc<0>(st, m, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes, flops);
   }
   {  // x_B += inv_B r_B
     CUtensorMap m = make_map(res, ns, nrhs);
-    const double bytes = ar * (ns / 2) * 128.0 * 3 + nblk * 32768.0;
-    const double flops = ar * nblk * 8.0 * 64 * 64;
+    const double bytes = ar * (ns / 2) * 128.0 * 3 + nblk * 65536.0;
+    const double flops = ar * nblk * 2.0 * 128 * 128;
     launch_tc<1>(st, m, Winv, (float*)x, nullptr, Ls, nblk, 0, color, nrhs, active, err, bytes, flops);
   }
 }
