@@ -18,9 +18,11 @@
 // stored.  Weights are stored pre-swizzled and fetched with one bulk copy per
 // chunk.  One thread issues the MMAs (M = 128, K = 8 per instruction) into a
 // TMEM accumulator; four warps read it back with tcgen05.ld (row = rhs =
-// lane) for the epilogue.  Every wait on an mbarrier is bounded: on expiry the
-// kernel records an error code, stops, waits (bounded) for its own copies and
-// frees its TMEM.
+// lane) for the epilogue.  Warp-specialised: a producer warp streams items
+// through S shared-memory stages, one thread issues the MMAs into two
+// alternating TMEM accumulators, four epilogue warps drain them.  Every wait on
+// an mbarrier is bounded: on expiry the kernel records an error code, stops,
+// waits (bounded) for its own copies and frees its TMEM.
 #include <cuda.h>
 
 #include "ops.cuh"
@@ -30,7 +32,6 @@ namespace {
 
 constexpr int TC_M = 128;          // rhs per tile (MMA M)
 constexpr int TC_CHUNK = 32;       // floats per site slab (16 complex)
-constexpr int TC_SLAB = TC_M * TC_CHUNK * 4;  // bytes of one A chunk (16 KB)
 constexpr long TC_SPIN = 1L << 26; // bounded waits: poll count ...
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // ... and wall time (2 s)
 
@@ -137,81 +138,81 @@ __device__ __forceinline__ int block_site(int k, int j, int Ls, int color) {
   return (2 * BT + (j >> 1)) * Ls + 2 * BX + (j & 1);
 }
 
-// MODE 0: KC = 5, N = 32, two pipeline stages.  MODE 1: KC = 4, N = 128, one stage.
+// MODE 0: KC = 5 site slabs, N = 32.   MODE 1: KC = 4 site slabs, N = 128.
 template <int MODE>
 struct TcCfg;
 template <>
 struct TcCfg<0> {
-  static constexpr int KC = 5, N = 32, STAGES = 2, NCOL = 32;
+  static constexpr int KC = 5, N = 32;
 };
 template <>
 struct TcCfg<1> {
-  static constexpr int KC = 4, N = 128, STAGES = 1, NCOL = 128;
+  static constexpr int KC = 4, N = 128;
 };
-template <int MODE>
-constexpr int tc_stage_bytes() {
-  return TcCfg<MODE>::KC * (TC_SLAB + TcCfg<MODE>::N * 128);
-}
-template <int MODE>
-constexpr int tc_smem_bytes() {
-  return TcCfg<MODE>::STAGES * tc_stage_bytes<MODE>() + 1024 /* alignment slack */ + 64;
-}
+constexpr int TC_MAX_STAGES = 8;
+constexpr int TC_THREADS = 192;  // warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 epilogue
+
+// bytes of one pipeline stage: KC A slabs of `rows` rhs rows, then KC B tiles of N rows (128 B each).
+// The MMA reads 128 A rows; rows past `rows` land in the next slab or the stage's B tiles (never outside
+// the stage) and only feed accumulator rows that are never stored.
+__host__ __device__ constexpr int tc_stage_bytes(int KC, int N, int rows) { return KC * (rows + N) * 128; }
 
 // items: MODE 0 with bmode = 0: every site; bmode = 1: the 4 sites of every colour-`color` 2x2 block.
 //        MODE 1: every colour-`color` 2x2 block.
+// Warp-specialised pipeline: the producer keeps up to `stages` items in flight in shared memory (full/empty
+// mbarriers), the MMA warp alternates between two TMEM accumulators (tmem_full/tmem_empty mbarriers), the
+// four epilogue warps drain one accumulator while the next item is multiplied.
 template <int MODE>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc(const __grid_constant__ CUtensorMap amap, const float* __restrict__ W, float* __restrict__ out,
-         const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int rows,
+         const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int rows, int stages,
          const int* __restrict__ active, int* err) {
   typedef TcCfg<MODE> CF;
-  constexpr int KC = CF::KC, N = CF::N, ST = CF::STAGES;
+  constexpr int KC = CF::KC, N = CF::N, NCOL = 2 * N < 32 ? 32 : 2 * N;
   constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t tma_bar[2];
-  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t full_bar[TC_MAX_STAGES], empty_bar[TC_MAX_STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
   __shared__ uint32_t s_taddr;
-  __shared__ int s_bad;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ int s_skip;
+  __shared__ volatile int s_bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) s_skip = *(volatile int*)err;  // an earlier launch gave up: do nothing until the host sees it
   __syncthreads();
   if (s_skip) return;
   const int rhs0 = blockIdx.y * TC_M;
   const long ncf = (long)Ls * Ls * TC_CHUNK;  // floats per rhs row
-  const uint32_t stage_tx = (uint32_t)(KC * (rows * 128 + N * 128));
-  auto sA = [&](int st, int kc) { return base + st * tc_stage_bytes<MODE>() + kc * TC_SLAB; };
-  auto sB = [&](int st, int kc) { return base + st * tc_stage_bytes<MODE>() + KC * TC_SLAB + kc * N * 128; };
+  const int sbytes = tc_stage_bytes(KC, N, rows);
+  const uint32_t stage_tx = (uint32_t)sbytes;
+  auto sA = [&](int st, int kc) { return base + st * sbytes + kc * rows * 128; };
+  auto sB = [&](int st, int kc) { return base + st * sbytes + KC * rows * 128 + kc * N * 128; };
+  auto center = [&](int item) -> int { return bmode ? block_site(item >> 2, item & 3, Ls, color) : item; };
   auto site_of = [&](int item, int kc) -> int {
     if (MODE == 1) return block_site(item, kc, Ls, color);
-    const int s = bmode ? block_site(item >> 2, item & 3, Ls, color) : item;
-    return nbr_site_tc(s, kc, Ls);
+    return nbr_site_tc(center(item), kc, Ls);
   };
   auto w_of = [&](int item, int kc) -> const float* {
     if (MODE == 1) return W + ((size_t)item * KC + kc) * N * TC_CHUNK;
-    const int s = bmode ? block_site(item >> 2, item & 3, Ls, color) : item;
-    return W + ((size_t)s * KC + kc) * N * TC_CHUNK;
-  };
-  auto issue = [&](int item, int st) {
-    mbar_expect_tx(&tma_bar[st], stage_tx);
-    for (int kc = 0; kc < KC; ++kc) {
-      tma_load_2d(sA(st, kc), &amap, site_of(item, kc) * TC_CHUNK, rhs0, &tma_bar[st]);
-      bulk_load(sB(st, kc), w_of(item, kc), N * 128, &tma_bar[st]);
-    }
+    return W + ((size_t)center(item) * KC + kc) * N * TC_CHUNK;
   };
 
   if (tid == 0) {
-    mbar_init(&tma_bar[0], 1);
-    mbar_init(&tma_bar[1], 1);
-    mbar_init(&mma_bar, 1);
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull_bar[a], 1);
+      mbar_init(&tempty_bar[a], 4);
+    }
     s_bad = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
-                 "r"((uint32_t)CF::NCOL)
+                 "r"((uint32_t)NCOL)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -219,96 +220,110 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = s_taddr;
-
   int n_my = 0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) ++n_my;
-  uint32_t tph[2] = {0u, 0u}, mph = 0u;
-  int pending = -1;  // stage with loads in flight not yet waited for (thread 0)
-  if (tid == 0 && n_my > 0) {
-    issue(blockIdx.x, 0);
-    pending = 0;
-  }
-  for (int i = 0; i < n_my; ++i) {
-    const int item = blockIdx.x + i * gridDim.x;
-    const int st = (ST == 2) ? (i & 1) : 0;
-    if (tid == 0) {
-      if (ST == 1 && i > 0) {  // one stage: this item's loads start once the previous item is done
-        issue(item, 0);
-        pending = 0;
-      }
-      if (ST == 2 && i + 1 < n_my) issue(item + gridDim.x, st ^ 1);
-      bool ok = mbar_wait(&tma_bar[st], tph[st]);
-      tph[st] ^= 1u;
-      pending = (ST == 2 && i + 1 < n_my) ? (st ^ 1) : -1;
-      if (!ok) {
-        atomicExch(err, 1);
-        s_bad = 1;
-      } else {
-        tc_fence_after();
+
+  if (warp == 0) {
+    // ---------------- producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < n_my && !s_bad; ++i) {
+        const int s = i % stages;
+        if (i >= stages && !mbar_wait(&empty_bar[s], (uint32_t)((i / stages) - 1) & 1u)) {
+          atomicExch(err, 1);
+          s_bad = 1;
+          break;
+        }
+        const int item = blockIdx.x + i * gridDim.x;
+        mbar_expect_tx(&full_bar[s], stage_tx);
         for (int kc = 0; kc < KC; ++kc) {
-          const uint64_t ad = sw128_desc(smem_u32(sA(st, kc)));
-          const uint64_t bd = sw128_desc(smem_u32(sB(st, kc)));
+          tma_load_2d(sA(s, kc), &amap, site_of(item, kc) * TC_CHUNK, rhs0, &full_bar[s]);
+          bulk_load(sB(s, kc), w_of(item, kc), N * 128, &full_bar[s]);
+        }
+        issued = i + 1;
+      }
+      // let the last loads land before the CTA can exit (bounded)
+      for (int i = std::max(0, issued - stages); i < issued; ++i)
+        mbar_wait(&full_bar[i % stages], (uint32_t)(i / stages) & 1u);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      for (int i = 0; i < n_my && !s_bad; ++i) {
+        const int s = i % stages, a = i & 1;
+        if (!mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1u)) {
+          atomicExch(err, 2);
+          s_bad = 1;
+          break;
+        }
+        if (i >= 2 && !mbar_wait(&tempty_bar[a], (uint32_t)((i >> 1) - 1) & 1u)) {
+          atomicExch(err, 3);
+          s_bad = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = taddr + (uint32_t)(a * N);
+        for (int kc = 0; kc < KC; ++kc) {
+          const uint64_t ad = sw128_desc(smem_u32(sA(s, kc)));
+          const uint64_t bd = sw128_desc(smem_u32(sB(s, kc)));
 #pragma unroll
           for (int k4 = 0; k4 < 4; ++k4)  // K = 8 tf32 = 32 B per instruction
-            mma_tf32(taddr, ad + 2 * k4, bd + 2 * k4, IDESC, (kc | k4) != 0);
+            mma_tf32(d, ad + 2 * k4, bd + 2 * k4, IDESC, (kc | k4) != 0);
         }
-        mma_commit(&mma_bar);
+        mma_commit(&empty_bar[s]);  // smem stage free once these MMAs completed
+        mma_commit(&tfull_bar[a]);  // accumulator a ready for the epilogue
       }
     }
-    __syncthreads();
-    if (s_bad) break;
-    if (!mbar_wait(&mma_bar, mph)) {
-      atomicExch(err, 2);
-      s_bad = 1;
-    }
-    mph ^= 1u;
-    tc_fence_after();
-    const int row = warp * 32 + lane;
+  } else {
+    // ---------------- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
     const int rhs = rhs0 + row;
-    const bool on = !s_bad && rhs < nrhs && !(active && !active[rhs]);
-    float v[32];
-    if (MODE == 0) {
-      tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), v);
-      if (on) {
-        const int s = bmode ? block_site(item >> 2, item & 3, Ls, color) : item;
-        float4* o = reinterpret_cast<float4*>(out + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
-        if (bvec) {
-          const float4* b = reinterpret_cast<const float4*>(bvec + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float4 bb = b[q];
-            o[q] = make_float4(bb.x - v[4 * q], bb.y - v[4 * q + 1], bb.z - v[4 * q + 2], bb.w - v[4 * q + 3]);
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        }
+    const bool live = rhs < nrhs && !(active && !active[rhs]);
+    for (int i = 0; i < n_my; ++i) {
+      const int a = i & 1;
+      if (s_bad || !mbar_wait(&tfull_bar[a], (uint32_t)(i >> 1) & 1u)) {
+        if (!s_bad) atomicExch(err, 4);
+        s_bad = 1;
+        break;
       }
-    } else {
+      tc_fence_after();
+      const int item = blockIdx.x + i * gridDim.x;
+      float v[32];
 #pragma unroll 1
-      for (int j = 0; j < 4; ++j) {
-        tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * j), v);
-        if (on) {
-          const int s = block_site(item, j, Ls, color);
+      for (int j = 0; j < N / 32; ++j) {
+        tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * N + 32 * j), v);
+        if (live) {
+          const int s = (MODE == 1) ? block_site(item, j, Ls, color) : center(item);
           float4* o = reinterpret_cast<float4*>(out + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
+          if (MODE == 1) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float4 a = o[q];
-            o[q] = make_float4(a.x + v[4 * q], a.y + v[4 * q + 1], a.z + v[4 * q + 2], a.w + v[4 * q + 3]);
+            for (int u = 0; u < 8; ++u) {
+              float4 x = o[u];
+              o[u] = make_float4(x.x + v[4 * u], x.y + v[4 * u + 1], x.z + v[4 * u + 2], x.w + v[4 * u + 3]);
+            }
+          } else if (bvec) {
+            const float4* bb = reinterpret_cast<const float4*>(bvec + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              float4 x = bb[u];
+              o[u] = make_float4(x.x - v[4 * u], x.y - v[4 * u + 1], x.z - v[4 * u + 2], x.w - v[4 * u + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) o[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[a])) : "memory");
     }
-    tc_fence_before();
-    __syncthreads();
-    if (s_bad) break;
   }
-  // on an early stop, wait (bounded) for this CTA's copies still in flight
-  if (tid == 0 && pending >= 0) mbar_wait(&tma_bar[pending], tph[pending]);
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"((uint32_t)CF::NCOL)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"((uint32_t)NCOL)
                  : "memory");
   }
 }
@@ -383,20 +398,25 @@ CUtensorMap make_map(const float2* v, int nsite, int nrhs) {
 template <int MODE>
 void launch_tc(cudaStream_t st, const CUtensorMap& m, const float* W, float* out, const float* b, int Ls, int nitems,
                int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops) {
+  typedef TcCfg<MODE> CF;
+  constexpr int SMEM_BUDGET = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
   static bool attr = false;
-  const int sm = tc_smem_bytes<MODE>();
   if (!attr) {
-    MG_CUDA(cudaFuncSetAttribute(k_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    MG_CUDA(cudaFuncSetAttribute(k_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET));
     attr = true;
   }
+  const int rows = box_rows(nrhs);
+  const int sbytes = tc_stage_bytes(CF::KC, CF::N, rows);
+  const int stages = std::max(1, std::min(TC_MAX_STAGES, (SMEM_BUDGET - 1024) / sbytes));
+  const int sm = stages * sbytes + 1024;
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int tiles = (nrhs + TC_M - 1) / TC_M;
   const int gx = std::max(1, std::min(nitems, (nsm + tiles - 1) / tiles));
   dim3 grid(gx, tiles);
-  MG_LAUNCH_W(bytes, flops, k_tc<MODE>, grid, 128, sm, st, m, W, out, b, Ls, nitems, bmode, color, nrhs,
-              box_rows(nrhs), active, err);
+  MG_LAUNCH_W(bytes, flops, k_tc<MODE>, grid, TC_THREADS, sm, st, m, W, out, b, Ls, nitems, bmode, color, nrhs, rows,
+              stages, active, err);
 }
 
 }  // namespace
