@@ -138,6 +138,8 @@ typedef struct {
   double kcycle_tol;     /* relative residual at which a K-cycle stops early (0.1) */
   int tensor_cores;      /* 1: inside the FP32 V-cycle, coarse levels with 16 dof per site run their
                             SAP sweeps and residuals as TF32 tcgen05 GEMMs over the rhs (1) */
+  int graphs;            /* 1: the V-cycle preconditioner is captured once per shape as a CUDA graph
+                            and replayed (not while the kernel timer runs or with K-cycles) (1) */
 } mg_params;
 
 int mg_params_default(mg_params* p);

@@ -25,7 +25,7 @@ class MgParams(C.Structure):
                 ("sap_block_coarse", C.c_int), ("setup_sweeps", C.c_int), ("pre_smooth", C.c_int),
                 ("post_smooth", C.c_int), ("seed", C.c_uint64), ("bootstrap", C.c_int),
                 ("bootstrap_its", C.c_int), ("kcycle_its", C.c_int), ("kcycle_tol", C.c_double),
-                ("tensor_cores", C.c_int)]
+                ("tensor_cores", C.c_int), ("graphs", C.c_int)]
 
 
 class SolveParams(C.Structure):

@@ -161,6 +161,7 @@ int mg_params_default(mg_params* p) {
   p->kcycle_its = 0;
   p->kcycle_tol = 0.1;
   p->tensor_cores = 1;
+  p->graphs = 1;
   return MGMLMC_OK;
 }
 

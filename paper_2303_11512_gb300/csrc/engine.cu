@@ -229,6 +229,73 @@ __global__ void k_gm_trisolve(int m, int nrhs, const double2* __restrict__ H, co
   }
 }
 
+// The V-cycle as a CUDA graph: a fixed launch sequence for a given (level, precision, nrhs, mask), captured
+// once on fixed input/output buffers after an eager warm-up pass has allocated every workspace it touches,
+// then replayed between two vector copies.  Not used while the per-kernel timer runs or with K-cycles
+// (their host decisions cannot be captured); a graph is re-captured whenever a buffer it refers to changed.
+template <typename R>
+static void vcycle_maybe_graph(mgmlmc_hier* h, int l, const typename CT<R>::T* in_vec, typename CT<R>::T* out_vec,
+                               int nrhs, const int* active) {
+  typedef typename CT<R>::T C;
+  if (!h->prm.graphs || g_timer || h->prm.kcycle_its > 0 || l == h->nlev - 1) {
+    vcycle<R>(h, l, in_vec, out_vec, nrhs, active);
+    return;
+  }
+  cudaStream_t st = h->ctx->stream;
+  const long n = h->lv[l].n;
+  const size_t bytes = sizeof(C) * n * nrhs;
+  const bool dp = sizeof(R) == 8;
+  C* gin = (C*)h->work(dp ? "vg_in64" : "vg_in32", l, bytes);
+  C* gout = (C*)h->work(dp ? "vg_out64" : "vg_out32", l, bytes);
+  auto& g = h->vgraphs[std::make_tuple(l, (int)sizeof(R), nrhs, (const void*)active)];
+  if (g.exec && (g.gen != h->gen || g.in != gin || g.out != gout)) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.uses = 0;
+  }
+  if (!g.exec && g.uses == 0) {  // eager warm-up: allocates the workspaces of this shape
+    vcycle<R>(h, l, in_vec, out_vec, nrhs, active);
+    g.uses = 1;
+    return;
+  }
+  if (!g.exec) {
+    const uint64_t gen0 = h->gen;
+    const int64_t before = g_launch_counter ? *g_launch_counter : 0;
+    cudaGraph_t graph = nullptr;
+    MG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    try {
+      vcycle<R>(h, l, gin, gout, nrhs, active);
+    } catch (...) {
+      h->capturing = false;
+      cudaStreamEndCapture(st, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      throw;
+    }
+    h->capturing = false;
+    MG_CUDA(cudaStreamEndCapture(st, &graph));
+    const int64_t captured = g_launch_counter ? *g_launch_counter - before : 0;
+    if (g_launch_counter) *g_launch_counter = before;  // capturing issued nothing
+    if (h->gen != gen0) {
+      cudaGraphDestroy(graph);
+      vcycle<R>(h, l, in_vec, out_vec, nrhs, active);
+      return;
+    }
+    MG_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
+    cudaGraphDestroy(graph);
+    g.gen = h->gen;
+    g.in = gin;
+    g.out = gout;
+    g.launches = captured;
+  }
+  MG_CUDA(cudaMemcpyAsync(gin, in_vec, bytes, cudaMemcpyDeviceToDevice, st));
+  MG_CUDA(cudaGraphLaunch(g.exec, st));
+  MG_CUDA(cudaMemcpyAsync(out_vec, gout, bytes, cudaMemcpyDeviceToDevice, st));
+  if (g_launch_counter) *g_launch_counter += g.launches;
+  ++g.uses;
+}
+
 template <typename R>
 struct GmState {
   typedef typename CT<R>::T C;
@@ -309,7 +376,7 @@ void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<
       C* Vj1 = s.V + (size_t)(j + 1) * vs;
       C* Zj = s.Z + (size_t)j * vs;
       if (precond)
-        vcycle<R>(h, l, Vj, Zj, nrhs, s.iact);
+        vcycle_maybe_graph<R>(h, l, Vj, Zj, nrhs, s.iact);
       else
         vcopy<C>(st, Vj, Zj, n, nrhs);
       op_apply<R>(h, l, Zj, Vj1, nullptr, nrhs, s.iact);

@@ -58,11 +58,35 @@ struct mgmlmc_hier {
   bool use_tc(int l) const {
     return prm.tensor_cores && l >= 1 && l < nlev && lv[l].dof == 16 && lv[l].tcW.p != nullptr;
   }
+  // generation of device buffers: bumped whenever a workspace is (re)allocated or the hierarchy is
+  // rebuilt, so captured CUDA graphs that hold old pointers are never replayed
+  uint64_t gen = 0;
+  bool capturing = false;
   void* work(const std::string& tag, int level, size_t bytes) {
     auto& b = ws[std::make_tuple(tag, level)];
-    b.ensure(bytes, stream);
+    if (bytes > b.bytes) {
+      if (capturing) throw mg::Error(MGMLMC_ERR_INVALID_ARG, "workspace growth during graph capture");
+      b.alloc(bytes, stream);
+      ++gen;
+    }
     return b.p;
   }
+  // captured V-cycles: key (level, precision, nrhs, active mask) -> executable graph on fixed in/out buffers
+  struct VGraph {
+    cudaGraphExec_t exec = nullptr;
+    void* in = nullptr;
+    void* out = nullptr;
+    uint64_t gen = 0;
+    int64_t launches = 0;  // kernels per replay
+    int uses = 0;
+  };
+  std::map<std::tuple<int, int, int, const void*>, VGraph> vgraphs;
+  void drop_graphs() {
+    for (auto& kv : vgraphs)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    vgraphs.clear();
+  }
+  ~mgmlmc_hier() { drop_graphs(); }
 };
 
 struct mgmlmc_sketch {

@@ -100,6 +100,7 @@ static void build_from_tv(mgmlmc_hier* h, int l, int* dfail) {
     build_sap(h, l + 1, dfail + 0);
   else
     build_coarsest(h, dfail + 2);
+  ++h->gen;  // operators changed: captured V-cycles must be rebuilt
 }
 
 static void check_fail(mgmlmc_hier* h, const int* dfail) {
