@@ -262,19 +262,24 @@ static void vcycle_maybe_graph(mgmlmc_hier* h, int l, const typename CT<R>::T* i
     const uint64_t gen0 = h->gen;
     const int64_t before = g_launch_counter ? *g_launch_counter : 0;
     cudaGraph_t graph = nullptr;
-    MG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    if (!h->capture_stream) MG_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = h->capture_stream;
+    MG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     h->capturing = true;
+    h->ctx->stream = cs;  // the V-cycle's launches go to the capturing stream
     try {
       vcycle<R>(h, l, gin, gout, nrhs, active);
     } catch (...) {
+      h->ctx->stream = st;
       h->capturing = false;
-      cudaStreamEndCapture(st, &graph);
+      cudaStreamEndCapture(cs, &graph);
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
       throw;
     }
+    h->ctx->stream = st;
     h->capturing = false;
-    MG_CUDA(cudaStreamEndCapture(st, &graph));
+    MG_CUDA(cudaStreamEndCapture(cs, &graph));
     const int64_t captured = g_launch_counter ? *g_launch_counter - before : 0;
     if (g_launch_counter) *g_launch_counter = before;  // capturing issued nothing
     if (h->gen != gen0) {

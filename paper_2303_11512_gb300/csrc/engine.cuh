@@ -81,12 +81,16 @@ struct mgmlmc_hier {
     int uses = 0;
   };
   std::map<std::tuple<int, int, int, const void*>, VGraph> vgraphs;
+  cudaStream_t capture_stream = nullptr;  // private stream to capture on (the legacy stream cannot be captured)
   void drop_graphs() {
     for (auto& kv : vgraphs)
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     vgraphs.clear();
   }
-  ~mgmlmc_hier() { drop_graphs(); }
+  ~mgmlmc_hier() {
+    drop_graphs();
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+  }
 };
 
 struct mgmlmc_sketch {
