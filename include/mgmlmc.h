@@ -194,7 +194,8 @@ typedef struct {
   int m;             /* FGMRES restart length (16) */
   double tol;        /* stop at true relative residual ||b - D x|| / ||b|| <= tol, per rhs (1e-10) */
   int maxit;         /* total inner iteration limit per solve (2000) */
-  int precond;       /* 1 = V-cycle preconditioner, 0 = none (GMRES) */
+  int precond;       /* 1 = V-cycle preconditioner, 0 = none (GMRES), 2 = V-cycle + learned correction
+                        on the fine level (FP32 inner solves; needs mg_attach_nn) */
   int prec;          /* mgmlmc_prec */
   double inner_tol;  /* MIXED: relative reduction of each FP32 inner solve (1e-5; FP32 arithmetic floors near 1e-6) */
 } solve_params;
@@ -272,6 +273,35 @@ int hutchpp_project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double* zeta,
  * launch fails, MGMLMC_OK otherwise (nrhs == 0 is a no-op). */
 int hutchpp_project_noalloc(void* stream, const double* Q, int d, const double* zeta, const double* y,
                             int64_t n, int nrhs, double* tau_out);
+
+/* ---- learned preconditioner (library extension; the paper has no learned part) ---- */
+
+/* A gauge-covariant convolutional network M ~ D^{-1} used as a correction after
+ * the V-cycle inside FGMRES (solve_params.precond = 2):  z = V(v);  z += M(v - D z).
+ * Layer l:  z_k(x) = sum_d sum_c W[d][k][c] T_d(x) a_c(x + d)  over the 9 offsets
+ * d = 3 (dt+1) + (dx+1) of the 3x3 neighbourhood, T_d(x) the parallel transporter
+ * from x + d to x (links with the antiperiodic sign on time-boundary crossings,
+ * diagonals the average of the two L-shaped paths); hidden layers apply
+ * z max(0, |z| + b_k)/|z|, the last is linear.  Channels 2 -> C -> ... -> 2;
+ * weights complex, used rounded to bfloat16, FP32 accumulation and FP32 master
+ * weights; loss (1/nrhs) sum ||M(r) - e||^2 / ||e||^2 on (residual, error) pairs.
+ * Flat parameter layout (floats): per layer W (9 * c_out * c_in complex,
+ * index (d * c_out + k) * c_in + c, re/im interleaved), then b (c_out) for
+ * hidden layers.  Fields: device complex64 [nrhs][site][2]. */
+typedef struct mgmlmc_nn mgmlmc_nn;
+int nn_create(mgmlmc_ctx* ctx, const double* U, int L, int layers, int channels, uint64_t seed, mgmlmc_nn** out);
+void nn_destroy(mgmlmc_nn* nn);
+int64_t nn_num_params(const mgmlmc_nn* nn);
+int nn_set_params(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const float* host_params);
+int nn_get_params(mgmlmc_ctx* ctx, const mgmlmc_nn* nn, float* host_params);
+int nn_forward(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, void* y, int nrhs);
+/* loss, and (host_grad != NULL) its gradient w.r.t. the bf16-rounded weights and the biases, flat layout */
+int nn_loss_grad(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, const void* e, int nrhs, double* loss,
+                 float* host_grad);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on the loss of (r, e); *loss = loss before the step */
+int nn_train_step(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, const void* e, int nrhs, double lr, double* loss);
+/* use nn in the fine-level preconditioner of h (precond = 2); NULL detaches. nn must outlive the attachment. */
+int mg_attach_nn(mgmlmc_ctx* ctx, mgmlmc_hier* h, mgmlmc_nn* nn);
 
 /* ---- Algorithm 2 end to end --------------------------------------------- */
 

@@ -92,6 +92,15 @@ SIGNATURES = {
     "hutchpp_sketch_get_q": (ip, [vp, vp, vp, C.POINTER(ip), C.POINTER(C.c_int64)]),
     "hutchpp_project": (ip, [vp, vp, vp, vp, C.c_int64, ip, dp]),
     "hutchpp_project_noalloc": (ip, [vp, vp, ip, vp, vp, C.c_int64, ip, vp]),
+    "nn_create": (ip, [vp, vp, ip, ip, ip, C.c_uint64, C.POINTER(vp)]),
+    "nn_destroy": (None, [vp]),
+    "nn_num_params": (C.c_int64, [vp]),
+    "nn_set_params": (ip, [vp, vp, vp]),
+    "nn_get_params": (ip, [vp, vp, vp]),
+    "nn_forward": (ip, [vp, vp, vp, vp, ip]),
+    "nn_loss_grad": (ip, [vp, vp, vp, vp, ip, dp, vp]),
+    "nn_train_step": (ip, [vp, vp, vp, vp, ip, C.c_double, dp]),
+    "mg_attach_nn": (ip, [vp, vp, vp]),
     "est_params_default": (ip, [C.POINTER(EstParams)]),
     "trace_estimate": (ip, [vp, vp, C.POINTER(EstParams), C.POINTER(EstResult)]),
     "mlmc_update_active": (ip, [ip, C.POINTER(ip), dp, C.POINTER(C.c_int64), dp, C.c_double, C.c_double, ip, ip]),

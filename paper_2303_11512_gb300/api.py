@@ -274,6 +274,87 @@ def hutchpp_project(ctx: Context, sketch: Sketch | None, zeta: torch.Tensor, y: 
     return out
 
 
+class Net:
+    """Learned gauge-covariant correction M ~ D^{-1} (see include/mgmlmc.h, nn_*)."""
+
+    def __init__(self, ctx: Context, U: torch.Tensor, L: int, layers: int = 4, channels: int = 16, seed: int = 0):
+        self.ctx, self.L = ctx, L
+        h = C.c_void_p()
+        check(_lib.load().nn_create(ctx.ptr, _ptr(U, torch.complex128), L, layers, channels, seed, C.byref(h)),
+              ctx.ptr)
+        self.ptr = h
+        self.nparams = int(_lib.load().nn_num_params(h))
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparams
+        check(_lib.load().nn_set_params(self.ctx.ptr, self.ptr, p.ctypes.data), self.ctx.ptr)
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.nparams, dtype=np.float32)
+        check(_lib.load().nn_get_params(self.ctx.ptr, self.ptr, p.ctypes.data), self.ctx.ptr)
+        return p
+
+    def forward(self, r: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+        y = torch.empty_like(r) if y is None else y
+        check(_lib.load().nn_forward(self.ctx.ptr, self.ptr, _ptr(r, torch.complex64), _ptr(y, torch.complex64),
+                                     r.shape[0]), self.ctx.ptr)
+        return y
+
+    def loss_grad(self, r: torch.Tensor, e: torch.Tensor):
+        loss = C.c_double()
+        g = np.empty(self.nparams, dtype=np.float32)
+        check(_lib.load().nn_loss_grad(self.ctx.ptr, self.ptr, _ptr(r, torch.complex64), _ptr(e, torch.complex64),
+                                       r.shape[0], C.byref(loss), g.ctypes.data), self.ctx.ptr)
+        return loss.value, g
+
+    def train_step(self, r: torch.Tensor, e: torch.Tensor, lr: float = 1e-3) -> float:
+        loss = C.c_double()
+        check(_lib.load().nn_train_step(self.ctx.ptr, self.ptr, _ptr(r, torch.complex64), _ptr(e, torch.complex64),
+                                        r.shape[0], lr, C.byref(loss)), self.ctx.ptr)
+        return loss.value
+
+    def attach(self, h: "Hierarchy"):
+        check(_lib.load().mg_attach_nn(self.ctx.ptr, h.ptr, self.ptr), self.ctx.ptr)
+
+    def close(self):
+        if self.ptr:
+            _lib.load().nn_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_params(W, b) -> np.ndarray:
+    """Flat float32 parameter vector from per-layer complex W[9][c_out][c_in] and real biases."""
+    out = []
+    for l, w in enumerate(W):
+        w = np.asarray(w, complex)
+        out.append(np.stack([w.real, w.imag], axis=-1).ravel())
+        if l < len(W) - 1:
+            out.append(np.asarray(b[l], float).ravel())
+    return np.concatenate(out).astype(np.float32)
+
+
+def unpack_params(p: np.ndarray, layers: int, channels: int):
+    dims = [2] + [channels] * (layers - 1) + [2]
+    W, b, o = [], [], 0
+    for l in range(layers):
+        ci, co = dims[l], dims[l + 1]
+        cnt = 9 * co * ci
+        w = p[o:o + 2 * cnt].reshape(9, co, ci, 2)
+        W.append(w[..., 0] + 1j * w[..., 1])
+        o += 2 * cnt
+        if l < layers - 1:
+            b.append(p[o:o + co].copy())
+            o += co
+    return W, b
+
+
 def hutchpp_project_noalloc(Q: torch.Tensor | None, zeta: torch.Tensor, y: torch.Tensor,
                             tau_out: torch.Tensor, stream: torch.cuda.Stream | None = None):
     """Projected samples into the device tensor `tau_out` ([nrhs] complex128) without any

@@ -468,6 +468,90 @@ int trace_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const est_params* p, est_res
   });
 }
 
+}  // extern "C"
+
+struct mgmlmc_nn {
+  mg::NNet net;
+};
+
+extern "C" {
+
+int nn_create(mgmlmc_ctx* ctx, const double* U, int L, int layers, int channels, uint64_t seed, mgmlmc_nn** out) {
+  if (out) *out = nullptr;
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(U && out, "null pointer");
+    std::unique_ptr<mgmlmc_nn> nn(new mgmlmc_nn);
+    nn_init(&nn->net, (const double2*)U, L, layers, channels, seed, ctx->stream);
+    *out = nn.release();
+  });
+}
+
+void nn_destroy(mgmlmc_nn* nn) {
+  if (!nn) return;
+  cudaStreamSynchronize(nn->net.st);
+  delete nn;
+}
+
+int64_t nn_num_params(const mgmlmc_nn* nn) { return nn ? (int64_t)nn->net.nparams : MGMLMC_ERR_INVALID_ARG; }
+
+int nn_set_params(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const float* host) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(nn && host, "null pointer");
+    MG_CUDA(cudaMemcpyAsync(nn->net.params.p, host, sizeof(float) * nn->net.nparams, cudaMemcpyHostToDevice,
+                            ctx->stream));
+    MG_CUDA(cudaMemsetAsync(nn->net.m.p, 0, sizeof(float) * nn->net.nparams, ctx->stream));
+    MG_CUDA(cudaMemsetAsync(nn->net.v.p, 0, sizeof(float) * nn->net.nparams, ctx->stream));
+    nn->net.step = 0;
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+int nn_get_params(mgmlmc_ctx* ctx, const mgmlmc_nn* nn, float* host) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(nn && host, "null pointer");
+    MG_CUDA(cudaMemcpyAsync(host, nn->net.params.p, sizeof(float) * nn->net.nparams, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+int nn_forward(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, void* y, int nrhs) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(nn && r && y && r != y, "null or aliased pointer");
+    if (nrhs <= 0) return;
+    mg::nn_forward(&nn->net, (const float2*)r, (float2*)y, nrhs, false, ctx->stream);
+  });
+}
+
+int nn_loss_grad(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, const void* e, int nrhs, double* loss,
+                 float* host_grad) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(nn && r && e && loss && nrhs > 0, "null pointer or empty batch");
+    *loss = mg::nn_backward(&nn->net, (const float2*)r, (const float2*)e, nrhs, ctx->stream, ctx->pinned);
+    if (host_grad) {
+      MG_CUDA(cudaMemcpyAsync(host_grad, nn->net.grad.p, sizeof(float) * nn->net.nparams, cudaMemcpyDeviceToHost,
+                              ctx->stream));
+      MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+  });
+}
+
+int nn_train_step(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, const void* e, int nrhs, double lr, double* loss) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(nn && r && e && loss && nrhs > 0 && lr > 0, "bad arguments");
+    *loss = mg::nn_backward(&nn->net, (const float2*)r, (const float2*)e, nrhs, ctx->stream, ctx->pinned);
+    mg::nn_adam(&nn->net, lr, ctx->stream);
+  });
+}
+
+int mg_attach_nn(mgmlmc_ctx* ctx, mgmlmc_hier* h, mgmlmc_nn* nn) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h, "null hierarchy");
+    MG_CHECK_ARG(!nn || nn->net.L == h->L, "network and hierarchy lattices differ");
+    h->nn = nn ? &nn->net : nullptr;
+  });
+}
+
 int mlmc_update_active(int nd, int* active, const double* V, const int64_t* N, const double* C, double eps,
                        double tau_abs, int policy, int min_samples) {
   if (nd <= 0 || nd > MGMLMC_MAX_LEVELS || !active || !V || !N || !C) return MGMLMC_ERR_INVALID_ARG;

@@ -344,7 +344,7 @@ static GmState<R> gm_state(mgmlmc_hier* h, int l, int nrhs, int m) {
 // Per-rhs iteration counts are added to its_acc (device, may be null).
 template <typename R>
 void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<R>::T* x, int nrhs, int m,
-                 double tol, int maxit, bool precond, const int* act_in, int* its_acc, double* relres_out,
+                 double tol, int maxit, int precond, const int* act_in, int* its_acc, double* relres_out,
                  int* cycles_out) {
   typedef typename CT<R>::T C;
   struct HintGuard {  // nested solves (K-cycle, bootstrap) restore the caller's hint
@@ -381,7 +381,18 @@ void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<
       C* Vj1 = s.V + (size_t)(j + 1) * vs;
       C* Zj = s.Z + (size_t)j * vs;
       if (precond)
+      {
         vcycle_maybe_graph<R>(h, l, Vj, Zj, nrhs, s.iact);
+        if constexpr (sizeof(R) == 4) {
+          if (precond == 2 && l == 0 && h->nn) {  // learned correction: z += M(v - D z)
+            C* tt = (C*)h->work("nn_t", l, sizeof(C) * n * nrhs);
+            C* cc = (C*)h->work("nn_c", l, sizeof(C) * n * nrhs);
+            op_apply<R>(h, l, Zj, tt, Vj, nrhs, s.iact);
+            nn_forward(h->nn, tt, cc, nrhs, false, st);
+            nn_add(st, Zj, cc, (size_t)n * nrhs);
+          }
+        }
+      }
       else
         vcopy<C>(st, Vj, Zj, n, nrhs);
       op_apply<R>(h, l, Zj, Vj1, nullptr, nrhs, s.iact);
@@ -418,9 +429,9 @@ void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<
   if (relres_out) MG_CUDA(cudaMemcpyAsync(relres_out, s.relres, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, st));
   if (cycles_out) *cycles_out = cycles;
 }
-template void fgmres_core<float>(mgmlmc_hier*, int, const float2*, float2*, int, int, double, int, bool, const int*,
+template void fgmres_core<float>(mgmlmc_hier*, int, const float2*, float2*, int, int, double, int, int, const int*,
                                  int*, double*, int*);
-template void fgmres_core<double>(mgmlmc_hier*, int, const double2*, double2*, int, int, double, int, bool,
+template void fgmres_core<double>(mgmlmc_hier*, int, const double2*, double2*, int, int, double, int, int,
                                   const int*, int*, double*, int*);
 
 __global__ void k_mixed_check(const double* __restrict__ rn2, const double* __restrict__ bn2, int* act,
@@ -489,7 +500,7 @@ SolveOut solve(mgmlmc_hier* h, int l, const void* b, void* x, int nrhs, const so
   int* its = (int*)h->work("sv_its", l, sizeof(int) * nrhs);
   double* relres = (double*)h->work("sv_rr", l, sizeof(double) * nrhs);
   MG_CUDA(cudaMemsetAsync(its, 0, sizeof(int) * nrhs, st));
-  const bool pc = sp.precond != 0;
+  const int pc = sp.precond;
   if (sp.prec == MGMLMC_FP64) {
     int cyc = 0;
     fgmres_core<double>(h, l, (const double2*)b, (double2*)x, nrhs, sp.m, sp.tol, sp.maxit, pc, nullptr, its, relres,

@@ -8,6 +8,7 @@
 #include <tuple>
 #include <vector>
 
+#include "nn.cuh"
 #include "ops.cuh"
 
 struct mgmlmc_ctx {
@@ -55,6 +56,7 @@ struct mgmlmc_hier {
   std::vector<mg::LevelData> lv;
   std::map<std::tuple<std::string, int>, mg::DBuf> ws;  // workspaces
   mg::DBuf tc_err;  // device int: set by a tensor-core kernel whose bounded wait expired
+  mg::NNet* nn = nullptr;  // learned fine-level correction (precond = 2), not owned
   bool use_tc(int l) const {
     return prm.tensor_cores && l >= 1 && l < nlev && lv[l].dof == 16 && lv[l].tcW.p != nullptr;
   }
@@ -124,7 +126,7 @@ void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>
 // Batched flexible GMRES(m) in precision R, x0 = 0; see engine.cu.
 template <typename R>
 void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<R>::T* x, int nrhs, int m,
-                 double tol, int maxit, bool precond, const int* act_in, int* its_acc, double* relres_out,
+                 double tol, int maxit, int precond, const int* act_in, int* its_acc, double* relres_out,
                  int* cycles_out);
 
 template <typename R>
