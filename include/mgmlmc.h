@@ -277,7 +277,9 @@ int hutchpp_project_noalloc(void* stream, const double* Q, int d, const double* 
 /* ---- learned preconditioner (library extension; the paper has no learned part) ---- */
 
 /* A gauge-covariant convolutional network M ~ D^{-1} used as a correction after
- * the V-cycle inside FGMRES (solve_params.precond = 2):  z = V(v);  z += M(v - D z).
+ * the V-cycle inside FGMRES (solve_params.precond = 2):  z = V(v);  t = v - D z;
+ * z += |t| M(t / |t|)  (the net sees unit-norm residuals, so train it on pairs
+ * (r / |r|, e / |r|)).
  * Layer l:  z_k(x) = sum_d sum_c W[d][k][c] T_d(x) a_c(x + d)  over the 9 offsets
  * d = 3 (dt+1) + (dx+1) of the 3x3 neighbourhood, T_d(x) the parallel transporter
  * from x + d to x (links with the antiperiodic sign on time-boundary crossings,

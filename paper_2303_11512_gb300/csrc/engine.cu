@@ -384,12 +384,17 @@ void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<
       {
         vcycle_maybe_graph<R>(h, l, Vj, Zj, nrhs, s.iact);
         if constexpr (sizeof(R) == 4) {
-          if (precond == 2 && l == 0 && h->nn) {  // learned correction: z += M(v - D z)
+          if (precond == 2 && l == 0 && h->nn) {  // learned correction: z += |t| M(t / |t|), t = v - D z
             C* tt = (C*)h->work("nn_t", l, sizeof(C) * n * nrhs);
             C* cc = (C*)h->work("nn_c", l, sizeof(C) * n * nrhs);
+            double* tn = (double*)h->work("nn_n", l, sizeof(double) * nrhs);
+            void* red = h->work("nn_red", l, reduce_work_bytes(n, nrhs, 1));
             op_apply<R>(h, l, Zj, tt, Vj, nrhs, s.iact);
+            vnorm2<C>(st, tt, n, nrhs, tn, red, s.iact);
+            sqrt_inplace(st, tn, nrhs);
+            vscale_inv<C>(st, tn, tt, tt, n, nrhs, s.iact);
             nn_forward(h->nn, tt, cc, nrhs, false, st);
-            nn_add(st, Zj, cc, (size_t)n * nrhs);
+            nn_add(st, Zj, cc, n, nrhs, tn);
           }
         }
       }

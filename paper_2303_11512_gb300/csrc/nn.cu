@@ -267,9 +267,14 @@ __global__ void k_nn_adam(float* __restrict__ p, const float* __restrict__ g, fl
   p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-__global__ void k_nn_add(float2* __restrict__ z, const float2* __restrict__ c, size_t total) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
-    z[i] = cadd(z[i], c[i]);
+__global__ void k_nn_add(float2* __restrict__ z, const float2* __restrict__ c, long n, const double* __restrict__ s) {
+  const int rhs = blockIdx.y;
+  const float f = s ? (float)s[rhs] : 1.f;
+  if (f == 0.f) return;  // masked or zero residual: no correction
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)rhs * n + i;
+    z[o] = cadd(z[o], cscale(c[o], f));
+  }
 }
 
 // ---- dispatch over the supported channel counts -------------------------------------------
@@ -456,8 +461,8 @@ void nn_adam(NNet* net, double lr, cudaStream_t st) {
             net->m.as<float>(), net->v.as<float>(), (int)net->nparams, (float)lr, b1, b2, c1, c2, 1e-8f);
 }
 
-void nn_add(cudaStream_t st, float2* z, const float2* c, size_t total) {
-  MG_LAUNCH(k_nn_add, 1024, 256, 0, st, z, c, total);
+void nn_add(cudaStream_t st, float2* z, const float2* c, long n, int nrhs, const double* scale) {
+  MG_LAUNCH(k_nn_add, dim3(std::min<long>(cdiv(n, 1024), 512), nrhs), 256, 0, st, z, c, n, scale);
 }
 
 }  // namespace mg

@@ -26,6 +26,7 @@ void nn_forward(NNet* net, const float2* r, float2* y, int nrhs, bool tape, cuda
 // loss (1/nrhs) sum ||M(r) - e||^2 / ||e||^2 and its gradient into net->grad
 double nn_backward(NNet* net, const float2* r, const float2* e, int nrhs, cudaStream_t st, int* pinned);
 void nn_adam(NNet* net, double lr, cudaStream_t st);
-void nn_add(cudaStream_t st, float2* z, const float2* c, size_t total);
+// z[rhs] += scale[rhs] * c[rhs]  (scale may be null: 1)
+void nn_add(cudaStream_t st, float2* z, const float2* c, long n, int nrhs, const double* scale);
 
 }  // namespace mg
