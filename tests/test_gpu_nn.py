@@ -126,6 +126,7 @@ def test_training_and_use_in_fgmres(api, ctx):
           % (l0, l, lt, {k: s1[k] for k in ("iters", "outer", "max_relres")},
              {k: s2[k] for k in ("iters", "outer", "max_relres")}))
     assert s1["converged"] and s2["converged"]
+    assert s2["iters"] < s1["iters"]          # what the trained network gains over the V-cycle alone
     assert torch.abs(x1 - x2).max().item() < 1e-7 * torch.abs(x1).max().item()
     print("\n[learned correction] loss %.4f -> %.4f (held-out %.4f); FGMRES iterations V-cycle %d, "
           "V-cycle + net %d" % (l0, l, lt, s1["iters"], s2["iters"]))
