@@ -402,10 +402,8 @@ void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<
         vcopy<C>(st, Vj, Zj, n, nrhs);
       op_apply<R>(h, l, Zj, Vj1, nullptr, nrhs, s.iact);
       vmultidot<C>(st, s.V, vs, j + 1, Vj1, n, nrhs, s.h1, s.red, s.iact);
-      vgs_update<C>(st, s.V, vs, j + 1, s.h1, Vj1, n, nrhs, s.iact);
-      vmultidot<C>(st, s.V, vs, j + 1, Vj1, n, nrhs, s.h2, s.red, s.iact);
-      vgs_update<C>(st, s.V, vs, j + 1, s.h2, Vj1, n, nrhs, s.iact);
-      vnorm2<C>(st, Vj1, n, nrhs, s.hn2, s.red, s.iact);
+      vgs_update_dot<C>(st, s.V, vs, j + 1, s.h1, Vj1, n, nrhs, s.h2, s.red, s.iact);
+      vgs_update_norm<C>(st, s.V, vs, j + 1, s.h2, Vj1, n, nrhs, s.hn2, s.red, s.iact);
       MG_CUDA(cudaMemsetAsync(s.count, 0, sizeof(int), st));
       MG_LAUNCH(k_gm_arnoldi, nb, 64, 0, st, j, m, nrhs, s.h1, s.h2, s.hn2, s.hn, s.H, s.cs, s.sn, s.g, s.iact,
                 s.kvec, s.its, s.bnorm, tol, maxit, s.count);

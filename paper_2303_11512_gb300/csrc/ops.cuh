@@ -51,10 +51,10 @@ void prolong_op(cudaStream_t st, const typename CT<R>::T* P, int Ls, int d, int 
 void gather_tv_blocks(cudaStream_t st, const double2* V, int Ls, int d, int agg, int ntv, double2* P);
 // orthonormalise every (aggregate, chirality) block of P (bsz x ntv): QR with real positive diag
 void orthonormalise_blocks(cudaStream_t st, double2* P, int nblocks, int bsz, int ntv, int* fail);
-// Galerkin probing: probes[p][n_l] = P e_{colour kappa, coarse dof j}, p = kappa * dc + j
-void make_probes(cudaStream_t st, const double2* P, int Ls, int d, int agg, int ntv, double2* probes);
-// scatter restricted probe images into the coarse stencil [site][5][dc][dc]
-void extract_stencil(cudaStream_t st, const double2* imgs, int Lc, int dc, double2* stencil);
+// Galerkin coarse stencil out[site][5][dc][dc] = P^H D_l P, D_l given by the prepared links
+// (wilson, d = 2, diagonal diag) or by the level-l stencil A[site][5][d][d]
+void galerkin(cudaStream_t st, const double2* A, bool wilson, double diag, int Ls, int d, int agg, int ntv,
+              const double2* P, double2* out);
 
 // ---------------------------------------------------------------- dense (coarsest)
 void dense_from_stencil(cudaStream_t st, const double2* stencil, int Ls, int d, double2* A);
@@ -102,6 +102,14 @@ void vmultidot(cudaStream_t st, const C* V, long vstride, int k, const C* w, lon
 template <typename C>
 void vgs_update(cudaStream_t st, const C* V, long vstride, int k, const double2* h, C* w, long n, int nrhs,
                 const int* active);
+// the two classical Gram-Schmidt passes, each update fused with the reduction that follows it:
+// w -= sum_i h[i][rhs] V_i, then h2[i][rhs] = V_i^H w   /   w -= sum_i h[i][rhs] V_i, then out[rhs] = ||w||^2
+template <typename C>
+void vgs_update_dot(cudaStream_t st, const C* V, long vstride, int k, const double2* h, C* w, long n, int nrhs,
+                    double2* h2, void* work, const int* active);
+template <typename C>
+void vgs_update_norm(cudaStream_t st, const C* V, long vstride, int k, const double2* h, C* w, long n, int nrhs,
+                     double* out, void* work, const int* active);
 // x += sum_i y[i][rhs] Z_i
 template <typename C>
 void vcombine(cudaStream_t st, const C* Z, long zstride, int k, const double2* y, C* x, long n, int nrhs,

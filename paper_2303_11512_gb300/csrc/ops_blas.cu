@@ -81,18 +81,69 @@ template void vnorm2<float2>(cudaStream_t, const float2*, long, int, double*, vo
 template void vnorm2<double2>(cudaStream_t, const double2*, long, int, double*, void*, const int*);
 
 // ---- multi-dot: h[i][rhs] = V_i^H w ---------------------------------------------------
-constexpr int MDC = 8;  // dot products per pass
+// Each thread accumulates its share of a chunk of dot products in registers; the block then
+// reduces all 2*chunk real values together (block_sum_many), one shared-memory pass in all.
+template <typename C> struct MdChunk { static constexpr int value = 16; };
+template <> struct MdChunk<double2> { static constexpr int value = 8; };
+
+// Transposed warp reduction of NV values per lane: at each step the lanes of a pair swap
+// halves of their value sets, so NV values take NV - 1 + log2(32 / NV) shuffles instead of
+// 5 NV.  Lane l returns the warp total of value (l >> s), s = log2(32 / NV).
+template <int NV>
+__device__ __forceinline__ double warp_sum_many(double (&v)[NV]) {
+  static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two <= 32");
+  const int lane = threadIdx.x & 31;
+  int o = 16;
+#pragma unroll
+  for (int half = NV / 2; half >= 1; half >>= 1, o >>= 1) {
+    const bool up = lane & o;
+#pragma unroll
+    for (int q = 0; q < half; ++q) {
+      const double send = up ? v[q] : v[q + half];
+      const double keep = up ? v[q + half] : v[q];
+      v[q] = keep + __shfl_xor_sync(0xffffffff, send, o);
+    }
+  }
+  double r = v[0];
+  for (; o; o >>= 1) r += __shfl_xor_sync(0xffffffff, r, o);
+  return r;
+}
+
+// Block (RT threads) totals of NV values; thread t < NV returns the total of value t
+// (other threads return 0).  sh holds (RT / 32) * NV doubles.
+template <int NV>
+__device__ __forceinline__ double block_sum_many(double (&v)[NV], double* sh) {
+  constexpr int S = (NV == 32) ? 0 : (NV == 16) ? 1 : (NV == 8) ? 2 : (NV == 4) ? 3 : (NV == 2) ? 4 : 5;
+  const double r = warp_sum_many<NV>(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();  // sh may still be read by a previous call
+  if ((l & ((1 << S) - 1)) == 0) sh[w * NV + (l >> S)] = r;
+  __syncthreads();
+  double t = 0;
+  if ((int)threadIdx.x < NV) {
+#pragma unroll
+    for (int q = 0; q < RT / 32; ++q) t += sh[q * NV + threadIdx.x];
+  }
+  return t;
+}
+
+// part[(i * nrhs + rhs) * RBLK + block] (component c) = t, for dot i, real (c = 0) / imaginary (c = 1)
+__device__ __forceinline__ void store_part(double2* part, int i, int nrhs, int rhs, int c, double t) {
+  reinterpret_cast<double*>(part + ((size_t)i * nrhs + rhs) * RBLK + blockIdx.x)[c] = t;
+}
 
 template <typename C>
 __global__ void __launch_bounds__(RT) k_multidot_part(const C* __restrict__ V, long vstride, int k,
                                                       const C* __restrict__ w, long n, double2* __restrict__ part,
                                                       const int* __restrict__ active) {
   typedef typename Acc<C>::R R;
-  __shared__ double sh[32];
+  constexpr int MDC = MdChunk<C>::value;
+  __shared__ double sh[(RT / 32) * 2 * MDC];
   const int rhs = blockIdx.y;
   const int nrhs = gridDim.y;
   const bool on = !(active && !active[rhs]);
   const C* W = w + (size_t)rhs * n;
+  const C* Vr = V + (size_t)rhs * n;
   for (int i0 = 0; i0 < k; i0 += MDC) {
     R ar[MDC], ai[MDC];
 #pragma unroll
@@ -104,19 +155,18 @@ __global__ void __launch_bounds__(RT) k_multidot_part(const C* __restrict__ V, l
 #pragma unroll
         for (int q = 0; q < MDC; ++q) {
           if (q < cnt) {
-            const C a = V[(size_t)(i0 + q) * vstride + (size_t)rhs * n + e];
+            const C a = Vr[(size_t)(i0 + q) * vstride + e];
             ar[q] = fma(a.x, b.x, fma(a.y, b.y, ar[q]));
             ai[q] = fma(a.x, b.y, fma(-a.y, b.x, ai[q]));
           }
         }
       }
     }
-    for (int q = 0; q < cnt; ++q) {
-      double re = block_sum((double)ar[q], sh);
-      double im = block_sum((double)ai[q], sh);
-      if (threadIdx.x == 0)
-        part[((size_t)(i0 + q) * nrhs + rhs) * RBLK + blockIdx.x] = make_double2(re, im);
-    }
+    double v[2 * MDC];
+#pragma unroll
+    for (int q = 0; q < MDC; ++q) { v[2 * q] = ar[q]; v[2 * q + 1] = ai[q]; }
+    const double t = block_sum_many<2 * MDC>(v, sh);
+    if ((int)threadIdx.x < 2 * cnt) store_part(part, i0 + (threadIdx.x >> 1), nrhs, rhs, threadIdx.x & 1, t);
   }
 }
 
@@ -196,6 +246,137 @@ template void vgs_update<double2>(cudaStream_t, const double2*, long, int, const
 template void vcombine<float2>(cudaStream_t, const float2*, long, int, const double2*, float2*, long, int, const int*);
 template void vcombine<double2>(cudaStream_t, const double2*, long, int, const double2*, double2*, long, int,
                                 const int*);
+
+// ---- fused classical Gram-Schmidt passes ------------------------------------------------------
+// First-pass update fused with the second pass's dot products: w -= sum_i h_i V_i, then
+// V_i^H w with the updated w; each thread keeps its V_i elements in registers between the two.
+template <typename C, int KM>
+__global__ void __launch_bounds__(RT, sizeof(C) == 8 ? 2 : 1) k_gs_update_dot(const C* __restrict__ V, long vstride, int k,
+                                                      const double2* __restrict__ h, C* __restrict__ w, long n,
+                                                      double2* __restrict__ part, const int* __restrict__ active) {
+  typedef typename Acc<C>::R R;
+  __shared__ C hs[KM];
+  __shared__ double sh[(RT / 32) * 2 * KM];
+  const int rhs = blockIdx.y, nrhs = gridDim.y;
+  const bool on = !(active && !active[rhs]);
+  if ((int)threadIdx.x < k) {
+    const double2 v = h[(size_t)threadIdx.x * nrhs + rhs];
+    hs[threadIdx.x] = cmake((R)v.x, (R)v.y);
+  }
+  __syncthreads();
+  R dr[KM], di[KM];
+#pragma unroll
+  for (int q = 0; q < KM; ++q) { dr[q] = 0; di[q] = 0; }
+  if (on) {
+    C* W = w + (size_t)rhs * n;
+    const C* Vr = V + (size_t)rhs * n;
+    for (long e = blockIdx.x * (long)RT + threadIdx.x; e < n; e += (long)RBLK * RT) {
+      C a[KM];
+      C acc = czero<C>();
+#pragma unroll
+      for (int q = 0; q < KM; ++q) {
+        if (q < k) {
+          a[q] = Vr[(size_t)q * vstride + e];
+          acc = cfma(hs[q], a[q], acc);
+        }
+      }
+      const C x = csub(W[e], acc);
+      W[e] = x;
+#pragma unroll
+      for (int q = 0; q < KM; ++q) {
+        if (q < k) {
+          dr[q] = fma(a[q].x, x.x, fma(a[q].y, x.y, dr[q]));
+          di[q] = fma(a[q].x, x.y, fma(-a[q].y, x.x, di[q]));
+        }
+      }
+    }
+  }
+  double v[2 * KM];
+#pragma unroll
+  for (int q = 0; q < KM; ++q) { v[2 * q] = dr[q]; v[2 * q + 1] = di[q]; }
+  const double t = block_sum_many<2 * KM>(v, sh);
+  if ((int)threadIdx.x < 2 * k) store_part(part, threadIdx.x >> 1, nrhs, rhs, threadIdx.x & 1, t);
+}
+
+// Second-pass update fused with the norm of the result: w -= sum_i h_i V_i, part = ||w||^2.
+template <typename C, int KM>
+__global__ void __launch_bounds__(RT) k_gs_update_norm(const C* __restrict__ V, long vstride, int k,
+                                                       const double2* __restrict__ h, C* __restrict__ w, long n,
+                                                       double* __restrict__ part, const int* __restrict__ active) {
+  typedef typename Acc<C>::R R;
+  __shared__ C hs[KM];
+  __shared__ double sh[32];
+  const int rhs = blockIdx.y, nrhs = gridDim.y;
+  if (active && !active[rhs]) {
+    if (threadIdx.x == 0) part[(size_t)rhs * RBLK + blockIdx.x] = 0.0;
+    return;
+  }
+  if ((int)threadIdx.x < k) {
+    const double2 v = h[(size_t)threadIdx.x * nrhs + rhs];
+    hs[threadIdx.x] = cmake((R)v.x, (R)v.y);
+  }
+  __syncthreads();
+  C* W = w + (size_t)rhs * n;
+  const C* Vr = V + (size_t)rhs * n;
+  R s = 0;
+  for (long e = blockIdx.x * (long)RT + threadIdx.x; e < n; e += (long)RBLK * RT) {
+    C acc = czero<C>();
+#pragma unroll
+    for (int q = 0; q < KM; ++q)
+      if (q < k) acc = cfma(hs[q], Vr[(size_t)q * vstride + e], acc);
+    const C x = csub(W[e], acc);
+    W[e] = x;
+    s += x.x * x.x + x.y * x.y;
+  }
+  const double r = block_sum((double)s, sh);
+  if (threadIdx.x == 0) part[(size_t)rhs * RBLK + blockIdx.x] = r;
+}
+
+template <typename C>
+void vgs_update_dot(cudaStream_t st, const C* V, long vstride, int k, const double2* h, C* w, long n, int nrhs,
+                    double2* h2, void* work, const int* active) {
+  if (k > 16) {
+    vgs_update<C>(st, V, vstride, k, h, w, n, nrhs, active);
+    vmultidot<C>(st, V, vstride, k, w, n, nrhs, h2, work, active);
+    return;
+  }
+  double2* part = reinterpret_cast<double2*>(work);
+  const double bytes = act_rhs(nrhs) * n * sizeof(C) * (k + 2.0), flops = act_rhs(nrhs) * n * 16.0 * k;
+  if (k <= 8)
+    MG_LAUNCH_W(bytes, flops, (k_gs_update_dot<C, 8>), dim3(RBLK, nrhs), RT, 0, st, V, vstride, k, h, w, n, part,
+                active);
+  else
+    MG_LAUNCH_W(bytes, flops, (k_gs_update_dot<C, 16>), dim3(RBLK, nrhs), RT, 0, st, V, vstride, k, h, w, n, part,
+                active);
+  MG_LAUNCH(k_finalize_cplx, cdiv((long)k * nrhs, 4), 128, 0, st, part, k * nrhs, h2);
+}
+
+template <typename C>
+void vgs_update_norm(cudaStream_t st, const C* V, long vstride, int k, const double2* h, C* w, long n, int nrhs,
+                     double* out, void* work, const int* active) {
+  if (k > 16) {
+    vgs_update<C>(st, V, vstride, k, h, w, n, nrhs, active);
+    vnorm2<C>(st, w, n, nrhs, out, work, active);
+    return;
+  }
+  double* part = reinterpret_cast<double*>(work);
+  const double bytes = act_rhs(nrhs) * n * sizeof(C) * (k + 2.0), flops = act_rhs(nrhs) * n * (8.0 * k + 4.0);
+  if (k <= 8)
+    MG_LAUNCH_W(bytes, flops, (k_gs_update_norm<C, 8>), dim3(RBLK, nrhs), RT, 0, st, V, vstride, k, h, w, n, part,
+                active);
+  else
+    MG_LAUNCH_W(bytes, flops, (k_gs_update_norm<C, 16>), dim3(RBLK, nrhs), RT, 0, st, V, vstride, k, h, w, n, part,
+                active);
+  MG_LAUNCH(k_finalize_real, cdiv(nrhs, 4), 128, 0, st, part, nrhs, out);
+}
+template void vgs_update_dot<float2>(cudaStream_t, const float2*, long, int, const double2*, float2*, long, int,
+                                     double2*, void*, const int*);
+template void vgs_update_dot<double2>(cudaStream_t, const double2*, long, int, const double2*, double2*, long, int,
+                                      double2*, void*, const int*);
+template void vgs_update_norm<float2>(cudaStream_t, const float2*, long, int, const double2*, float2*, long, int,
+                                      double*, void*, const int*);
+template void vgs_update_norm<double2>(cudaStream_t, const double2*, long, int, const double2*, double2*, long, int,
+                                       double*, void*, const int*);
 
 // ---- elementwise -------------------------------------------------------------------------------
 template <typename C> void vzero(cudaStream_t st, C* x, long n, int nrhs) {

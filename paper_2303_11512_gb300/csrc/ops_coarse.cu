@@ -1,7 +1,7 @@
 // Coarse-level kernels: 5-point block stencil apply, SAP block matrices and
 // smoother on coarse levels, aggregation restriction/prolongation (R = P^H,
 // Section 3.1), the per-aggregate orthonormalisation of the test vectors and
-// the Galerkin construction D_{l+1} = P_l^H D_l P_l by colour probing.
+// the Galerkin construction D_{l+1} = P_l^H D_l P_l, block by block.
 //
 // Stencil layout: st[site][dir][i][j], dir = 0 self, 1 +x, 2 -x, 3 +t, 4 -t;
 // (D x)(s)_i = sum_dir sum_j st[s][dir][i][j] x(s + dir)_j, periodic (the
@@ -423,57 +423,143 @@ void orthonormalise_blocks(cudaStream_t stm, double2* P, int nblocks, int bsz, i
   MG_LAUNCH(k_orthonormalise, cdiv(nblocks, 4), 128, 0, stm, P, nblocks, bsz, ntv, fail);
 }
 
-// ---- Galerkin probing -------------------------------------------------------------
-// 16 aggregate colours (X mod 4) + 4 (T mod 4): the five aggregates B, B +- x,
-// B +- t always carry distinct colours, so the restricted image of probe
-// (kappa, j) at coarse site B holds exactly column j of D_c[B, B + dir] for the
-// dir with colour(B + dir) = kappa.
-__device__ __forceinline__ int agg_colour(int T, int X) { return (X & 3) + 4 * (T & 3); }
+// ---- Galerkin coarse operator ------------------------------------------------------
+// D_{l+1} = P^H D_l P (Section 3.1), one CTA per coarse site B, block by block: for every fine
+// site s of aggregate B and stencil direction f, with s' the f-neighbour of s,
+//   D_{l+1}[B, f or self] += P(s)^H D_l(s, f) P(s'),
+// where P(s) (d x dc) is block diagonal in chirality and s' lies in B itself or in the aggregate
+// adjacent to B in direction f (a fine hop crosses only the aggregate face it points to).
+__device__ __forceinline__ void wilson_hop(const double2* __restrict__ lk, double diag, int L, int s, int f,
+                                           double2* M) {
+  double2 w;
+  switch (f) {
+    case 0:
+      M[0] = make_double2(diag, 0); M[1] = make_double2(0, 0);
+      M[2] = make_double2(0, 0); M[3] = make_double2(diag, 0);
+      return;
+    case 1:  // +x: (1 - sigma_1) W_0(s)
+      w = lk[2 * s];
+      M[0] = w; M[1] = cneg(w); M[2] = cneg(w); M[3] = w;
+      return;
+    case 2:  // -x: (1 + sigma_1) conj(W_0(s - x))
+      w = cconj(lk[2 * nbr_site(s, 2, L)]);
+      M[0] = w; M[1] = w; M[2] = w; M[3] = w;
+      return;
+    case 3:  // +t: (1 - sigma_2) W_1(s)
+      w = lk[2 * s + 1];
+      M[0] = w; M[1] = cmuli(w); M[2] = cmulmi(w); M[3] = w;
+      return;
+    default:  // -t: (1 + sigma_2) conj(W_1(s - t))
+      w = cconj(lk[2 * nbr_site(s, 4, L) + 1]);
+      M[0] = w; M[1] = cmulmi(w); M[2] = cmuli(w); M[3] = w;
+      return;
+  }
+}
 
-__global__ void k_make_probes(const double2* __restrict__ P, int Ls, int d, int agg, int ntv,
-                              double2* __restrict__ probes) {
-  const int hd = d / 2, na = agg * agg, bsz = na * hd, dc = 2 * ntv;
-  const int Lc = Ls / agg;
-  const size_t n = (size_t)Ls * Ls * d;
-  const int p = blockIdx.y;
-  const int kappa = p / dc, jc = p % dc, cj = jc / ntv, m = jc % ntv;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t site = q / d;
-    const int k = q % d;
-    const int t = site / Ls, x = site % Ls;
-    const int T = t / agg, X = x / agg;
-    const int c = k / hd;
-    double2 v = make_double2(0, 0);
-    if (c == cj && agg_colour(T, X) == kappa) {
-      const int js = (t % agg) * agg + x % agg;
-      const int j = js * hd + (k % hd);
-      v = P[(((size_t)(T * Lc + X) * 2 + c) * bsz + j) * ntv + m];
+constexpr int GAL_T = 256;   // threads per coarse site
+constexpr int GAL_E = 4;     // coarse block entries per thread (dc <= 32)
+
+template <bool WILSON>
+__global__ void __launch_bounds__(GAL_T) k_galerkin(const double2* __restrict__ A, double diag, int Ls, int d,
+                                                    int agg, int ntv, const double2* __restrict__ P,
+                                                    double2* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int hd = d / 2, na = agg * agg, bsz = na * hd, dc = 2 * ntv, Lc = Ls / agg;
+  const int dd = d * d, ddc = d * dc, dcc = dc * dc;
+  double2* sA = reinterpret_cast<double2*>(smem_raw);  // [f][r][k]   D_l(s, f)
+  double2* sT = sA + 5 * dd;                            // [f][r][j]   D_l(s, f) P(s'_f)
+  __shared__ int s_nb[5], s_js[5];                      // aggregate and local site of s'_f
+  const int B = blockIdx.x, BT = B / Lc, BX = B % Lc;
+  const size_t pblk = (size_t)2 * bsz * ntv;
+  const double2* PB = P + (size_t)B * pblk;
+  double2 acc[5][GAL_E];
+#pragma unroll
+  for (int c = 0; c < 5; ++c)
+#pragma unroll
+    for (int q = 0; q < GAL_E; ++q) acc[c][q] = make_double2(0, 0);
+  for (int js = 0; js < na; ++js) {
+    const int s = (BT * agg + js / agg) * Ls + BX * agg + js % agg;
+    bool inside[5];  // s'_f in B: the f contribution goes to the self block
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      const int s2 = nbr_site(s, f, Ls), t2 = s2 / Ls, x2 = s2 % Ls;
+      inside[f] = (t2 / agg) * Lc + x2 / agg == B;
     }
-    probes[(size_t)p * n + q] = v;
+    __syncthreads();  // the previous site's sA / sT / s_nb / s_js are consumed
+    if (threadIdx.x < 5) {
+      const int s2 = nbr_site(s, threadIdx.x, Ls), t2 = s2 / Ls, x2 = s2 % Ls;
+      s_nb[threadIdx.x] = (t2 / agg) * Lc + x2 / agg;
+      s_js[threadIdx.x] = (t2 % agg) * agg + x2 % agg;
+    }
+    if (WILSON) {
+      if (threadIdx.x < 5) wilson_hop(A, diag, Ls, s, threadIdx.x, sA + threadIdx.x * 4);
+    } else {
+      const double2* As = A + (size_t)s * 5 * dd;
+      for (int e = threadIdx.x; e < 5 * dd; e += GAL_T) sA[e] = __ldg(As + e);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 5 * ddc; e += GAL_T) {
+      const int f = e / ddc, rem = e % ddc, r = rem / dc, j = rem % dc, cj = j / ntv, m = j % ntv;
+      const double2* p = P + (size_t)s_nb[f] * pblk + ((size_t)cj * bsz + s_js[f] * hd) * ntv + m;
+      const double2* a = sA + f * dd + r * d + cj * hd;
+      double2 t = make_double2(0, 0);
+      for (int k = 0; k < hd; ++k) t = cfma(a[k], __ldg(p + (size_t)k * ntv), t);
+      sT[e] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < GAL_E; ++q) {
+      const int e = threadIdx.x + q * GAL_T;
+      if (e < dcc) {
+        const int i = e / dc, j = e % dc, ci = i / ntv, mi = i % ntv;
+        const double2* p = PB + ((size_t)ci * bsz + js * hd) * ntv + mi;
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          const double2* t = sT + f * ddc + (ci * hd) * dc + j;
+          double2 v = make_double2(0, 0);
+          for (int k = 0; k < hd; ++k) v = cfmac(__ldg(p + (size_t)k * ntv), t[k * dc], v);
+          if (inside[f])
+            acc[0][q] = cadd(acc[0][q], v);
+          else
+            acc[f][q] = cadd(acc[f][q], v);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < GAL_E; ++q) {
+    const int e = threadIdx.x + q * GAL_T;
+    if (e < dcc)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) out[((size_t)B * 5 + c) * dcc + e] = acc[c][q];
   }
 }
 
-void make_probes(cudaStream_t stm, const double2* P, int Ls, int d, int agg, int ntv, double2* probes) {
-  dim3 grid(256, 16 * 2 * ntv);
-  MG_LAUNCH(k_make_probes, grid, 256, 0, stm, P, Ls, d, agg, ntv, probes);
-}
-
-__global__ void k_extract_stencil(const double2* __restrict__ imgs, int Lc, int dc, double2* __restrict__ stencil) {
-  const size_t nc = (size_t)Lc * Lc * dc;
-  const size_t total = (size_t)Lc * Lc * 5 * dc * dc;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int j = e % dc;
-    const int i = (e / dc) % dc;
-    const int dir = (e / ((size_t)dc * dc)) % 5;
-    const int s = (int)(e / ((size_t)5 * dc * dc));
-    const int nb = nbr_site(s, dir, Lc);
-    const int kappa = agg_colour(nb / Lc, nb % Lc);
-    stencil[e] = imgs[(size_t)(kappa * dc + j) * nc + (size_t)s * dc + i];
+void galerkin(cudaStream_t stm, const double2* A, bool wilson, double diag, int Ls, int d, int agg, int ntv,
+              const double2* P, double2* out) {
+  const int dc = 2 * ntv, Lc = Ls / agg;
+  MG_CHECK_ARG(dc * dc <= GAL_E * GAL_T && d % 2 == 0 && (!wilson || d == 2), "Galerkin block sizes");
+  const size_t sm = sizeof(double2) * 5 * ((size_t)d * d + (size_t)d * dc);
+  MG_CHECK_ARG(sm <= 200 * 1024, "Galerkin blocks too large for shared memory");
+  const double na = agg * agg, hd = d / 2;
+  const double flops = (double)Lc * Lc * na * 5.0 * 8.0 * hd * ((double)d * dc + (double)dc * dc);
+  const double bytes = (double)Lc * Lc * (na * (wilson ? 32.0 : 5.0 * d * d * 16.0) + 5.0 * dc * dc * 16.0 +
+                                          2.0 * na * hd * ntv * 16.0);
+  if (wilson) {
+    static bool done = false;
+    if (!done) {
+      MG_CUDA(cudaFuncSetAttribute(k_galerkin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      done = true;
+    }
+    MG_LAUNCH_W(bytes, flops, k_galerkin<true>, Lc * Lc, GAL_T, sm, stm, A, diag, Ls, d, agg, ntv, P, out);
+  } else {
+    static bool done = false;
+    if (!done) {
+      MG_CUDA(cudaFuncSetAttribute(k_galerkin<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      done = true;
+    }
+    MG_LAUNCH_W(bytes, flops, k_galerkin<false>, Lc * Lc, GAL_T, sm, stm, A, diag, Ls, d, agg, ntv, P, out);
   }
-}
-
-void extract_stencil(cudaStream_t stm, const double2* imgs, int Lc, int dc, double2* stencil) {
-  MG_LAUNCH(k_extract_stencil, 1024, 256, 0, stm, imgs, Lc, dc, stencil);
 }
 
 // ---- coarsest level as a dense matrix -------------------------------------------------

@@ -1,6 +1,6 @@
 // Multigrid set-up (Section 3.1 / Section 4): SAP block inverses, test
-// vectors, orthonormal aggregation prolongators, Galerkin coarse stencils by
-// colour probing, the coarsest dense inverse (its trace is tau_L of
+// vectors, orthonormal aggregation prolongators, Galerkin coarse stencils
+// P^H D P, the coarsest dense inverse (its trace is tau_L of
 // Algorithm 2), and the optional bootstrap rounds.
 #include <algorithm>
 
@@ -67,7 +67,6 @@ static void build_from_tv(mgmlmc_hier* h, int l, int* dfail) {
   LevelData& lv = h->lv[l];
   LevelData& lc = h->lv[l + 1];
   const int Ls = lv.side, d = lv.dof, ntv = p.ntv;
-  const long n = lv.n;
   const int Lc = Ls / p.agg, dc = 2 * ntv;
   const int bsz = p.agg * p.agg * d / 2;
   const size_t pcount = (size_t)Lc * Lc * 2 * bsz * ntv;
@@ -75,21 +74,15 @@ static void build_from_tv(mgmlmc_hier* h, int l, int* dfail) {
   gather_tv_blocks(st, lv.tv.as<double2>(), Ls, d, p.agg, ntv, lv.P64.as<double2>());
   orthonormalise_blocks(st, lv.P64.as<double2>(), Lc * Lc * 2, bsz, ntv, dfail + 1);
   to_fp32(st, lv.P64, lv.P32, pcount);
-  // Galerkin by colour probing: 16 aggregate colours x dc probe vectors
-  const int np = 16 * dc;
-  const long nc = (long)Lc * Lc * dc;
+  // Galerkin coarse operator, block by block
   {
-    DBuf probes(sizeof(double2) * n * np, st), imgs(sizeof(double2) * n * np, st);
-    make_probes(st, lv.P64.as<double2>(), Ls, d, p.agg, ntv, probes.as<double2>());
-    op_apply<double>(h, l, probes.as<double2>(), imgs.as<double2>(), nullptr, np, nullptr);
-    probes.release();
-    DBuf cimgs(sizeof(double2) * nc * np, st);
-    restrict_op<double>(st, lv.P64.as<double2>(), Ls, d, p.agg, ntv, imgs.as<double2>(), cimgs.as<double2>(), np,
-                        nullptr);
-    imgs.release();
     const size_t scount = (size_t)Lc * Lc * 5 * dc * dc;
     lc.st64.alloc(sizeof(double2) * scount, st);
-    extract_stencil(st, cimgs.as<double2>(), Lc, dc, lc.st64.as<double2>());
+    if (l == 0)
+      galerkin(st, lv.links64.as<double2>(), true, lv.diag, Ls, d, p.agg, ntv, lv.P64.as<double2>(),
+               lc.st64.as<double2>());
+    else
+      galerkin(st, lv.st64.as<double2>(), false, 0.0, Ls, d, p.agg, ntv, lv.P64.as<double2>(), lc.st64.as<double2>());
     to_fp32(st, lc.st64, lc.st32, scount);
     if (p.tensor_cores && dc == 16) {
       lc.tcW.alloc(sizeof(float) * tc_stencil_weight_floats(Lc * Lc), st);
