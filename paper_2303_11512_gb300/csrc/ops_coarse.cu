@@ -22,49 +22,73 @@ __device__ __forceinline__ int nbr_site(int s, int dir, int Ls) {
 }
 
 // ---- coarse stencil apply -----------------------------------------------------
-template <typename R, bool RES>
-__global__ void __launch_bounds__(256) k_coarse_apply(const typename CT<R>::T* __restrict__ st, int Ls, int d,
+// CTA per site: the 5 stencil blocks (transposed in shared memory) are applied to the
+// rhs in groups of 256 / d; DT = d at compile time (0: runtime d).
+template <typename R, bool RES, int DT>
+__global__ void __launch_bounds__(256) k_coarse_apply(const typename CT<R>::T* __restrict__ st, int Ls, int d_,
                                                       const typename CT<R>::T* __restrict__ x,
                                                       typename CT<R>::T* __restrict__ y,
                                                       const typename CT<R>::T* __restrict__ b, int nrhs,
                                                       const int* __restrict__ active) {
   typedef typename CT<R>::T C;
+  const int d = DT ? DT : d_;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sst = reinterpret_cast<C*>(smem_raw);  // [dir][j][i] (transposed)
-  const int G = blockDim.x / d;
+  const int G = 256 / d;
   C* sx = sst + 5 * d * d;                  // [g][dir][j]
   const int s = blockIdx.x;
   const int dd = d * d;
   const C* S = st + (size_t)s * 5 * dd;
-  for (int e = threadIdx.x; e < 5 * dd; e += blockDim.x) {
-    const int dir = e / dd, r = e % dd, i = r / d, j = r % d;
+  for (int e = threadIdx.x; e < 5 * dd; e += 256) {
+    const int dir = e / dd, r = e - dir * dd, i = r / d, j = r - i * d;
     sst[dir * dd + j * d + i] = S[e];
   }
-  int nb[5];
-#pragma unroll
-  for (int dir = 0; dir < 5; ++dir) nb[dir] = nbr_site(s, dir, Ls);
   const size_t n = (size_t)Ls * Ls * d;
-  const int g = threadIdx.x / d, i = threadIdx.x % d;
+  const int g = threadIdx.x / d, i = threadIdx.x - g * d;
   for (int r0 = 0; r0 < nrhs; r0 += G) {
     __syncthreads();
-    for (int q = threadIdx.x; q < G * 5 * d; q += blockDim.x) {
-      const int gg = q / (5 * d), rem = q % (5 * d), dir = rem / d, j = rem % d;
+    for (int q = threadIdx.x; q < G * 5 * d; q += 256) {
+      const int gg = q / (5 * d), rem = q - gg * 5 * d, dir = rem / d, j = rem - dir * d;
       const int rhs = r0 + gg;
-      if (rhs < nrhs) sx[q] = __ldg(x + rhs * n + (size_t)nb[dir] * d + j);
+      if (rhs < nrhs && !(active && !active[rhs]))
+        sx[q] = __ldg(x + rhs * n + (size_t)nbr_site(s, dir, Ls) * d + j);
     }
     __syncthreads();
     const int rhs = r0 + g;
-    if (g < G && rhs < nrhs && !(active && !active[rhs])) {
+    if (rhs < nrhs && !(active && !active[rhs])) {
       C acc = czero<C>();
+#pragma unroll
       for (int dir = 0; dir < 5; ++dir) {
         const C* a = sst + dir * dd + i;
         const C* v = sx + (g * 5 + dir) * d;
-#pragma unroll 4
+#pragma unroll 16
         for (int j = 0; j < d; ++j) acc = cfma(a[j * d], v[j], acc);
       }
       const size_t o = rhs * n + (size_t)s * d + i;
       y[o] = RES ? csub(b[o], acc) : acc;
     }
+  }
+}
+
+template <typename K>
+static void set_smem_attr(K kernel, bool& done) {
+  if (!done) {
+    MG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    done = true;
+  }
+}
+
+template <typename R, bool RES>
+static void coarse_apply_launch(cudaStream_t stm, const typename CT<R>::T* st, int Ls, int d,
+                                const typename CT<R>::T* x, typename CT<R>::T* y, const typename CT<R>::T* b,
+                                int nrhs, const int* active, size_t sm, double bytes, double flops) {
+  static bool done[2] = {false, false};
+  if (d == 16) {
+    set_smem_attr(k_coarse_apply<R, RES, 16>, done[0]);
+    MG_LAUNCH_W(bytes, flops, (k_coarse_apply<R, RES, 16>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
+  } else {
+    set_smem_attr(k_coarse_apply<R, RES, 0>, done[1]);
+    MG_LAUNCH_W(bytes, flops, (k_coarse_apply<R, RES, 0>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
   }
 }
 
@@ -75,24 +99,13 @@ void coarse_apply(cudaStream_t stm, const typename CT<R>::T* st, int Ls, int d, 
   MG_CHECK_ARG(d <= 64 && 256 % d == 0, "coarse dof must divide 256");
   const int G = 256 / d;
   size_t sm = sizeof(C) * (5 * d * d + G * 5 * d);
-  static bool attr_set[2][2] = {{false, false}, {false, false}};
-  const int ri = sizeof(R) == 8;
   const double ns = (double)Ls * Ls, cs = sizeof(C), ar = act_rhs(nrhs);
   const double bytes = ar * ns * d * cs * (b ? 3 : 2) + ns * 5.0 * d * d * cs;
   const double flops = ar * ns * 8.0 * 5.0 * d * d;
-  if (b) {
-    if (!attr_set[ri][1]) {
-      MG_CUDA(cudaFuncSetAttribute(k_coarse_apply<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr_set[ri][1] = true;
-    }
-    MG_LAUNCH_W(bytes, flops, (k_coarse_apply<R, true>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
-  } else {
-    if (!attr_set[ri][0]) {
-      MG_CUDA(cudaFuncSetAttribute(k_coarse_apply<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr_set[ri][0] = true;
-    }
-    MG_LAUNCH_W(bytes, flops, (k_coarse_apply<R, false>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
-  }
+  if (b)
+    coarse_apply_launch<R, true>(stm, st, Ls, d, x, y, b, nrhs, active, sm, bytes, flops);
+  else
+    coarse_apply_launch<R, false>(stm, st, Ls, d, x, y, b, nrhs, active, sm, bytes, flops);
 }
 template void coarse_apply<float>(cudaStream_t, const float2*, int, int, const float2*, float2*, const float2*,
                                   int, const int*);
@@ -220,85 +233,95 @@ template void sap_half_coarse<double>(cudaStream_t, const double2*, int, int, in
 // ---- restriction / prolongation ---------------------------------------------------
 // Aggregate (T, X) of agg x agg sites; block of chirality c has rows
 // j = js * hd + k' (js = jt * agg + jx local site, hd = d / 2 dof per chirality)
-// mapping to fine dof (site(js)) * d + c * hd + k'.
-template <typename R>
-__global__ void __launch_bounds__(256) k_restrict(const typename CT<R>::T* __restrict__ P, int Ls, int d, int agg,
-                                                  int ntv, const typename CT<R>::T* __restrict__ xf,
+// mapping to fine dof (site(js)) * d + c * hd + k'.  One CTA per aggregate, its P blocks
+// in shared memory, rhs in groups.  DT / AT / NT = d / agg / ntv at compile time (0: runtime).
+template <typename R, int DT, int AT, int NT>
+__global__ void __launch_bounds__(256) k_restrict(const typename CT<R>::T* __restrict__ P, int Ls, int d_, int agg_,
+                                                  int ntv_, const typename CT<R>::T* __restrict__ xf,
                                                   typename CT<R>::T* __restrict__ xc, int nrhs,
                                                   const int* __restrict__ active) {
   typedef typename CT<R>::T C;
+  const int d = DT ? DT : d_, agg = AT ? AT : agg_, ntv = NT ? NT : ntv_;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int hd = d / 2, na = agg * agg, bsz = na * hd, dc = 2 * ntv, fa = na * d;
-  const int G = max(1, (int)blockDim.x / dc);
+  const int G = max(1, 256 / dc);
   C* sP = reinterpret_cast<C*>(smem_raw);  // [c][j][m]
   C* sx = sP + 2 * bsz * ntv;              // [g][js * d + k]
   const int Lc = Ls / agg;
-  const int a = blockIdx.x, T = a / Lc, X = a % Lc;
+  const int a = blockIdx.x, T = a / Lc, X = a - T * Lc;
   const C* Pa = P + (size_t)a * 2 * bsz * ntv;
-  for (int e = threadIdx.x; e < 2 * bsz * ntv; e += blockDim.x) sP[e] = Pa[e];
+  for (int e = threadIdx.x; e < 2 * bsz * ntv; e += 256) sP[e] = Pa[e];
   const size_t n = (size_t)Ls * Ls * d, nc = (size_t)Lc * Lc * dc;
   for (int r0 = 0; r0 < nrhs; r0 += G) {
     __syncthreads();
-    for (int q = threadIdx.x; q < G * fa; q += blockDim.x) {
-      const int g = q / fa, rem = q % fa, js = rem / d, k = rem % d;
+    for (int q = threadIdx.x; q < G * fa; q += 256) {
+      const int g = q / fa, rem = q - g * fa, js = rem / d, k = rem - js * d;
       const int rhs = r0 + g;
-      if (rhs < nrhs) {
-        const size_t site = (size_t)(agg * T + js / agg) * Ls + agg * X + js % agg;
+      if (rhs < nrhs && !(active && !active[rhs])) {
+        const int jt = js / agg, jx = js - jt * agg;
+        const size_t site = (size_t)(agg * T + jt) * Ls + agg * X + jx;
         sx[q] = __ldg(xf + rhs * n + site * d + k);
       }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < G * dc; q += blockDim.x) {
-      const int g = q / dc, o = q % dc, c = o / ntv, m = o % ntv;
+    for (int q = threadIdx.x; q < G * dc; q += 256) {
+      const int g = q / dc, o = q - g * dc, c = o / ntv, m = o - c * ntv;
       const int rhs = r0 + g;
       if (rhs < nrhs && !(active && !active[rhs])) {
         C acc = czero<C>();
         const C* pc = sP + (size_t)c * bsz * ntv + m;
         const C* xv = sx + g * fa + c * hd;
-        for (int j = 0; j < bsz; ++j) acc = cfmac(pc[j * ntv], xv[(j / hd) * d + j % hd], acc);
+#pragma unroll 16
+        for (int j = 0; j < bsz; ++j) {
+          const int js = j / hd, kp = j - js * hd;
+          acc = cfmac(pc[j * ntv], xv[js * d + kp], acc);
+        }
         xc[rhs * nc + (size_t)a * dc + o] = acc;
       }
     }
   }
 }
 
-template <typename R, bool ADD>
-__global__ void __launch_bounds__(256) k_prolong(const typename CT<R>::T* __restrict__ P, int Ls, int d, int agg,
-                                                 int ntv, const typename CT<R>::T* __restrict__ xc,
+template <typename R, bool ADD, int DT, int AT, int NT>
+__global__ void __launch_bounds__(256) k_prolong(const typename CT<R>::T* __restrict__ P, int Ls, int d_, int agg_,
+                                                 int ntv_, const typename CT<R>::T* __restrict__ xc,
                                                  typename CT<R>::T* __restrict__ xf, int nrhs,
                                                  const int* __restrict__ active) {
   typedef typename CT<R>::T C;
+  const int d = DT ? DT : d_, agg = AT ? AT : agg_, ntv = NT ? NT : ntv_;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int hd = d / 2, na = agg * agg, bsz = na * hd, dc = 2 * ntv, fa = na * d;
-  const int G = max(1, (int)blockDim.x / fa);
+  const int G = max(1, 256 / fa);
   C* sP = reinterpret_cast<C*>(smem_raw);  // [c][m][j] (transposed)
   C* sc = sP + 2 * bsz * ntv;              // [g][dc]
   const int Lc = Ls / agg;
-  const int a = blockIdx.x, T = a / Lc, X = a % Lc;
+  const int a = blockIdx.x, T = a / Lc, X = a - T * Lc;
   const C* Pa = P + (size_t)a * 2 * bsz * ntv;
-  for (int e = threadIdx.x; e < 2 * bsz * ntv; e += blockDim.x) {
-    const int c = e / (bsz * ntv), r = e % (bsz * ntv), j = r / ntv, m = r % ntv;
+  for (int e = threadIdx.x; e < 2 * bsz * ntv; e += 256) {
+    const int c = e / (bsz * ntv), r = e - c * bsz * ntv, j = r / ntv, m = r - j * ntv;
     sP[(c * ntv + m) * bsz + j] = Pa[e];
   }
   const size_t n = (size_t)Ls * Ls * d, nc = (size_t)Lc * Lc * dc;
   for (int r0 = 0; r0 < nrhs; r0 += G) {
     __syncthreads();
-    for (int q = threadIdx.x; q < G * dc; q += blockDim.x) {
-      const int g = q / dc, o = q % dc;
+    for (int q = threadIdx.x; q < G * dc; q += 256) {
+      const int g = q / dc, o = q - g * dc;
       const int rhs = r0 + g;
-      if (rhs < nrhs) sc[q] = __ldg(xc + rhs * nc + (size_t)a * dc + o);
+      if (rhs < nrhs && !(active && !active[rhs])) sc[q] = __ldg(xc + rhs * nc + (size_t)a * dc + o);
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < G * fa; q += blockDim.x) {
-      const int g = q / fa, rem = q % fa, js = rem / d, k = rem % d;
+    for (int q = threadIdx.x; q < G * fa; q += 256) {
+      const int g = q / fa, rem = q - g * fa, js = rem / d, k = rem - js * d;
       const int rhs = r0 + g;
       if (rhs < nrhs && !(active && !active[rhs])) {
-        const int c = k / hd, kp = k % hd, j = js * hd + kp;
+        const int c = k / hd, kp = k - c * hd, j = js * hd + kp;
         C acc = czero<C>();
         const C* pc = sP + (size_t)c * ntv * bsz + j;
         const C* cv = sc + g * dc + c * ntv;
+#pragma unroll 8
         for (int m = 0; m < ntv; ++m) acc = cfma(pc[m * bsz], cv[m], acc);
-        const size_t site = (size_t)(agg * T + js / agg) * Ls + agg * X + js % agg;
+        const int jt = js / agg, jx = js - jt * agg;
+        const size_t site = (size_t)(agg * T + jt) * Ls + agg * X + jx;
         C* p = xf + rhs * n + site * d + k;
         *p = ADD ? cadd(*p, acc) : acc;
       }
@@ -306,12 +329,12 @@ __global__ void __launch_bounds__(256) k_prolong(const typename CT<R>::T* __rest
   }
 }
 
-template <typename K>
-static void set_smem_attr(K kernel, bool& done) {
-  if (!done) {
-    MG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    done = true;
-  }
+// compile-time shapes of the default hierarchy (agg 4, ntv 8: fine d = 2, coarse d = 16)
+enum { SHAPE_GENERIC = 0, SHAPE_FINE = 1, SHAPE_COARSE = 2 };
+static int transfer_shape(int d, int agg, int ntv) {
+  if (agg == 4 && ntv == 8 && d == 2) return SHAPE_FINE;
+  if (agg == 4 && ntv == 8 && d == 16) return SHAPE_COARSE;
+  return SHAPE_GENERIC;
 }
 
 template <typename R>
@@ -321,13 +344,51 @@ void restrict_op(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, in
   const int na = agg * agg, bsz = na * d / 2, dc = 2 * ntv;
   const int G = std::max(1, 256 / dc);
   size_t sm = sizeof(C) * ((size_t)2 * bsz * ntv + (size_t)G * na * d);
-  static bool done[2] = {false, false};
-  set_smem_attr(k_restrict<R>, done[sizeof(R) == 8]);
+  static bool done[3] = {false, false, false};
   const int Lc = Ls / agg;
   const double nag = (double)Lc * Lc, cs = sizeof(C), ar = act_rhs(nrhs);
   const double bytes = nag * (ar * (na * d + dc) * cs + 2.0 * bsz * ntv * cs);
   const double flops = nag * ar * 8.0 * 2.0 * bsz * ntv;
-  MG_LAUNCH_W(bytes, flops, k_restrict<R>, Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs, active);
+  switch (transfer_shape(d, agg, ntv)) {
+    case SHAPE_FINE:
+      set_smem_attr(k_restrict<R, 2, 4, 8>, done[1]);
+      MG_LAUNCH_W(bytes, flops, (k_restrict<R, 2, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs,
+                  active);
+      break;
+    case SHAPE_COARSE:
+      set_smem_attr(k_restrict<R, 16, 4, 8>, done[2]);
+      MG_LAUNCH_W(bytes, flops, (k_restrict<R, 16, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs,
+                  active);
+      break;
+    default:
+      set_smem_attr(k_restrict<R, 0, 0, 0>, done[0]);
+      MG_LAUNCH_W(bytes, flops, (k_restrict<R, 0, 0, 0>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs,
+                  active);
+  }
+}
+
+template <typename R, bool ADD>
+static void prolong_launch(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, int agg, int ntv,
+                           const typename CT<R>::T* xc, typename CT<R>::T* xf, int nrhs, const int* active,
+                           size_t sm, double bytes, double flops) {
+  static bool done[3] = {false, false, false};
+  const int Lc = Ls / agg;
+  switch (transfer_shape(d, agg, ntv)) {
+    case SHAPE_FINE:
+      set_smem_attr(k_prolong<R, ADD, 2, 4, 8>, done[1]);
+      MG_LAUNCH_W(bytes, flops, (k_prolong<R, ADD, 2, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf,
+                  nrhs, active);
+      break;
+    case SHAPE_COARSE:
+      set_smem_attr(k_prolong<R, ADD, 16, 4, 8>, done[2]);
+      MG_LAUNCH_W(bytes, flops, (k_prolong<R, ADD, 16, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf,
+                  nrhs, active);
+      break;
+    default:
+      set_smem_attr(k_prolong<R, ADD, 0, 0, 0>, done[0]);
+      MG_LAUNCH_W(bytes, flops, (k_prolong<R, ADD, 0, 0, 0>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf,
+                  nrhs, active);
+  }
 }
 
 template <typename R>
@@ -337,18 +398,14 @@ void prolong_op(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, int
   const int na = agg * agg, bsz = na * d / 2, dc = 2 * ntv, fa = na * d;
   const int G = std::max(1, 256 / fa);
   size_t sm = sizeof(C) * ((size_t)2 * bsz * ntv + (size_t)G * dc);
-  static bool done[2][2] = {{false, false}, {false, false}};
   const int Lc = Ls / agg;
   const double nag = (double)Lc * Lc, cs = sizeof(C), ar = act_rhs(nrhs);
   const double bytes = nag * (ar * ((add ? 2.0 : 1.0) * fa + dc) * cs + 2.0 * bsz * ntv * cs);
   const double flops = nag * ar * 8.0 * 2.0 * bsz * ntv;
-  if (add) {
-    set_smem_attr(k_prolong<R, true>, done[sizeof(R) == 8][1]);
-    MG_LAUNCH_W(bytes, flops, (k_prolong<R, true>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active);
-  } else {
-    set_smem_attr(k_prolong<R, false>, done[sizeof(R) == 8][0]);
-    MG_LAUNCH_W(bytes, flops, (k_prolong<R, false>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active);
-  }
+  if (add)
+    prolong_launch<R, true>(stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active, sm, bytes, flops);
+  else
+    prolong_launch<R, false>(stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active, sm, bytes, flops);
 }
 template void restrict_op<float>(cudaStream_t, const float2*, int, int, int, int, const float2*, float2*, int,
                                  const int*);
