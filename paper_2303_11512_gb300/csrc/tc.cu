@@ -4,8 +4,8 @@
 // (Galerkin stencil, SAP block inverse) is a small dense complex matrix per
 // site or block applied to all right-hand sides at once: with the rhs on the
 // M dimension that is a batched GEMM  Y^T[rhs, n] = sum_k X^T[rhs, k] E[n, k]
-// with the complex matrix embedded as a real one (E[2i+a][2j+b] =
-// [[Re, -Im], [Im, Re]]), and FP32 data read directly as TF32.
+// with the complex matrix embedded as a real one (output rows Re y_i = [Re w_ij, -Im w_ij],
+// Im y_i = [Im w_ij, Re w_ij] over k = 2j + {0, 1}), and FP32 data read directly as TF32.
 //
 //   mode 0 (stencil):   per site s, K = 5 chunks (x at s, s+x, s-x, s+t, s-t),
 //                       N = 32:   y = D x   or   y = b - D x
@@ -15,14 +15,17 @@
 // Data movement: the rhs x 32-float slab of one site is one TMA box (the launch's
 // rhs count rounded up to 8, at most 128 rows, x 128 B, 128-byte swizzle) straight
 // from the canonical [rhs][site][dof] vector; MMA rows beyond the box are never
-// stored.  Weights are stored pre-swizzled and fetched with one bulk copy per
-// chunk.  One thread issues the MMAs (M = 128, K = 8 per instruction) into a
-// TMEM accumulator; four warps read it back with tcgen05.ld (row = rhs =
-// lane) for the epilogue.  Warp-specialised: a producer warp streams items
-// through S shared-memory stages, one thread issues the MMAs into two
-// alternating TMEM accumulators, four epilogue warps drain them.  Every wait on
-// an mbarrier is bounded: on expiry the kernel records an error code, stops,
-// waits (bounded) for its own copies and frees its TMEM.
+// stored.  Weights are stored pre-swizzled, Re rows only (half the real embedding),
+// fetched with one bulk copy per chunk; two expander warps derive the Im rows in
+// shared memory.  One thread issues the MMAs (M = 128, K = 8 per instruction) into
+// TMEM accumulators; epilogue warps read them back with tcgen05.ld (row = rhs =
+// lane).  Warp-specialised: a producer warp streams items through S shared-memory
+// stages (lane k issuing the copies of chunk k), the expander completes each
+// stage's weights, one thread issues the MMAs into four rotating TMEM
+// accumulators, and eight epilogue warps (two per TMEM lane quarter, alternating
+// items, the additive input fetched a few steps ahead) drain them.  Every wait on
+// an mbarrier is bounded: on expiry the kernel records an error code, stops, waits
+// (bounded) for its own copies and frees its TMEM.
 #include <cuda.h>
 
 #include "ops.cuh"
@@ -48,18 +51,39 @@ __device__ __forceinline__ uint64_t gtimer_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-// bounded wait: gives up after TC_WAIT_NS of wall time (or TC_SPIN polls)
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+// non-blocking test of the phase
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+// bounded wait: gives up after TC_WAIT_NS of wall time (or TC_SPIN polls).  A phase that has already
+// completed is seen by one non-blocking test; the wall clock is first read after 256 unsuccessful polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  const uint64_t t0 = gtimer_ns();
+  if (mbar_test(bar, phase)) return true;
+  uint64_t t0 = 0;
   for (long it = 0; it < TC_SPIN; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    if (done) return true;
-    if ((it & 255) == 255 && gtimer_ns() - t0 > TC_WAIT_NS) break;
+    if (mbar_try(bar, phase)) return true;
+    if ((it & 255) == 255) {
+      const uint64_t now = gtimer_ns();
+      if (t0 == 0)
+        t0 = now;
+      else if (now - t0 > TC_WAIT_NS)
+        break;
+    }
   }
   return false;
 }
@@ -104,20 +128,18 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-// 32 lanes x 32 consecutive 32-bit TMEM columns -> 32 registers per thread
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
+// two loads of 32 lanes x 8 consecutive 32-bit TMEM columns -> v[0..7], v[8..15]
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float* v) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(ta));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(tb));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ int nbr_site_tc(int s, int dir, int Ls) {
@@ -150,7 +172,12 @@ struct TcCfg<1> {
   static constexpr int KC = 4, N = 128;
 };
 constexpr int TC_MAX_STAGES = 8;
-constexpr int TC_THREADS = 192;  // warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 epilogue
+constexpr int TC_EPI_WARPS = 8;  // two epilogue warps per TMEM lane quarter, alternating items
+constexpr int TC_EXP_WARPS = 2;  // expander warps: build the Im rows of each weight tile in shared memory
+constexpr int TC_EXP_WARP0 = 2 + TC_EPI_WARPS;
+// warp 0 TMA producer, warp 1 MMA issuer, then the epilogue warps, then the expander warps
+constexpr int TC_THREADS = 32 * (TC_EXP_WARP0 + TC_EXP_WARPS);
+constexpr int TC_NACC = 4;       // TMEM accumulators in flight
 
 // bytes of one pipeline stage: KC A slabs of `rows` rhs rows, then KC B tiles of N rows (128 B each).
 // The MMA reads 128 A rows; rows past `rows` land in the next slab or the stage's B tiles (never outside
@@ -168,12 +195,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
          const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int rows, int stages,
          const int* __restrict__ active, int* err) {
   typedef TcCfg<MODE> CF;
-  constexpr int KC = CF::KC, N = CF::N, NCOL = 2 * N < 32 ? 32 : 2 * N;
+  constexpr int KC = CF::KC, N = CF::N, NCOL = TC_NACC * N < 32 ? 32 : TC_NACC * N;
   constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[TC_MAX_STAGES], empty_bar[TC_MAX_STAGES];
-  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
+  __shared__ __align__(8) uint64_t full_bar[TC_MAX_STAGES], empty_bar[TC_MAX_STAGES], xfull_bar[TC_MAX_STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar[TC_NACC], tempty_bar[TC_NACC];
   __shared__ uint32_t s_taddr;
   __shared__ int s_skip;
   __shared__ volatile int s_bad;
@@ -184,7 +211,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int rhs0 = blockIdx.y * TC_M;
   const long ncf = (long)Ls * Ls * TC_CHUNK;  // floats per rhs row
   const int sbytes = tc_stage_bytes(KC, N, rows);
-  const uint32_t stage_tx = (uint32_t)sbytes;
+  const uint32_t stage_tx = (uint32_t)(KC * (rows + N / 2) * 128);  // A slabs + the stored (Re) half of B
   auto sA = [&](int st, int kc) { return base + st * sbytes + kc * rows * 128; };
   auto sB = [&](int st, int kc) { return base + st * sbytes + KC * rows * 128 + kc * N * 128; };
   auto center = [&](int item) -> int { return bmode ? block_site(item >> 2, item & 3, Ls, color) : item; };
@@ -193,18 +220,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     return nbr_site_tc(center(item), kc, Ls);
   };
   auto w_of = [&](int item, int kc) -> const float* {
-    if (MODE == 1) return W + ((size_t)item * KC + kc) * N * TC_CHUNK;
-    return W + ((size_t)center(item) * KC + kc) * N * TC_CHUNK;
+    if (MODE == 1) return W + ((size_t)item * KC + kc) * (N / 2) * TC_CHUNK;
+    return W + ((size_t)center(item) * KC + kc) * (N / 2) * TC_CHUNK;
   };
 
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
+      mbar_init(&xfull_bar[s], TC_EXP_WARPS);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < TC_NACC; ++a) {
       mbar_init(&tfull_bar[a], 1);
-      mbar_init(&tempty_bar[a], 4);
+      mbar_init(&tempty_bar[a], 4);  // the four lane-quarter warps of the item's parity
     }
     s_bad = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -224,39 +252,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) ++n_my;
 
   if (warp == 0) {
-    // ---------------- producer
-    if (lane == 0) {
-      int issued = 0;
-      for (int i = 0; i < n_my && !s_bad; ++i) {
-        const int s = i % stages;
-        if (i >= stages && !mbar_wait(&empty_bar[s], (uint32_t)((i / stages) - 1) & 1u)) {
-          atomicExch(err, 1);
-          s_bad = 1;
-          break;
-        }
-        const int item = blockIdx.x + i * gridDim.x;
-        mbar_expect_tx(&full_bar[s], stage_tx);
-        for (int kc = 0; kc < KC; ++kc) {
-          tma_load_2d(sA(s, kc), &amap, site_of(item, kc) * TC_CHUNK, rhs0, &full_bar[s]);
-          bulk_load(sB(s, kc), w_of(item, kc), N * 128, &full_bar[s]);
-        }
-        issued = i + 1;
+    // ---------------- producer: lane kc < KC computes the addresses of chunk kc and issues its two copies
+    int issued = 0;
+    for (int i = 0; i < n_my; ++i) {
+      const int s = i % stages;
+      int ok = lane == 0 ? !s_bad : 0;
+      if (lane == 0 && ok && i >= stages && !mbar_wait(&empty_bar[s], (uint32_t)((i / stages) - 1) & 1u)) {
+        atomicExch(err, 1);
+        s_bad = 1;
+        ok = 0;
       }
-      // let the last loads land before the CTA can exit (bounded)
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      const int item = blockIdx.x + i * gridDim.x;
+      if (lane == 0) mbar_expect_tx(&full_bar[s], stage_tx);
+      __syncwarp();
+      if (lane < KC) {
+        tma_load_2d(sA(s, lane), &amap, site_of(item, lane) * TC_CHUNK, rhs0, &full_bar[s]);
+        bulk_load(sB(s, lane), w_of(item, lane), (N / 2) * 128, &full_bar[s]);
+      }
+      issued = i + 1;
+    }
+    // let the last loads land before the CTA can exit (bounded)
+    if (lane == 0)
       for (int i = std::max(0, issued - stages); i < issued; ++i)
         mbar_wait(&full_bar[i % stages], (uint32_t)(i / stages) & 1u);
-    }
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
       for (int i = 0; i < n_my && !s_bad; ++i) {
-        const int s = i % stages, a = i & 1;
-        if (!mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1u)) {
+        const int s = i % stages, a = i % TC_NACC;
+        if (!mbar_wait(&xfull_bar[s], (uint32_t)(i / stages) & 1u)) {
           atomicExch(err, 2);
           s_bad = 1;
           break;
         }
-        if (i >= 2 && !mbar_wait(&tempty_bar[a], (uint32_t)((i >> 1) - 1) & 1u)) {
+        if (i >= TC_NACC && !mbar_wait(&tempty_bar[a], (uint32_t)((i / TC_NACC) - 1) & 1u)) {
           atomicExch(err, 3);
           s_bad = 1;
           break;
@@ -274,44 +304,102 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mma_commit(&tfull_bar[a]);  // accumulator a ready for the epilogue
       }
     }
+  } else if (warp >= TC_EXP_WARP0) {
+    // ---------------- expander: the Im rows of every B tile from its stored Re rows, (a, b) -> (-b, a);
+    // row n + N/2 has the swizzle phase of row n, so each 16-byte chunk keeps its position
+    const int et = (warp - TC_EXP_WARP0) * 32 + lane;
+    constexpr int HALF4 = (N / 2) * 8;  // float4 per stored half tile
+    constexpr int TILE4 = N * 8;        // float4 per full tile
+    constexpr int PER = KC * HALF4 / (32 * TC_EXP_WARPS);
+    constexpr int BATCH = PER % 8 == 0 ? 8 : PER % 5 == 0 ? 5 : PER % 4 == 0 ? 4 : PER % 2 == 0 ? 2 : 1;
+    static_assert(KC * HALF4 % (32 * TC_EXP_WARPS) == 0, "expander work must divide evenly");
+    for (int i = 0; i < n_my; ++i) {
+      const int s = i % stages;
+      if (s_bad || !mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1u)) {
+        if (!s_bad) atomicExch(err, 5);
+        s_bad = 1;
+        break;
+      }
+      float4* sb0 = reinterpret_cast<float4*>(sB(s, 0));  // element e: tile e / HALF4, offset e % HALF4
+#pragma unroll
+      for (int u0 = 0; u0 < PER; u0 += BATCH) {
+        float4 v[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+          const int e = et + (u0 + u) * 32 * TC_EXP_WARPS, kc = e / HALF4;
+          v[u] = sb0[kc * TILE4 + (e - kc * HALF4)];
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+          const int e = et + (u0 + u) * 32 * TC_EXP_WARPS, kc = e / HALF4;
+          sb0[kc * TILE4 + (e - kc * HALF4) + HALF4] = make_float4(-v[u].y, v[u].x, -v[u].w, v[u].z);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> MMA reads
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&xfull_bar[s])) : "memory");
+    }
   } else {
-    // ---------------- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
-    const int q = warp & 3;
+    // ---------------- epilogue: warp w owns TMEM lane quarter w % 4 and the items of parity (w - 2) / 4
+    const int q = warp & 3, par = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     const int rhs = rhs0 + row;
     const bool live = rhs < nrhs && !(active && !active[rhs]);
-    for (int i = 0; i < n_my; ++i) {
-      const int a = i & 1;
-      if (s_bad || !mbar_wait(&tfull_bar[a], (uint32_t)(i >> 1) & 1u)) {
+    const bool quarter_live = rhs0 + q * 32 < nrhs;  // warp-uniform: some row of this quarter exists
+    // MODE 1 adds into x, MODE 0 with bvec subtracts from b.  The work of an item is split in steps of
+    // 8 complex outputs (half a site slab); the additive input of step t + RD is fetched at step t.
+    const float* in = (MODE == 1) ? out : bvec;
+    constexpr int NSTEP = N / 16, RD = NSTEP < 4 ? NSTEP : 4;
+    static_assert(NSTEP % RD == 0, "prefetch ring must divide the steps of an item");
+    auto step_ptr = [&](const float* v, int i, int t) -> const float* {
+      const int item = blockIdx.x + i * gridDim.x, j = t >> 1;
+      const int st = (MODE == 1) ? block_site(item, j, Ls, color) : center(item);
+      return v + (size_t)rhs * ncf + (size_t)st * TC_CHUNK + 16 * (t & 1);
+    };
+    float4 ring[RD][4];
+    auto prefetch = [&](float4 (&dst)[4], int i, int t) {
+      if (in && live && i < n_my) {
+        const float4* src = reinterpret_cast<const float4*>(step_ptr(in, i, t));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dst[u] = src[u];
+      }
+    };
+#pragma unroll
+    for (int g = 0; g < RD; ++g) prefetch(ring[g], par + 2 * (g / NSTEP), g % NSTEP);
+    for (int i = par; i < n_my; i += 2) {
+      const int a = i % TC_NACC;
+      if (s_bad || !mbar_wait(&tfull_bar[a], (uint32_t)(i / TC_NACC) & 1u)) {
         if (!s_bad) atomicExch(err, 4);
         s_bad = 1;
         break;
       }
       tc_fence_after();
-      const int item = blockIdx.x + i * gridDim.x;
-      float v[32];
-#pragma unroll 1
-      for (int j = 0; j < N / 32; ++j) {
-        tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * N + 32 * j), v);
+      const uint32_t tq = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * N);
+#pragma unroll
+      for (int t = 0; t < NSTEP; ++t) {
+        float4 cur[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cur[u] = ring[t % RD][u];
+        prefetch(ring[t % RD], i + 2 * ((t + RD) / NSTEP), (t + RD) % NSTEP);
+        if (!quarter_live) continue;
+        // v[0..7] = Re, v[8..15] = Im of complex outputs 8t .. 8t + 7
+        float v[16];
+        tmem_ld8x2(tq + 8 * t, tq + N / 2 + 8 * t, v);
         if (live) {
-          const int s = (MODE == 1) ? block_site(item, j, Ls, color) : center(item);
-          float4* o = reinterpret_cast<float4*>(out + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
+          float4* o = reinterpret_cast<float4*>(const_cast<float*>(step_ptr(out, i, t)));
           if (MODE == 1) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              float4 x = o[u];
-              o[u] = make_float4(x.x + v[4 * u], x.y + v[4 * u + 1], x.z + v[4 * u + 2], x.w + v[4 * u + 3]);
-            }
+            for (int u = 0; u < 4; ++u)
+              o[u] = make_float4(cur[u].x + v[2 * u], cur[u].y + v[8 + 2 * u], cur[u].z + v[2 * u + 1],
+                                 cur[u].w + v[9 + 2 * u]);
           } else if (bvec) {
-            const float4* bb = reinterpret_cast<const float4*>(bvec + (size_t)rhs * ncf + (size_t)s * TC_CHUNK);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              float4 x = bb[u];
-              o[u] = make_float4(x.x - v[4 * u], x.y - v[4 * u + 1], x.z - v[4 * u + 2], x.w - v[4 * u + 3]);
-            }
+            for (int u = 0; u < 4; ++u)
+              o[u] = make_float4(cur[u].x - v[2 * u], cur[u].y - v[8 + 2 * u], cur[u].z - v[2 * u + 1],
+                                 cur[u].w - v[9 + 2 * u]);
           } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) o[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+            for (int u = 0; u < 4; ++u) o[u] = make_float4(v[2 * u], v[8 + 2 * u], v[2 * u + 1], v[9 + 2 * u]);
           }
         }
       }
@@ -328,37 +416,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-// real embedding of a complex d x d matrix block into the swizzled K-major B image:
-// element (n, k) of an N x 32 tile sits at n * 32 + (((k >> 2) ^ (n & 7)) << 2) + (k & 3)
+// Weight images.  The real embedding of a complex output row i is the pair of B rows
+//   Re y_i:  k = 2j + b ->  (Re w_ij, -Im w_ij)        Im y_i:  k = 2j + b -> (Im w_ij, Re w_ij),
+// the second a fixed rearrangement of the first.  Only the Re rows are stored (N/2 rows per K chunk,
+// swizzled K-major: element (n, k) at n * 32 + (((k >> 2) ^ (n & 7)) << 2) + (k & 3)); the kernel's
+// expander warps build the Im rows in shared memory, so TMEM columns [0, N/2) hold Re y, [N/2, N) Im y.
 __device__ __forceinline__ int sw_index(int n, int k) { return n * 32 + ((((k >> 2) ^ (n & 7)) << 2) | (k & 3)); }
 
 __global__ void k_tc_stencil_weights(const float2* __restrict__ st, int nsite, float* __restrict__ W) {
-  // st[site][dir][16][16] complex -> W[site][dir][32 x 32] tf32
-  const size_t total = (size_t)nsite * 5 * 32 * 32;
+  // st[site][dir][16][16] complex -> W[site][dir][16 x 32]
+  const size_t total = (size_t)nsite * 5 * 16 * 32;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int k = e % 32, n = (e / 32) % 32;
-    const size_t sd = e / 1024;  // site * 5 + dir
-    const int i = n >> 1, a = n & 1, j = k >> 1, b = k & 1;
+    const int k = e % 32, i = (e / 32) % 16;
+    const size_t sd = e / 512;  // site * 5 + dir
+    const int j = k >> 1, b = k & 1;
     const float2 z = st[sd * 256 + i * 16 + j];
-    const float v = (a == b) ? z.x : (a == 1 ? z.y : -z.y);
-    W[sd * 1024 + sw_index(n, k)] = v;
+    W[sd * 512 + sw_index(i, k)] = b ? -z.y : z.x;
   }
 }
 
 __global__ void k_tc_blockinv_weights(const float2* __restrict__ inv, int Ls, int color, int nblk, float* __restrict__ W) {
-  // colour-`color` blocks only, in their item order: inv[block][64][64] -> W[item][kc 4][128 x 32]
-  const size_t total = (size_t)nblk * 4 * 128 * 32;
+  // colour-`color` blocks only, in their item order: inv[block][64][64] -> W[item][kc 4][64 x 32]
+  const size_t total = (size_t)nblk * 4 * 64 * 32;
   const int nbx = Ls / 2, half = nbx / 2;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int kk = e % 32, n = (e / 32) % 128, kc = (e / 4096) % 4;
-    const int item = (int)(e / 16384);
+    const int kk = e % 32, i = (e / 32) % 64, kc = (e / 2048) % 4;
+    const int item = (int)(e / 8192);
     const int BT = item / half, BX = 2 * (item % half) + ((BT + color) & 1);
     const int blk = BT * nbx + BX;
     const int kg = kc * 32 + kk;  // real input index 2 * (16 * site_j + dof) + b
-    const int i = n >> 1, a = n & 1, j = kg >> 1, b = kg & 1;
+    const int j = kg >> 1, b = kg & 1;
     const float2 z = inv[(size_t)blk * 4096 + i * 64 + j];
-    const float v = (a == b) ? z.x : (a == 1 ? z.y : -z.y);
-    W[((size_t)item * 4 + kc) * 4096 + sw_index(n, kk)] = v;
+    W[((size_t)item * 4 + kc) * 2048 + sw_index(i, kk)] = b ? -z.y : z.x;
   }
 }
 
@@ -421,8 +510,8 @@ void launch_tc(cudaStream_t st, const CUtensorMap& m, const float* W, float* out
 
 }  // namespace
 
-size_t tc_stencil_weight_floats(int nsite) { return (size_t)nsite * 5 * 1024; }
-size_t tc_blockinv_weight_floats(int Ls) { return (size_t)(Ls / 2) * (Ls / 2) / 2 * 4 * 4096; }
+size_t tc_stencil_weight_floats(int nsite) { return (size_t)nsite * 5 * 512; }
+size_t tc_blockinv_weight_floats(int Ls) { return (size_t)(Ls / 2) * (Ls / 2) / 2 * 4 * 2048; }
 
 void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, float* W) {
   MG_LAUNCH(k_tc_stencil_weights, 1024, 256, 0, st, st32, nsite, W);
@@ -438,7 +527,7 @@ void tc_stencil_apply(cudaStream_t st, const float* W, int Ls, const float2* x, 
   const int ns = Ls * Ls;
   CUtensorMap m = make_map(x, ns, nrhs);
   const double ar = act_rhs(nrhs);
-  const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + ns * 5.0 * 4096;
+  const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + ns * 5.0 * 2048;
   const double flops = ar * ns * 2.0 * 32 * 160;
   launch_tc<0>(st, m, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
 }
@@ -450,13 +539,13 @@ void tc_sap_half(cudaStream_t st, const float* Wst, const float* Winv, int Ls, c
   const double ar = act_rhs(nrhs);
   {  // residual on the sites of the colour's blocks
     CUtensorMap m = make_map(x, ns, nrhs);
-    const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 4096;
+    const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 2048;
     const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
     launch_tc<0>(st, m, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes, flops);
   }
   {  // x_B += inv_B r_B
     CUtensorMap m = make_map(res, ns, nrhs);
-    const double bytes = ar * (ns / 2) * 128.0 * 3 + nblk * 65536.0;
+    const double bytes = ar * (ns / 2) * 128.0 * 3 + nblk * 32768.0;
     const double flops = ar * nblk * 2.0 * 128 * 128;
     launch_tc<1>(st, m, Winv, (float*)x, nullptr, Ls, nblk, 0, color, nrhs, active, err, bytes, flops);
   }
