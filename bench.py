@@ -53,6 +53,8 @@ def peaks() -> dict:
     # FP64 at the nominal 1.25 TFLOP/s of the part
     p["fp32_alu_tflops"] = 152 * 128 * 2 * 2.070e9 / 1e12
     p["fp64_alu_tflops"] = 1.25
+    # dense TF32 tensor rate: the measured sustained bf16 rate times the nominal tf32 / bf16 ratio (1.1 / 2.25)
+    p["tf32_tensor_tflops_sustained"] = p["bf16_tflops_sustained"] * 1.1 / 2.25
     return p
 
 
@@ -249,12 +251,16 @@ def main():
     flops_l = info["flops"] / info["launches"]
     ai = flops_l / max(bytes_l, 1.0)
     fp64 = "double" in dom
-    alu_peak = P["fp64_alu_tflops"] if fp64 else P["fp32_alu_tflops"]
-    ridge = alu_peak * 1e12 / (P["hbm_gbs"] * 1e9)
+    tensor = dom.startswith("k_tc")  # TF32 tcgen05 kernels: compute roof is the TF32 tensor rate
+    if tensor:
+        comp_peak, comp_bound = P["tf32_tensor_tflops_sustained"], "tensor"
+    else:
+        comp_peak, comp_bound = (P["fp64_alu_tflops"] if fp64 else P["fp32_alu_tflops"]), "alu"
+    ridge = comp_peak * 1e12 / (P["hbm_gbs"] * 1e9)
     if ai <= ridge:
         roof = dict(bound="hbm", achieved=bytes_l / (avg_ms * 1e-3) / 1e9, peak=P["hbm_gbs"], unit="GB/s")
     else:
-        roof = dict(bound="alu", achieved=flops_l / (avg_ms * 1e-3) / 1e12, peak=alu_peak, unit="TFLOP/s")
+        roof = dict(bound=comp_bound, achieved=flops_l / (avg_ms * 1e-3) / 1e12, peak=comp_peak, unit="TFLOP/s")
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof.update(kernel=dom, launches=info["launches"], avg_launch_ms=avg_ms, share=info["ms"] / max(tot_ms, 1e-9),
                 bytes_per_launch=bytes_l, flops_per_launch=flops_l, peak_src=P["src"], traffic=None)
