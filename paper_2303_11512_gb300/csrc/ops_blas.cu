@@ -132,12 +132,11 @@ __device__ __forceinline__ void store_part(double2* part, int i, int nrhs, int r
   reinterpret_cast<double*>(part + ((size_t)i * nrhs + rhs) * RBLK + blockIdx.x)[c] = t;
 }
 
-template <typename C>
+template <typename C, int MDC>
 __global__ void __launch_bounds__(RT) k_multidot_part(const C* __restrict__ V, long vstride, int k,
                                                       const C* __restrict__ w, long n, double2* __restrict__ part,
                                                       const int* __restrict__ active) {
   typedef typename Acc<C>::R R;
-  constexpr int MDC = MdChunk<C>::value;
   __shared__ double sh[(RT / 32) * 2 * MDC];
   const int rhs = blockIdx.y;
   const int nrhs = gridDim.y;
@@ -183,8 +182,14 @@ template <typename C>
 void vmultidot(cudaStream_t st, const C* V, long vstride, int k, const C* w, long n, int nrhs, double2* h,
                void* work, const int* active) {
   double2* part = reinterpret_cast<double2*>(work);
-  MG_LAUNCH_W(act_rhs(nrhs) * n * sizeof(C) * (k + 1.0), act_rhs(nrhs) * n * 8.0 * k, k_multidot_part<C>,
-              dim3(RBLK, nrhs), RT, 0, st, V, vstride, k, w, n, part, active);
+  // chunk of dot products per pass: 8 when that covers k (fewer registers, more resident blocks)
+  const double bytes = act_rhs(nrhs) * n * sizeof(C) * (k + 1.0), flops = act_rhs(nrhs) * n * 8.0 * k;
+  if (k <= 8)
+    MG_LAUNCH_W(bytes, flops, (k_multidot_part<C, 8>), dim3(RBLK, nrhs), RT, 0, st, V, vstride, k, w, n, part,
+                active);
+  else
+    MG_LAUNCH_W(bytes, flops, (k_multidot_part<C, MdChunk<C>::value>), dim3(RBLK, nrhs), RT, 0, st, V, vstride, k,
+                w, n, part, active);
   MG_LAUNCH(k_finalize_cplx, cdiv((long)k * nrhs, 4), 128, 0, st, part, k * nrhs, h);
 }
 template void vmultidot<float2>(cudaStream_t, const float2*, long, int, const float2*, long, int, double2*, void*,
