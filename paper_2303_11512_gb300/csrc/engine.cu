@@ -581,6 +581,76 @@ SolveOut level_sample(mgmlmc_hier* h, int l, const double2* zeta, double2* y, in
   return o;
 }
 
+// Level-difference applications of several levels at once (items with distinct levels).  Difference l needs
+// solves on levels l and l+1, so the second term of difference m-1 and the first term of difference m fall on
+// the same level m; each level is solved once with those right-hand sides side by side.  Every right-hand side
+// is iterated independently (per-rhs masks, reductions and stopping), so each item's result and iteration
+// counts are those of level_sample on its own.
+void multi_level_sample(mgmlmc_hier* h, std::vector<LsItem>& items, const solve_params& sp) {
+  cudaStream_t st = h->ctx->stream;
+  solve_params s2 = sp;
+  if (s2.prec == MGMLMC_FP32) s2.prec = MGMLMC_MIXED;  // samples are FP64 vectors
+  const int nlev = h->nlev;
+  struct Part { const double2* src; int nrhs, item, term; };
+  std::vector<std::vector<Part>> parts(nlev);
+  std::vector<double2*> x1(items.size()), x2(items.size());
+  std::vector<int> seen(nlev, 0);
+  for (size_t i = 0; i < items.size(); ++i) {
+    const LsItem& it = items[i];
+    MG_CHECK_ARG(it.l >= 0 && it.l + 1 < nlev, "level difference index out of range");
+    MG_CHECK_ARG(!seen[it.l], "one item per level difference");
+    seen[it.l] = 1;
+    if (it.nrhs <= 0) continue;
+    double2* zc = (double2*)h->work("mls_zc", it.l, sizeof(double2) * h->lv[it.l + 1].n * it.nrhs);
+    restrict_level<double>(h, it.l, it.zeta, zc, it.nrhs);
+    parts[it.l].push_back({it.zeta, it.nrhs, (int)i, 0});
+    parts[it.l + 1].push_back({zc, it.nrhs, (int)i, 1});
+  }
+  std::vector<SolveOut> first(items.size()), second(items.size());
+  for (int m = 0; m < nlev; ++m) {
+    if (parts[m].empty()) continue;
+    const long n = h->lv[m].n;
+    int tot = 0;
+    for (const Part& q : parts[m]) tot += q.nrhs;
+    const double2* b = parts[m][0].src;
+    if (parts[m].size() > 1) {
+      double2* bb = (double2*)h->work("mls_b", m, sizeof(double2) * n * tot);
+      int off = 0;
+      for (const Part& q : parts[m]) {
+        MG_CUDA(cudaMemcpyAsync(bb + (size_t)off * n, q.src, sizeof(double2) * n * q.nrhs, cudaMemcpyDeviceToDevice,
+                                st));
+        off += q.nrhs;
+      }
+      b = bb;
+    }
+    double2* x = (double2*)h->work("mls_x", m, sizeof(double2) * n * tot);
+    SolveOut o = solve(h, m, b, x, tot, s2);
+    int off = 0;
+    for (const Part& q : parts[m]) {
+      SolveOut& d = q.term == 0 ? first[q.item] : second[q.item];
+      d = o;
+      d.its.assign(o.its.begin() + off, o.its.begin() + off + q.nrhs);
+      d.total_iters = 0;
+      d.iters = 0;
+      for (int v : d.its) { d.total_iters += v; d.iters = std::max(d.iters, v); }
+      (q.term == 0 ? x1 : x2)[q.item] = x + (size_t)off * n;
+      off += q.nrhs;
+    }
+  }
+  for (size_t i = 0; i < items.size(); ++i) {
+    LsItem& it = items[i];
+    if (it.nrhs <= 0) continue;
+    prolong_level<double>(h, it.l, x2[i], it.y, it.nrhs);
+    vsub_from(st, x1[i], it.y, h->lv[it.l].n, it.nrhs);  // y = x1 - P x2
+    SolveOut o = first[i];
+    o.converged = first[i].converged && second[i].converged;
+    o.max_relres = std::max(first[i].max_relres, second[i].max_relres);
+    o.iters = std::max(first[i].iters, second[i].iters);
+    o.total_iters = first[i].total_iters + second[i].total_iters;
+    it.out = o;
+  }
+}
+
 void restrict_to_level(mgmlmc_hier* h, int l, const double2* zfine, double2* out, int nrhs) {
   cudaStream_t st = h->ctx->stream;
   if (l == 0) {
@@ -656,6 +726,61 @@ mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int
   return sk.release();
 }
 
+// The sketches of all level differences at once (Algorithm 2's deflation part for every l with d[l] > 0): the
+// power sweeps and the low-rank traces of the levels advance together so that the solves of neighbouring
+// differences on a shared level run as one batch (multi_level_sample).  Each level's Q and tau_lr equal those of
+// sketch_qr for that level.
+void sketch_qr_all(mgmlmc_hier* h, const int* d, int k, uint64_t seed, int form, const solve_params& sp,
+                   std::vector<std::unique_ptr<mgmlmc_sketch>>& out, std::vector<double2>& tau_lr) {
+  MG_CHECK_ARG(k >= 1, "at least one power sweep");
+  cudaStream_t st = h->ctx->stream;
+  const int nd = h->nlev - 1;
+  out.clear();
+  out.resize(nd);
+  tau_lr.assign(nd, make_double2(0, 0));
+  std::vector<LsItem> items;
+  std::vector<double2*> S(nd, nullptr), Y(nd, nullptr);
+  for (int l = 0; l < nd; ++l) {
+    if (d[l] <= 0) continue;
+    MG_CHECK_ARG(d[l] <= 32, "sketch size d must be 1..32");
+    const long n = h->lv[l].n;
+    out[l].reset(new mgmlmc_sketch);
+    out[l]->level = l; out[l]->d = d[l]; out[l]->n = n; out[l]->st = st;
+    out[l]->Q.alloc(sizeof(double2) * n * d[l], st);
+    S[l] = out[l]->Q.as<double2>();
+    Y[l] = (double2*)h->work("sk_Y", l, sizeof(double2) * n * d[l]);
+    make_level_vectors(h, l, form, seed, MGMLMC_PHASE_SKETCH, 0, d[l], S[l]);
+    LsItem it;
+    it.l = l; it.zeta = S[l]; it.y = Y[l]; it.nrhs = d[l];
+    items.push_back(it);
+  }
+  if (items.empty()) return;
+  for (int sweep = 0; sweep <= k; ++sweep) {
+    multi_level_sample(h, items, sp);
+    for (const LsItem& it : items)
+      if (!it.out.converged)
+        throw Error(MGMLMC_ERR_NOT_CONVERGED, sweep < k ? "sketch solves did not converge"
+                                                        : "low-rank solves did not converge");
+    if (sweep == k) break;
+    for (const LsItem& it : items) {
+      cholesky_qr2(h, Y[it.l], d[it.l], h->lv[it.l].n);
+      vcopy<double2>(st, Y[it.l], S[it.l], h->lv[it.l].n, d[it.l]);
+    }
+  }
+  for (const LsItem& it : items) {
+    const int l = it.l;
+    double2* dots = (double2*)h->work("sk_dots", l, sizeof(double2) * d[l]);
+    void* red = h->work("sk_red", l, reduce_work_bytes(h->lv[l].n, d[l], 1));
+    vdot<double2>(st, S[l], Y[l], h->lv[l].n, d[l], dots, red, nullptr);
+    std::vector<double2> hd(d[l]);
+    MG_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double2) * d[l], cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+    double2 t = make_double2(0, 0);
+    for (int i = 0; i < d[l]; ++i) t = cadd(t, hd[i]);
+    tau_lr[l] = t;
+  }
+}
+
 void project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double2* zeta, const double2* y, long n, int nrhs,
              double2* tau_host) {
   cudaStream_t st = ctx->stream;
@@ -724,21 +849,17 @@ struct LevelStats {  // Welford on real and imaginary parts
 
 void estimate(mgmlmc_hier* h, const est_params& p, est_result* res) {
   mgmlmc_ctx* ctx = h->ctx;
-  cudaStream_t st = ctx->stream;
   const int nd = h->nlev - 1;
   MG_CHECK_ARG(p.eps > 0, "eps must be positive");
   MG_CHECK_ARG(p.nrhs_max >= 1 && p.nrhs_first >= 1, "batch sizes must be positive");
   MG_CHECK_ARG(p.min_samples >= 2, "min_samples must be >= 2");
   std::memset(res, 0, sizeof(*res));
   res->nlev = h->nlev;
-  std::vector<std::unique_ptr<mgmlmc_sketch>> sk(nd);
-  std::vector<double2> tau_lr(nd, make_double2(0, 0));
-  for (int l = 0; l < nd; ++l) {
-    if (p.d[l] > 0) {
-      sk[l].reset(sketch_qr(h, l, p.d[l], p.k, p.seed, p.form, p.solve, &tau_lr[l]));
-      res->solves += (int64_t)2 * p.d[l] * (p.k + 1);
-    }
-  }
+  std::vector<std::unique_ptr<mgmlmc_sketch>> sk;
+  std::vector<double2> tau_lr;
+  sketch_qr_all(h, p.d, p.k, p.seed, p.form, p.solve, sk, tau_lr);
+  for (int l = 0; l < nd; ++l)
+    if (p.d[l] > 0) res->solves += (int64_t)2 * p.d[l] * (p.k + 1);
   const double2 tauL = h->lv[h->nlev - 1].trace;
   std::vector<std::vector<double2>> samp(nd);
   std::vector<std::vector<double>> scost(nd);
@@ -746,23 +867,38 @@ void estimate(mgmlmc_hier* h, const est_params& p, est_result* res) {
   std::vector<int> active(nd, 1);
   int64_t s = 0;
   const int64_t maxs = p.max_samples > 0 ? p.max_samples : (int64_t)1 << 40;
-  auto run_batch = [&](int l, int nb) {
-    const long n = h->lv[l].n;
-    double2* z = (double2*)h->work("est_z", l, sizeof(double2) * n * nb);
-    double2* y = (double2*)h->work("est_y", l, sizeof(double2) * n * nb);
-    const int64_t s0 = (int64_t)samp[l].size();
-    make_level_vectors(h, l, p.form, p.seed, MGMLMC_PHASE_STOCH, s0, nb, z);
-    SolveOut o = level_sample(h, l, z, y, nb, p.solve);
-    if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "sample solves did not converge");
-    std::vector<double2> t(nb);
-    project(ctx, sk[l].get(), z, y, n, nb, t.data());
-    const double nnz_l = (double)h->lv[l].n * (l == 0 ? 9.0 : 5.0 * h->lv[l].dof);
-    for (int r = 0; r < nb; ++r) {
-      samp[l].push_back(t[r]);
-      scost[l].push_back(p.cost_mode == 1 ? (double)(o.its[r] + 1) * nnz_l : p.cost[l]);
+  // one round: a batch of nb[l] new samples for every level with nb[l] > 0, all level differences applied
+  // together (shared-level solves batched; each sample is the one level_sample would give)
+  auto run_batches = [&](const std::vector<int>& nb) {
+    std::vector<LsItem> items;
+    for (int l = 0; l < nd; ++l) {
+      if (nb[l] <= 0) continue;
+      const long n = h->lv[l].n;
+      LsItem it;
+      it.l = l;
+      it.nrhs = nb[l];
+      double2* z = (double2*)h->work("est_z", l, sizeof(double2) * n * nb[l]);
+      it.zeta = z;
+      it.y = (double2*)h->work("est_y", l, sizeof(double2) * n * nb[l]);
+      make_level_vectors(h, l, p.form, p.seed, MGMLMC_PHASE_STOCH, (int64_t)samp[l].size(), nb[l], z);
+      items.push_back(it);
     }
-    res->solves += 2 * nb;
-    res->inner_iters += o.total_iters;
+    if (items.empty()) return;
+    multi_level_sample(h, items, p.solve);
+    for (const LsItem& it : items) {
+      const int l = it.l, b = it.nrhs;
+      const SolveOut& o = it.out;
+      if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "sample solves did not converge");
+      std::vector<double2> t(b);
+      project(ctx, sk[l].get(), it.zeta, it.y, h->lv[l].n, b, t.data());
+      const double nnz_l = (double)h->lv[l].n * (l == 0 ? 9.0 : 5.0 * h->lv[l].dof);
+      for (int r = 0; r < b; ++r) {
+        samp[l].push_back(t[r]);
+        scost[l].push_back(p.cost_mode == 1 ? (double)(o.its[r] + 1) * nnz_l : p.cost[l]);
+      }
+      res->solves += 2 * b;
+      res->inner_iters += o.total_iters;
+    }
   };
   auto batch_size = [&](int l) -> int {
     if (samp[l].empty()) return p.nrhs_first;
@@ -794,8 +930,10 @@ void estimate(mgmlmc_hier* h, const est_params& p, est_result* res) {
     bool any = false;
     for (int l = 0; l < nd; ++l) any |= active[l] != 0;
     if (!any) break;
+    std::vector<int> nb(nd, 0);
     for (int l = 0; l < nd; ++l)
-      if (active[l] && (int64_t)samp[l].size() <= s) run_batch(l, batch_size(l));
+      if (active[l] && (int64_t)samp[l].size() <= s) nb[l] = batch_size(l);
+    run_batches(nb);
     ++s;
     for (int l = 0; l < nd; ++l)
       if (active[l]) stats[l].add(samp[l][s - 1], scost[l][s - 1]);
@@ -835,7 +973,6 @@ void estimate(mgmlmc_hier* h, const est_params& p, est_result* res) {
   res->tau_L[1] = tauL.y;
   res->sigma = std::sqrt(var);
   res->steps = (int)s;
-  (void)st;
 }
 
 }  // namespace mg

@@ -149,6 +149,15 @@ struct SolveOut {
 SolveOut solve(mgmlmc_hier* h, int l, const void* b, void* x, int nrhs, const solve_params& sp);
 // y = (D_l^{-1} - P_l D_{l+1}^{-1} P_l^H) zeta, FP64 vectors
 SolveOut level_sample(mgmlmc_hier* h, int l, const double2* zeta, double2* y, int nrhs, const solve_params& sp);
+// several level differences in one pass, solves on a shared level batched together (see engine.cu)
+struct LsItem {
+  int l = 0;
+  const double2* zeta = nullptr;
+  double2* y = nullptr;
+  int nrhs = 0;
+  SolveOut out;
+};
+void multi_level_sample(mgmlmc_hier* h, std::vector<LsItem>& items, const solve_params& sp);
 void restrict_to_level(mgmlmc_hier* h, int l, const double2* zfine, double2* out, int nrhs);
 // fills zeta (level-l vectors, FP64) for samples sample0.. of level difference l
 void make_level_vectors(mgmlmc_hier* h, int l, int form, uint64_t seed, int phase, int64_t sample0, int nrhs,
