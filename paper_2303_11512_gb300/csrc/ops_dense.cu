@@ -105,73 +105,166 @@ void invert_small_batched(cudaStream_t st, double2* A, int nmat, int bd, int* fa
   MG_LAUNCH(k_invert_small, nmat, 256, sm, st, A, bd, fail);
 }
 
-// ---- large in-place inverse, one pivot step per pair of launches ------------------------------
-__global__ void __launch_bounds__(1024) k_gj_pivot(double2* __restrict__ A, int n, int k, int* piv,
-                                                   double2* __restrict__ f, int* fail) {
-  __shared__ double sb[32];
-  __shared__ int si[32];
-  __shared__ int s_p;
-  double best = -1.0;
-  int bi = k;
-  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-    double v = cabs2(A[(size_t)i * n + k]);
-    if (v > best) { best = v; bi = i; }
+// ---- large in-place inverse: Gauss-Jordan with partial pivoting in one cooperative kernel ------------
+// The CTAs of the grid (all resident, cooperative launch) sweep the columns in step: per column k the pivot
+// p = argmax_{i >= k} |A_ik| (ties: smallest i) is found from per-CTA partial maxima, rows k and p are swapped,
+// the pivot row is scaled by a = 1 / A_pk (its column-k entry becomes a) and every other row i loses
+// f_i x (pivot row), its column-k entry becoming -f_i a.  Two grid barriers per column; each barrier spins
+// on a generation counter with an iteration limit (timeout flag, all CTAs then leave).  Columns are
+// unscrambled afterwards by the recorded swaps in reverse order.
+constexpr int GJ_T = 512;
+constexpr long GJ_SPIN = 1L << 28;  // polls of the generation counter (well over a second)
+
+struct GjShared {
+  double best;
+  int idx;
+  int ok;
+};
+
+__device__ __forceinline__ bool gj_barrier(unsigned* bar, unsigned nb, int* timeout, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == nb - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long it = 0;
+      while (*gen == g) {
+        if (++it > GJ_SPIN) {
+          atomicExch(timeout, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *s_ok = ok && !*(volatile int*)timeout;
   }
+  __syncthreads();
+  return *s_ok;
+}
+
+// block-wide argmax (value, smallest index on ties), result in thread 0
+__device__ __forceinline__ void gj_block_argmax(double& best, int& idx, double* sb, int* si) {
+#pragma unroll
   for (int o = 16; o; o >>= 1) {
-    double ob = __shfl_xor_sync(0xffffffff, best, o);
-    int oi = __shfl_xor_sync(0xffffffff, bi, o);
-    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    const double ob = __shfl_xor_sync(0xffffffff, best, o);
+    const int oi = __shfl_xor_sync(0xffffffff, idx, o);
+    if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
   }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { sb[w] = best; si[w] = bi; }
+  __syncthreads();
+  if (l == 0) { sb[w] = best; si[w] = idx; }
   __syncthreads();
   if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    best = l < nw ? sb[l] : -1.0;
-    bi = l < nw ? si[l] : k;
+    best = l < GJ_T / 32 ? sb[l] : -1.0;
+    idx = l < GJ_T / 32 ? si[l] : 0x7fffffff;
+#pragma unroll
     for (int o = 16; o; o >>= 1) {
-      double ob = __shfl_xor_sync(0xffffffff, best, o);
-      int oi = __shfl_xor_sync(0xffffffff, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (l == 0) {
-      s_p = bi;
-      piv[k] = bi;
-      if (!(best > 0.0)) atomicExch(fail, 1);
-    }
-  }
-  __syncthreads();
-  const int p = s_p;
-  if (p != k)
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      double2 t = A[(size_t)k * n + j];
-      A[(size_t)k * n + j] = A[(size_t)p * n + j];
-      A[(size_t)p * n + j] = t;
-    }
-  __syncthreads();
-  const double2 a = crecip(A[(size_t)k * n + k]);
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    double2 v = (j == k) ? make_double2(1, 0) : A[(size_t)k * n + j];
-    A[(size_t)k * n + j] = cmul(v, a);
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    if (i == k) {
-      f[i] = make_double2(0, 0);
-    } else {
-      f[i] = A[(size_t)i * n + k];
-      A[(size_t)i * n + k] = make_double2(0, 0);
+      const double ob = __shfl_xor_sync(0xffffffff, best, o);
+      const int oi = __shfl_xor_sync(0xffffffff, idx, o);
+      if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
     }
   }
 }
 
-__global__ void k_gj_elim(double2* __restrict__ A, int n, int k, const double2* __restrict__ f) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
-  if (j >= n || i == k) return;
-  const double2 fi = f[i];
-  if (fi.x == 0.0 && fi.y == 0.0) return;
-  A[(size_t)i * n + j] = csub(A[(size_t)i * n + j], cmul(fi, A[(size_t)k * n + j]));
+// slots: per-CTA (max, index) of the current pivot column; rowbuf / colbuf: pivot row and multipliers;
+// okbuf: the old row k (the new row p)
+__global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A, int n, int* __restrict__ piv,
+                                                 double2* __restrict__ rowbuf, double2* __restrict__ colbuf,
+                                                 double2* __restrict__ okbuf,
+                                                 double* __restrict__ slot_v, int* __restrict__ slot_i,
+                                                 unsigned* bar, int* fail, int* timeout) {
+  __shared__ double sb[GJ_T / 32];
+  __shared__ int si[GJ_T / 32];
+  __shared__ int s_ok, s_p;
+  __shared__ double2 s_a;
+  const unsigned nb = gridDim.x;
+  const int gtid = blockIdx.x * GJ_T + threadIdx.x, gsz = nb * GJ_T;
+  // column 0 partial maxima
+  {
+    double best = -1.0;
+    int idx = 0x7fffffff;
+    for (int i = gtid; i < n; i += gsz) {
+      const double v = cabs2(A[(size_t)i * n]);
+      if (v > best || (v == best && i < idx)) { best = v; idx = i; }
+    }
+    gj_block_argmax(best, idx, sb, si);
+    if (threadIdx.x == 0) { slot_v[blockIdx.x] = best; slot_i[blockIdx.x] = idx; }
+  }
+  if (!gj_barrier(bar, nb, timeout, &s_ok)) return;
+  for (int k = 0; k < n; ++k) {
+    // pivot from the partial maxima (every CTA reaches the same decision)
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int idx = 0x7fffffff;
+      for (unsigned c = threadIdx.x; c < nb; c += 32) {
+        const double v = slot_v[c];
+        const int i = slot_i[c];
+        if (v > best || (v == best && i < idx)) { best = v; idx = i; }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffff, best, o);
+        const int oi = __shfl_xor_sync(0xffffffff, idx, o);
+        if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+      }
+      if (threadIdx.x == 0) {
+        const bool good = best > 0.0 && idx >= k && idx < n;
+        s_p = good ? idx : k;
+        if (!good && blockIdx.x == 0) atomicExch(fail, 1);
+        s_a = good ? crecip(A[(size_t)s_p * n + k]) : make_double2(0, 0);
+        if (blockIdx.x == 0) piv[k] = s_p;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    const double2 a = s_a;
+    // rows k and p swapped logically (A is not written in this phase, so every CTA has read A_pk first):
+    // the new pivot row (old row p) scaled into rowbuf, old row k kept in okbuf for row p, multipliers of
+    // the swapped column k in colbuf
+    for (int j = gtid; j < n; j += gsz) {
+      okbuf[j] = A[(size_t)k * n + j];
+      rowbuf[j] = (j == k) ? a : cmul(A[(size_t)p * n + j], a);
+    }
+    for (int i = gtid; i < n; i += gsz)
+      colbuf[i] = (i == k) ? make_double2(0, 0) : (i == p ? A[(size_t)k * n + k] : A[(size_t)i * n + k]);
+    if (!gj_barrier(bar, nb, timeout, &s_ok)) return;
+    // eliminate; track the next pivot column's partial maximum
+    double best = -1.0;
+    int idx = 0x7fffffff;
+    const int kn = k + 1;
+#pragma unroll 2
+    for (int i = blockIdx.x; i < n; i += (int)nb) {
+#pragma unroll 4
+      for (int j = threadIdx.x; j < n; j += GJ_T) {
+        const size_t e = (size_t)i * n + j;
+        double2 v;
+        if (i == k) {
+          v = rowbuf[j];
+        } else {
+          const double2 f = colbuf[i], r = rowbuf[j];
+          if (j == k)
+            v = cneg(cmul(f, r));
+          else
+            v = csub(i == p ? okbuf[j] : A[e], cmul(f, r));
+        }
+        A[e] = v;
+        if (j == kn && i >= kn) {
+          const double m = cabs2(v);
+          if (m > best || (m == best && i < idx)) { best = m; idx = i; }
+        }
+      }
+    }
+    gj_block_argmax(best, idx, sb, si);
+    if (threadIdx.x == 0) { slot_v[blockIdx.x] = best; slot_i[blockIdx.x] = idx; }
+    if (!gj_barrier(bar, nb, timeout, &s_ok)) return;
+  }
 }
 
 __global__ void k_gj_unscramble(double2* __restrict__ A, int n, const int* __restrict__ piv) {
@@ -187,11 +280,35 @@ __global__ void k_gj_unscramble(double2* __restrict__ A, int n, const int* __res
   }
 }
 
-void invert_large(cudaStream_t st, double2* A, int n, int* piv, double2* work, int* fail) {
-  for (int k = 0; k < n; ++k) {
-    MG_LAUNCH(k_gj_pivot, 1, 1024, 0, st, A, n, k, piv, work, fail);
-    MG_LAUNCH(k_gj_elim, dim3(cdiv(n, 256), n), 256, 0, st, A, n, k, work);
+size_t invert_large_work_bytes(int n) {
+  return sizeof(double2) * 3 * (size_t)n + (sizeof(double) + sizeof(int)) * 1024 + 64;
+}
+
+void invert_large(cudaStream_t st, double2* A, int n, int* piv, void* work, int* fail, int* timeout) {
+  int dev = 0, nsm = 0, per = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_coop, GJ_T, 0));
+  // one resident CTA per SM (at most one row per CTA), all co-resident as the cooperative launch requires
+  const int grid = std::max(1, std::min(std::min(nsm * std::min(std::max(per, 1), 1), 1024), n));
+  char* w = (char*)work;
+  double2* rowbuf = (double2*)w;
+  double2* colbuf = rowbuf + n;
+  double2* okbuf = colbuf + n;
+  double* slot_v = (double*)(okbuf + n);
+  int* slot_i = (int*)(slot_v + 1024);
+  unsigned* bar = (unsigned*)(slot_i + 1024);
+  MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+  void* args[] = {&A, &n, &piv, &rowbuf, &colbuf, &okbuf, &slot_v, &slot_i, &bar, &fail, &timeout};
+  KTimer* t = g_timer;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (t && t->want("k_gj_coop")) { ea = t->get(); eb = t->get(); MG_CUDA(cudaEventRecord(ea, st)); }
+  MG_CUDA(cudaLaunchCooperativeKernel((void*)k_gj_coop, dim3(grid), dim3(GJ_T), args, 0, st));
+  if (ea) {
+    MG_CUDA(cudaEventRecord(eb, st));
+    t->recs.push_back({"k_gj_coop", __PRETTY_FUNCTION__, 32.0 * n * (double)n * n, 8.0 * n * (double)n * n, ea, eb});
   }
+  if (g_launch_counter) ++*g_launch_counter;
   MG_LAUNCH(k_gj_unscramble, 1, 1024, 0, st, A, n, piv);
 }
 

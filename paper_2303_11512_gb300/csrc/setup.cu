@@ -51,8 +51,8 @@ static void build_coarsest(mgmlmc_hier* h, int* dfail) {
   MG_CHECK_ARG(n <= 8192, "coarsest level too large for the dense inverse");
   lc.inv64.alloc(sizeof(double2) * (size_t)n * n, st);
   dense_from_stencil(st, lc.st64.as<double2>(), lc.side, lc.dof, lc.inv64.as<double2>());
-  DBuf piv(sizeof(int) * n, st), work(sizeof(double2) * n, st), tr(sizeof(double2), st);
-  invert_large(st, lc.inv64.as<double2>(), n, piv.as<int>(), work.as<double2>(), dfail);
+  DBuf piv(sizeof(int) * n, st), work(invert_large_work_bytes(n), st), tr(sizeof(double2), st);
+  invert_large(st, lc.inv64.as<double2>(), n, piv.as<int>(), work.p, dfail, dfail + 1);
   to_fp32(st, lc.inv64, lc.inv32, (size_t)n * n);
   trace_dense(st, lc.inv64.as<double2>(), n, tr.as<double2>());
   MG_CUDA(cudaMemcpyAsync(&lc.trace, tr.p, sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -103,6 +103,7 @@ static void check_fail(mgmlmc_hier* h, const int* dfail) {
   if (fl[0]) throw Error(MGMLMC_ERR_NAN, "singular SAP block");
   if (fl[1]) throw Error(MGMLMC_ERR_NAN, "test-vector block of zero norm");
   if (fl[2]) throw Error(MGMLMC_ERR_NAN, "singular coarsest operator");
+  if (fl[3]) throw Error(MGMLMC_ERR_TIMEOUT, "coarsest inversion: grid barrier timed out");
 }
 
 void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U) {
