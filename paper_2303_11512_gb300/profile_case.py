@@ -45,7 +45,8 @@ def main():
         for _ in range(10):
             api.schwinger_apply(ctx, U, a.L, m0, x, y, api.FP32)
     else:
-        h = api.mg_setup(ctx, U, a.L, m0, ntv=W["ntv"], bootstrap=W["bootstrap"], bootstrap_its=W["bootstrap_its"])
+        h = api.mg_setup(ctx, U, a.L, m0, ntv=W["ntv"], bootstrap=W["bootstrap"], bootstrap_its=W["bootstrap_its"],
+                         pre_smooth=W["pre_smooth"], post_smooth=W["post_smooth"])
         b = api.mgmlmc_rademacher(ctx, 1, 0, 0, 0, h.n[a.level], a.nrhs)
         x = torch.empty_like(b)
         st = api.fgmres_batched(ctx, h, a.level, b, x, prec=api.MIXED, tol=1e-10)
