@@ -107,19 +107,14 @@ void invert_small_batched(cudaStream_t st, double2* A, int nmat, int bd, int* fa
 
 // ---- large in-place inverse: Gauss-Jordan with partial pivoting in one cooperative kernel ------------
 // The CTAs of the grid (all resident, cooperative launch) sweep the columns in step: per column k the pivot
-// p = argmax_{i >= k} |A_ik| (ties: smallest i) is found from per-CTA partial maxima, rows k and p are swapped,
+// p = argmax_{i >= k} |A_ik| (ties: smallest i) comes from per-CTA partial maxima, rows k and p are swapped,
 // the pivot row is scaled by a = 1 / A_pk (its column-k entry becomes a) and every other row i loses
-// f_i x (pivot row), its column-k entry becoming -f_i a.  Two grid barriers per column; each barrier spins
-// on a generation counter with an iteration limit (timeout flag, all CTAs then leave).  Columns are
-// unscrambled afterwards by the recorded swaps in reverse order.
+// f_i x (pivot row), its column-k entry becoming -f_i a.  Column k reads one matrix buffer and writes the
+// other (ping-pong), so every CTA can read the pivot row and column while others already write: one grid
+// barrier per column.  The barrier spins on a generation counter with an iteration limit (timeout flag, all
+// CTAs then leave).  Columns are unscrambled afterwards by the recorded swaps in reverse order.
 constexpr int GJ_T = 512;
 constexpr long GJ_SPIN = 1L << 28;  // polls of the generation counter (well over a second)
-
-struct GjShared {
-  double best;
-  int idx;
-  int ok;
-};
 
 __device__ __forceinline__ bool gj_barrier(unsigned* bar, unsigned nb, int* timeout, int* s_ok) {
   __syncthreads();
@@ -173,25 +168,24 @@ __device__ __forceinline__ void gj_block_argmax(double& best, int& idx, double* 
   }
 }
 
-// slots: per-CTA (max, index) of the current pivot column; rowbuf / colbuf: pivot row and multipliers;
-// okbuf: the old row k (the new row p)
-__global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A, int n, int* __restrict__ piv,
-                                                 double2* __restrict__ rowbuf, double2* __restrict__ colbuf,
-                                                 double2* __restrict__ okbuf,
-                                                 double* __restrict__ slot_v, int* __restrict__ slot_i,
-                                                 unsigned* bar, int* fail, int* timeout) {
+// A0: the matrix (result written back here); A1: scratch of the same size; slots: per-CTA (max, index)
+// of the next pivot column, double-buffered by column parity
+__global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A0, double2* __restrict__ A1, int n,
+                                                    int* __restrict__ piv, double* __restrict__ slot_v,
+                                                    int* __restrict__ slot_i, unsigned* bar, int* fail,
+                                                    int* timeout) {
   __shared__ double sb[GJ_T / 32];
   __shared__ int si[GJ_T / 32];
   __shared__ int s_ok, s_p;
   __shared__ double2 s_a;
+  extern __shared__ double2 s_row[];  // the scaled pivot row of the current column
   const unsigned nb = gridDim.x;
-  const int gtid = blockIdx.x * GJ_T + threadIdx.x, gsz = nb * GJ_T;
-  // column 0 partial maxima
+  // column 0 partial maxima into slot set 0
   {
     double best = -1.0;
     int idx = 0x7fffffff;
-    for (int i = gtid; i < n; i += gsz) {
-      const double v = cabs2(A[(size_t)i * n]);
+    for (int i = blockIdx.x * GJ_T + threadIdx.x; i < n; i += nb * GJ_T) {
+      const double v = cabs2(A0[(size_t)i * n]);
       if (v > best || (v == best && i < idx)) { best = v; idx = i; }
     }
     gj_block_argmax(best, idx, sb, si);
@@ -199,13 +193,17 @@ __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A, in
   }
   if (!gj_barrier(bar, nb, timeout, &s_ok)) return;
   for (int k = 0; k < n; ++k) {
+    const double2* __restrict__ cur = (k & 1) ? A1 : A0;
+    double2* __restrict__ nxt = (k & 1) ? A0 : A1;
+    const double* sv = slot_v + (k & 1) * 1024;
+    const int* sx = slot_i + (k & 1) * 1024;
     // pivot from the partial maxima (every CTA reaches the same decision)
     if (threadIdx.x < 32) {
       double best = -1.0;
       int idx = 0x7fffffff;
       for (unsigned c = threadIdx.x; c < nb; c += 32) {
-        const double v = slot_v[c];
-        const int i = slot_i[c];
+        const double v = sv[c];
+        const int i = sx[c];
         if (v > best || (v == best && i < idx)) { best = v; idx = i; }
       }
 #pragma unroll
@@ -218,43 +216,35 @@ __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A, in
         const bool good = best > 0.0 && idx >= k && idx < n;
         s_p = good ? idx : k;
         if (!good && blockIdx.x == 0) atomicExch(fail, 1);
-        s_a = good ? crecip(A[(size_t)s_p * n + k]) : make_double2(0, 0);
+        s_a = good ? crecip(cur[(size_t)s_p * n + k]) : make_double2(0, 0);
         if (blockIdx.x == 0) piv[k] = s_p;
       }
     }
     __syncthreads();
     const int p = s_p;
     const double2 a = s_a;
-    // rows k and p swapped logically (A is not written in this phase, so every CTA has read A_pk first):
-    // the new pivot row (old row p) scaled into rowbuf, old row k kept in okbuf for row p, multipliers of
-    // the swapped column k in colbuf
-    for (int j = gtid; j < n; j += gsz) {
-      okbuf[j] = A[(size_t)k * n + j];
-      rowbuf[j] = (j == k) ? a : cmul(A[(size_t)p * n + j], a);
-    }
-    for (int i = gtid; i < n; i += gsz)
-      colbuf[i] = (i == k) ? make_double2(0, 0) : (i == p ? A[(size_t)k * n + k] : A[(size_t)i * n + k]);
-    if (!gj_barrier(bar, nb, timeout, &s_ok)) return;
-    // eliminate; track the next pivot column's partial maximum
+    const double2 fk = cur[(size_t)k * n + k];  // multiplier of row p after the swap
+    for (int j = threadIdx.x; j < n; j += GJ_T) s_row[j] = (j == k) ? a : cmul(cur[(size_t)p * n + j], a);
+    __syncthreads();
+    // eliminate into nxt; track the next pivot column's partial maximum
     double best = -1.0;
     int idx = 0x7fffffff;
     const int kn = k + 1;
 #pragma unroll 2
     for (int i = blockIdx.x; i < n; i += (int)nb) {
+      const double2 f = (i == k) ? make_double2(0, 0) : (i == p ? fk : cur[(size_t)i * n + k]);
+      const double2* src = cur + (size_t)(i == p ? k : i) * n;  // row p takes the old row k
 #pragma unroll 4
       for (int j = threadIdx.x; j < n; j += GJ_T) {
-        const size_t e = (size_t)i * n + j;
+        const double2 r = s_row[j];  // new pivot row
         double2 v;
-        if (i == k) {
-          v = rowbuf[j];
-        } else {
-          const double2 f = colbuf[i], r = rowbuf[j];
-          if (j == k)
-            v = cneg(cmul(f, r));
-          else
-            v = csub(i == p ? okbuf[j] : A[e], cmul(f, r));
-        }
-        A[e] = v;
+        if (i == k)
+          v = r;
+        else if (j == k)
+          v = cneg(cmul(f, r));
+        else
+          v = csub(src[j], cmul(f, r));
+        nxt[(size_t)i * n + j] = v;
         if (j == kn && i >= kn) {
           const double m = cabs2(v);
           if (m > best || (m == best && i < idx)) { best = m; idx = i; }
@@ -262,7 +252,10 @@ __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A, in
       }
     }
     gj_block_argmax(best, idx, sb, si);
-    if (threadIdx.x == 0) { slot_v[blockIdx.x] = best; slot_i[blockIdx.x] = idx; }
+    if (threadIdx.x == 0) {
+      slot_v[((k + 1) & 1) * 1024 + blockIdx.x] = best;
+      slot_i[((k + 1) & 1) * 1024 + blockIdx.x] = idx;
+    }
     if (!gj_barrier(bar, nb, timeout, &s_ok)) return;
   }
 }
@@ -281,34 +274,41 @@ __global__ void k_gj_unscramble(double2* __restrict__ A, int n, const int* __res
 }
 
 size_t invert_large_work_bytes(int n) {
-  return sizeof(double2) * 3 * (size_t)n + (sizeof(double) + sizeof(int)) * 1024 + 64;
+  return sizeof(double2) * (size_t)n * n + (sizeof(double) + sizeof(int)) * 2048 + 64;
 }
 
 void invert_large(cudaStream_t st, double2* A, int n, int* piv, void* work, int* fail, int* timeout) {
   int dev = 0, nsm = 0, per = 0;
   MG_CUDA(cudaGetDevice(&dev));
   MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_coop, GJ_T, 0));
+  const size_t sm = sizeof(double2) * (size_t)n;
+  static bool attr = false;
+  if (!attr) {
+    MG_CUDA(cudaFuncSetAttribute(k_gj_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    attr = true;
+  }
+  MG_CHECK_ARG(sm <= 160 * 1024, "coarsest level too large for the pivot row in shared memory");
+  MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_coop, GJ_T, sm));
   // one resident CTA per SM (at most one row per CTA), all co-resident as the cooperative launch requires
   const int grid = std::max(1, std::min(std::min(nsm * std::min(std::max(per, 1), 1), 1024), n));
   char* w = (char*)work;
-  double2* rowbuf = (double2*)w;
-  double2* colbuf = rowbuf + n;
-  double2* okbuf = colbuf + n;
-  double* slot_v = (double*)(okbuf + n);
-  int* slot_i = (int*)(slot_v + 1024);
-  unsigned* bar = (unsigned*)(slot_i + 1024);
+  double2* A1 = (double2*)w;
+  double* slot_v = (double*)(A1 + (size_t)n * n);
+  int* slot_i = (int*)(slot_v + 2048);
+  unsigned* bar = (unsigned*)(slot_i + 2048);
   MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
-  void* args[] = {&A, &n, &piv, &rowbuf, &colbuf, &okbuf, &slot_v, &slot_i, &bar, &fail, &timeout};
+  void* args[] = {&A, &A1, &n, &piv, &slot_v, &slot_i, &bar, &fail, &timeout};
   KTimer* t = g_timer;
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (t && t->want("k_gj_coop")) { ea = t->get(); eb = t->get(); MG_CUDA(cudaEventRecord(ea, st)); }
-  MG_CUDA(cudaLaunchCooperativeKernel((void*)k_gj_coop, dim3(grid), dim3(GJ_T), args, 0, st));
+  MG_CUDA(cudaLaunchCooperativeKernel((void*)k_gj_coop, dim3(grid), dim3(GJ_T), args, sm, st));
   if (ea) {
     MG_CUDA(cudaEventRecord(eb, st));
     t->recs.push_back({"k_gj_coop", __PRETTY_FUNCTION__, 32.0 * n * (double)n * n, 8.0 * n * (double)n * n, ea, eb});
   }
   if (g_launch_counter) ++*g_launch_counter;
+  if (n & 1)  // odd column count: the last column wrote the scratch buffer
+    MG_CUDA(cudaMemcpyAsync(A, A1, sizeof(double2) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
   MG_LAUNCH(k_gj_unscramble, 1, 1024, 0, st, A, n, piv);
 }
 
