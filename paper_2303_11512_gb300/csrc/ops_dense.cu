@@ -20,15 +20,21 @@ __device__ __forceinline__ double2 crecip(double2 a) {
 }  // namespace
 
 // ---- batched small inverse (one CTA per matrix) ------------------------------------------------
-__global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, int bd, int* fail) {
+// Gauss-Jordan with partial pivoting in shared memory, three barriers per column: pivot search (warp 0, also
+// the reciprocal of the pivot), then the row swap, pivot-row scaling and multipliers (read all, barrier,
+// write all), then the rank-1 elimination.  BD = block dimension at compile time (0: runtime bd).
+template <int BD>
+__global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, int bd_, int* fail) {
+  const int bd = BD ? BD : bd_;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* A = reinterpret_cast<double2*>(smem_raw);
   double2* sf = A + bd * bd;
   int* perm = reinterpret_cast<int*>(sf + bd);
   __shared__ int s_p;
   __shared__ int s_bad;
+  __shared__ double2 s_a;
   double2* G = Ag + (size_t)blockIdx.x * bd * bd;
-  for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) A[e] = G[e];
+  for (int e = threadIdx.x; e < bd * bd; e += 256) A[e] = G[e];
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
   for (int k = 0; k < bd; ++k) {
@@ -48,32 +54,32 @@ __global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, 
         s_p = bi;
         perm[k] = bi;
         if (!(best > 0.0)) s_bad = 1;
+        s_a = best > 0.0 ? crecip(A[bi * bd + k]) : make_double2(0, 0);
       }
     }
     __syncthreads();
     if (s_bad) break;
     const int p = s_p;
-    if (p != k)
-      for (int j = threadIdx.x; j < bd; j += blockDim.x) {
-        double2 t = A[k * bd + j];
-        A[k * bd + j] = A[p * bd + j];
-        A[p * bd + j] = t;
-      }
-    __syncthreads();
-    const double2 a = crecip(A[k * bd + k]);
-    __syncthreads();
-    for (int j = threadIdx.x; j < bd; j += blockDim.x) {
-      double2 v = (j == k) ? make_double2(1, 0) : A[k * bd + j];
-      A[k * bd + j] = cmul(v, a);
+    const double2 a = s_a;
+    // swap rows k and p, scale the pivot row, multipliers of the swapped column k
+    double2 tk, tp, ck, akk;
+    const int t = threadIdx.x;
+    if (t < bd) {
+      tk = A[k * bd + t];
+      tp = A[p * bd + t];
+      ck = A[t * bd + k];
+      akk = A[k * bd + k];
     }
-    for (int i = threadIdx.x; i < bd; i += blockDim.x) sf[i] = (i == k) ? make_double2(0, 0) : A[i * bd + k];
     __syncthreads();
-    for (int i = threadIdx.x; i < bd; i += blockDim.x)
-      if (i != k) A[i * bd + k] = make_double2(0, 0);
+    if (t < bd) {
+      if (p != k) A[p * bd + t] = tk;
+      A[k * bd + t] = (t == k) ? a : cmul(tp, a);
+      sf[t] = (t == k) ? make_double2(0, 0) : (t == p ? akk : ck);
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) {
-      const int i = e / bd, j = e % bd;
-      if (i != k) A[e] = csub(A[e], cmul(sf[i], A[k * bd + j]));
+    for (int e = threadIdx.x; e < bd * bd; e += 256) {
+      const int i = e / bd, j = e - i * bd;
+      if (i != k) A[e] = csub(j == k ? make_double2(0, 0) : A[e], cmul(sf[i], A[k * bd + j]));
     }
     __syncthreads();
   }
@@ -84,25 +90,36 @@ __global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, 
   for (int k = bd - 1; k >= 0; --k) {
     const int p = perm[k];
     if (p != k)
-      for (int i = threadIdx.x; i < bd; i += blockDim.x) {
+      for (int i = threadIdx.x; i < bd; i += 256) {
         double2 t = A[i * bd + k];
         A[i * bd + k] = A[i * bd + p];
         A[i * bd + p] = t;
       }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < bd * bd; e += blockDim.x) G[e] = A[e];
+  for (int e = threadIdx.x; e < bd * bd; e += 256) G[e] = A[e];
 }
 
 void invert_small_batched(cudaStream_t st, double2* A, int nmat, int bd, int* fail) {
   MG_CHECK_ARG(bd <= 64, "small inverse limited to 64 x 64");
   size_t sm = sizeof(double2) * ((size_t)bd * bd + bd) + sizeof(int) * bd + 16;
-  static bool done = false;
-  if (!done) {
-    MG_CUDA(cudaFuncSetAttribute(k_invert_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    done = true;
+  static bool done[3] = {false, false, false};
+  auto attr = [&](auto kern, int i) {
+    if (!done[i]) {
+      MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+      done[i] = true;
+    }
+  };
+  if (bd == 64) {
+    attr(k_invert_small<64>, 0);
+    MG_LAUNCH(k_invert_small<64>, nmat, 256, sm, st, A, bd, fail);
+  } else if (bd == 32) {
+    attr(k_invert_small<32>, 1);
+    MG_LAUNCH(k_invert_small<32>, nmat, 256, sm, st, A, bd, fail);
+  } else {
+    attr(k_invert_small<0>, 2);
+    MG_LAUNCH(k_invert_small<0>, nmat, 256, sm, st, A, bd, fail);
   }
-  MG_LAUNCH(k_invert_small, nmat, 256, sm, st, A, bd, fail);
 }
 
 // ---- large in-place inverse: Gauss-Jordan with partial pivoting in one cooperative kernel ------------
