@@ -27,8 +27,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# V(2,2): of V(1,1) .. V(4,4), K-cycles and bootstrap 1-3 measured on this workload, the fastest set-up + estimate
-WORKLOAD = dict(L=512, beta=5.0, seed=0, ntv=8, d=32, k=2, eps=1e-3, nrhs_max=256, nrhs_first=16,
+# V(2,2): of V(1,1) .. V(4,4), K-cycles and bootstrap 1-3 measured on this workload, the fastest set-up + estimate.
+# First batch of 8 samples per level (then batches sized from the variances, up to 256): the stop rule needs 6-8
+# samples on levels 0 and 1 here, so a first batch of 16 only computed samples that are discarded.
+WORKLOAD = dict(L=512, beta=5.0, seed=0, ntv=8, d=32, k=2, eps=1e-3, nrhs_max=256, nrhs_first=8,
                 bootstrap=2, bootstrap_its=6, kcycle_its=0, pre_smooth=2, post_smooth=2)
 FALLBACK_M0 = {512: -0.07, 128: -0.1199}
 
