@@ -55,6 +55,7 @@ void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>
                const int* active) {
   const LevelData& L = h->lv[l];
   cudaStream_t st = h->ctx->stream;
+  if (sizeof(R) == 8 && !L.sap64_ok) throw Error(MGMLMC_ERR_INVALID_ARG, "FP64 SAP inverse not built at this level");
   if constexpr (sizeof(R) == 4) {
     if (h->use_tc(l) && L.sap_bs == 2 && L.tcInv[0].p) {
       float2* res = (float2*)h->work("tc_res", l, sizeof(float2) * L.n * nrhs);
@@ -89,6 +90,7 @@ void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T
   cudaStream_t st = h->ctx->stream;
   const LevelData& L = h->lv[l];
   if (l == h->nlev - 1) {
+    if (sizeof(R) == 8 && !L.inv64_ok) throw Error(MGMLMC_ERR_INVALID_ARG, "FP64 coarsest inverse not built");
     dense_apply<R>(st, inv_of<R>(L), (int)L.n, r, e, nrhs, active);
     return;
   }
@@ -492,6 +494,8 @@ SolveOut solve(mgmlmc_hier* h, int l, const void* b, void* x, int nrhs, const so
   const long n = h->lv[l].n;
   MG_CHECK_ARG(l >= 0 && l < h->nlev, "level out of range");
   if (l == h->nlev - 1) {  // coarsest: dense inverse, exact up to rounding
+    if (sp.prec != MGMLMC_FP32 && !h->lv[l].inv64_ok)
+      throw Error(MGMLMC_ERR_INVALID_ARG, "FP64 coarsest inverse not built");
     if (sp.prec == MGMLMC_FP32)
       dense_apply<float>(st, h->lv[l].inv32.as<float2>(), (int)n, (const float2*)b, (float2*)x, nrhs, nullptr);
     else

@@ -42,6 +42,8 @@ struct LevelData {
   // coarsest level: dense inverse
   DBuf inv64, inv32;
   double2 trace = make_double2(0, 0);
+  // FP64 SAP inverses / coarsest inverse current (intermediate bootstrap rounds build FP32 ones only)
+  bool sap64_ok = false, inv64_ok = false;
 };
 
 }  // namespace mg

@@ -58,12 +58,14 @@ void galerkin(cudaStream_t st, const double2* A, bool wilson, double diag, int L
 
 // ---------------------------------------------------------------- dense (coarsest)
 void dense_from_stencil(cudaStream_t st, const double2* stencil, int Ls, int d, double2* A);
-// batched in-place Gauss-Jordan inverse with partial pivoting (one CTA per matrix, bd <= 64)
-void invert_small_batched(cudaStream_t st, double2* A, int nmat, int bd, int* fail);
+// batched in-place Gauss-Jordan inverse with partial pivoting (one CTA per matrix, bd <= 64), C = double2 / float2
+template <typename C>
+void invert_small_batched(cudaStream_t st, C* A, int nmat, int bd, int* fail);
 // in-place inverse of one n x n matrix (large n), one cooperative kernel; work: invert_large_work_bytes(n);
-// fail set on a zero pivot, timeout on an expired grid barrier
+// fail set on a zero pivot, timeout on an expired grid barrier; C = double2 / float2
 size_t invert_large_work_bytes(int n);
-void invert_large(cudaStream_t st, double2* A, int n, int* piv, void* work, int* fail, int* timeout);
+template <typename C>
+void invert_large(cudaStream_t st, C* A, int n, int* piv, void* work, int* fail, int* timeout);
 template <typename R>
 void dense_apply(cudaStream_t st, const typename CT<R>::T* A, int n, const typename CT<R>::T* x,
                  typename CT<R>::T* y, int nrhs, const int* active);

@@ -13,9 +13,14 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double cabs2(float2 a) { return (double)a.x * a.x + (double)a.y * a.y; }
 __device__ __forceinline__ double2 crecip(double2 a) {
   const double s = 1.0 / cabs2(a);
   return make_double2(a.x * s, -a.y * s);
+}
+__device__ __forceinline__ float2 crecip(float2 a) {
+  const float s = 1.0f / (a.x * a.x + a.y * a.y);
+  return make_float2(a.x * s, -a.y * s);
 }
 }  // namespace
 
@@ -23,17 +28,17 @@ __device__ __forceinline__ double2 crecip(double2 a) {
 // Gauss-Jordan with partial pivoting in shared memory, three barriers per column: pivot search (warp 0, also
 // the reciprocal of the pivot), then the row swap, pivot-row scaling and multipliers (read all, barrier,
 // write all), then the rank-1 elimination.  BD = block dimension at compile time (0: runtime bd).
-template <int BD>
-__global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, int bd_, int* fail) {
+template <typename C, int BD>
+__global__ void __launch_bounds__(256) k_invert_small(C* __restrict__ Ag, int bd_, int* fail) {
   const int bd = BD ? BD : bd_;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* A = reinterpret_cast<double2*>(smem_raw);
-  double2* sf = A + bd * bd;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* sf = A + bd * bd;
   int* perm = reinterpret_cast<int*>(sf + bd);
   __shared__ int s_p;
   __shared__ int s_bad;
-  __shared__ double2 s_a;
-  double2* G = Ag + (size_t)blockIdx.x * bd * bd;
+  __shared__ C s_a;
+  C* G = Ag + (size_t)blockIdx.x * bd * bd;
   for (int e = threadIdx.x; e < bd * bd; e += 256) A[e] = G[e];
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
@@ -54,15 +59,15 @@ __global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, 
         s_p = bi;
         perm[k] = bi;
         if (!(best > 0.0)) s_bad = 1;
-        s_a = best > 0.0 ? crecip(A[bi * bd + k]) : make_double2(0, 0);
+        s_a = best > 0.0 ? crecip(A[bi * bd + k]) : czero<C>();
       }
     }
     __syncthreads();
     if (s_bad) break;
     const int p = s_p;
-    const double2 a = s_a;
+    const C a = s_a;
     // swap rows k and p, scale the pivot row, multipliers of the swapped column k
-    double2 tk, tp, ck, akk;
+    C tk, tp, ck, akk;
     const int t = threadIdx.x;
     if (t < bd) {
       tk = A[k * bd + t];
@@ -74,12 +79,12 @@ __global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, 
     if (t < bd) {
       if (p != k) A[p * bd + t] = tk;
       A[k * bd + t] = (t == k) ? a : cmul(tp, a);
-      sf[t] = (t == k) ? make_double2(0, 0) : (t == p ? akk : ck);
+      sf[t] = (t == k) ? czero<C>() : (t == p ? akk : ck);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < bd * bd; e += 256) {
       const int i = e / bd, j = e - i * bd;
-      if (i != k) A[e] = csub(j == k ? make_double2(0, 0) : A[e], cmul(sf[i], A[k * bd + j]));
+      if (i != k) A[e] = csub(j == k ? czero<C>() : A[e], cmul(sf[i], A[k * bd + j]));
     }
     __syncthreads();
   }
@@ -91,7 +96,7 @@ __global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, 
     const int p = perm[k];
     if (p != k)
       for (int i = threadIdx.x; i < bd; i += 256) {
-        double2 t = A[i * bd + k];
+        C t = A[i * bd + k];
         A[i * bd + k] = A[i * bd + p];
         A[i * bd + p] = t;
       }
@@ -100,9 +105,10 @@ __global__ void __launch_bounds__(256) k_invert_small(double2* __restrict__ Ag, 
   for (int e = threadIdx.x; e < bd * bd; e += 256) G[e] = A[e];
 }
 
-void invert_small_batched(cudaStream_t st, double2* A, int nmat, int bd, int* fail) {
+template <typename C>
+void invert_small_batched(cudaStream_t st, C* A, int nmat, int bd, int* fail) {
   MG_CHECK_ARG(bd <= 64, "small inverse limited to 64 x 64");
-  size_t sm = sizeof(double2) * ((size_t)bd * bd + bd) + sizeof(int) * bd + 16;
+  size_t sm = sizeof(C) * ((size_t)bd * bd + bd) + sizeof(int) * bd + 16;
   static bool done[3] = {false, false, false};
   auto attr = [&](auto kern, int i) {
     if (!done[i]) {
@@ -111,16 +117,18 @@ void invert_small_batched(cudaStream_t st, double2* A, int nmat, int bd, int* fa
     }
   };
   if (bd == 64) {
-    attr(k_invert_small<64>, 0);
-    MG_LAUNCH(k_invert_small<64>, nmat, 256, sm, st, A, bd, fail);
+    attr(k_invert_small<C, 64>, 0);
+    MG_LAUNCH((k_invert_small<C, 64>), nmat, 256, sm, st, A, bd, fail);
   } else if (bd == 32) {
-    attr(k_invert_small<32>, 1);
-    MG_LAUNCH(k_invert_small<32>, nmat, 256, sm, st, A, bd, fail);
+    attr(k_invert_small<C, 32>, 1);
+    MG_LAUNCH((k_invert_small<C, 32>), nmat, 256, sm, st, A, bd, fail);
   } else {
-    attr(k_invert_small<0>, 2);
-    MG_LAUNCH(k_invert_small<0>, nmat, 256, sm, st, A, bd, fail);
+    attr(k_invert_small<C, 0>, 2);
+    MG_LAUNCH((k_invert_small<C, 0>), nmat, 256, sm, st, A, bd, fail);
   }
 }
+template void invert_small_batched<double2>(cudaStream_t, double2*, int, int, int*);
+template void invert_small_batched<float2>(cudaStream_t, float2*, int, int, int*);
 
 // ---- large in-place inverse: Gauss-Jordan with partial pivoting in one cooperative kernel ------------
 // The CTAs of the grid (all resident, cooperative launch) sweep the columns in step: per column k the pivot
@@ -187,15 +195,17 @@ __device__ __forceinline__ void gj_block_argmax(double& best, int& idx, double* 
 
 // A0: the matrix (result written back here); A1: scratch of the same size; slots: per-CTA (max, index)
 // of the next pivot column, double-buffered by column parity
-__global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A0, double2* __restrict__ A1, int n,
+template <typename C>
+__global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(C* __restrict__ A0, C* __restrict__ A1, int n,
                                                     int* __restrict__ piv, double* __restrict__ slot_v,
                                                     int* __restrict__ slot_i, unsigned* bar, int* fail,
                                                     int* timeout) {
   __shared__ double sb[GJ_T / 32];
   __shared__ int si[GJ_T / 32];
   __shared__ int s_ok, s_p;
-  __shared__ double2 s_a;
-  extern __shared__ double2 s_row[];  // the scaled pivot row of the current column
+  __shared__ C s_a;
+  extern __shared__ __align__(16) unsigned char gj_smem[];
+  C* s_row = reinterpret_cast<C*>(gj_smem);  // the scaled pivot row of the current column
   const unsigned nb = gridDim.x;
   // column 0 partial maxima into slot set 0
   {
@@ -210,8 +220,8 @@ __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A0, d
   }
   if (!gj_barrier(bar, nb, timeout, &s_ok)) return;
   for (int k = 0; k < n; ++k) {
-    const double2* __restrict__ cur = (k & 1) ? A1 : A0;
-    double2* __restrict__ nxt = (k & 1) ? A0 : A1;
+    const C* __restrict__ cur = (k & 1) ? A1 : A0;
+    C* __restrict__ nxt = (k & 1) ? A0 : A1;
     const double* sv = slot_v + (k & 1) * 1024;
     const int* sx = slot_i + (k & 1) * 1024;
     // pivot from the partial maxima (every CTA reaches the same decision)
@@ -233,14 +243,14 @@ __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A0, d
         const bool good = best > 0.0 && idx >= k && idx < n;
         s_p = good ? idx : k;
         if (!good && blockIdx.x == 0) atomicExch(fail, 1);
-        s_a = good ? crecip(cur[(size_t)s_p * n + k]) : make_double2(0, 0);
+        s_a = good ? crecip(cur[(size_t)s_p * n + k]) : czero<C>();
         if (blockIdx.x == 0) piv[k] = s_p;
       }
     }
     __syncthreads();
     const int p = s_p;
-    const double2 a = s_a;
-    const double2 fk = cur[(size_t)k * n + k];  // multiplier of row p after the swap
+    const C a = s_a;
+    const C fk = cur[(size_t)k * n + k];  // multiplier of row p after the swap
     for (int j = threadIdx.x; j < n; j += GJ_T) s_row[j] = (j == k) ? a : cmul(cur[(size_t)p * n + j], a);
     __syncthreads();
     // eliminate into nxt; track the next pivot column's partial maximum
@@ -249,12 +259,12 @@ __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A0, d
     const int kn = k + 1;
 #pragma unroll 2
     for (int i = blockIdx.x; i < n; i += (int)nb) {
-      const double2 f = (i == k) ? make_double2(0, 0) : (i == p ? fk : cur[(size_t)i * n + k]);
-      const double2* src = cur + (size_t)(i == p ? k : i) * n;  // row p takes the old row k
+      const C f = (i == k) ? czero<C>() : (i == p ? fk : cur[(size_t)i * n + k]);
+      const C* src = cur + (size_t)(i == p ? k : i) * n;  // row p takes the old row k
 #pragma unroll 4
       for (int j = threadIdx.x; j < n; j += GJ_T) {
-        const double2 r = s_row[j];  // new pivot row
-        double2 v;
+        const C r = s_row[j];  // new pivot row
+        C v;
         if (i == k)
           v = r;
         else if (j == k)
@@ -277,12 +287,13 @@ __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(double2* __restrict__ A0, d
   }
 }
 
-__global__ void k_gj_unscramble(double2* __restrict__ A, int n, const int* __restrict__ piv) {
+template <typename C>
+__global__ void k_gj_unscramble(C* __restrict__ A, int n, const int* __restrict__ piv) {
   for (int k = n - 1; k >= 0; --k) {
     const int p = piv[k];
     if (p != k)
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double2 t = A[(size_t)i * n + k];
+        C t = A[(size_t)i * n + k];
         A[(size_t)i * n + k] = A[(size_t)i * n + p];
         A[(size_t)i * n + p] = t;
       }
@@ -294,40 +305,44 @@ size_t invert_large_work_bytes(int n) {
   return sizeof(double2) * (size_t)n * n + (sizeof(double) + sizeof(int)) * 2048 + 64;
 }
 
-void invert_large(cudaStream_t st, double2* A, int n, int* piv, void* work, int* fail, int* timeout) {
+template <typename C>
+void invert_large(cudaStream_t st, C* A, int n, int* piv, void* work, int* fail, int* timeout) {
   int dev = 0, nsm = 0, per = 0;
   MG_CUDA(cudaGetDevice(&dev));
   MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const size_t sm = sizeof(double2) * (size_t)n;
+  const size_t sm = sizeof(C) * (size_t)n;
   static bool attr = false;
   if (!attr) {
-    MG_CUDA(cudaFuncSetAttribute(k_gj_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    MG_CUDA(cudaFuncSetAttribute(k_gj_coop<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     attr = true;
   }
   MG_CHECK_ARG(sm <= 160 * 1024, "coarsest level too large for the pivot row in shared memory");
-  MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_coop, GJ_T, sm));
+  MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_coop<C>, GJ_T, sm));
   // one resident CTA per SM (at most one row per CTA), all co-resident as the cooperative launch requires
   const int grid = std::max(1, std::min(std::min(nsm * std::min(std::max(per, 1), 1), 1024), n));
   char* w = (char*)work;
-  double2* A1 = (double2*)w;
-  double* slot_v = (double*)(A1 + (size_t)n * n);
+  C* A1 = (C*)w;
+  double* slot_v = (double*)(w + sizeof(double2) * (size_t)n * n);
   int* slot_i = (int*)(slot_v + 2048);
   unsigned* bar = (unsigned*)(slot_i + 2048);
   MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
   void* args[] = {&A, &A1, &n, &piv, &slot_v, &slot_i, &bar, &fail, &timeout};
   KTimer* t = g_timer;
   cudaEvent_t ea = nullptr, eb = nullptr;
-  if (t && t->want("k_gj_coop")) { ea = t->get(); eb = t->get(); MG_CUDA(cudaEventRecord(ea, st)); }
-  MG_CUDA(cudaLaunchCooperativeKernel((void*)k_gj_coop, dim3(grid), dim3(GJ_T), args, sm, st));
+  const char* name = sizeof(C) == 8 ? "k_gj_coop<float2>" : "k_gj_coop<double2>";
+  if (t && t->want(name)) { ea = t->get(); eb = t->get(); MG_CUDA(cudaEventRecord(ea, st)); }
+  MG_CUDA(cudaLaunchCooperativeKernel((void*)k_gj_coop<C>, dim3(grid), dim3(GJ_T), args, sm, st));
   if (ea) {
     MG_CUDA(cudaEventRecord(eb, st));
-    t->recs.push_back({"k_gj_coop", __PRETTY_FUNCTION__, 32.0 * n * (double)n * n, 8.0 * n * (double)n * n, ea, eb});
+    t->recs.push_back({name, __PRETTY_FUNCTION__, 2.0 * sizeof(C) * n * (double)n * n, 8.0 * n * (double)n * n, ea, eb});
   }
   if (g_launch_counter) ++*g_launch_counter;
   if (n & 1)  // odd column count: the last column wrote the scratch buffer
-    MG_CUDA(cudaMemcpyAsync(A, A1, sizeof(double2) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
-  MG_LAUNCH(k_gj_unscramble, 1, 1024, 0, st, A, n, piv);
+    MG_CUDA(cudaMemcpyAsync(A, A1, sizeof(C) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
+  MG_LAUNCH(k_gj_unscramble<C>, 1, 1024, 0, st, A, n, piv);
 }
+template void invert_large<double2>(cudaStream_t, double2*, int, int*, void*, int*, int*);
+template void invert_large<float2>(cudaStream_t, float2*, int, int*, void*, int*, int*);
 
 // ---- y = A x for the coarsest level (n x n dense, nrhs columns) --------------------------------
 template <typename R>

@@ -22,8 +22,9 @@ static int default_levels(int L, int agg) {
   return lv;
 }
 
-// SAP block inverses of level l (FP64 master and FP32 copy)
-static void build_sap(mgmlmc_hier* h, int l, int* dfail) {
+// SAP block inverses of level l: the block matrices in FP64, inverted in FP64 (FP32 copy alongside) or, for an
+// intermediate bootstrap round whose hierarchy only serves FP32 solves, inverted in FP32 only
+static void build_sap(mgmlmc_hier* h, int l, int* dfail, bool fp64) {
   cudaStream_t st = h->stream;
   LevelData& lv = h->lv[l];
   const int Ls = lv.side, d = lv.dof, bs = lv.sap_bs, bd = lv.sap_bd;
@@ -33,8 +34,14 @@ static void build_sap(mgmlmc_hier* h, int l, int* dfail) {
     fine_block_matrices(st, lv.links64.as<double2>(), lv.diag, Ls, bs, lv.sapinv64.as<double2>());
   else
     coarse_block_matrices(st, lv.st64.as<double2>(), Ls, d, bs, lv.sapinv64.as<double2>());
-  invert_small_batched(st, lv.sapinv64.as<double2>(), nb, bd, dfail);
-  to_fp32(st, lv.sapinv64, lv.sapinv32, (size_t)nb * bd * bd);
+  if (fp64) {
+    invert_small_batched<double2>(st, lv.sapinv64.as<double2>(), nb, bd, dfail);
+    to_fp32(st, lv.sapinv64, lv.sapinv32, (size_t)nb * bd * bd);
+  } else {
+    to_fp32(st, lv.sapinv64, lv.sapinv32, (size_t)nb * bd * bd);
+    invert_small_batched<float2>(st, lv.sapinv32.as<float2>(), nb, bd, dfail);
+  }
+  lv.sap64_ok = fp64;
   if (h->prm.tensor_cores && l >= 1 && d == 16 && bs == 2) {
     for (int c = 0; c < 2; ++c) {
       lv.tcInv[c].alloc(sizeof(float) * tc_blockinv_weight_floats(Ls), st);
@@ -43,8 +50,9 @@ static void build_sap(mgmlmc_hier* h, int l, int* dfail) {
   }
 }
 
-// dense FP64 inverse of the coarsest level and its trace
-static void build_coarsest(mgmlmc_hier* h, int* dfail) {
+// dense inverse of the coarsest level: FP64 with its trace (tau_L of Algorithm 2), or FP32 only for an
+// intermediate bootstrap round
+static void build_coarsest(mgmlmc_hier* h, int* dfail, bool fp64) {
   cudaStream_t st = h->stream;
   LevelData& lc = h->lv[h->nlev - 1];
   const int n = (int)lc.n;
@@ -52,7 +60,14 @@ static void build_coarsest(mgmlmc_hier* h, int* dfail) {
   lc.inv64.alloc(sizeof(double2) * (size_t)n * n, st);
   dense_from_stencil(st, lc.st64.as<double2>(), lc.side, lc.dof, lc.inv64.as<double2>());
   DBuf piv(sizeof(int) * n, st), work(invert_large_work_bytes(n), st), tr(sizeof(double2), st);
-  invert_large(st, lc.inv64.as<double2>(), n, piv.as<int>(), work.p, dfail, dfail + 1);
+  lc.inv64_ok = fp64;
+  if (!fp64) {
+    to_fp32(st, lc.inv64, lc.inv32, (size_t)n * n);
+    invert_large<float2>(st, lc.inv32.as<float2>(), n, piv.as<int>(), work.p, dfail, dfail + 1);
+    MG_CUDA(cudaStreamSynchronize(st));  // piv / work are released at return
+    return;
+  }
+  invert_large<double2>(st, lc.inv64.as<double2>(), n, piv.as<int>(), work.p, dfail, dfail + 1);
   to_fp32(st, lc.inv64, lc.inv32, (size_t)n * n);
   trace_dense(st, lc.inv64.as<double2>(), n, tr.as<double2>());
   MG_CUDA(cudaMemcpyAsync(&lc.trace, tr.p, sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -61,7 +76,7 @@ static void build_coarsest(mgmlmc_hier* h, int* dfail) {
 
 // P_l from the level-l test vectors lv.tv (ntv x n_l, FP64), D_{l+1} = P^H D_l P,
 // then the smoother (or dense inverse) of level l+1.
-static void build_from_tv(mgmlmc_hier* h, int l, int* dfail) {
+static void build_from_tv(mgmlmc_hier* h, int l, int* dfail, bool sap64, bool coarsest64) {
   cudaStream_t st = h->stream;
   const mg_params& p = h->prm;
   LevelData& lv = h->lv[l];
@@ -90,9 +105,9 @@ static void build_from_tv(mgmlmc_hier* h, int l, int* dfail) {
     }
   }
   if (l + 1 < h->nlev - 1)
-    build_sap(h, l + 1, dfail + 0);
+    build_sap(h, l + 1, dfail + 0, sap64);
   else
-    build_coarsest(h, dfail + 2);
+    build_coarsest(h, dfail + 2, coarsest64);
   ++h->gen;  // operators changed: captured V-cycles must be rebuilt
 }
 
@@ -149,7 +164,7 @@ void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U) {
   l0.links64.alloc(sizeof(double2) * 2 * L * L, st);
   l0.links32.alloc(sizeof(float2) * 2 * L * L, st);
   prepare_links(st, U, L, l0.links64.as<double2>(), l0.links32.as<float2>());
-  build_sap(h, 0, dfail + 0);
+  build_sap(h, 0, dfail + 0, true);
 
   // initial phase: complex Rademacher test vectors smoothed by SAP sweeps for D_l v = 0
   const int ntv = p.ntv;
@@ -163,7 +178,9 @@ void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U) {
       vzero<double2>(st, f0.as<double2>(), n, ntv);
       for (int s = 0; s < p.setup_sweeps; ++s) sap_sweep<double>(h, l, f0.as<double2>(), lv.tv.as<double2>(), ntv, nullptr);
     }
-    build_from_tv(h, l, dfail);
+    // the next level's FP64 SAP inverse smooths its test vectors; the coarsest inverse is final only
+    // without bootstrap rounds (otherwise FP32 serves the bootstrap solves)
+    build_from_tv(h, l, dfail, true, p.bootstrap == 0);
   }
   check_fail(h, dfail);
 
@@ -180,7 +197,8 @@ void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U) {
       fgmres_core<float>(h, l, b32.as<float2>(), x32.as<float2>(), ntv, p.bootstrap_its, 1e-30, p.bootstrap_its, true,
                          nullptr, nullptr, nullptr, nullptr);
       vconvert<double2, float2>(st, x32.as<float2>(), lv.tv.as<double2>(), n, ntv, nullptr, nullptr);
-      build_from_tv(h, l, dfail);
+      const bool final_round = it == p.bootstrap - 1;  // earlier rounds only feed FP32 bootstrap solves
+      build_from_tv(h, l, dfail, final_round, final_round);
     }
     check_fail(h, dfail);
   }
