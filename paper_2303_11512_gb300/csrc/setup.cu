@@ -173,14 +173,20 @@ void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U) {
     const long n = lv.n;
     lv.tv.alloc(sizeof(double2) * n * ntv, st);
     complex_rademacher_fill(st, p.seed, l, MGMLMC_PHASE_TESTVEC, 0, n, ntv, lv.tv.as<double2>());
-    {
+    if (p.bootstrap == 0) {  // this hierarchy is the final one: FP64 throughout
       DBuf f0(sizeof(double2) * n * ntv, st);
       vzero<double2>(st, f0.as<double2>(), n, ntv);
       for (int s = 0; s < p.setup_sweeps; ++s) sap_sweep<double>(h, l, f0.as<double2>(), lv.tv.as<double2>(), ntv, nullptr);
+    } else {  // only a seed for the bootstrap rounds: smoothed in FP32
+      DBuf f0(sizeof(float2) * n * ntv, st), t32(sizeof(float2) * n * ntv, st);
+      vzero<float2>(st, f0.as<float2>(), n, ntv);
+      vconvert<float2, double2>(st, lv.tv.as<double2>(), t32.as<float2>(), n, ntv, nullptr, nullptr);
+      for (int s = 0; s < p.setup_sweeps; ++s) sap_sweep<float>(h, l, f0.as<float2>(), t32.as<float2>(), ntv, nullptr);
+      vconvert<double2, float2>(st, t32.as<float2>(), lv.tv.as<double2>(), n, ntv, nullptr, nullptr);
     }
-    // the next level's FP64 SAP inverse smooths its test vectors; the coarsest inverse is final only
-    // without bootstrap rounds (otherwise FP32 serves the bootstrap solves)
-    build_from_tv(h, l, dfail, true, p.bootstrap == 0);
+    // without bootstrap rounds this is the final hierarchy (FP64 inverses); otherwise FP32 inverses serve the
+    // FP32 smoothing above and the bootstrap solves
+    build_from_tv(h, l, dfail, p.bootstrap == 0, p.bootstrap == 0);
   }
   check_fail(h, dfail);
 
