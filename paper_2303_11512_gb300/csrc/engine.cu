@@ -67,7 +67,8 @@ void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>
   }
   for (int color = 0; color < 2; ++color) {
     if (l == 0)
-      sap_half_fine<R>(st, links_of<R>(L), (R)L.diag, L.side, L.sap_bs, sapinv_of<R>(L), f, x, color, nrhs, active);
+      sap_half_fine<R>(st, links_of<R>(L), (R)L.diag, L.side, L.sap_bs, sapinv_of<R>(L), f, x, color, nrhs, active,
+                       sizeof(R) == 4 && L.sapinv32_t);
     else
       sap_half_coarse<R>(st, st_of<R>(L), L.side, L.dof, L.sap_bs, sapinv_of<R>(L), f, x, color, nrhs, active);
   }

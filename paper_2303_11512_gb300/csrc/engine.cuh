@@ -44,6 +44,7 @@ struct LevelData {
   double2 trace = make_double2(0, 0);
   // FP64 SAP inverses / coarsest inverse current (intermediate bootstrap rounds build FP32 ones only)
   bool sap64_ok = false, inv64_ok = false;
+  bool sapinv32_t = false;  // FP32 SAP inverses stored transposed (fine level)
 };
 
 }  // namespace mg

@@ -29,10 +29,12 @@ void coarse_block_matrices(cudaStream_t st, const double2* stencil, int Ls, int 
 
 // ---------------------------------------------------------------- SAP
 // one colour half-sweep: x_B += inv_B (f - D x)_B on the blocks of colour `color`.
+// inv_transposed: block inverses stored transposed (inv[b][j][i]), as blocks_to_fp32_transposed writes them
 template <typename R>
 void sap_half_fine(cudaStream_t st, const typename CT<R>::T* links, R diag, int L, int bs,
                    const typename CT<R>::T* inv, const typename CT<R>::T* f, typename CT<R>::T* x,
-                   int color, int nrhs, const int* active);
+                   int color, int nrhs, const int* active, bool inv_transposed = false);
+void blocks_to_fp32_transposed(cudaStream_t st, const double2* in, int nb, int bd, float2* out);
 template <typename R>
 void sap_half_coarse(cudaStream_t st, const typename CT<R>::T* stencil, int Ls, int d, int bs,
                      const typename CT<R>::T* inv, const typename CT<R>::T* f, typename CT<R>::T* x,

@@ -199,7 +199,7 @@ void fine_block_matrices(cudaStream_t st, const double2* l64, double diag, int L
 // ---- SAP half sweep on the fine level ----------------------------------------
 // One CTA per block of the colour; the block inverse is staged in shared memory
 // once and applied to all right-hand sides in groups of G.
-template <typename R, int BS>
+template <typename R, int BS, bool TRANS>
 __global__ void __launch_bounds__(256) k_sap_fine(const typename CT<R>::T* __restrict__ lk, R diag, int L,
                                                   const typename CT<R>::T* __restrict__ inv,
                                                   const typename CT<R>::T* __restrict__ f,
@@ -218,7 +218,10 @@ __global__ void __launch_bounds__(256) k_sap_fine(const typename CT<R>::T* __res
   const int BX = 2 * (k % half) + ((BT + color) & 1);
   const int blk = BT * nbx + BX;
   const C* I = inv + (size_t)blk * BD * BD;
-  for (int e = threadIdx.x; e < BD * BD; e += blockDim.x) sinv[(e % BD) * BD + e / BD] = I[e];
+  if (TRANS)  // stored transposed already: a straight, conflict-free copy
+    for (int e = threadIdx.x; e < BD * BD; e += blockDim.x) sinv[e] = I[e];
+  else
+    for (int e = threadIdx.x; e < BD * BD; e += blockDim.x) sinv[(e % BD) * BD + e / BD] = I[e];
   const int V = L * L;
   const size_t n = 2 * (size_t)V;
   for (int r0 = 0; r0 < nrhs; r0 += G) {
@@ -256,21 +259,42 @@ __global__ void __launch_bounds__(256) k_sap_fine(const typename CT<R>::T* __res
 template <typename R>
 void sap_half_fine(cudaStream_t st, const typename CT<R>::T* links, R diag, int L, int bs,
                    const typename CT<R>::T* inv, const typename CT<R>::T* f, typename CT<R>::T* x, int color,
-                   int nrhs, const int* active) {
+                   int nrhs, const int* active, bool inv_transposed) {
   MG_CHECK_ARG(bs == 4 || bs == 2, "fine SAP block side must be 2 or 4");
   const int nb = (L / bs) * (L / bs) / 2;
   // per block and rhs: x, f read and x written on the block (bd complex each); inverse once per block
   const double bd = 2.0 * bs * bs, cs = sizeof(typename CT<R>::T), ar = act_rhs(nrhs);
   const double bytes = nb * (ar * 3 * bd * cs + bd * bd * cs);
   const double flops = nb * ar * (bs * bs * 56.0 + 8.0 * bd * bd);
-  if (bs == 4)
-    MG_LAUNCH_W(bytes, flops, (k_sap_fine<R, 4>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs, active);
+  if (bs == 4 && inv_transposed)
+    MG_LAUNCH_W(bytes, flops, (k_sap_fine<R, 4, true>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs, active);
+  else if (bs == 4)
+    MG_LAUNCH_W(bytes, flops, (k_sap_fine<R, 4, false>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs,
+                active);
+  else if (inv_transposed)
+    MG_LAUNCH_W(bytes, flops, (k_sap_fine<R, 2, true>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs, active);
   else
-    MG_LAUNCH_W(bytes, flops, (k_sap_fine<R, 2>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs, active);
+    MG_LAUNCH_W(bytes, flops, (k_sap_fine<R, 2, false>), nb, 256, 0, st, links, diag, L, inv, f, x, color, nrhs,
+                active);
 }
 template void sap_half_fine<float>(cudaStream_t, const float2*, float, int, int, const float2*, const float2*,
-                                   float2*, int, int, const int*);
+                                   float2*, int, int, const int*, bool);
 template void sap_half_fine<double>(cudaStream_t, const double2*, double, int, int, const double2*,
-                                    const double2*, double2*, int, int, const int*);
+                                    const double2*, double2*, int, int, const int*, bool);
+
+// out[b][j][i] = (float) in[b][i][j] for nb blocks of bd x bd
+__global__ void k_blocks_to_fp32_transposed(const double2* __restrict__ in, int nb, int bd, float2* __restrict__ out) {
+  const size_t total = (size_t)nb * bd * bd;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = e / ((size_t)bd * bd);
+    const int r = (int)(e - b * bd * bd), i = r / bd, j = r - i * bd;
+    const double2 v = in[e];
+    out[b * bd * bd + (size_t)j * bd + i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+void blocks_to_fp32_transposed(cudaStream_t st, const double2* in, int nb, int bd, float2* out) {
+  MG_LAUNCH(k_blocks_to_fp32_transposed, 1024, 256, 0, st, in, nb, bd, out);
+}
 
 }  // namespace mg

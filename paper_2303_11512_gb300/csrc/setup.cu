@@ -34,7 +34,13 @@ static void build_sap(mgmlmc_hier* h, int l, int* dfail, bool fp64) {
     fine_block_matrices(st, lv.links64.as<double2>(), lv.diag, Ls, bs, lv.sapinv64.as<double2>());
   else
     coarse_block_matrices(st, lv.st64.as<double2>(), Ls, d, bs, lv.sapinv64.as<double2>());
-  if (fp64) {
+  lv.sapinv32_t = false;
+  if (fp64 && l == 0) {  // the fine CUDA-core smoother reads its FP32 inverses transposed
+    invert_small_batched<double2>(st, lv.sapinv64.as<double2>(), nb, bd, dfail);
+    lv.sapinv32.alloc(sizeof(float2) * (size_t)nb * bd * bd, st);
+    blocks_to_fp32_transposed(st, lv.sapinv64.as<double2>(), nb, bd, lv.sapinv32.as<float2>());
+    lv.sapinv32_t = true;
+  } else if (fp64) {
     invert_small_batched<double2>(st, lv.sapinv64.as<double2>(), nb, bd, dfail);
     to_fp32(st, lv.sapinv64, lv.sapinv32, (size_t)nb * bd * bd);
   } else {
