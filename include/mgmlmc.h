@@ -131,7 +131,10 @@ typedef struct {
                             vectors of every level by bootstrap_its FGMRES iterations on D_l v_new = v
                             preconditioned by the current hierarchy, then rebuilds P_l and D_{l+1}
                             (the adaptive part of the DD-alpha-AMG set-up; with 0 the hierarchy is
-                            the deterministic one the CPU oracle reproduces) */
+                            the deterministic one the CPU oracle reproduces).  With bootstrap > 0 the
+                            seed hierarchy and all rounds but the last only drive FP32 bootstrap
+                            solves: their test-vector smoothing and SAP / coarsest inverses are
+                            FP32; the last round builds the full FP64 hierarchy */
   int bootstrap_its;     /* (6) */
   int kcycle_its;        /* 0 = V-cycle; k > 0 = K-cycle: the coarse correction of levels below the
                             first runs k FGMRES iterations preconditioned by the next V/K-cycle (0) */
