@@ -6,8 +6,11 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <stdexcept>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mgmlmc.h"
@@ -29,6 +32,19 @@ struct Error : public std::runtime_error {
                         std::string(#call) + ": " + cudaGetErrorString(e_));       \
     }                                                                              \
   } while (0)
+
+// Raise a kernel's dynamic shared-memory limit once per (kernel, device, size): the attribute belongs to the
+// device's context, so a process that drives several GPUs needs it set on each.
+inline void ensure_max_smem(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> done;
+  int dev = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(std::make_tuple(kernel, dev, bytes))) return;
+  MG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert(std::make_tuple(kernel, dev, bytes));
+}
 
 #define MG_CHECK_ARG(cond, msg)                                                    \
   do {                                                                             \

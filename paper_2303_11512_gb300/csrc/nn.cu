@@ -428,12 +428,7 @@ double nn_backward(NNet* net, const float2* r, const float2* e, int nrhs, cudaSt
     DBuf part(sizeof(float2) * (size_t)nblk * cnt, st);
     const size_t sm = sizeof(float2) * NN_WCH * (9 * ci + co);
     with_dims(ci, co, [&](auto CI, auto CO) {
-      static bool attr = false;
-      if (!attr) {
-        MG_CUDA(cudaFuncSetAttribute(k_nn_bwd_w<CI.value, CO.value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     160 * 1024));
-        attr = true;
-      }
+      ensure_max_smem((const void*)k_nn_bwd_w<CI.value, CO.value>, 160 * 1024);
       MG_LAUNCH((k_nn_bwd_w<CI.value, CO.value>), nblk, 256, sm, st, net->T.as<float2>(), a_in, gz, L,
                 part.as<float2>());
     });

@@ -71,23 +71,19 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const typename CT<R>::T* _
 }
 
 template <typename K>
-static void set_smem_attr(K kernel, bool& done) {
-  if (!done) {
-    MG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    done = true;
-  }
+static void set_smem_attr(K kernel) {
+  ensure_max_smem((const void*)kernel, 200 * 1024);
 }
 
 template <typename R, bool RES>
 static void coarse_apply_launch(cudaStream_t stm, const typename CT<R>::T* st, int Ls, int d,
                                 const typename CT<R>::T* x, typename CT<R>::T* y, const typename CT<R>::T* b,
                                 int nrhs, const int* active, size_t sm, double bytes, double flops) {
-  static bool done[2] = {false, false};
   if (d == 16) {
-    set_smem_attr(k_coarse_apply<R, RES, 16>, done[0]);
+    set_smem_attr(k_coarse_apply<R, RES, 16>);
     MG_LAUNCH_W(bytes, flops, (k_coarse_apply<R, RES, 16>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
   } else {
-    set_smem_attr(k_coarse_apply<R, RES, 0>, done[1]);
+    set_smem_attr(k_coarse_apply<R, RES, 0>);
     MG_LAUNCH_W(bytes, flops, (k_coarse_apply<R, RES, 0>), Ls * Ls, 256, sm, stm, st, Ls, d, x, y, b, nrhs, active);
   }
 }
@@ -213,12 +209,7 @@ void sap_half_coarse(cudaStream_t stm, const typename CT<R>::T* st, int Ls, int 
   const int G = std::max(1, 256 / bd);
   size_t sm = sizeof(C) * ((size_t)bd * bd + (size_t)ns * 5 * d * d + (size_t)G * bd);
   MG_CHECK_ARG(sm <= 220 * 1024, "coarse SAP block too large for shared memory");
-  static bool attr[2] = {false, false};
-  const int ri = sizeof(R) == 8;
-  if (!attr[ri]) {
-    MG_CUDA(cudaFuncSetAttribute(k_sap_coarse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr[ri] = true;
-  }
+  ensure_max_smem((const void*)k_sap_coarse<R>, 220 * 1024);
   const int nb = (Ls / bs) * (Ls / bs) / 2;
   const double cs = sizeof(C), ar = act_rhs(nrhs);
   const double bytes = nb * (ar * 3.0 * bd * cs + ((double)bd * bd + ns * 5.0 * d * d) * cs);
@@ -344,24 +335,23 @@ void restrict_op(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, in
   const int na = agg * agg, bsz = na * d / 2, dc = 2 * ntv;
   const int G = std::max(1, 256 / dc);
   size_t sm = sizeof(C) * ((size_t)2 * bsz * ntv + (size_t)G * na * d);
-  static bool done[3] = {false, false, false};
   const int Lc = Ls / agg;
   const double nag = (double)Lc * Lc, cs = sizeof(C), ar = act_rhs(nrhs);
   const double bytes = nag * (ar * (na * d + dc) * cs + 2.0 * bsz * ntv * cs);
   const double flops = nag * ar * 8.0 * 2.0 * bsz * ntv;
   switch (transfer_shape(d, agg, ntv)) {
     case SHAPE_FINE:
-      set_smem_attr(k_restrict<R, 2, 4, 8>, done[1]);
+      set_smem_attr(k_restrict<R, 2, 4, 8>);
       MG_LAUNCH_W(bytes, flops, (k_restrict<R, 2, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs,
                   active);
       break;
     case SHAPE_COARSE:
-      set_smem_attr(k_restrict<R, 16, 4, 8>, done[2]);
+      set_smem_attr(k_restrict<R, 16, 4, 8>);
       MG_LAUNCH_W(bytes, flops, (k_restrict<R, 16, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs,
                   active);
       break;
     default:
-      set_smem_attr(k_restrict<R, 0, 0, 0>, done[0]);
+      set_smem_attr(k_restrict<R, 0, 0, 0>);
       MG_LAUNCH_W(bytes, flops, (k_restrict<R, 0, 0, 0>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xf, xc, nrhs,
                   active);
   }
@@ -371,21 +361,20 @@ template <typename R, bool ADD>
 static void prolong_launch(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, int agg, int ntv,
                            const typename CT<R>::T* xc, typename CT<R>::T* xf, int nrhs, const int* active,
                            size_t sm, double bytes, double flops) {
-  static bool done[3] = {false, false, false};
   const int Lc = Ls / agg;
   switch (transfer_shape(d, agg, ntv)) {
     case SHAPE_FINE:
-      set_smem_attr(k_prolong<R, ADD, 2, 4, 8>, done[1]);
+      set_smem_attr(k_prolong<R, ADD, 2, 4, 8>);
       MG_LAUNCH_W(bytes, flops, (k_prolong<R, ADD, 2, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf,
                   nrhs, active);
       break;
     case SHAPE_COARSE:
-      set_smem_attr(k_prolong<R, ADD, 16, 4, 8>, done[2]);
+      set_smem_attr(k_prolong<R, ADD, 16, 4, 8>);
       MG_LAUNCH_W(bytes, flops, (k_prolong<R, ADD, 16, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf,
                   nrhs, active);
       break;
     default:
-      set_smem_attr(k_prolong<R, ADD, 0, 0, 0>, done[0]);
+      set_smem_attr(k_prolong<R, ADD, 0, 0, 0>);
       MG_LAUNCH_W(bytes, flops, (k_prolong<R, ADD, 0, 0, 0>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf,
                   nrhs, active);
   }
@@ -603,18 +592,10 @@ void galerkin(cudaStream_t stm, const double2* A, bool wilson, double diag, int 
   const double bytes = (double)Lc * Lc * (na * (wilson ? 32.0 : 5.0 * d * d * 16.0) + 5.0 * dc * dc * 16.0 +
                                           2.0 * na * hd * ntv * 16.0);
   if (wilson) {
-    static bool done = false;
-    if (!done) {
-      MG_CUDA(cudaFuncSetAttribute(k_galerkin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      done = true;
-    }
+    ensure_max_smem((const void*)k_galerkin<true>, 200 * 1024);
     MG_LAUNCH_W(bytes, flops, k_galerkin<true>, Lc * Lc, GAL_T, sm, stm, A, diag, Ls, d, agg, ntv, P, out);
   } else {
-    static bool done = false;
-    if (!done) {
-      MG_CUDA(cudaFuncSetAttribute(k_galerkin<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      done = true;
-    }
+    ensure_max_smem((const void*)k_galerkin<false>, 200 * 1024);
     MG_LAUNCH_W(bytes, flops, k_galerkin<false>, Lc * Lc, GAL_T, sm, stm, A, diag, Ls, d, agg, ntv, P, out);
   }
 }

@@ -109,13 +109,7 @@ template <typename C>
 void invert_small_batched(cudaStream_t st, C* A, int nmat, int bd, int* fail) {
   MG_CHECK_ARG(bd <= 64, "small inverse limited to 64 x 64");
   size_t sm = sizeof(C) * ((size_t)bd * bd + bd) + sizeof(int) * bd + 16;
-  static bool done[3] = {false, false, false};
-  auto attr = [&](auto kern, int i) {
-    if (!done[i]) {
-      MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-      done[i] = true;
-    }
-  };
+  auto attr = [&](auto kern, int) { ensure_max_smem((const void*)kern, 100 * 1024); };
   if (bd == 64) {
     attr(k_invert_small<C, 64>, 0);
     MG_LAUNCH((k_invert_small<C, 64>), nmat, 256, sm, st, A, bd, fail);
@@ -311,11 +305,7 @@ void invert_large(cudaStream_t st, C* A, int n, int* piv, void* work, int* fail,
   MG_CUDA(cudaGetDevice(&dev));
   MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const size_t sm = sizeof(C) * (size_t)n;
-  static bool attr = false;
-  if (!attr) {
-    MG_CUDA(cudaFuncSetAttribute(k_gj_coop<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-    attr = true;
-  }
+  ensure_max_smem((const void*)k_gj_coop<C>, 160 * 1024);
   MG_CHECK_ARG(sm <= 160 * 1024, "coarsest level too large for the pivot row in shared memory");
   MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_coop<C>, GJ_T, sm));
   // one resident CTA per SM (at most one row per CTA), all co-resident as the cooperative launch requires

@@ -489,11 +489,7 @@ void launch_tc(cudaStream_t st, const CUtensorMap& m, const float* W, float* out
                int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops) {
   typedef TcCfg<MODE> CF;
   constexpr int SMEM_BUDGET = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
-  static bool attr = false;
-  if (!attr) {
-    MG_CUDA(cudaFuncSetAttribute(k_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET));
-    attr = true;
-  }
+  ensure_max_smem((const void*)k_tc<MODE>, SMEM_BUDGET);
   const int rows = box_rows(nrhs);
   const int sbytes = tc_stage_bytes(CF::KC, CF::N, rows);
   const int stages = std::max(1, std::min(TC_MAX_STAGES, (SMEM_BUDGET - 1024) / sbytes));
