@@ -407,13 +407,20 @@ size_t gram_work_bytes(int d, long n) {
   return sizeof(double2) * (size_t)GBLK * d * d;
 }
 
+// G is Hermitian: thread t < d(d+1)/2 accumulates the upper-triangle entry (i, j), i <= j (packed so that the
+// working threads fill whole warps), and writes it and its conjugate mirror.
 __global__ void __launch_bounds__(1024) k_gram_part(const double2* __restrict__ Y, int d, long n,
                                                     double2* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* Ys = reinterpret_cast<double2*>(smem_raw);  // [GCH][d]
   const int tid = threadIdx.x;
-  const int i = tid / d, j = tid % d;
-  const bool on = tid < d * d;
+  int i = 0, j = 0;
+  {
+    int t = tid;
+    while (i < d && t >= d - i) { t -= d - i; ++i; }
+    j = i + t;
+  }
+  const bool on = i < d;
   double2 acc = make_double2(0, 0);
   for (long e0 = (long)blockIdx.x * GCH; e0 < n; e0 += (long)gridDim.x * GCH) {
     __syncthreads();
@@ -426,7 +433,10 @@ __global__ void __launch_bounds__(1024) k_gram_part(const double2* __restrict__ 
 #pragma unroll 8
       for (int e = 0; e < GCH; ++e) acc = cfmac(Ys[e * d + i], Ys[e * d + j], acc);
   }
-  if (on) part[((size_t)blockIdx.x * d + i) * d + j] = acc;
+  if (on) {
+    part[((size_t)blockIdx.x * d + i) * d + j] = acc;
+    if (i != j) part[((size_t)blockIdx.x * d + j) * d + i] = cconj(acc);
+  }
 }
 
 __global__ void k_gram_final(const double2* __restrict__ part, int d, int nb, double2* __restrict__ G) {
