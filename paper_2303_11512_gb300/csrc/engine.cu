@@ -105,7 +105,10 @@ void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T
   bool done = false;
   if constexpr (sizeof(R) == 4) {
     if (h->use_tc(l)) {  // res = r - D e on the tensor cores (preconditioner accuracy)
-      tc_stencil_apply(st, L.tcW.as<float>(), L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
+      if (h->prm.pre_smooth > 0 && L.sap_bs == 2 && L.tcInv[0].p)  // zero on the blocks the sweep solved last
+        tc_residual_after_sap(st, L.tcW.as<float>(), L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
+      else
+        tc_stencil_apply(st, L.tcW.as<float>(), L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
       done = true;
     }
   }

@@ -150,6 +150,9 @@ void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color
 void tc_stencil_apply(cudaStream_t st, const float* W, int Ls, const float2* x, float2* y, const float2* b, int nrhs,
                       const int* active, int* err);
 // one SAP colour half sweep with 2x2-site blocks: res = f - D x on the colour's sites, x_B += inv_B res_B
+// res = f - D x on colour-0 block sites, 0 on colour-1 block sites (valid right after a SAP sweep)
+void tc_residual_after_sap(cudaStream_t st, const float* Wst, int Ls, const float2* x, float2* res, const float2* f,
+                           int nrhs, const int* active, int* err);
 void tc_sap_half(cudaStream_t st, const float* Wst, const float* Winv, int Ls, const float2* f, float2* x,
                  float2* res, int color, int nrhs, const int* active, int* err);
 

@@ -528,6 +528,36 @@ void tc_stencil_apply(cudaStream_t st, const float* W, int Ls, const float2* x, 
   launch_tc<0>(st, m, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
 }
 
+// zero the sites of every colour-`color` 2x2 block of res ([rhs][site][16 complex])
+__global__ void k_zero_colour_blocks(float2* __restrict__ res, int Ls, int color, int nrhs, const int* active) {
+  const int nblk = Ls * Ls / 8;  // blocks of one colour
+  const size_t per_rhs = (size_t)nblk * 4 * 8;  // float4 per rhs: 4 sites x 16 complex = 8 float4 each
+  const size_t total = per_rhs * nrhs;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int rhs = (int)(e / per_rhs);
+    if (active && !active[rhs]) continue;
+    const size_t r = e - (size_t)rhs * per_rhs;
+    const int item = (int)(r / 32), j = (int)(r % 32) >> 3, u = (int)(r & 7);
+    const int s = block_site(item, j, Ls, color);
+    reinterpret_cast<float4*>(res + ((size_t)rhs * Ls * Ls + s) * 16)[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// res = f - D x on the sites of the colour-0 blocks and 0 on the colour-1 blocks: the V-cycle residual after
+// a SAP sweep whose last half sweep solved the colour-1 blocks, where it vanishes (the blocks of one colour do
+// not couple to each other, so their solves leave f - D x = 0 on them)
+void tc_residual_after_sap(cudaStream_t st, const float* Wst, int Ls, const float2* x, float2* res, const float2* f,
+                           int nrhs, const int* active, int* err) {
+  if (nrhs <= 0) return;
+  const int ns = Ls * Ls;
+  const double ar = act_rhs(nrhs);
+  CUtensorMap m = make_map(x, ns, nrhs);
+  const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 2048;
+  const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
+  launch_tc<0>(st, m, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, 0, nrhs, active, err, bytes, flops);
+  MG_LAUNCH_W(ar * (ns / 2) * 128.0, 0, k_zero_colour_blocks, 1024, 256, 0, st, res, Ls, 1, nrhs, active);
+}
+
 void tc_sap_half(cudaStream_t st, const float* Wst, const float* Winv, int Ls, const float2* f, float2* x,
                  float2* res, int color, int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
