@@ -28,6 +28,18 @@ colour-1 blocks, each by x_B += D_BB^{-1} (f - D x)_B with the exact inverse
 of the diagonal block.
 
 Galerkin coarse operator D_{l+1} = P_l^H D_l P_l.
+
+V-cycle (the multigrid solver of Section 4, "done via multigrid"): on level
+l < L-1, e = 0; pre_smooth SAP sweeps for D_l e = r; coarse correction
+e += P_l V_{l+1}(P_l^H (r - D_l e)); post_smooth SAP sweeps; on the coarsest
+level e = D_L^{-1} r exactly.
+
+A hierarchy whose prolongators come from elsewhere (the GPU's adaptive
+bootstrap set-up, which has many valid outcomes) is rebuilt from them by
+Hierarchy.from_prolongators: the oracle then forms its own Galerkin operators
+P^H D P from its own fine operator, and check_prolongator verifies the
+defining properties of P (orthonormal columns, aggregate and chirality
+support).
 """
 from __future__ import annotations
 
@@ -137,6 +149,41 @@ def prolongator(V: np.ndarray, Ls: int, d: int, agg: int, ntv: int) -> sp.csr_ma
                          shape=(n, nc)).tocsr()
 
 
+def prolongator_from_blocks(B: np.ndarray, Ls: int, d: int, agg: int, ntv: int) -> sp.csr_matrix:
+    """Sparse P (n_l x n_{l+1}) from its aggregate blocks B[T*Lc+X, c, j, m] (row j of block (X, T, c)
+    is the j-th fine dof of aggregate_blocks, column m is coarse dof c*ntv+m of coarse site (X, T))."""
+    Lc = Ls // agg
+    dcoarse = 2 * ntv
+    blocks = aggregate_blocks(Ls, d, agg)
+    rows, cols, vals = [], [], []
+    for T in range(Lc):
+        for X in range(Lc):
+            for c in range(2):
+                I = blocks[X, T, c]
+                base = (T * Lc + X) * dcoarse + c * ntv
+                for m in range(ntv):
+                    rows.append(I)
+                    cols.append(np.full(I.size, base + m))
+                    vals.append(B[T * Lc + X, c, :, m])
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(Ls * Ls * d, Lc * Lc * dcoarse)).tocsr()
+
+
+def check_prolongator(P: sp.spmatrix, Ls: int, d: int, agg: int) -> dict:
+    """Defining properties of an aggregation prolongator (Section 3.1): max |P^H P - I| and whether every
+    non-zero joins a fine dof to a coarse dof of its own aggregate and of its own chirality."""
+    Pc = P.tocoo()
+    dc = P.shape[1] // ((Ls // agg) ** 2)
+    Lc = Ls // agg
+    orth = float(np.abs((P.conj().T @ P).toarray() - np.eye(P.shape[1])).max())
+    fs, fk = Pc.row // d, Pc.row % d
+    cs, ck = Pc.col // dc, Pc.col % dc
+    ft, fx, ct, cx = fs // Ls, fs % Ls, cs // Lc, cs % Lc
+    support = bool(np.all(ft // agg == ct) and np.all(fx // agg == cx))
+    chiral = bool(np.all(chirality(fk, d) == chirality(ck, dc)))
+    return dict(orth=orth, support=support, chirality=chiral)
+
+
 def stencil_blocks(Dl: sp.spmatrix, Ls: int, d: int) -> np.ndarray:
     """Blocks of a nearest-neighbour level operator: S[T, X, dir, d, d],
     dir = 0 self, 1 +x, 2 -x, 3 +t, 4 -t; S[B, dir] = D[rows of B, cols of B+dir]."""
@@ -183,6 +230,58 @@ class Hierarchy:
             self.side.append(Ls // agg)
             self.dof.append(2 * ntv)
         self.n = [Dl.shape[0] for Dl in self.D]
+        self.sap_block = tuple(sap_block)
+        self._sap = {}
+
+    @classmethod
+    def from_prolongators(cls, D0: sp.csr_matrix, L: int, Ps, agg: int = 4, sap_block=(4, 2)) -> "Hierarchy":
+        """Hierarchy with the given prolongators P_l (sparse, imported as data) and the oracle's own Galerkin
+        operators D_{l+1} = P_l^H D_l P_l built from the oracle's fine operator D0."""
+        H = cls.__new__(cls)
+        H.levels = len(Ps) + 1
+        H.agg = agg
+        H.D = [sp.csr_matrix(D0)]
+        H.P = []
+        H.side = [L]
+        H.dof = [2]
+        for l, P in enumerate(Ps):
+            P = sp.csr_matrix(P)
+            if P.shape[0] != H.D[l].shape[0]:
+                raise ValueError("prolongator %d has %d rows, level has %d dof" % (l, P.shape[0], H.D[l].shape[0]))
+            H.P.append(P)
+            H.D.append((P.conj().T @ H.D[l] @ P).tocsr())
+            H.side.append(H.side[l] // agg)
+            H.dof.append(P.shape[1] // (H.side[l + 1] ** 2))
+        H.ntv = H.dof[-1] // 2 if len(Ps) else 0
+        H.n = [Dl.shape[0] for Dl in H.D]
+        H.sap_block = tuple(sap_block)
+        H._sap = {}
+        return H
+
+    def sap(self, l: int) -> SAP:
+        """The SAP smoother of level l (block side sap_block[0] on the fine level, sap_block[1] above)."""
+        if l not in self._sap:
+            b = self.sap_block[0] if l == 0 else self.sap_block[1]
+            self._sap[l] = SAP(self.D[l], self.side[l], self.dof[l], b)
+        return self._sap[l]
+
+    def vcycle(self, l: int, r: np.ndarray, pre: int = 1, post: int = 1) -> np.ndarray:
+        """One V(pre, post)-cycle from level l as an approximate solve e ~ D_l^{-1} r (r: (n,) or (n, k))."""
+        r = np.asarray(r, dtype=complex)
+        if l == self.levels - 1:
+            if not hasattr(self, "_coarsest_inv"):
+                self._coarsest_inv = np.linalg.inv(self.D[l].toarray())
+            return self._coarsest_inv @ r
+        S = self.sap(l)
+        e = np.zeros_like(r)
+        for _ in range(pre):
+            S.sweep(r, e)
+        res = r - self.D[l] @ e
+        P = self.P[l]
+        e = e + P @ self.vcycle(l + 1, P.conj().T @ res, pre, post)
+        for _ in range(post):
+            S.sweep(r, e)
+        return e
 
     def Phat(self, l: int) -> sp.csr_matrix:
         """Accumulated prolongation P_1 ... P_{l-1} (fine x n_l); identity at l = 0."""

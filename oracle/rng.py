@@ -18,6 +18,11 @@ generator from its published definition:
 `sample` < 2^48, `level` < 256, `phase` < 256.  A real Rademacher vector of
 length n has entries sign(0..n-1); a complex one (used for multigrid test
 vectors) has re = sign(2i), im = sign(2i+1).
+
+Z4 noise (the complex alternative of Section 2, whose Hutchinson variance is
+||offdiag(A)||_F^2 instead of 1/2 ||offdiag(A + A^T)||_F^2): entry i is
+i^q with q = the top two bits of word(i) (q = word(i) >> 62), i.e. one of
+1, i, -1, -i with equal probability; E|z|^2 = 1, E z = E z^2 = 0.
 """
 from __future__ import annotations
 
@@ -67,6 +72,28 @@ def rademacher_block(seed: int, level: int, phase: int, sample0: int, n: int, k:
     """n x k matrix whose column j is rademacher(..., sample0 + j, n) (complex128)."""
     return np.stack([rademacher(seed, level, phase, sample0 + j, n) for j in range(k)],
                     axis=1).astype(complex)
+
+
+def z4(seed: int, level: int, phase: int, sample: int, n: int) -> np.ndarray:
+    """Z4 vector of length n: entry i = 1j ** (word(i) >> 62) (complex128)."""
+    q = (words(seed, level, phase, sample, n) >> np.uint64(62)).astype(np.int64)
+    return np.array([1.0, 1j, -1.0, -1j])[q]
+
+
+NOISE_RADEMACHER = 0
+NOISE_Z4 = 1
+
+
+def noise(kind: int, seed: int, level: int, phase: int, sample: int, n: int) -> np.ndarray:
+    """The isotropic random vector of eq. random_props: Rademacher (kind 0) or Z4 (kind 1), complex128."""
+    if kind == NOISE_Z4:
+        return z4(seed, level, phase, sample, n)
+    return rademacher(seed, level, phase, sample, n).astype(complex)
+
+
+def noise_block(kind: int, seed: int, level: int, phase: int, sample0: int, n: int, k: int) -> np.ndarray:
+    """n x k matrix whose column j is noise(kind, ..., sample0 + j, n)."""
+    return np.stack([noise(kind, seed, level, phase, sample0 + j, n) for j in range(k)], axis=1)
 
 
 def complex_rademacher(seed: int, level: int, phase: int, sample: int, n: int) -> np.ndarray:

@@ -128,3 +128,78 @@ def test_telescoping_sum_equals_trace(small3):
         tL = complex(np.trace(np.linalg.inv(small3.D[2].toarray())))
         total = sum(diffs) + tL
         assert abs(total - trace_inverse_dense(small3.D[0].toarray())) < 1e-10 * abs(total)
+
+
+def _sap_iteration_matrix(sap, n):
+    """I - M D of one SAP sweep, built from the block inverses as dense matrices (the two colours in order)."""
+    D = sap.D.toarray()
+    S = np.eye(n, dtype=complex)
+    for I, inv in sap.sets:
+        M = np.zeros((n, n), dtype=complex)
+        for b in range(len(I)):
+            M[np.ix_(I[b], I[b])] = inv[b]
+        S = (np.eye(n) - M @ D) @ S
+    return S
+
+
+def test_vcycle_two_level_without_smoothing_is_coarse_correction(small3):
+    """V(0,0) on a two-level hierarchy is the coarse-grid correction P D_c^{-1} P^H exactly."""
+    H = mg.Hierarchy.from_prolongators(small3.D[0], 32, small3.P[:1], agg=2, sap_block=(4, 2))
+    P, Dc = H.P[0].toarray(), H.D[1].toarray()
+    r = np.random.default_rng(4).standard_normal((H.n[0], 2)) + 0j
+    ref = P @ np.linalg.solve(Dc, P.conj().T @ r)
+    assert np.abs(H.vcycle(0, r, 0, 0) - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("pre,post", [(1, 1), (2, 1)])
+def test_vcycle_error_propagator(small3, pre, post):
+    """Three-level V(pre, post) cycle: with B_l the cycle as a linear map, the error propagator
+    I - B_l D_l equals S^post (I - P_l B_{l+1} P_l^H D_l) S^pre, S the SAP sweep's iteration matrix,
+    and B_L = D_L^{-1} on the coarsest level (built from dense blocks, independent of vcycle)."""
+    H = mg.Hierarchy.from_prolongators(small3.D[0], 32, small3.P, agg=2, sap_block=(4, 2))
+    B = [None] * H.levels
+    B[-1] = np.linalg.inv(H.D[-1].toarray())
+    for l in range(H.levels - 2, -1, -1):
+        n = H.n[l]
+        S = _sap_iteration_matrix(H.sap(l), n)
+        P, D = H.P[l].toarray(), H.D[l].toarray()
+        C = np.eye(n) - P @ B[l + 1] @ P.conj().T @ D
+        E = np.linalg.matrix_power(S, post) @ C @ np.linalg.matrix_power(S, pre)
+        B[l] = (np.eye(n) - E) @ np.linalg.inv(D)
+    r = np.random.default_rng(5).standard_normal((H.n[0], 3)) + 1j * np.random.default_rng(6).standard_normal(
+        (H.n[0], 3))
+    got = H.vcycle(0, r, pre, post)
+    ref = B[0] @ r
+    assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
+    # the cycle contracts the error of the fine system
+    D0 = H.D[0].toarray()
+    assert np.linalg.norm(np.eye(H.n[0]) - B[0] @ D0, 2) < 1.0
+
+
+def test_imported_prolongators_rebuild_the_hierarchy(hier):
+    """from_prolongators with the oracle's own P gives back its Galerkin operators; check_prolongator
+    accepts them; the GPU block layout round-trips; a row moved into another aggregate is caught."""
+    H2 = mg.Hierarchy.from_prolongators(hier.D[0], 64, hier.P, agg=4)
+    for l in range(hier.levels):
+        assert abs(H2.D[l] - hier.D[l]).max() < 1e-13
+    for l, P in enumerate(hier.P):
+        c = mg.check_prolongator(P, hier.side[l], hier.dof[l], 4)
+        assert c["orth"] < 1e-13 and c["support"] and c["chirality"]
+        Ls, d, Lc = hier.side[l], hier.dof[l], hier.side[l + 1]
+        ntv = hier.dof[l + 1] // 2
+        blocks = mg.aggregate_blocks(Ls, d, 4)
+        Pr = P.tocsr()
+        B = np.empty((Lc * Lc, 2, blocks.shape[-1], ntv), dtype=complex)
+        for T in range(Lc):
+            for X in range(Lc):
+                for ch in range(2):
+                    cols = (T * Lc + X) * 2 * ntv + ch * ntv + np.arange(ntv)
+                    B[T * Lc + X, ch] = Pr[blocks[X, T, ch]][:, cols].toarray()
+        assert abs(mg.prolongator_from_blocks(B, Ls, d, 4, ntv) - P).max() == 0
+    # planted mistake: swap one fine row of aggregate (0, 0) with a row of aggregate (1, 0)
+    P = hier.P[0].tolil()
+    i, j = 0, 2 * 4 + 0          # fine dof of site (0,0) and of site (4,0)
+    ri, rj = P.getrow(i).copy(), P.getrow(j).copy()
+    P[i, :] = rj
+    P[j, :] = ri
+    assert not mg.check_prolongator(P.tocsr(), 64, 2, 4)["support"]

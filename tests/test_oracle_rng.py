@@ -40,3 +40,23 @@ def test_streams_are_distinct():
     assert np.array_equal(a, rng.rademacher(1, 0, rng.PHASE_STOCH, 0, 256))
     # prefix property: component i does not depend on the vector length
     assert np.array_equal(a[:100], rng.rademacher(1, 0, rng.PHASE_STOCH, 0, 100))
+
+
+def test_z4_values_isotropy_and_second_moment():
+    """Z4 entries are the fourth roots of unity, equally likely; E|z|^2 = 1, E z = 0 and E z^2 = 0 (unlike
+    real Rademacher vectors, for which z^2 = 1)."""
+    n, s = 4096, 64
+    Z = np.stack([rng.z4(11, 1, rng.PHASE_STOCH, j, n) for j in range(s)])
+    vals, counts = np.unique(np.round(Z, 12), return_counts=True)
+    assert set(vals.tolist()) == {1, 1j, -1, -1j}
+    assert np.all(np.abs(counts / Z.size - 0.25) < 5 * np.sqrt(0.25 * 0.75 / Z.size))
+    assert np.allclose(np.abs(Z), 1.0)
+    assert abs(Z.mean()) < 5 / np.sqrt(Z.size)
+    assert abs((Z ** 2).mean()) < 5 / np.sqrt(Z.size)
+    C = np.conj(Z) @ Z.T / n
+    assert np.abs(C[~np.eye(s, dtype=bool)]).max() < 6 / np.sqrt(n)
+    # same counter words as the Rademacher stream: the real sign is the top bit
+    r = rng.rademacher(11, 1, rng.PHASE_STOCH, 3, n)
+    z = rng.z4(11, 1, rng.PHASE_STOCH, 3, n)
+    assert np.array_equal(np.where(np.isin(z, [1, 1j]), 1.0, -1.0), r)
+    assert np.array_equal(rng.noise(rng.NOISE_Z4, 11, 1, 0, 3, n), z)
