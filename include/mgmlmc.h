@@ -64,6 +64,17 @@ enum mgmlmc_form {
 
 enum mgmlmc_policy { MGMLMC_OPTIMAL = 0, MGMLMC_UNIFORM = 1 };
 
+enum mgmlmc_noise { /* distribution of the random vectors (Section 1, eq. random_props; Section 2) */
+  MGMLMC_NOISE_RADEMACHER = 0, /* real +-1 entries */
+  MGMLMC_NOISE_Z4 = 1          /* entries 1, i, -1, -i: variance ||offdiag(A)||_F^2 instead of 1/2 ||offdiag(A+A^T)||_F^2 */
+};
+
+enum mgmlmc_weight { /* the matrix whose trace is estimated (Section 1: traces "after multiplication with gamma-matrices") */
+  MGMLMC_TRACE_PLAIN = 0,  /* tr(D^{-1}) */
+  MGMLMC_TRACE_GAMMA5 = 1  /* tr(gamma5 D^{-1}), gamma5 = sigma_3 (chirality sign; on coarse levels the sign of the
+                              chirality block, which the aggregation preserves) */
+};
+
 enum mgmlmc_phase { /* streams of the counter-based Rademacher generator */
   MGMLMC_PHASE_STOCH = 0, MGMLMC_PHASE_SKETCH = 1, MGMLMC_PHASE_TESTVEC = 2, MGMLMC_PHASE_HUTCH = 3
 };
@@ -114,6 +125,10 @@ int schwinger_apply(mgmlmc_ctx* ctx, const double* U, int L, double m0,
  * word(i) = mix64(key + 0x9E3779B97F4A7C15 * (i+1)); sign = top bit. */
 int mgmlmc_rademacher(mgmlmc_ctx* ctx, uint64_t seed, int level, int phase,
                       int64_t sample0, int64_t n, int nrhs, double* out);
+/* Same streams with the distribution `kind` (mgmlmc_noise): MGMLMC_NOISE_RADEMACHER gives the vectors of
+ * mgmlmc_rademacher, MGMLMC_NOISE_Z4 entry i = i^q with q = word(i) >> 62 (the top two bits). */
+int mgmlmc_noise(mgmlmc_ctx* ctx, int kind, uint64_t seed, int level, int phase,
+                 int64_t sample0, int64_t n, int nrhs, double* out);
 
 /* ---- multigrid hierarchy (Section 3.1; set-up of Section 4) ------------- */
 
@@ -186,6 +201,20 @@ int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x
  * bounded wait (it then stopped early and freed its tensor memory), else OK. */
 int mg_tc_status(mgmlmc_ctx* ctx, mgmlmc_hier* h);
 
+/* In-place inverse of one dense n x n matrix on the device (the coarsest-level
+ * direct solve of Section 3.1: tau_L of Algorithm 2 is the trace of D_L^{-1}):
+ * Gauss-Jordan elimination with partial pivoting (largest |A_ik|, ties to the
+ * smallest row) in one cooperative kernel whose CTAs meet at a grid barrier per
+ * column.  A: device, row-major, complex128 (prec MGMLMC_FP64) or complex64
+ * (MGMLMC_FP32), 1 <= n <= 8192 (the pivot row is staged in shared memory).
+ * barrier_polls: poll limit of every barrier wait (0 = the default, about a
+ * second); negative = self-test of the bounded wait: the barrier then waits for
+ * one arrival more than the grid has, so every wait runs out after
+ * -barrier_polls polls and the call returns MGMLMC_ERR_TIMEOUT with A left
+ * partly eliminated (the kernel stops at the first expired wait; the device
+ * stays usable).  Returns MGMLMC_ERR_NAN for a zero pivot (singular A). */
+int mg_dense_inverse(mgmlmc_ctx* ctx, void* A, int n, int prec, int64_t barrier_polls);
+
 /* One V-cycle from level l as an approximate solve x ~ D_l^{-1} b: SAP
  * pre-smoothing, coarse correction P_l V(l+1)(P_l^H r), SAP post-smoothing;
  * the coarsest level applies its dense inverse.  prec FP64 or FP32. */
@@ -222,11 +251,14 @@ int fgmres_batched(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* b, vo
 
 /* ---- MG-MLMC level differences (Section 3.1, Algorithm 2) -------------- */
 
-/* y = (D_l^{-1} - P_l D_{l+1}^{-1} P_l^H) zeta on level l (0 <= l < nlev-1):
- * the level difference of eq. mlmc_dec_trace_reduced; for the accumulated form
- * of eq. mlmc_decomp_matrix apply it to Rhat_l zeta and prolong.  zeta, y:
- * device complex128 [nrhs][n_l]; solves to sp->tol. */
-int mlmc_level_sample(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const double* zeta,
+/* Level difference l (0 <= l < nlev-1) applied to nrhs vectors; solves to sp->tol.
+ *   form MGMLMC_REDUCED:      y = (D_l^{-1} - P_l D_{l+1}^{-1} P_l^H) zeta
+ *                             (eq. mlmc_dec_trace_reduced), zeta and y level-size [nrhs][n_l];
+ *   form MGMLMC_ACCUMULATED:  y = (Phat_l D_l^{-1} Rhat_l - Phat_{l+1} D_{l+1}^{-1} Rhat_{l+1}) zeta
+ *                             (eq. mlmc_decomp_matrix), zeta and y fine-size [nrhs][n_0]; computed as
+ *                             Phat_l A_l Rhat_l zeta with the reduced A_l (Rhat_l = Phat_l^H).
+ * zeta, y: device complex128, must not alias. */
+int mlmc_level_sample(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, int form, const double* zeta,
                       double* y, int nrhs, const solve_params* sp, solve_stats* st);
 
 /* out = Rhat_l zeta = P_{l-1}^H ... P_0^H zeta (fine -> level l), FP64. */
@@ -244,6 +276,12 @@ int mg_restrict_to_level(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const doubl
 int hutchpp_sketch_qr(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, int d, int k, uint64_t seed,
                       int form, const solve_params* sp, mgmlmc_sketch** out, double* tau_lr);
 void hutchpp_sketch_destroy(mgmlmc_sketch* s);
+/* The QR step of the sketch (Algorithm 2, "Compute QR-factoriz. Y_l = Q_l K_l") in place on a caller's
+ * basis: Y (device complex128 [d][n], vector i at Y + i n) becomes Q with Q^H Q = I by CholeskyQR2 (Gram
+ * matrix G = Y^H Y in FP64, Cholesky G = R^H R with real positive diagonal, Y <- Y R^{-1}, done twice).
+ * 1 <= d <= 32, n >= d.  Returns MGMLMC_ERR_NOT_POSDEF when a Gram matrix is not positive definite (Y of
+ * rank < d); Y is then left partly transformed. */
+int hutchpp_cholqr2(mgmlmc_ctx* ctx, double* Y, int d, int64_t n);
 /* Copy Q to a device buffer complex128 [d][n_l]. */
 int hutchpp_sketch_get_q(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, double* q_dev, int* d, int64_t* n);
 
@@ -263,7 +301,8 @@ int hutchpp_project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double* zeta,
  * no context is needed.  Partial sums go to a fixed file-scope device array of
  * about 4.3 MB that every GPU loading the library holds until exit; the first
  * call on a device (with that device current) looks up the array's device
- * address once, so make that first call before any stream capture.  Every call
+ * address once per CUDA context, so make that first call before any stream
+ * capture (and again first after a cudaDeviceReset).  Every call
  * overwrites the slots it later reads (no state carries over), but all calls
  * share the one array: calls that overlap on the GPU (other streams, other host
  * threads) race and give wrong results.
@@ -273,7 +312,10 @@ int hutchpp_project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double* zeta,
  *   tau_out  DEVICE complex128 [nrhs]: tau_r = zeta_r^H y_r - (Q^H zeta_r)^H (Q^H y_r)
  * Returns MGMLMC_ERR_INVALID_ARG for nrhs > 256, d > 32, negative sizes or null
  * pointers (nothing is launched), MGMLMC_ERR_CUDA if the address lookup or a
- * launch fails, MGMLMC_OK otherwise (nrhs == 0 is a no-op). */
+ * launch fails (an error left pending by earlier work on the calling thread is
+ * picked up and reported here too), MGMLMC_OK otherwise (nrhs == 0 is a no-op).
+ * The pointers themselves cannot be checked: shapes and devices are the
+ * caller's responsibility (the Python binding checks them). */
 int hutchpp_project_noalloc(void* stream, const double* Q, int d, const double* zeta, const double* y,
                             int64_t n, int nrhs, double* tau_out);
 
@@ -326,6 +368,8 @@ typedef struct {
   solve_params solve;
   double* sample_out[MGMLMC_MAX_LEVELS]; /* optional host buffers, complex128 [sample_cap] */
   int64_t sample_cap;
+  int noise;                        /* mgmlmc_noise of the sketch and stochastic vectors (Rademacher) */
+  int weight;                       /* mgmlmc_weight: tr(D^{-1}) or tr(gamma5 D^{-1}) (plain) */
 } est_params;
 
 typedef struct {
@@ -342,6 +386,9 @@ typedef struct {
   int64_t solves;                   /* linear solves (right-hand sides) issued */
   int64_t inner_iters;              /* total inner Krylov iterations */
   int steps;                        /* s at which Algorithm 2 stopped */
+  double flops;                     /* counted operator flops of all solves (sketches included): sum over
+                                       solves of (inner iterations + 1) x the nnz flops of the level's operator
+                                       (8 flops per complex non-zero), the cost model of Section 4 */
 } est_result;
 
 int est_params_default(est_params* p);
@@ -352,6 +399,38 @@ int est_params_default(est_params* p);
  * sample (s = 1, 2, ...) on them, so the stopping decisions are those of the
  * per-sample algorithm and extra batch samples are discarded. */
 int trace_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const est_params* p, est_result* r);
+
+/* ---- plain Hutchinson (Algorithm 1) ------------------------------------- */
+
+typedef struct {
+  double eps;          /* target relative 1-sigma accuracy */
+  int nrhs_first;      /* first batch of samples (32) */
+  int nrhs_max;        /* largest batch (256) */
+  uint64_t seed;       /* sample s uses the stream (seed, level 0, MGMLMC_PHASE_HUTCH, s) */
+  int noise;           /* mgmlmc_noise */
+  int weight;          /* mgmlmc_weight */
+  int min_samples;     /* >= 2 */
+  int64_t max_samples;
+  solve_params solve;  /* solves on level 0 (e.g. precond = 0, m = 30: unpreconditioned GMRES(30)) */
+  double* sample_out;  /* optional host buffer, complex128 [sample_cap] */
+  int64_t sample_cap;
+} hutch_params;
+
+typedef struct {
+  double tau[2];       /* estimate of tr(D^{-1}) (or tr(gamma5 D^{-1})) */
+  double sigma;        /* sqrt(V / s) */
+  int64_t N;           /* samples used (s at the stop) */
+  int64_t computed;    /* samples computed (>= N) */
+  int64_t solves;
+  int64_t inner_iters;
+} hutch_result;
+
+int hutch_params_default(hutch_params* p);
+
+/* Algorithm 1 on the fine operator of h: tau_s = zeta_s^H D^{-1} zeta_s (or zeta_s^H gamma5 D^{-1} zeta_s),
+ * stop once V/s <= (eps |tau|)^2.  Samples are solved in batches; the host replays the per-sample stop, so
+ * N is that of the per-sample algorithm and surplus samples are discarded. */
+int hutchinson_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const hutch_params* p, hutch_result* r);
 
 /* The target-accuracy update of Algorithm 2 for one step (host only, no GPU):
  * active[l] (in/out, 0/1) becomes 0 when V[l]/N[l] <= rho_l^2 with

@@ -175,7 +175,8 @@ def check_prolongator(P: sp.spmatrix, Ls: int, d: int, agg: int) -> dict:
     Pc = P.tocoo()
     dc = P.shape[1] // ((Ls // agg) ** 2)
     Lc = Ls // agg
-    orth = float(np.abs((P.conj().T @ P).toarray() - np.eye(P.shape[1])).max())
+    G = (P.conj().T @ P - sp.identity(P.shape[1], dtype=complex, format="csr")).tocsr()  # sparse: blocks
+    orth = float(np.abs(G.data).max()) if G.nnz else 0.0
     fs, fk = Pc.row // d, Pc.row % d
     cs, ck = Pc.col // dc, Pc.col % dc
     ft, fx, ct, cx = fs // Ls, fs % Ls, cs // Lc, cs % Lc
@@ -197,6 +198,25 @@ def stencil_blocks(Dl: sp.spmatrix, Ls: int, d: int) -> np.ndarray:
                 s2 = ((T + dt) % Ls) * Ls + (X + dx) % Ls
                 S[T, X, di] = Dd[r][:, s2 * d + k].toarray()
     return S
+
+
+def sparse_from_stencil(S: np.ndarray, Ls: int, d: int) -> sp.csr_matrix:
+    """The level operator from its blocks (inverse of stencil_blocks): S[site T*Ls+X, dir, d, d], dir = self,
+    +x, -x, +t, -t, block (s, dir) = D[rows of s, cols of s+dir]; coinciding neighbours add up."""
+    S = np.asarray(S).reshape(Ls * Ls, 5, d, d)
+    s = np.arange(Ls * Ls)
+    T, X = s // Ls, s % Ls
+    nbr = [s, T * Ls + (X + 1) % Ls, T * Ls + (X - 1) % Ls, ((T + 1) % Ls) * Ls + X, ((T - 1) % Ls) * Ls + X]
+    i, j = np.meshgrid(np.arange(d), np.arange(d), indexing="ij")
+    rows, cols, vals = [], [], []
+    for di in range(5):
+        rows.append((s[:, None, None] * d + i[None]).ravel())
+        cols.append((nbr[di][:, None, None] * d + j[None]).ravel())
+        vals.append(S[:, di].ravel())
+    n = Ls * Ls * d
+    D = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)).tocsr()
+    D.sum_duplicates()
+    return D
 
 
 class Hierarchy:

@@ -18,6 +18,8 @@ FP64, FP32, MIXED, TF32 = 0, 1, 2, 3
 ACCUMULATED, REDUCED = 0, 1
 OPTIMAL, UNIFORM = 0, 1
 PHASE_STOCH, PHASE_SKETCH, PHASE_TESTVEC, PHASE_HUTCH = 0, 1, 2, 3
+NOISE_RADEMACHER, NOISE_Z4 = 0, 1
+TRACE_PLAIN, TRACE_GAMMA5 = 0, 1
 
 
 class MgParams(C.Structure):
@@ -43,7 +45,8 @@ class EstParams(C.Structure):
                 ("nrhs_first", C.c_int), ("policy", C.c_int), ("form", C.c_int), ("seed", C.c_uint64),
                 ("cost", C.c_double * MAX_LEVELS), ("cost_mode", C.c_int), ("min_samples", C.c_int),
                 ("max_samples", C.c_int64), ("solve", SolveParams),
-                ("sample_out", C.POINTER(C.c_double) * MAX_LEVELS), ("sample_cap", C.c_int64)]
+                ("sample_out", C.POINTER(C.c_double) * MAX_LEVELS), ("sample_cap", C.c_int64),
+                ("noise", C.c_int), ("weight", C.c_int)]
 
 
 class EstResult(C.Structure):
@@ -51,7 +54,18 @@ class EstResult(C.Structure):
                 ("N", C.c_int64 * MAX_LEVELS), ("computed", C.c_int64 * MAX_LEVELS),
                 ("mean", (C.c_double * 2) * MAX_LEVELS), ("V", C.c_double * MAX_LEVELS),
                 ("C", C.c_double * MAX_LEVELS), ("tau_lr", (C.c_double * 2) * MAX_LEVELS),
-                ("solves", C.c_int64), ("inner_iters", C.c_int64), ("steps", C.c_int)]
+                ("solves", C.c_int64), ("inner_iters", C.c_int64), ("steps", C.c_int), ("flops", C.c_double)]
+
+
+class HutchParams(C.Structure):
+    _fields_ = [("eps", C.c_double), ("nrhs_first", C.c_int), ("nrhs_max", C.c_int), ("seed", C.c_uint64),
+                ("noise", C.c_int), ("weight", C.c_int), ("min_samples", C.c_int), ("max_samples", C.c_int64),
+                ("solve", SolveParams), ("sample_out", C.POINTER(C.c_double)), ("sample_cap", C.c_int64)]
+
+
+class HutchResult(C.Structure):
+    _fields_ = [("tau", C.c_double * 2), ("sigma", C.c_double), ("N", C.c_int64), ("computed", C.c_int64),
+                ("solves", C.c_int64), ("inner_iters", C.c_int64)]
 
 
 vp = C.c_void_p
@@ -69,6 +83,7 @@ SIGNATURES = {
     "mgmlmc_timing_report": (ip, [vp, C.c_char_p, C.c_int64]),
     "schwinger_apply": (ip, [vp, vp, ip, C.c_double, vp, vp, ip, ip]),
     "mgmlmc_rademacher": (ip, [vp, C.c_uint64, ip, ip, C.c_int64, C.c_int64, ip, vp]),
+    "mgmlmc_noise": (ip, [vp, ip, C.c_uint64, ip, ip, C.c_int64, C.c_int64, ip, vp]),
     "mg_params_default": (ip, [C.POINTER(MgParams)]),
     "mg_setup": (ip, [vp, vp, ip, C.c_double, C.POINTER(MgParams), C.POINTER(vp)]),
     "mg_destroy": (None, [vp]),
@@ -81,11 +96,13 @@ SIGNATURES = {
     "mg_get_prolongator": (ip, [vp, vp, ip, vp]),
     "mg_get_stencil": (ip, [vp, vp, ip, vp]),
     "mg_vcycle": (ip, [vp, vp, ip, vp, vp, ip, ip]),
+    "mg_dense_inverse": (ip, [vp, vp, ip, ip, C.c_int64]),
+    "hutchpp_cholqr2": (ip, [vp, vp, ip, C.c_int64]),
     "mg_smooth": (ip, [vp, vp, ip, vp, vp, ip, ip, ip]),
     "mg_tc_status": (ip, [vp, vp]),
     "solve_params_default": (ip, [C.POINTER(SolveParams)]),
     "fgmres_batched": (ip, [vp, vp, ip, vp, vp, ip, C.POINTER(SolveParams), C.POINTER(SolveStats), vp]),
-    "mlmc_level_sample": (ip, [vp, vp, ip, vp, vp, ip, C.POINTER(SolveParams), C.POINTER(SolveStats)]),
+    "mlmc_level_sample": (ip, [vp, vp, ip, ip, vp, vp, ip, C.POINTER(SolveParams), C.POINTER(SolveStats)]),
     "mg_restrict_to_level": (ip, [vp, vp, ip, vp, vp, ip]),
     "hutchpp_sketch_qr": (ip, [vp, vp, ip, ip, ip, C.c_uint64, ip, C.POINTER(SolveParams), C.POINTER(vp), dp]),
     "hutchpp_sketch_destroy": (None, [vp]),
@@ -103,6 +120,8 @@ SIGNATURES = {
     "mg_attach_nn": (ip, [vp, vp, vp]),
     "est_params_default": (ip, [C.POINTER(EstParams)]),
     "trace_estimate": (ip, [vp, vp, C.POINTER(EstParams), C.POINTER(EstResult)]),
+    "hutch_params_default": (ip, [C.POINTER(HutchParams)]),
+    "hutchinson_estimate": (ip, [vp, vp, C.POINTER(HutchParams), C.POINTER(HutchResult)]),
     "mlmc_update_active": (ip, [ip, C.POINTER(ip), dp, C.POINTER(C.c_int64), dp, C.c_double, C.c_double, ip, ip]),
 }
 

@@ -13,13 +13,15 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (ACCUMULATED, FP32, FP64, MIXED, OPTIMAL, REDUCED, TF32, UNIFORM, EstParams, EstResult,
-                   MgParams, SolveParams, SolveStats, check)
+from ._lib import (ACCUMULATED, FP32, FP64, MIXED, NOISE_RADEMACHER, NOISE_Z4, OPTIMAL, REDUCED, TF32,
+                   TRACE_GAMMA5, TRACE_PLAIN, UNIFORM, EstParams, EstResult, HutchParams, HutchResult, MgParams,
+                   SolveParams, SolveStats, check)
 
 __all__ = ["Context", "Hierarchy", "Sketch", "schwinger_apply", "mgmlmc_rademacher", "mg_setup",
            "fgmres_batched", "mlmc_level_sample", "mg_restrict_to_level", "hutchpp_sketch_qr",
-           "hutchpp_project", "trace_estimate", "mlmc_update_active", "FP64", "FP32", "MIXED",
-           "ACCUMULATED", "REDUCED", "OPTIMAL", "UNIFORM"]
+           "hutchpp_project", "trace_estimate", "hutchinson_estimate", "mgmlmc_noise", "mlmc_update_active",
+           "FP64", "FP32", "MIXED", "ACCUMULATED", "REDUCED", "OPTIMAL", "UNIFORM", "NOISE_RADEMACHER", "NOISE_Z4",
+           "TRACE_PLAIN", "TRACE_GAMMA5"]
 
 
 def _ptr(t: torch.Tensor, dtype=None) -> int:
@@ -92,6 +94,16 @@ def mgmlmc_rademacher(ctx: Context, seed: int, level: int, phase: int, sample0: 
         out = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
     check(_lib.load().mgmlmc_rademacher(ctx.ptr, seed, level, phase, sample0, n, nrhs,
                                         _ptr(out, torch.complex128)), ctx.ptr)
+    return out
+
+
+def mgmlmc_noise(ctx: Context, kind: int, seed: int, level: int, phase: int, sample0: int, n: int, nrhs: int,
+                 out: torch.Tensor | None = None) -> torch.Tensor:
+    """Rademacher (kind NOISE_RADEMACHER) or Z4 (NOISE_Z4) vectors of the counter-based streams."""
+    if out is None:
+        out = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
+    check(_lib.load().mgmlmc_noise(ctx.ptr, kind, seed, level, phase, sample0, n, nrhs,
+                                   _ptr(out, torch.complex128)), ctx.ptr)
     return out
 
 
@@ -212,10 +224,15 @@ def fgmres_batched(ctx: Context, h: Hierarchy, level: int, b: torch.Tensor, x: t
 
 
 def mlmc_level_sample(ctx: Context, h: Hierarchy, level: int, zeta: torch.Tensor, y: torch.Tensor,
-                      **solve) -> dict:
+                      form: int = REDUCED, **solve) -> dict:
+    """Level difference `level` applied to zeta: level-size vectors (REDUCED) or fine-size vectors
+    (ACCUMULATED, y = Phat A Rhat zeta)."""
+    n = h.n[0] if form == ACCUMULATED else h.n[level]
+    if zeta.shape[-1] != n or y.shape != zeta.shape:
+        raise ValueError("zeta and y must be [nrhs, %d] for this form" % n)
     sp = solve_params(**solve)
     st = SolveStats()
-    check(_lib.load().mlmc_level_sample(ctx.ptr, h.ptr, level, _ptr(zeta, torch.complex128),
+    check(_lib.load().mlmc_level_sample(ctx.ptr, h.ptr, level, form, _ptr(zeta, torch.complex128),
                                         _ptr(y, torch.complex128), zeta.shape[0], C.byref(sp), C.byref(st)),
           ctx.ptr)
     return _stats(st)
@@ -263,6 +280,21 @@ def hutchpp_sketch_qr(ctx: Context, h: Hierarchy, level: int, d: int, k: int, se
     check(_lib.load().hutchpp_sketch_qr(ctx.ptr, h.ptr, level, d, k, seed, form, C.byref(sp), C.byref(s), t),
           ctx.ptr)
     return Sketch(ctx, s), complex(t[0], t[1])
+
+
+def mg_dense_inverse(ctx: Context, A: torch.Tensor, prec: int = FP64, barrier_polls: int = 0):
+    """In-place inverse of the square device matrix A (complex128 for FP64, complex64 for FP32)."""
+    if A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be square")
+    check(_lib.load().mg_dense_inverse(ctx.ptr, _ptr(A, _vec_dtype(prec)), A.shape[0], prec, barrier_polls),
+          ctx.ptr)
+
+
+def hutchpp_cholqr2(ctx: Context, Y: torch.Tensor):
+    """In-place CholeskyQR2 of the basis Y [d, n] (rows are the vectors), complex128."""
+    if Y.dim() != 2:
+        raise ValueError("Y must be [d, n]")
+    check(_lib.load().hutchpp_cholqr2(ctx.ptr, _ptr(Y, torch.complex128), Y.shape[0], Y.shape[1]), ctx.ptr)
 
 
 def hutchpp_project(ctx: Context, sketch: Sketch | None, zeta: torch.Tensor, y: torch.Tensor) -> np.ndarray:
@@ -355,13 +387,37 @@ def unpack_params(p: np.ndarray, layers: int, channels: int):
     return W, b
 
 
+def check_noalloc_args(Q, zeta, y, tau_out, device=None):
+    """Shape and device checks of hutchpp_project_noalloc's tensors (the C entry point receives bare pointers
+    and cannot check them): zeta and y [nrhs, n] alike, Q [d, n], tau_out with at least nrhs entries, every
+    tensor on `device` (the device the launches go to; not checked when None).  Raises ValueError."""
+    if zeta.dim() != 2:
+        raise ValueError("zeta must be [nrhs, n]")
+    nrhs, n = zeta.shape
+    if tuple(y.shape) != (nrhs, n):
+        raise ValueError("y must have the shape of zeta, %s, got %s" % (tuple(zeta.shape), tuple(y.shape)))
+    if Q is not None and (Q.dim() != 2 or Q.shape[1] != n):
+        raise ValueError("Q must be [d, %d], got %s" % (n, tuple(Q.shape)))
+    if tau_out.numel() < nrhs:
+        raise ValueError("tau_out holds %d entries, %d needed" % (tau_out.numel(), nrhs))
+    if device is not None:
+        for name, t in (("Q", Q), ("zeta", zeta), ("y", y), ("tau_out", tau_out)):
+            if t is not None and t.device != device:
+                raise ValueError("%s is on %s, the launches go to %s" % (name, t.device, device))
+    return nrhs, n, (0 if Q is None else Q.shape[0])
+
+
 def hutchpp_project_noalloc(Q: torch.Tensor | None, zeta: torch.Tensor, y: torch.Tensor,
                             tau_out: torch.Tensor, stream: torch.cuda.Stream | None = None):
     """Projected samples into the device tensor `tau_out` ([nrhs] complex128) without any
-    device allocation inside the library (for callers that cannot allocate; see the header)."""
+    device allocation inside the library (for callers that cannot allocate; see the header).
+    The launches go to the current device on `stream` (default: its current stream); every tensor
+    must live on that device."""
     s = stream if stream is not None else torch.cuda.current_stream()
-    nrhs, n = zeta.shape
-    d = 0 if Q is None else Q.shape[0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if s.device != dev:
+        raise ValueError("stream is on %s, the current device is %s" % (s.device, dev))
+    nrhs, n, d = check_noalloc_args(Q, zeta, y, tau_out, dev)
     check(_lib.load().hutchpp_project_noalloc(C.c_void_p(s.cuda_stream), _ptr(Q, torch.complex128) if d else None,
                                               d, _ptr(zeta, torch.complex128), _ptr(y, torch.complex128), n, nrhs,
                                               _ptr(tau_out, torch.complex128)))
@@ -370,7 +426,8 @@ def hutchpp_project_noalloc(Q: torch.Tensor | None, zeta: torch.Tensor, y: torch
 def trace_estimate(ctx: Context, h: Hierarchy, eps: float = 1e-3, d=32, k: int = 2, nrhs_max: int = 256,
                    nrhs_first: int = 32, policy: int = OPTIMAL, form: int = ACCUMULATED, seed: int = 0,
                    cost=None, cost_mode: int = 0, min_samples: int = 2, max_samples: int = 1 << 20,
-                   keep_samples: int = 0, **solve) -> dict:
+                   keep_samples: int = 0, noise: int = NOISE_RADEMACHER, weight: int = TRACE_PLAIN,
+                   **solve) -> dict:
     p = EstParams()
     lib = _lib.load()
     lib.est_params_default(C.byref(p))
@@ -382,6 +439,7 @@ def trace_estimate(ctx: Context, h: Hierarchy, eps: float = 1e-3, d=32, k: int =
     p.eps, p.k, p.nrhs_max, p.nrhs_first = eps, k, nrhs_max, nrhs_first
     p.policy, p.form, p.seed, p.cost_mode = policy, form, seed, cost_mode
     p.min_samples, p.max_samples = min_samples, max_samples
+    p.noise, p.weight = noise, weight
     p.solve = solve_params(**solve)
     bufs = []
     if keep_samples:
@@ -397,9 +455,33 @@ def trace_estimate(ctx: Context, h: Hierarchy, eps: float = 1e-3, d=32, k: int =
                mean=[complex(r.mean[l][0], r.mean[l][1]) for l in range(nd)],
                V=[r.V[l] for l in range(nd)], C=[r.C[l] for l in range(nd)],
                tau_lr=[complex(r.tau_lr[l][0], r.tau_lr[l][1]) for l in range(nd)],
-               solves=r.solves, inner_iters=r.inner_iters, steps=r.steps)
+               solves=r.solves, inner_iters=r.inner_iters, steps=r.steps, flops=r.flops)
     if keep_samples:
         out["samples"] = [bufs[l].view(np.complex128)[: min(keep_samples, out["computed"][l])] for l in range(nd)]
+    return out
+
+
+def hutchinson_estimate(ctx: Context, h: Hierarchy, eps: float = 1e-2, seed: int = 0, nrhs_first: int = 32,
+                        nrhs_max: int = 256, noise: int = NOISE_RADEMACHER, weight: int = TRACE_PLAIN,
+                        min_samples: int = 2, max_samples: int = 1 << 20, keep_samples: int = 0, **solve) -> dict:
+    """Plain Hutchinson (Algorithm 1) on the fine operator of h."""
+    p = HutchParams()
+    lib = _lib.load()
+    lib.hutch_params_default(C.byref(p))
+    p.eps, p.seed, p.nrhs_first, p.nrhs_max = eps, seed, nrhs_first, nrhs_max
+    p.noise, p.weight, p.min_samples, p.max_samples = noise, weight, min_samples, max_samples
+    p.solve = solve_params(**solve)
+    buf = None
+    if keep_samples:
+        buf = np.zeros(2 * keep_samples, dtype=np.float64)
+        p.sample_out = buf.ctypes.data_as(C.POINTER(C.c_double))
+        p.sample_cap = keep_samples
+    r = HutchResult()
+    check(lib.hutchinson_estimate(ctx.ptr, h.ptr, C.byref(p), C.byref(r)), ctx.ptr)
+    out = dict(tau=complex(r.tau[0], r.tau[1]), sigma=r.sigma, N=r.N, computed=r.computed, solves=r.solves,
+               inner_iters=r.inner_iters)
+    if keep_samples:
+        out["samples"] = buf.view(np.complex128)[: min(keep_samples, r.computed)]
     return out
 
 

@@ -145,6 +145,18 @@ int mgmlmc_rademacher(mgmlmc_ctx* ctx, uint64_t seed, int level, int phase, int6
   });
 }
 
+int mgmlmc_noise(mgmlmc_ctx* ctx, int kind, uint64_t seed, int level, int phase, int64_t sample0, int64_t n,
+                 int nrhs, double* out) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(out, "null pointer");
+    MG_CHECK_ARG(kind == MGMLMC_NOISE_RADEMACHER || kind == MGMLMC_NOISE_Z4, "unknown noise");
+    MG_CHECK_ARG(level >= 0 && level < 256 && phase >= 0 && phase < 256, "level/phase out of range");
+    MG_CHECK_ARG(sample0 >= 0 && n >= 0 && nrhs >= 0, "negative size");
+    if (n == 0 || nrhs == 0) return;
+    noise_fill(ctx->stream, kind, seed, level, phase, sample0, (long)n, nrhs, (double2*)out);
+  });
+}
+
 int mg_params_default(mg_params* p) {
   if (!p) return MGMLMC_ERR_INVALID_ARG;
   p->levels = 0;
@@ -310,6 +322,27 @@ int mg_get_stencil(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* hos
   });
 }
 
+int mg_dense_inverse(mgmlmc_ctx* ctx, void* A, int n, int prec, int64_t barrier_polls) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(A, "null pointer");
+    MG_CHECK_ARG(n >= 1 && n <= 8192, "n must be 1..8192");
+    MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32, "FP64 or FP32");
+    cudaStream_t st = ctx->stream;
+    DBuf piv(sizeof(int) * n, st), work(invert_large_work_bytes(n), st), flags(2 * sizeof(int), st);
+    MG_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), st));
+    int* f = flags.as<int>();
+    if (prec == MGMLMC_FP64)
+      invert_large<double2>(st, (double2*)A, n, piv.as<int>(), work.p, f, f + 1, (long)barrier_polls);
+    else
+      invert_large<float2>(st, (float2*)A, n, piv.as<int>(), work.p, f, f + 1, (long)barrier_polls);
+    int hf[2];
+    MG_CUDA(cudaMemcpyAsync(hf, f, sizeof(hf), cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+    if (hf[1]) throw Error(MGMLMC_ERR_TIMEOUT, "dense inverse: a grid-barrier wait ran out");
+    if (hf[0]) throw Error(MGMLMC_ERR_NAN, "dense inverse: zero pivot (singular matrix)");
+  });
+}
+
 int mg_vcycle(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* b, void* x, int nrhs, int prec) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && b && x && b != x, "null or aliased pointer");
@@ -366,15 +399,18 @@ int fgmres_batched(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* b, vo
   return rc;
 }
 
-int mlmc_level_sample(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const double* zeta, double* y, int nrhs,
+int mlmc_level_sample(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, int form, const double* zeta, double* y, int nrhs,
                       const solve_params* sp, solve_stats* st) {
   int nc = 0;
   int rc = guarded(ctx, [&] {
     MG_CHECK_ARG(h && zeta && y && sp && (const void*)zeta != (void*)y, "null or aliased pointer");
     const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "level difference out of range");
+    MG_CHECK_ARG(form == MGMLMC_ACCUMULATED || form == MGMLMC_REDUCED, "unknown form");
     if (nrhs <= 0) return;
-    SolveOut o = level_sample(h, level, (const double2*)zeta, (double2*)y, nrhs, *sp);
+    SolveOut o = form == MGMLMC_ACCUMULATED
+                     ? level_sample_accumulated(h, level, (const double2*)zeta, (double2*)y, nrhs, *sp)
+                     : level_sample(h, level, (const double2*)zeta, (double2*)y, nrhs, *sp);
     fill_stats(o, st);
     nc = !o.converged;
   });
@@ -414,6 +450,15 @@ void hutchpp_sketch_destroy(mgmlmc_sketch* s) {
   if (!s) return;
   cudaStreamSynchronize(s->st);
   delete s;
+}
+
+int hutchpp_cholqr2(mgmlmc_ctx* ctx, double* Y, int d, int64_t n) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(Y, "null pointer");
+    MG_CHECK_ARG(d >= 1 && d <= 32, "d must be 1..32");
+    MG_CHECK_ARG(n >= d, "need n >= d");
+    cholesky_qr2(ctx, (double2*)Y, d, (long)n);
+  });
 }
 
 int hutchpp_sketch_get_q(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, double* q_dev, int* d, int64_t* n) {
@@ -456,7 +501,33 @@ int est_params_default(est_params* p) {
   p->min_samples = 2;
   p->max_samples = 1 << 20;
   solve_params_default(&p->solve);
+  p->noise = MGMLMC_NOISE_RADEMACHER;
+  p->weight = MGMLMC_TRACE_PLAIN;
   return MGMLMC_OK;
+}
+
+int hutch_params_default(hutch_params* p) {
+  if (!p) return MGMLMC_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->eps = 1e-2;
+  p->nrhs_first = 32;
+  p->nrhs_max = 256;
+  p->noise = MGMLMC_NOISE_RADEMACHER;
+  p->weight = MGMLMC_TRACE_PLAIN;
+  p->min_samples = 2;
+  p->max_samples = 1 << 20;
+  solve_params_default(&p->solve);
+  return MGMLMC_OK;
+}
+
+int hutchinson_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const hutch_params* p, hutch_result* r) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && p && r, "null pointer");
+    h->ctx = ctx;
+    MG_CHECK_ARG(p->solve.tol > 0 && p->solve.maxit > 0, "tol and maxit must be positive");
+    check_prec(p->solve.prec);
+    hutchinson(h, *p, r);
+  });
 }
 
 int trace_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const est_params* p, est_result* r) {

@@ -142,8 +142,8 @@ __global__ void k_gm_init(const double* __restrict__ bn2, const int* __restrict_
   if (r >= nrhs) return;
   const double b = sqrt(bn2[r]);
   bnorm[r] = b;
-  act[r] = (b > 0.0) && (act_in ? act_in[r] : 1);
-  relres[r] = 0.0;
+  act[r] = (b > 0.0) && isfinite(b) && (act_in ? act_in[r] : 1);
+  relres[r] = isfinite(b) ? 0.0 : b;  // a NaN/Inf right-hand side is reported, not solved
   its[r] = 0;
 }
 
@@ -462,8 +462,8 @@ __global__ void k_mixed_check(const double* __restrict__ rn2, const double* __re
 __global__ void k_init_act(const double* __restrict__ bn2, int* act, double* relres, int nrhs) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
-  act[r] = bn2[r] > 0.0;
-  relres[r] = 0.0;
+  act[r] = bn2[r] > 0.0 && isfinite(bn2[r]);
+  relres[r] = isfinite(bn2[r]) ? 0.0 : bn2[r];  // a NaN/Inf right-hand side is reported, not solved
 }
 
 static SolveOut finish_out(mgmlmc_ctx* ctx, const int* its_dev, const double* relres_dev, int nrhs, double tol,
@@ -481,11 +481,8 @@ static SolveOut finish_out(mgmlmc_ctx* ctx, const int* its_dev, const double* re
   for (int r = 0; r < nrhs; ++r) {
     o.iters = std::max(o.iters, o.its[r]);
     o.total_iters += o.its[r];
-    if (!(rr[r] == rr[r])) {
-      o.max_relres = rr[r];
-      o.converged = 0;
-      continue;
-    }
+    if (!std::isfinite(rr[r]))
+      throw Error(MGMLMC_ERR_NAN, "a residual norm became NaN or infinite (right-hand side " + std::to_string(r) + ")");
     o.max_relres = std::max(o.max_relres, rr[r]);
     if (rr[r] > tol) o.converged = 0;
   }
@@ -589,6 +586,14 @@ SolveOut level_sample(mgmlmc_hier* h, int l, const double2* zeta, double2* y, in
   return o;
 }
 
+// non-zeros of D_m as the cost model counts them: 9 per fine row, a 5-point block stencil on coarse levels, the
+// dense inverse on the coarsest level
+static double level_nnz(const mgmlmc_hier* h, int m) {
+  const LevelData& L = h->lv[m];
+  if (m == h->nlev - 1) return (double)L.n * (double)L.n;
+  return (double)L.n * (m == 0 ? 9.0 : 5.0 * L.dof);
+}
+
 // Level-difference applications of several levels at once (items with distinct levels).  Difference l needs
 // solves on levels l and l+1, so the second term of difference m-1 and the first term of difference m fall on
 // the same level m; each level is solved once with those right-hand sides side by side.  Every right-hand side
@@ -615,6 +620,7 @@ void multi_level_sample(mgmlmc_hier* h, std::vector<LsItem>& items, const solve_
     parts[it.l + 1].push_back({zc, it.nrhs, (int)i, 1});
   }
   std::vector<SolveOut> first(items.size()), second(items.size());
+  std::vector<double> flops(items.size(), 0.0);
   for (int m = 0; m < nlev; ++m) {
     if (parts[m].empty()) continue;
     const long n = h->lv[m].n;
@@ -642,6 +648,7 @@ void multi_level_sample(mgmlmc_hier* h, std::vector<LsItem>& items, const solve_
       d.iters = 0;
       for (int v : d.its) { d.total_iters += v; d.iters = std::max(d.iters, v); }
       (q.term == 0 ? x1 : x2)[q.item] = x + (size_t)off * n;
+      flops[q.item] += 8.0 * level_nnz(h, m) * (double)(d.total_iters + q.nrhs);
       off += q.nrhs;
     }
   }
@@ -656,6 +663,7 @@ void multi_level_sample(mgmlmc_hier* h, std::vector<LsItem>& items, const solve_
     o.iters = std::max(first[i].iters, second[i].iters);
     o.total_iters = first[i].total_iters + second[i].total_iters;
     it.out = o;
+    it.flops = flops[i];
   }
 }
 
@@ -675,31 +683,48 @@ void restrict_to_level(mgmlmc_hier* h, int l, const double2* zfine, double2* out
 }
 
 void make_level_vectors(mgmlmc_hier* h, int l, int form, uint64_t seed, int phase, int64_t sample0, int nrhs,
-                        double2* out) {
+                        double2* out, int noise) {
   cudaStream_t st = h->ctx->stream;
   if (form == MGMLMC_REDUCED || l == 0) {
-    rademacher_fill(st, seed, l, phase, sample0, h->lv[l].n, nrhs, out);
+    noise_fill(st, noise, seed, l, phase, sample0, h->lv[l].n, nrhs, out);
     return;
   }
   double2* zf = (double2*)h->work("mlv_fine", 0, sizeof(double2) * h->lv[0].n * nrhs);
-  rademacher_fill(st, seed, l, phase, sample0, h->lv[0].n, nrhs, zf);
+  noise_fill(st, noise, seed, l, phase, sample0, h->lv[0].n, nrhs, zf);
   restrict_to_level(h, l, zf, out, nrhs);
 }
 
+SolveOut level_sample_accumulated(mgmlmc_hier* h, int l, const double2* zeta_fine, double2* y_fine, int nrhs,
+                                  const solve_params& sp) {
+  if (l == 0) return level_sample(h, 0, zeta_fine, y_fine, nrhs, sp);
+  const long nl = h->lv[l].n;
+  double2* zl = (double2*)h->work("lsa_z", l, sizeof(double2) * nl * nrhs);
+  double2* yl = (double2*)h->work("lsa_y", l, sizeof(double2) * nl * nrhs);
+  restrict_to_level(h, l, zeta_fine, zl, nrhs);
+  SolveOut o = level_sample(h, l, zl, yl, nrhs, sp);
+  const double2* src = yl;  // y_fine = P_0 ... P_{l-1} yl
+  for (int k = l - 1; k >= 0; --k) {
+    double2* dst = k == 0 ? y_fine : (double2*)h->work("lsa_p", k, sizeof(double2) * h->lv[k].n * nrhs);
+    prolong_level<double>(h, k, src, dst, nrhs);
+    src = dst;
+  }
+  return o;
+}
+
 // ---------------------------------------------------------------- Hutch++
-static void cholesky_qr2(mgmlmc_hier* h, double2* Y, int d, long n) {
-  cudaStream_t st = h->ctx->stream;
-  void* work = h->work("cq_work", 0, gram_work_bytes(d, n));
-  double2* G = (double2*)h->work("cq_G", 0, sizeof(double2) * d * d * 2);
+void cholesky_qr2(mgmlmc_ctx* ctx, double2* Y, int d, long n) {
+  cudaStream_t st = ctx->stream;
+  void* work = ctx->work("cq_work", gram_work_bytes(d, n));
+  double2* G = (double2*)ctx->work("cq_G", sizeof(double2) * d * d * 2);
   double2* Rinv = G + d * d;
-  int* fail = (int*)h->work("cq_fail", 0, sizeof(int));
+  int* fail = (int*)ctx->work("cq_fail", sizeof(int));
   MG_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), st));
   for (int pass = 0; pass < 2; ++pass) {
     gram(st, Y, d, n, G, work);
     chol_inv_upper(st, G, d, Rinv, fail);
     right_mul_upper(st, Y, d, n, Rinv);
   }
-  if (read_flag(h->ctx, fail)) throw Error(MGMLMC_ERR_NOT_POSDEF, "CholeskyQR2: Gram matrix not positive definite");
+  if (read_flag(ctx, fail)) throw Error(MGMLMC_ERR_NOT_POSDEF, "CholeskyQR2: Gram matrix not positive definite");
 }
 
 mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int form, const solve_params& sp,
@@ -717,7 +742,7 @@ mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int
   for (int it = 0; it < k; ++it) {
     SolveOut o = level_sample(h, l, S, Y, d, sp);
     if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "sketch solves did not converge");
-    cholesky_qr2(h, Y, d, n);
+    cholesky_qr2(h->ctx, Y, d, n);
     vcopy<double2>(st, Y, S, n, d);
   }
   SolveOut o = level_sample(h, l, S, Y, d, sp);
@@ -738,8 +763,12 @@ mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int
 // power sweeps and the low-rank traces of the levels advance together so that the solves of neighbouring
 // differences on a shared level run as one batch (multi_level_sample).  Each level's Q and tau_lr equal those of
 // sketch_qr for that level.
+// With weight = MGMLMC_TRACE_GAMMA5 every level difference A_l is replaced by gamma5_l A_l (the matrix whose trace
+// is estimated), so Y = gamma5_l A_l S and tau_lr = sum_i q_i^H gamma5_l A_l q_i.  `flops` accumulates the counted
+// operator flops of the sketch solves.
 void sketch_qr_all(mgmlmc_hier* h, const int* d, int k, uint64_t seed, int form, const solve_params& sp,
-                   std::vector<std::unique_ptr<mgmlmc_sketch>>& out, std::vector<double2>& tau_lr) {
+                   std::vector<std::unique_ptr<mgmlmc_sketch>>& out, std::vector<double2>& tau_lr, int noise,
+                   int weight, double* flops) {
   MG_CHECK_ARG(k >= 1, "at least one power sweep");
   cudaStream_t st = h->ctx->stream;
   const int nd = h->nlev - 1;
@@ -757,7 +786,7 @@ void sketch_qr_all(mgmlmc_hier* h, const int* d, int k, uint64_t seed, int form,
     out[l]->Q.alloc(sizeof(double2) * n * d[l], st);
     S[l] = out[l]->Q.as<double2>();
     Y[l] = (double2*)h->work("sk_Y", l, sizeof(double2) * n * d[l]);
-    make_level_vectors(h, l, form, seed, MGMLMC_PHASE_SKETCH, 0, d[l], S[l]);
+    make_level_vectors(h, l, form, seed, MGMLMC_PHASE_SKETCH, 0, d[l], S[l], noise);
     LsItem it;
     it.l = l; it.zeta = S[l]; it.y = Y[l]; it.nrhs = d[l];
     items.push_back(it);
@@ -765,13 +794,16 @@ void sketch_qr_all(mgmlmc_hier* h, const int* d, int k, uint64_t seed, int form,
   if (items.empty()) return;
   for (int sweep = 0; sweep <= k; ++sweep) {
     multi_level_sample(h, items, sp);
-    for (const LsItem& it : items)
+    for (const LsItem& it : items) {
       if (!it.out.converged)
         throw Error(MGMLMC_ERR_NOT_CONVERGED, sweep < k ? "sketch solves did not converge"
                                                         : "low-rank solves did not converge");
+      if (flops) *flops += it.flops;
+      if (weight == MGMLMC_TRACE_GAMMA5) gamma5_apply(st, Y[it.l], h->lv[it.l].dof, h->lv[it.l].n, it.nrhs);
+    }
     if (sweep == k) break;
     for (const LsItem& it : items) {
-      cholesky_qr2(h, Y[it.l], d[it.l], h->lv[it.l].n);
+      cholesky_qr2(h->ctx, Y[it.l], d[it.l], h->lv[it.l].n);
       vcopy<double2>(st, Y[it.l], S[it.l], h->lv[it.l].n, d[it.l]);
     }
   }
@@ -789,30 +821,31 @@ void sketch_qr_all(mgmlmc_hier* h, const int* d, int k, uint64_t seed, int form,
   }
 }
 
+// tau_r = a_r - sum_i conj(c_ir) g_ir with c = Q^H zeta, g = Q^H y (stored after c), in a fixed order
+__global__ void k_proj_combine(double2* __restrict__ a, const double2* __restrict__ c, int d, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  double2 t = a[r];
+  for (int i = 0; i < d; ++i) t = csub(t, cmulc(c[(size_t)i * nrhs + r], c[(size_t)(d + i) * nrhs + r]));
+  a[r] = t;
+}
+
 void project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double2* zeta, const double2* y, long n, int nrhs,
              double2* tau_host) {
   cudaStream_t st = ctx->stream;
   const int d = s ? s->d : 0;
-  DBuf a(sizeof(double2) * nrhs, st);
-  DBuf red(reduce_work_bytes(n, nrhs, 1), st);
-  vdot<double2>(st, zeta, y, n, nrhs, a.as<double2>(), red.p, nullptr);
-  std::vector<double2> ha(nrhs), hc, hg;
+  double2* a = (double2*)ctx->work("pj_a", sizeof(double2) * nrhs);
+  vdot<double2>(st, zeta, y, n, nrhs, a, ctx->work("pj_red", reduce_work_bytes(n, nrhs, 1)), nullptr);
   if (d > 0) {
     MG_CHECK_ARG(s->n == n, "sketch and vectors differ in size");
-    DBuf c(sizeof(double2) * d * nrhs * 2, st);
-    DBuf w(proj_work_bytes(d, n, nrhs), st);
-    proj_coeffs(st, s->Q.as<double2>(), d, zeta, n, nrhs, c.as<double2>(), w.p);
-    proj_coeffs(st, s->Q.as<double2>(), d, y, n, nrhs, c.as<double2>() + (size_t)d * nrhs, w.p);
-    hc.resize((size_t)d * nrhs * 2);
-    MG_CUDA(cudaMemcpyAsync(hc.data(), c.p, sizeof(double2) * hc.size(), cudaMemcpyDeviceToHost, st));
+    double2* c = (double2*)ctx->work("pj_c", sizeof(double2) * d * nrhs * 2);
+    void* w = ctx->work("pj_w", proj_work_bytes(d, n, nrhs));
+    proj_coeffs(st, s->Q.as<double2>(), d, zeta, n, nrhs, c, w);
+    proj_coeffs(st, s->Q.as<double2>(), d, y, n, nrhs, c + (size_t)d * nrhs, w);
+    MG_LAUNCH(k_proj_combine, cdiv(nrhs, 64), 64, 0, st, a, c, d, nrhs);
   }
-  MG_CUDA(cudaMemcpyAsync(ha.data(), a.p, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
+  MG_CUDA(cudaMemcpyAsync(tau_host, a, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
   MG_CUDA(cudaStreamSynchronize(st));
-  for (int r = 0; r < nrhs; ++r) {
-    double2 t = ha[r];
-    for (int i = 0; i < d; ++i) t = csub(t, cmulc(hc[(size_t)i * nrhs + r], hc[(size_t)(d + i) * nrhs + r]));
-    tau_host[r] = t;
-  }
 }
 
 // ---------------------------------------------------------------- Algorithm 2
@@ -865,10 +898,14 @@ void estimate(mgmlmc_hier* h, const est_params& p, est_result* res) {
   res->nlev = h->nlev;
   std::vector<std::unique_ptr<mgmlmc_sketch>> sk;
   std::vector<double2> tau_lr;
-  sketch_qr_all(h, p.d, p.k, p.seed, p.form, p.solve, sk, tau_lr);
+  MG_CHECK_ARG(p.noise == MGMLMC_NOISE_RADEMACHER || p.noise == MGMLMC_NOISE_Z4, "unknown noise");
+  MG_CHECK_ARG(p.weight == MGMLMC_TRACE_PLAIN || p.weight == MGMLMC_TRACE_GAMMA5, "unknown trace weight");
+  const bool g5 = p.weight == MGMLMC_TRACE_GAMMA5;
+  double flops = 0;
+  sketch_qr_all(h, p.d, p.k, p.seed, p.form, p.solve, sk, tau_lr, p.noise, p.weight, &flops);
   for (int l = 0; l < nd; ++l)
     if (p.d[l] > 0) res->solves += (int64_t)2 * p.d[l] * (p.k + 1);
-  const double2 tauL = h->lv[h->nlev - 1].trace;
+  const double2 tauL = g5 ? h->lv[h->nlev - 1].trace_g5 : h->lv[h->nlev - 1].trace;
   std::vector<std::vector<double2>> samp(nd);
   std::vector<std::vector<double>> scost(nd);
   std::vector<LevelStats> stats(nd);
@@ -888,7 +925,7 @@ void estimate(mgmlmc_hier* h, const est_params& p, est_result* res) {
       double2* z = (double2*)h->work("est_z", l, sizeof(double2) * n * nb[l]);
       it.zeta = z;
       it.y = (double2*)h->work("est_y", l, sizeof(double2) * n * nb[l]);
-      make_level_vectors(h, l, p.form, p.seed, MGMLMC_PHASE_STOCH, (int64_t)samp[l].size(), nb[l], z);
+      make_level_vectors(h, l, p.form, p.seed, MGMLMC_PHASE_STOCH, (int64_t)samp[l].size(), nb[l], z, p.noise);
       items.push_back(it);
     }
     if (items.empty()) return;
@@ -897,6 +934,8 @@ void estimate(mgmlmc_hier* h, const est_params& p, est_result* res) {
       const int l = it.l, b = it.nrhs;
       const SolveOut& o = it.out;
       if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "sample solves did not converge");
+      flops += it.flops;
+      if (g5) gamma5_apply(ctx->stream, it.y, h->lv[l].dof, h->lv[l].n, b);
       std::vector<double2> t(b);
       project(ctx, sk[l].get(), it.zeta, it.y, h->lv[l].n, b, t.data());
       const double nnz_l = (double)h->lv[l].n * (l == 0 ? 9.0 : 5.0 * h->lv[l].dof);
@@ -981,6 +1020,67 @@ void estimate(mgmlmc_hier* h, const est_params& p, est_result* res) {
   res->tau_L[1] = tauL.y;
   res->sigma = std::sqrt(var);
   res->steps = (int)s;
+  res->flops = flops;
+}
+
+// ---------------------------------------------------------------- Algorithm 1
+void hutchinson(mgmlmc_hier* h, const hutch_params& p, hutch_result* res) {
+  mgmlmc_ctx* ctx = h->ctx;
+  cudaStream_t st = ctx->stream;
+  MG_CHECK_ARG(p.eps > 0, "eps must be positive");
+  MG_CHECK_ARG(p.nrhs_max >= 1 && p.nrhs_first >= 1, "batch sizes must be positive");
+  MG_CHECK_ARG(p.min_samples >= 2, "min_samples must be >= 2");
+  MG_CHECK_ARG(p.noise == MGMLMC_NOISE_RADEMACHER || p.noise == MGMLMC_NOISE_Z4, "unknown noise");
+  MG_CHECK_ARG(p.weight == MGMLMC_TRACE_PLAIN || p.weight == MGMLMC_TRACE_GAMMA5, "unknown trace weight");
+  std::memset(res, 0, sizeof(*res));
+  solve_params sp = p.solve;
+  if (sp.prec == MGMLMC_FP32) sp.prec = MGMLMC_MIXED;  // samples are FP64 vectors
+  const long n = h->lv[0].n;
+  const int64_t maxs = p.max_samples > 0 ? p.max_samples : (int64_t)1 << 40;
+  std::vector<double2> samp;
+  LevelStats S;
+  bool done = false;
+  while (!done && (int64_t)samp.size() < maxs) {
+    int64_t want = p.nrhs_first;
+    if (S.N >= 2) {  // samples still needed by the current variance: V / (eps |tau|)^2
+      const double t = std::hypot(S.mr, S.mi) * p.eps;
+      if (t > 0) want = (int64_t)std::ceil(1.15 * S.var() / (t * t)) - S.N + 1;
+      want = std::max<int64_t>(want, 8);
+      want = ((want + 7) / 8) * 8;
+    }
+    want = std::min<int64_t>(std::min<int64_t>(want, p.nrhs_max), maxs - (int64_t)samp.size());
+    const int b = (int)std::max<int64_t>(1, want);
+    double2* z = (double2*)h->work("hu_z", 0, sizeof(double2) * n * b);
+    double2* x = (double2*)h->work("hu_x", 0, sizeof(double2) * n * b);
+    noise_fill(st, p.noise, p.seed, 0, MGMLMC_PHASE_HUTCH, (int64_t)samp.size(), n, b, z);
+    SolveOut o = solve(h, 0, z, x, b, sp);
+    if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "Hutchinson solves did not converge");
+    if (p.weight == MGMLMC_TRACE_GAMMA5) gamma5_apply(st, x, h->lv[0].dof, n, b);
+    std::vector<double2> t(b);
+    project(ctx, nullptr, z, x, n, b, t.data());
+    res->solves += b;
+    res->inner_iters += o.total_iters;
+    samp.insert(samp.end(), t.begin(), t.end());
+    for (int r = 0; r < b && !done; ++r) {  // Algorithm 1, one sample at a time
+      S.add(t[r], 0.0);
+      if (S.N >= p.min_samples) {
+        const double tol = std::hypot(S.mr, S.mi) * p.eps;
+        if (S.var() / S.N <= tol * tol) done = true;
+      }
+    }
+  }
+  res->tau[0] = S.mr;
+  res->tau[1] = S.mi;
+  res->sigma = S.N >= 2 ? std::sqrt(S.var() / S.N) : NAN;
+  res->N = S.N;
+  res->computed = res->solves;
+  if (p.sample_out) {
+    const int64_t cnt = std::min<int64_t>(p.sample_cap, (int64_t)samp.size());
+    for (int64_t i = 0; i < cnt; ++i) {
+      p.sample_out[2 * i] = samp[i].x;
+      p.sample_out[2 * i + 1] = samp[i].y;
+    }
+  }
 }
 
 }  // namespace mg

@@ -19,6 +19,12 @@ struct mgmlmc_ctx {
   int* pinned = nullptr;  // small pinned host buffer for flags
   double* pinned_d = nullptr;
   mg::KTimer timer;
+  std::map<std::string, mg::DBuf> ws;  // workspaces of calls that have no hierarchy (projection)
+  void* work(const std::string& tag, size_t bytes) {
+    auto& b = ws[tag];
+    if (bytes > b.bytes) b.alloc(bytes, stream);
+    return b.p;
+  }
 };
 
 namespace mg {
@@ -41,7 +47,8 @@ struct LevelData {
   DBuf tcW, tcInv[2];
   // coarsest level: dense inverse
   DBuf inv64, inv32;
-  double2 trace = make_double2(0, 0);
+  double2 trace = make_double2(0, 0);     // coarsest level: tr(D_L^{-1})
+  double2 trace_g5 = make_double2(0, 0);  // coarsest level: tr(gamma5_L D_L^{-1})
   // FP64 SAP inverses / coarsest inverse current (intermediate bootstrap rounds build FP32 ones only)
   bool sap64_ok = false, inv64_ok = false;
   bool sapinv32_t = false;  // FP32 SAP inverses stored transposed (fine level)
@@ -159,12 +166,19 @@ struct LsItem {
   double2* y = nullptr;
   int nrhs = 0;
   SolveOut out;
+  double flops = 0;  // counted operator flops of the item's solves: 8 nnz(D_m) (iterations + 1) per rhs
 };
 void multi_level_sample(mgmlmc_hier* h, std::vector<LsItem>& items, const solve_params& sp);
 void restrict_to_level(mgmlmc_hier* h, int l, const double2* zfine, double2* out, int nrhs);
 // fills zeta (level-l vectors, FP64) for samples sample0.. of level difference l
 void make_level_vectors(mgmlmc_hier* h, int l, int form, uint64_t seed, int phase, int64_t sample0, int nrhs,
-                        double2* out);
+                        double2* out, int noise = MGMLMC_NOISE_RADEMACHER);
+// the accumulated level difference on fine-size vectors: y = Phat_l A_l Rhat_l zeta
+SolveOut level_sample_accumulated(mgmlmc_hier* h, int l, const double2* zeta_fine, double2* y_fine, int nrhs,
+                                  const solve_params& sp);
+void hutchinson(mgmlmc_hier* h, const hutch_params& p, hutch_result* r);
+// in-place CholeskyQR2 of Y = [d][n] (FP64): Y <- Q with Q^H Q = I, R with real positive diagonal
+void cholesky_qr2(mgmlmc_ctx* ctx, double2* Y, int d, long n);
 mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int form, const solve_params& sp,
                          double2* tau_lr);
 void project(mgmlmc_ctx* ctx, const mgmlmc_sketch* s, const double2* zeta, const double2* y, long n, int nrhs,

@@ -12,7 +12,11 @@
 // holds it (NA_SCRATCH_BYTES, about 4.3 MB) until the process exits.  Host code
 // cannot use the array's name as a device address (it names a host-side stand-in),
 // so the first call on each device resolves the real address with
-// cudaGetSymbolAddress while that device is current and caches it.
+// cudaGetSymbolAddress while that device is current and caches it together with
+// the CUDA context it belongs to; a call that finds another context current (after
+// cudaDeviceReset, say, the module and its array are loaded anew) looks it up again.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -33,7 +37,29 @@ static __device__ __align__(256) double2 g_na_scratch[NA_SCRATCH];
 
 std::mutex g_na_mu;
 constexpr int NA_MAX_DEVICES = 64;
-double2* g_na_ptr[NA_MAX_DEVICES] = {};
+struct NaSlot {
+  CUcontext ctx = nullptr;  // context the cached address belongs to
+  double2* ptr = nullptr;
+};
+NaSlot g_na_slot[NA_MAX_DEVICES];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+// cuCtxGetCurrent from the driver (through the runtime's entry-point query, so nothing links libcuda)
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
 
 // Partial sums over row chunk blockIdx.x for the rhs group blockIdx.y:
 // a = zeta^H y, c_i = q_i^H zeta, g_i = q_i^H y.  Every slot a launch later reads
@@ -102,7 +128,8 @@ __global__ void k_na_final(int d, int nrhs, const double2* __restrict__ scratch,
   tau[r] = a;
 }
 
-// Device address of the scratch array for the current device, resolved once.
+// Device address of the scratch array for the current device and context: looked up once per (device,
+// context) with that device current, then cached.
 int na_scratch_ptr(double2** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -110,17 +137,22 @@ int na_scratch_ptr(double2** out) {
     return MGMLMC_ERR_CUDA;
   }
   if (dev < 0 || dev >= NA_MAX_DEVICES) return MGMLMC_ERR_INVALID_ARG;
+  CUcontext cur = nullptr;
+  CtxGetCurrentFn get = ctx_get_current();
+  const bool known_ctx = get && get(&cur) == CUDA_SUCCESS && cur;
   std::lock_guard<std::mutex> lock(g_na_mu);
-  if (!g_na_ptr[dev]) {
+  NaSlot& slot = g_na_slot[dev];
+  if (!slot.ptr || !known_ctx || slot.ctx != cur) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       return MGMLMC_ERR_CUDA;
     }
-    g_na_ptr[dev] = static_cast<double2*>(p);
+    slot.ptr = static_cast<double2*>(p);
+    slot.ctx = known_ctx ? cur : nullptr;  // without a context handle the lookup repeats on every call
   }
-  *out = g_na_ptr[dev];
+  *out = slot.ptr;
   return MGMLMC_OK;
 }
 
@@ -137,8 +169,11 @@ extern "C" int hutchpp_project_noalloc(void* stream, const double* Q, int d, con
   if (rc != MGMLMC_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   dim3 grid(NA_CHUNKS, (nrhs + NA_RG - 1) / NA_RG);
+  // Each launch is checked right after it is issued.  cudaGetLastError also returns (and clears) an error left
+  // pending by earlier, unrelated work on this thread, which is then reported here as MGMLMC_ERR_CUDA.
   k_na_partial<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(Q), d, reinterpret_cast<const double2*>(zeta),
                                      reinterpret_cast<const double2*>(y), (long)n, nrhs, scratch);
+  if (cudaGetLastError() != cudaSuccess) return MGMLMC_ERR_CUDA;
   k_na_final<<<(nrhs + 63) / 64, 64, 0, st>>>(d, nrhs, scratch, reinterpret_cast<double2*>(tau_out));
   if (cudaGetLastError() != cudaSuccess) return MGMLMC_ERR_CUDA;
   return MGMLMC_OK;

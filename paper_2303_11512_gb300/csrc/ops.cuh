@@ -12,6 +12,8 @@ namespace mg {
 // links out[site][mu] = -1/2 * eta * U_mu(site); eta = -1 on the t links of the
 // last time slice (antiperiodic fermion boundary folded into the link).
 void prepare_links(cudaStream_t st, const double2* U, int L, double2* l64, float2* l32);
+// *bad = 1 if some link of U is NaN or infinite (bad is not cleared)
+void check_links(cudaStream_t st, const double2* U, int L, int* bad);
 // y = D x, or y = b - D x when b != nullptr.
 template <typename R>
 void wilson_apply(cudaStream_t st, const typename CT<R>::T* links, R diag, int L,
@@ -66,12 +68,15 @@ void invert_small_batched(cudaStream_t st, C* A, int nmat, int bd, int* fail);
 // in-place inverse of one n x n matrix (large n), one cooperative kernel; work: invert_large_work_bytes(n);
 // fail set on a zero pivot, timeout on an expired grid barrier; C = double2 / float2
 size_t invert_large_work_bytes(int n);
+// polls: poll limit of each grid-barrier wait (0 = default, about a second; < 0 = bounded-wait self-test:
+// the barrier expects one arrival more than the grid has, so every wait runs out after -polls polls)
 template <typename C>
-void invert_large(cudaStream_t st, C* A, int n, int* piv, void* work, int* fail, int* timeout);
+void invert_large(cudaStream_t st, C* A, int n, int* piv, void* work, int* fail, int* timeout, long polls = 0);
 template <typename R>
 void dense_apply(cudaStream_t st, const typename CT<R>::T* A, int n, const typename CT<R>::T* x,
                  typename CT<R>::T* y, int nrhs, const int* active);
-void trace_dense(cudaStream_t st, const double2* A, int n, double2* out);
+// sum_i A_ii, or with g5_dof > 0 sum_i gamma5_i A_ii (gamma5_i = -1 for dof i % g5_dof >= g5_dof / 2)
+void trace_dense(cudaStream_t st, const double2* A, int n, double2* out, int g5_dof = 0);
 
 // ---------------------------------------------------------------- BLAS-1 (per rhs)
 template <typename C> void vzero(cudaStream_t st, C* x, long n, int nrhs);
@@ -126,6 +131,11 @@ void rademacher_fill(cudaStream_t st, uint64_t seed, int level, int phase, int64
                      int nrhs, double2* out);
 void complex_rademacher_fill(cudaStream_t st, uint64_t seed, int level, int phase, int64_t sample0, long n,
                              int nrhs, double2* out);
+// isotropic noise of eq. random_props: kind MGMLMC_NOISE_RADEMACHER (real +-1) or MGMLMC_NOISE_Z4 (i^q)
+void noise_fill(cudaStream_t st, int kind, uint64_t seed, int level, int phase, int64_t sample0, long n, int nrhs,
+                double2* out);
+// y <- gamma5 y (chirality-1 components negated; dof per site `dof`)
+void gamma5_apply(cudaStream_t st, double2* y, int dof, long n, int nrhs);
 
 // ---------------------------------------------------------------- Hutch++ (FP64)
 // G = Y^H Y, Y = [d][n]; out d x d (row-major, G[i][j] = y_i^H y_j)

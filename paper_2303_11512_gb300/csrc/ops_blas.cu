@@ -527,4 +527,35 @@ void complex_rademacher_fill(cudaStream_t st, uint64_t seed, int level, int phas
   MG_LAUNCH(k_rademacher<true>, dim3(ew_blocks(n), nrhs), 256, 0, st, seed, level, phase, sample0, n, out);
 }
 
+// Z4 noise: entry i = i^q, q = the top two bits of the same counter word whose top bit gives the Rademacher sign
+__global__ void k_z4(uint64_t seed, int level, int phase, int64_t sample0, long n, double2* __restrict__ out) {
+  const int rhs = blockIdx.y;
+  const uint64_t key = stream_key(seed, level, phase, (uint64_t)(sample0 + rhs));
+  double2* O = out + (size_t)rhs * n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const unsigned q = (unsigned)(mix64(key + 0x9E3779B97F4A7C15ull * ((uint64_t)i + 1)) >> 62);
+    const double re = q == 0 ? 1.0 : q == 2 ? -1.0 : 0.0;
+    const double im = q == 1 ? 1.0 : q == 3 ? -1.0 : 0.0;
+    O[i] = make_double2(re, im);
+  }
+}
+void noise_fill(cudaStream_t st, int kind, uint64_t seed, int level, int phase, int64_t sample0, long n, int nrhs,
+                double2* out) {
+  if (kind == MGMLMC_NOISE_Z4)
+    MG_LAUNCH(k_z4, dim3(ew_blocks(n), nrhs), 256, 0, st, seed, level, phase, sample0, n, out);
+  else
+    rademacher_fill(st, seed, level, phase, sample0, n, nrhs, out);
+}
+
+// y <- gamma5 y in place: the components of chirality 1 change sign (dof index >= dof / 2 of each site; on the
+// fine level dof = 2, so spin 1)
+__global__ void k_gamma5(double2* __restrict__ y, int dof, size_t total) {
+  const int half = dof / 2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    if ((int)(e % dof) >= half) y[e] = cneg(y[e]);
+}
+void gamma5_apply(cudaStream_t st, double2* y, int dof, long n, int nrhs) {
+  MG_LAUNCH_W(32.0 * n * nrhs, 0, k_gamma5, 1024, 256, 0, st, y, dof, (size_t)n * nrhs);
+}
+
 }  // namespace mg

@@ -133,23 +133,25 @@ template void invert_small_batched<float2>(cudaStream_t, float2*, int, int, int*
 // barrier per column.  The barrier spins on a generation counter with an iteration limit (timeout flag, all
 // CTAs then leave).  Columns are unscrambled afterwards by the recorded swaps in reverse order.
 constexpr int GJ_T = 512;
-constexpr long GJ_SPIN = 1L << 28;  // polls of the generation counter (well over a second)
+constexpr long GJ_SPIN = 1L << 28;  // default polls of the generation counter (well over a second)
 
-__device__ __forceinline__ bool gj_barrier(unsigned* bar, unsigned nb, int* timeout, int* s_ok) {
+// `expect` arrivals release the barrier (the grid size; one more in the bounded-wait self-test, where nothing
+// releases it and every wait runs out after `polls` polls)
+__device__ __forceinline__ bool gj_barrier(unsigned* bar, unsigned expect, long polls, int* timeout, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = bar + 1;
     const unsigned g = *gen;
     __threadfence();
     int ok = 1;
-    if (atomicAdd(bar, 1u) == nb - 1) {
+    if (atomicAdd(bar, 1u) == expect - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
       long it = 0;
       while (*gen == g) {
-        if (++it > GJ_SPIN) {
+        if (++it > polls) {
           atomicExch(timeout, 1);
           ok = 0;
           break;
@@ -193,7 +195,7 @@ template <typename C>
 __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(C* __restrict__ A0, C* __restrict__ A1, int n,
                                                     int* __restrict__ piv, double* __restrict__ slot_v,
                                                     int* __restrict__ slot_i, unsigned* bar, int* fail,
-                                                    int* timeout) {
+                                                    int* timeout, long polls, unsigned expect) {
   __shared__ double sb[GJ_T / 32];
   __shared__ int si[GJ_T / 32];
   __shared__ int s_ok, s_p;
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(C* __restrict__ A0, C* __re
     gj_block_argmax(best, idx, sb, si);
     if (threadIdx.x == 0) { slot_v[blockIdx.x] = best; slot_i[blockIdx.x] = idx; }
   }
-  if (!gj_barrier(bar, nb, timeout, &s_ok)) return;
+  if (!gj_barrier(bar, expect, polls, timeout, &s_ok)) return;
   for (int k = 0; k < n; ++k) {
     const C* __restrict__ cur = (k & 1) ? A1 : A0;
     C* __restrict__ nxt = (k & 1) ? A0 : A1;
@@ -277,15 +279,19 @@ __global__ void __launch_bounds__(GJ_T, 1) k_gj_coop(C* __restrict__ A0, C* __re
       slot_v[((k + 1) & 1) * 1024 + blockIdx.x] = best;
       slot_i[((k + 1) & 1) * 1024 + blockIdx.x] = idx;
     }
-    if (!gj_barrier(bar, nb, timeout, &s_ok)) return;
+    if (!gj_barrier(bar, expect, polls, timeout, &s_ok)) return;
   }
 }
 
+// Undo the column swaps of the recorded pivots.  Skipped when the elimination stopped early (a barrier ran out or
+// a zero pivot), since the pivot record is then incomplete; entries outside [k, n) are ignored.
 template <typename C>
-__global__ void k_gj_unscramble(C* __restrict__ A, int n, const int* __restrict__ piv) {
+__global__ void k_gj_unscramble(C* __restrict__ A, int n, const int* __restrict__ piv, const int* __restrict__ fail,
+                                const int* __restrict__ timeout) {
+  if (*(volatile const int*)timeout || *(volatile const int*)fail) return;
   for (int k = n - 1; k >= 0; --k) {
     const int p = piv[k];
-    if (p != k)
+    if (p != k && p > k && p < n)
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         C t = A[(size_t)i * n + k];
         A[(size_t)i * n + k] = A[(size_t)i * n + p];
@@ -300,7 +306,7 @@ size_t invert_large_work_bytes(int n) {
 }
 
 template <typename C>
-void invert_large(cudaStream_t st, C* A, int n, int* piv, void* work, int* fail, int* timeout) {
+void invert_large(cudaStream_t st, C* A, int n, int* piv, void* work, int* fail, int* timeout, long polls) {
   int dev = 0, nsm = 0, per = 0;
   MG_CUDA(cudaGetDevice(&dev));
   MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -316,7 +322,10 @@ void invert_large(cudaStream_t st, C* A, int n, int* piv, void* work, int* fail,
   int* slot_i = (int*)(slot_v + 2048);
   unsigned* bar = (unsigned*)(slot_i + 2048);
   MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
-  void* args[] = {&A, &A1, &n, &piv, &slot_v, &slot_i, &bar, &fail, &timeout};
+  // polls == 0: the default limit; polls < 0: bounded-wait self-test (one arrival more than the grid has)
+  long lim = polls == 0 ? GJ_SPIN : (polls > 0 ? polls : -polls);
+  unsigned expect = (unsigned)grid + (polls < 0 ? 1u : 0u);
+  void* args[] = {&A, &A1, &n, &piv, &slot_v, &slot_i, &bar, &fail, &timeout, &lim, &expect};
   KTimer* t = g_timer;
   cudaEvent_t ea = nullptr, eb = nullptr;
   const char* name = sizeof(C) == 8 ? "k_gj_coop<float2>" : "k_gj_coop<double2>";
@@ -329,10 +338,10 @@ void invert_large(cudaStream_t st, C* A, int n, int* piv, void* work, int* fail,
   if (g_launch_counter) ++*g_launch_counter;
   if (n & 1)  // odd column count: the last column wrote the scratch buffer
     MG_CUDA(cudaMemcpyAsync(A, A1, sizeof(C) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
-  MG_LAUNCH(k_gj_unscramble<C>, 1, 1024, 0, st, A, n, piv);
+  MG_LAUNCH(k_gj_unscramble<C>, 1, 1024, 0, st, A, n, piv, fail, timeout);
 }
-template void invert_large<double2>(cudaStream_t, double2*, int, int*, void*, int*, int*);
-template void invert_large<float2>(cudaStream_t, float2*, int, int*, void*, int*, int*);
+template void invert_large<double2>(cudaStream_t, double2*, int, int*, void*, int*, int*, long);
+template void invert_large<float2>(cudaStream_t, float2*, int, int*, void*, int*, int*, long);
 
 // ---- y = A x for the coarsest level (n x n dense, nrhs columns) --------------------------------
 template <typename R>
@@ -371,12 +380,14 @@ void dense_apply(cudaStream_t st, const typename CT<R>::T* A, int n, const typen
 template void dense_apply<float>(cudaStream_t, const float2*, int, const float2*, float2*, int, const int*);
 template void dense_apply<double>(cudaStream_t, const double2*, int, const double2*, double2*, int, const int*);
 
-__global__ void k_trace(const double2* __restrict__ A, int n, double2* out) {
+// sum_i w_i A_ii with w_i = 1, or (g5_dof > 0) the gamma5 sign of dof i % g5_dof (-1 in its upper half)
+__global__ void k_trace(const double2* __restrict__ A, int n, int g5_dof, double2* out) {
   __shared__ double sr[32], si[32];
   double re = 0, im = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    re += A[(size_t)i * n + i].x;
-    im += A[(size_t)i * n + i].y;
+    const double w = (g5_dof > 0 && i % g5_dof >= g5_dof / 2) ? -1.0 : 1.0;
+    re += w * A[(size_t)i * n + i].x;
+    im += w * A[(size_t)i * n + i].y;
   }
   re = warp_sum(re);
   im = warp_sum(im);
@@ -392,8 +403,8 @@ __global__ void k_trace(const double2* __restrict__ A, int n, double2* out) {
     if (l == 0) *out = make_double2(re, im);
   }
 }
-void trace_dense(cudaStream_t st, const double2* A, int n, double2* out) {
-  MG_LAUNCH(k_trace, 1, 1024, 0, st, A, n, out);
+void trace_dense(cudaStream_t st, const double2* A, int n, double2* out, int g5_dof) {
+  MG_LAUNCH(k_trace, 1, 1024, 0, st, A, n, g5_dof, out);
 }
 
 // ---- CholeskyQR2 pieces ---------------------------------------------------------------------------

@@ -31,6 +31,17 @@ __global__ void k_prepare_links(const double2* __restrict__ U, int L, double2* _
   if (l32) l32[i] = make_float2((float)w.x, (float)w.y);
 }
 
+// bad = 1 if some link is not a finite complex number
+__global__ void k_check_links(const double2* __restrict__ U, long count, int* bad) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    const double2 u = U[i];
+    if (!isfinite(u.x) || !isfinite(u.y)) atomicExch(bad, 1);
+  }
+}
+void check_links(cudaStream_t st, const double2* U, int L, int* bad) {
+  MG_LAUNCH(k_check_links, cdiv(2L * L * L, 256), 256, 0, st, U, 2L * L * L, bad);
+}
+
 void prepare_links(cudaStream_t st, const double2* U, int L, double2* l64, float2* l32) {
   MG_LAUNCH(k_prepare_links, cdiv(2L * L * L, 256), 256, 0, st, U, L, l64, l32);
 }

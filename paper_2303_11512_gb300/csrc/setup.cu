@@ -4,6 +4,8 @@
 // Algorithm 2), and the optional bootstrap rounds.
 #include <algorithm>
 
+#include <cmath>
+
 #include "engine.cuh"
 
 namespace mg {
@@ -65,7 +67,7 @@ static void build_coarsest(mgmlmc_hier* h, int* dfail, bool fp64) {
   MG_CHECK_ARG(n <= 8192, "coarsest level too large for the dense inverse");
   lc.inv64.alloc(sizeof(double2) * (size_t)n * n, st);
   dense_from_stencil(st, lc.st64.as<double2>(), lc.side, lc.dof, lc.inv64.as<double2>());
-  DBuf piv(sizeof(int) * n, st), work(invert_large_work_bytes(n), st), tr(sizeof(double2), st);
+  DBuf piv(sizeof(int) * n, st), work(invert_large_work_bytes(n), st), tr(2 * sizeof(double2), st);
   lc.inv64_ok = fp64;
   if (!fp64) {
     to_fp32(st, lc.inv64, lc.inv32, (size_t)n * n);
@@ -76,8 +78,12 @@ static void build_coarsest(mgmlmc_hier* h, int* dfail, bool fp64) {
   invert_large<double2>(st, lc.inv64.as<double2>(), n, piv.as<int>(), work.p, dfail, dfail + 1);
   to_fp32(st, lc.inv64, lc.inv32, (size_t)n * n);
   trace_dense(st, lc.inv64.as<double2>(), n, tr.as<double2>());
-  MG_CUDA(cudaMemcpyAsync(&lc.trace, tr.p, sizeof(double2), cudaMemcpyDeviceToHost, st));
+  trace_dense(st, lc.inv64.as<double2>(), n, tr.as<double2>() + 1, lc.dof);
+  double2 both[2];
+  MG_CUDA(cudaMemcpyAsync(both, tr.p, 2 * sizeof(double2), cudaMemcpyDeviceToHost, st));
   MG_CUDA(cudaStreamSynchronize(st));
+  lc.trace = both[0];
+  lc.trace_g5 = both[1];
 }
 
 // P_l from the level-l test vectors lv.tv (ntv x n_l, FP64), D_{l+1} = P^H D_l P,
@@ -165,6 +171,14 @@ void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U) {
   h->tc_err.alloc(sizeof(int), st);
   MG_CUDA(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), st));
 
+  MG_CHECK_ARG(std::isfinite(h->m0), "m0 must be finite");
+  check_links(st, U, L, dfail + 1);
+  {
+    int bad = 0;
+    MG_CUDA(cudaMemcpyAsync(&bad, dfail + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+    if (bad) throw Error(MGMLMC_ERR_NAN, "gauge field holds a NaN or infinite link");
+  }
   LevelData& l0 = h->lv[0];
   l0.diag = h->m0 + 2.0;
   l0.links64.alloc(sizeof(double2) * 2 * L * L, st);

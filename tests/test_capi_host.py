@@ -64,3 +64,28 @@ def test_stop_rule_matches_oracle(lib):
             a = api.mlmc_update_active(act, V, N, Cs, eps, tau, pol, 2)
             b = update_active(act, V, N, Cs, eps, tau, name, 2)
             assert a == b, (trial, V, N, Cs, act, eps, tau, name)
+
+
+def test_noalloc_wrapper_rejects_mismatched_tensors():
+    """hutchpp_project_noalloc's C entry point gets bare pointers; the binding checks shapes before any
+    launch, so a mismatch raises ValueError instead of an out-of-bounds device access."""
+    torch = pytest.importorskip("torch")
+    from paper_2303_11512_gb300.api import check_noalloc_args
+    z = torch.zeros((5, 64), dtype=torch.complex128)
+    Q = torch.zeros((4, 64), dtype=torch.complex128)
+    tau = torch.zeros(5, dtype=torch.complex128)
+    assert check_noalloc_args(Q, z, z.clone(), tau) == (5, 64, 4)
+    assert check_noalloc_args(None, z, z.clone(), tau) == (5, 64, 0)
+    bad = [
+        (Q, z, torch.zeros((5, 63), dtype=torch.complex128), tau),   # y shape
+        (Q, z, torch.zeros((4, 64), dtype=torch.complex128), tau),   # y rows
+        (torch.zeros((4, 32), dtype=torch.complex128), z, z, tau),   # Q columns
+        (torch.zeros(64, dtype=torch.complex128), z, z, tau),        # Q rank
+        (Q, z, z, torch.zeros(4, dtype=torch.complex128)),           # tau_out too short
+        (Q, torch.zeros(64, dtype=torch.complex128), z, tau),        # zeta rank
+    ]
+    for args in bad:
+        with pytest.raises(ValueError):
+            check_noalloc_args(*args)
+    with pytest.raises(ValueError):   # a tensor on another device than the launches
+        check_noalloc_args(Q, z, z, tau, torch.device("meta"))

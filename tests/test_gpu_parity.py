@@ -209,33 +209,6 @@ def test_tensor_core_stencil(api, ctx):
     assert h.tc_status() == 0
 
 
-def test_tensor_core_many_items_per_cta(api, ctx):
-    """L = 256 (level-1 side 64): every CTA of the tcgen05 kernels walks several sites/blocks, exercising the
-    pipeline stages; checked against the FP64 CUDA-core stencil and the FP32 CUDA-core smoother."""
-    L = 256
-    U = gauge.links(gauge.quenched_u1(L, 5.0, 20, 3))
-    h = api.mg_setup(ctx, cuda(U), L, -0.05, ntv=8, setup_sweeps=2, seed=1)
-    try:
-        l = 1
-        n = h.n[l]
-        for nrhs in (8, 200):
-            x = rand_vecs(n, nrhs, 70 + nrhs)
-            y64 = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
-            h.apply(l, cuda(x), y64, api.FP64)
-            y32 = torch.empty((nrhs, n), dtype=torch.complex64, device="cuda")
-            h.apply(l, cuda(x.astype(np.complex64)), y32, api.TF32)
-            assert relerr(y32.cpu().numpy(), y64.cpu().numpy()) < 5e-3
-            f = cuda(rand_vecs(n, nrhs, 80 + nrhs).astype(np.complex64))
-            xa = cuda(x.astype(np.complex64))
-            xb = xa.clone()
-            h.smooth(l, f, xa, api.FP32, 2)
-            h.smooth(l, f, xb, api.TF32, 2)
-            assert relerr(xb.cpu().numpy(), xa.cpu().numpy()) < 5e-3
-        assert h.tc_status() == 0
-    finally:
-        h.close()
-
-
 # ---------------------------------------------------------------- solver
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 @pytest.mark.parametrize("level", [0, 1])

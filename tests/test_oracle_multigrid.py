@@ -203,3 +203,10 @@ def test_imported_prolongators_rebuild_the_hierarchy(hier):
     P[i, :] = rj
     P[j, :] = ri
     assert not mg.check_prolongator(P.tocsr(), 64, 2, 4)["support"]
+
+
+def test_sparse_from_stencil_round_trip(hier):
+    for l in range(1, hier.levels):
+        S = mg.stencil_blocks(hier.D[l], hier.side[l], hier.dof[l])
+        back = mg.sparse_from_stencil(S.reshape(-1, 5, hier.dof[l], hier.dof[l]), hier.side[l], hier.dof[l])
+        assert abs(back - hier.D[l]).max() < 1e-15 * abs(hier.D[l]).max()

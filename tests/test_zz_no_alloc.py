@@ -14,9 +14,17 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+def _ref(Q, z, y):
+    """tau_r = zeta_r^H y_r - (Q^H zeta_r)^H (Q^H y_r) in numpy FP64 (Q rows are the basis vectors)."""
+    Qm = Q.T
+    c = Qm.conj().T @ z.T
+    g = Qm.conj().T @ y.T
+    return np.einsum("rn,rn->r", np.conj(z), y) - np.einsum("ir,ir->r", np.conj(c), g)
+
+
 def test_noalloc_projection_matches_hutchpp_project():
-    import __graft_entry__ as g
-    g.build()
+    import __graft_entry__ as gentry
+    gentry.build()
     from paper_2303_11512_gb300 import _lib, api
     from synthetic import gauge
 
@@ -50,3 +58,33 @@ def test_noalloc_projection_matches_hutchpp_project():
     sk.close()
     h.close()
     ctx.close()
+
+
+def test_noalloc_at_the_limits_tiny_rows_and_side_stream():
+    """nrhs = 256 and d = 32 fill the scratch array completely; n = 8 leaves most row chunks empty (they must
+    contribute zeros); a call on a side stream, synchronised before the comparison.  Reference: numpy FP64."""
+    import __graft_entry__ as gentry
+    gentry.build()
+    from paper_2303_11512_gb300 import api
+
+    rs = np.random.default_rng(11)
+    for nrhs, d, n in ((256, 32, 3000), (7, 4, 8), (3, 0, 8)):
+        Qn = np.linalg.qr(rs.standard_normal((n, max(d, 1))) + 1j * rs.standard_normal((n, max(d, 1))))[0].T[:d]
+        z = rs.standard_normal((nrhs, n)) + 1j * rs.standard_normal((nrhs, n))
+        y = rs.standard_normal((nrhs, n)) + 1j * rs.standard_normal((nrhs, n))
+        ref = _ref(Qn, z, y) if d else np.einsum("rn,rn->r", np.conj(z), y)
+        Qd = torch.from_numpy(np.ascontiguousarray(Qn)).cuda() if d else None
+        tau = torch.full((nrhs,), float("nan"), dtype=torch.complex128, device="cuda")
+        api.hutchpp_project_noalloc(Qd, torch.from_numpy(z).cuda(), torch.from_numpy(y).cuda(), tau)
+        torch.cuda.synchronize()
+        assert np.abs(tau.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    side = torch.cuda.Stream()
+    z = torch.from_numpy(rs.standard_normal((9, 500)) + 0j).cuda()
+    y = torch.from_numpy(rs.standard_normal((9, 500)) + 0j).cuda()
+    tau = torch.full((9,), float("nan"), dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        api.hutchpp_project_noalloc(None, z, y, tau, stream=side)
+    side.synchronize()
+    ref = np.einsum("rn,rn->r", np.conj(z.cpu().numpy()), y.cpu().numpy())
+    assert np.abs(tau.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
