@@ -160,6 +160,40 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ profiling cases (ncu captures)
+def profile_case(args):
+    """Small self-contained GPU cases whose kernels an ncu capture can select (-k, -s, -c): the workload's
+    hierarchy and one solve on a level, or the fine stencil alone.  Prints nothing timed."""
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2303_11512_gb300 import api
+    from synthetic import gauge
+    W = WORKLOAD
+    L = args.L
+    m0 = mass_for(L, W["beta"], W["seed"])
+    U = torch.from_numpy(gauge.links(gauge.field(L, W["beta"], W["seed"]))).cuda()
+    ctx = api.Context()
+    if args.profile_case == "stencil":
+        n = 2 * L * L
+        x = torch.randn((args.profile_nrhs, n), dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(10):
+            api.schwinger_apply(ctx, U, L, m0, x, y, api.FP32)
+    else:
+        h = api.mg_setup(ctx, U, L, m0, ntv=W["ntv"], bootstrap=args.profile_bootstrap,
+                         bootstrap_its=W["bootstrap_its"], pre_smooth=W["pre_smooth"], post_smooth=W["post_smooth"])
+        b = api.mgmlmc_rademacher(ctx, 1, 0, 0, 0, h.n[args.profile_level], args.profile_nrhs)
+        x = torch.empty_like(b)
+        st = api.fgmres_batched(ctx, h, args.profile_level, b, x, prec=api.MIXED, tol=1e-10)
+        print("iters", st["iters"], "relres", st["max_relres"])
+        h.close()
+    torch.cuda.synchronize()
+    ctx.close()
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -175,9 +209,19 @@ def main():
     ap.add_argument("--ref-L", type=int, default=32)
     ap.add_argument("--ref-eps", type=float, default=1e-3)
     ap.add_argument("--timing-filter", default="")
+    ap.add_argument("--profile-case", choices=["solve", "stencil"], default=None,
+                    help="run one small case for an ncu capture instead of the benchmark: 'solve' = one mixed "
+                         "FGMRES solve on --profile-level with --profile-nrhs rhs on the workload hierarchy, "
+                         "'stencil' = ten FP32 fine-stencil applications to --profile-nrhs vectors")
+    ap.add_argument("--profile-level", type=int, default=1)
+    ap.add_argument("--profile-nrhs", type=int, default=64)
+    ap.add_argument("--profile-bootstrap", type=int, default=WORKLOAD["bootstrap"],
+                    help="bootstrap rounds of the profiled hierarchy (0: no tensor-core launches before the solve)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return profile_case(args)
 
     import numpy as np
     import torch

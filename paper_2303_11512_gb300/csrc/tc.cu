@@ -160,43 +160,56 @@ __device__ __forceinline__ int block_site(int k, int j, int Ls, int color) {
   return (2 * BT + (j >> 1)) * Ls + 2 * BX + (j & 1);
 }
 
-// MODE 0: KC = 5 site slabs, N = 32.   MODE 1: KC = 4 site slabs, N = 128.
+// MODE 0: KC = 5 site slabs; the vectors are the A operand (rows = rhs, M = 64 or 128), the weights B (N = 32).
+// MODE 1: KC = 4 site slabs; the block inverse is the A operand (M = 128 outputs), the residual slabs B
+//         (rows = rhs, N = the launch's rhs count rounded up to 16): the transposed product, so a small batch
+//         is not padded to 128 MMA rows.
 template <int MODE>
 struct TcCfg;
 template <>
 struct TcCfg<0> {
-  static constexpr int KC = 5, N = 32;
+  static constexpr int KC = 5, NW = 32;  // NW: weight rows per chunk (outputs of one site, real embedding)
 };
 template <>
 struct TcCfg<1> {
-  static constexpr int KC = 4, N = 128;
+  static constexpr int KC = 4, NW = 128;  // outputs of the 4 block sites
 };
 constexpr int TC_MAX_STAGES = 8;
-constexpr int TC_EPI_WARPS = 8;  // two epilogue warps per TMEM lane quarter, alternating items
-constexpr int TC_EXP_WARPS = 2;  // expander warps: build the Im rows of each weight tile in shared memory
-constexpr int TC_EXP_WARP0 = 2 + TC_EPI_WARPS;
-// warp 0 TMA producer, warp 1 MMA issuer, then the epilogue warps, then the expander warps
+constexpr int TC_PROD_WARPS = 5;  // one producer warp per chunk: the copies of an item are issued in parallel
+constexpr int TC_MMA_WARPS = 1;   // one MMA-issuing thread
+constexpr int TC_EPI_WARPS = 8;   // two epilogue warps per TMEM lane quarter, alternating items
+constexpr int TC_EXP_WARPS = 2;   // expander warps: build the Im rows of each weight tile in shared memory
+constexpr int TC_MMA_WARP0 = TC_PROD_WARPS;
+constexpr int TC_EPI_WARP0 = TC_MMA_WARP0 + TC_MMA_WARPS;
+constexpr int TC_EXP_WARP0 = TC_EPI_WARP0 + TC_EPI_WARPS;
+// producer warps, MMA warps, epilogue warps, expander warps
 constexpr int TC_THREADS = 32 * (TC_EXP_WARP0 + TC_EXP_WARPS);
 constexpr int TC_NACC = 4;       // TMEM accumulators in flight
 
-// bytes of one pipeline stage: KC A slabs of `rows` rhs rows, then KC B tiles of N rows (128 B each).
-// The MMA reads 128 A rows; rows past `rows` land in the next slab or the stage's B tiles (never outside
-// the stage) and only feed accumulator rows that are never stored.
-__host__ __device__ constexpr int tc_stage_bytes(int KC, int N, int rows) { return KC * (rows + N) * 128; }
+// bytes of one pipeline stage: KC vector slabs of `vrows` rhs rows and KC weight tiles of NW rows (128 B each).
+// In MODE 0 the MMA reads M >= vrows A rows from a vector slab; rows past `vrows` land in the next slab or the
+// stage's weight tiles (never outside the stage) and only feed accumulator rows that are never stored.
+__host__ __device__ constexpr int tc_stage_bytes(int KC, int NW, int vrows) { return KC * (vrows + NW) * 128; }
 
 // items: MODE 0 with bmode = 0: every site; bmode = 1: the 4 sites of every colour-`color` 2x2 block.
 //        MODE 1: every colour-`color` 2x2 block.
+// mm: MMA M of MODE 0 (64 when the launch has <= 64 rhs, else 128; it is also the rhs tile of blockIdx.y);
+// vrows: rows of a vector slab (MODE 0: rhs rounded up to 8; MODE 1: to 16, the MMA N).
 // Warp-specialised pipeline: the producer keeps up to `stages` items in flight in shared memory (full/empty
-// mbarriers), the MMA warp alternates between two TMEM accumulators (tmem_full/tmem_empty mbarriers), the
-// four epilogue warps drain one accumulator while the next item is multiplied.
+// mbarriers), the MMA thread rotates over TC_NACC TMEM accumulators (tmem_full/tmem_empty mbarriers), the
+// epilogue warps drain one accumulator while the next item is multiplied.
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc(const __grid_constant__ CUtensorMap amap, const float* __restrict__ W, float* __restrict__ out,
-         const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int rows, int stages,
-         const int* __restrict__ active, int* err) {
+         const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int vrows, int mm,
+         int stages, const int* __restrict__ active, int* err) {
   typedef TcCfg<MODE> CF;
-  constexpr int KC = CF::KC, N = CF::N, NCOL = TC_NACC * N < 32 ? 32 : TC_NACC * N;
-  constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
+  constexpr int KC = CF::KC, NW = CF::NW;
+  const int acc_cols = MODE == 0 ? NW : vrows;  // TMEM columns of one accumulator
+  const int tile_rhs = MODE == 0 ? mm : TC_M;   // rhs covered by one blockIdx.y
+  const uint32_t idesc = MODE == 0 ? idesc_tf32(mm, NW) : idesc_tf32(TC_M, vrows);
+  uint32_t ncol = 32;
+  while (ncol < (uint32_t)(TC_NACC * acc_cols)) ncol <<= 1;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[TC_MAX_STAGES], empty_bar[TC_MAX_STAGES], xfull_bar[TC_MAX_STAGES];
@@ -204,29 +217,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint32_t s_taddr;
   __shared__ int s_skip;
   __shared__ volatile int s_bad;
+  __shared__ unsigned char s_live[TC_M];  // MODE 1: rhs rhs0 + c exists and is active
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rhs0 = blockIdx.y * tile_rhs;
   if (tid == 0) s_skip = *(volatile int*)err;  // an earlier launch gave up: do nothing until the host sees it
+  if (MODE == 1 && tid < TC_M) {
+    const int r = rhs0 + tid;
+    s_live[tid] = r < nrhs && !(active && !active[r]);
+  }
   __syncthreads();
   if (s_skip) return;
-  const int rhs0 = blockIdx.y * TC_M;
   const long ncf = (long)Ls * Ls * TC_CHUNK;  // floats per rhs row
-  const int sbytes = tc_stage_bytes(KC, N, rows);
-  const uint32_t stage_tx = (uint32_t)(KC * (rows + N / 2) * 128);  // A slabs + the stored (Re) half of B
-  auto sA = [&](int st, int kc) { return base + st * sbytes + kc * rows * 128; };
-  auto sB = [&](int st, int kc) { return base + st * sbytes + KC * rows * 128 + kc * N * 128; };
+  const int sbytes = tc_stage_bytes(KC, NW, vrows);
+  const uint32_t chunk_tx = (uint32_t)((vrows + NW / 2) * 128);  // one vector slab + one stored (Re) weight half
+  // vector slab and weight tile of chunk kc in stage st (MODE 0: slabs first; MODE 1: weight tiles first)
+  auto sV = [&](int st, int kc) {
+    return MODE == 0 ? base + st * sbytes + kc * vrows * 128 : base + st * sbytes + KC * NW * 128 + kc * vrows * 128;
+  };
+  auto sW = [&](int st, int kc) {
+    return MODE == 0 ? base + st * sbytes + KC * vrows * 128 + kc * NW * 128 : base + st * sbytes + kc * NW * 128;
+  };
   auto center = [&](int item) -> int { return bmode ? block_site(item >> 2, item & 3, Ls, color) : item; };
   auto site_of = [&](int item, int kc) -> int {
     if (MODE == 1) return block_site(item, kc, Ls, color);
     return nbr_site_tc(center(item), kc, Ls);
   };
   auto w_of = [&](int item, int kc) -> const float* {
-    if (MODE == 1) return W + ((size_t)item * KC + kc) * (N / 2) * TC_CHUNK;
-    return W + ((size_t)center(item) * KC + kc) * (N / 2) * TC_CHUNK;
+    if (MODE == 1) return W + ((size_t)item * KC + kc) * (NW / 2) * TC_CHUNK;
+    return W + ((size_t)center(item) * KC + kc) * (NW / 2) * TC_CHUNK;
   };
 
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) {
-      mbar_init(&full_bar[s], 1);
+      mbar_init(&full_bar[s], KC);  // one arrive.expect_tx per producer warp
       mbar_init(&empty_bar[s], 1);
       mbar_init(&xfull_bar[s], TC_EXP_WARPS);
     }
@@ -240,7 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
-                 "r"((uint32_t)NCOL)
+                 "r"(ncol)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -251,32 +274,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   int n_my = 0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) ++n_my;
 
-  if (warp == 0) {
-    // ---------------- producer: lane kc < KC computes the addresses of chunk kc and issues its two copies
-    int issued = 0;
-    for (int i = 0; i < n_my; ++i) {
-      const int s = i % stages;
-      int ok = lane == 0 ? !s_bad : 0;
-      if (lane == 0 && ok && i >= stages && !mbar_wait(&empty_bar[s], (uint32_t)((i / stages) - 1) & 1u)) {
-        atomicExch(err, 1);
-        s_bad = 1;
-        ok = 0;
+  if (warp < TC_PROD_WARPS) {
+    // ---------------- producers: warp kc (< KC) issues chunk kc of every item, lane 0 the vector slab (TMA),
+    // lane 1 the stored weight half; the stage's full barrier completes once all KC warps arrived and every
+    // announced byte landed
+    const int kc = warp;
+    if (kc < KC) {
+      int issued = 0;
+      for (int i = 0; i < n_my; ++i) {
+        const int s = i % stages;
+        int ok = lane == 0 ? !s_bad : 0;
+        if (lane == 0 && ok && i >= stages && !mbar_wait(&empty_bar[s], (uint32_t)((i / stages) - 1) & 1u)) {
+          atomicExch(err, 1);
+          s_bad = 1;
+          ok = 0;
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+        const int item = blockIdx.x + i * gridDim.x;
+        // the warp posts its own bytes before either of its copies is issued, so the stage's transaction
+        // count never runs ahead of the bytes announced for it
+        if (lane == 0) mbar_expect_tx(&full_bar[s], chunk_tx);
+        __syncwarp();
+        if (lane == 0)
+          tma_load_2d(sV(s, kc), &amap, site_of(item, kc) * TC_CHUNK, rhs0, &full_bar[s]);
+        else if (lane == 1)
+          bulk_load(sW(s, kc), w_of(item, kc), (NW / 2) * 128, &full_bar[s]);
+        issued = i + 1;
       }
-      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      const int item = blockIdx.x + i * gridDim.x;
-      if (lane == 0) mbar_expect_tx(&full_bar[s], stage_tx);
-      __syncwarp();
-      if (lane < KC) {
-        tma_load_2d(sA(s, lane), &amap, site_of(item, lane) * TC_CHUNK, rhs0, &full_bar[s]);
-        bulk_load(sB(s, lane), w_of(item, lane), (N / 2) * 128, &full_bar[s]);
-      }
-      issued = i + 1;
+      // let the last loads (of every producer warp) land before the CTA can exit (bounded)
+      if (kc == 0 && lane == 0)
+        for (int i = std::max(0, issued - stages); i < issued; ++i)
+          mbar_wait(&full_bar[i % stages], (uint32_t)(i / stages) & 1u);
     }
-    // let the last loads land before the CTA can exit (bounded)
-    if (lane == 0)
-      for (int i = std::max(0, issued - stages); i < issued; ++i)
-        mbar_wait(&full_bar[i % stages], (uint32_t)(i / stages) & 1u);
-  } else if (warp == 1) {
+  } else if (warp < TC_EPI_WARP0) {
     // ---------------- MMA issuer
     if (lane == 0) {
       for (int i = 0; i < n_my && !s_bad; ++i) {
@@ -292,24 +322,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d = taddr + (uint32_t)(a * N);
+        const uint32_t d = taddr + (uint32_t)(a * acc_cols);
         for (int kc = 0; kc < KC; ++kc) {
-          const uint64_t ad = sw128_desc(smem_u32(sA(s, kc)));
-          const uint64_t bd = sw128_desc(smem_u32(sB(s, kc)));
+          const uint64_t vd = sw128_desc(smem_u32(sV(s, kc)));
+          const uint64_t wd = sw128_desc(smem_u32(sW(s, kc)));
+          const uint64_t ad = MODE == 0 ? vd : wd, bd = MODE == 0 ? wd : vd;
 #pragma unroll
           for (int k4 = 0; k4 < 4; ++k4)  // K = 8 tf32 = 32 B per instruction
-            mma_tf32(d, ad + 2 * k4, bd + 2 * k4, IDESC, (kc | k4) != 0);
+            mma_tf32(d, ad + 2 * k4, bd + 2 * k4, idesc, (kc | k4) != 0);
         }
         mma_commit(&empty_bar[s]);  // smem stage free once these MMAs completed
         mma_commit(&tfull_bar[a]);  // accumulator a ready for the epilogue
       }
     }
   } else if (warp >= TC_EXP_WARP0) {
-    // ---------------- expander: the Im rows of every B tile from its stored Re rows, (a, b) -> (-b, a);
-    // row n + N/2 has the swizzle phase of row n, so each 16-byte chunk keeps its position
+    // ---------------- expander: the Im rows of every weight tile from its stored Re rows, (a, b) -> (-b, a);
+    // row n + NW/2 has the swizzle phase of row n, so each 16-byte chunk keeps its position
     const int et = (warp - TC_EXP_WARP0) * 32 + lane;
-    constexpr int HALF4 = (N / 2) * 8;  // float4 per stored half tile
-    constexpr int TILE4 = N * 8;        // float4 per full tile
+    constexpr int HALF4 = (NW / 2) * 8;  // float4 per stored half tile
+    constexpr int TILE4 = NW * 8;        // float4 per full tile
     constexpr int PER = KC * HALF4 / (32 * TC_EXP_WARPS);
     constexpr int BATCH = PER % 8 == 0 ? 8 : PER % 5 == 0 ? 5 : PER % 4 == 0 ? 4 : PER % 2 == 0 ? 2 : 1;
     static_assert(KC * HALF4 % (32 * TC_EXP_WARPS) == 0, "expander work must divide evenly");
@@ -320,7 +351,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         s_bad = 1;
         break;
       }
-      float4* sb0 = reinterpret_cast<float4*>(sB(s, 0));  // element e: tile e / HALF4, offset e % HALF4
+      float4* sb0 = reinterpret_cast<float4*>(sW(s, 0));  // element e: tile e / HALF4, offset e % HALF4
 #pragma unroll
       for (int u0 = 0; u0 < PER; u0 += BATCH) {
         float4 v[BATCH];
@@ -339,22 +370,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&xfull_bar[s])) : "memory");
     }
-  } else {
-    // ---------------- epilogue: warp w owns TMEM lane quarter w % 4 and the items of parity (w - 2) / 4
-    const int q = warp & 3, par = (warp - 2) >> 2;
-    const int row = q * 32 + lane;
+  } else if (MODE == 0) {
+    // ---------------- epilogue (rows = rhs): warp w owns TMEM lane quarter w % 4 and the items of parity
+    // (w - 2) / 4.  With M = 128 accumulator row r sits in lane r; with M = 64 row r sits in lane
+    // 32 (r / 16) + r % 16, so the quarter's lanes 16..31 are unused.
+    const int q = warp & 3, par = (warp - TC_EPI_WARP0) >> 2;
+    const bool valid_lane = mm == 128 || lane < 16;
+    const int row = mm == 128 ? q * 32 + lane : q * 16 + lane;
     const int rhs = rhs0 + row;
-    const bool live = rhs < nrhs && !(active && !active[rhs]);
-    const bool quarter_live = rhs0 + q * 32 < nrhs;  // warp-uniform: some row of this quarter exists
-    // MODE 1 adds into x, MODE 0 with bvec subtracts from b.  The work of an item is split in steps of
-    // 8 complex outputs (half a site slab); the additive input of step t + RD is fetched at step t.
-    const float* in = (MODE == 1) ? out : bvec;
-    constexpr int NSTEP = N / 16, RD = NSTEP < 4 ? NSTEP : 4;
+    const bool live = valid_lane && rhs < nrhs && !(active && !active[rhs]);
+    const bool quarter_live = rhs0 + q * (mm == 128 ? 32 : 16) < nrhs;  // warp-uniform
+    // with bvec the output is b - D x; the work of an item is split in steps of 8 complex outputs (half a site
+    // slab); the additive input of step t + RD is fetched at step t.
+    const float* in = bvec;
+    constexpr int NSTEP = NW / 16, RD = NSTEP < 4 ? NSTEP : 4;
     static_assert(NSTEP % RD == 0, "prefetch ring must divide the steps of an item");
     auto step_ptr = [&](const float* v, int i, int t) -> const float* {
-      const int item = blockIdx.x + i * gridDim.x, j = t >> 1;
-      const int st = (MODE == 1) ? block_site(item, j, Ls, color) : center(item);
-      return v + (size_t)rhs * ncf + (size_t)st * TC_CHUNK + 16 * (t & 1);
+      const int item = blockIdx.x + i * gridDim.x;
+      return v + (size_t)rhs * ncf + (size_t)center(item) * TC_CHUNK + 16 * (t & 1);
     };
     float4 ring[RD][4];
     auto prefetch = [&](float4 (&dst)[4], int i, int t) {
@@ -374,7 +407,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t tq = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * N);
+      const uint32_t tq = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * acc_cols);
 #pragma unroll
       for (int t = 0; t < NSTEP; ++t) {
         float4 cur[4];
@@ -384,15 +417,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!quarter_live) continue;
         // v[0..7] = Re, v[8..15] = Im of complex outputs 8t .. 8t + 7
         float v[16];
-        tmem_ld8x2(tq + 8 * t, tq + N / 2 + 8 * t, v);
+        tmem_ld8x2(tq + 8 * t, tq + NW / 2 + 8 * t, v);
         if (live) {
           float4* o = reinterpret_cast<float4*>(const_cast<float*>(step_ptr(out, i, t)));
-          if (MODE == 1) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              o[u] = make_float4(cur[u].x + v[2 * u], cur[u].y + v[8 + 2 * u], cur[u].z + v[2 * u + 1],
-                                 cur[u].w + v[9 + 2 * u]);
-          } else if (bvec) {
+          if (bvec) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
               o[u] = make_float4(cur[u].x - v[2 * u], cur[u].y - v[8 + 2 * u], cur[u].z - v[2 * u + 1],
@@ -407,12 +435,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[a])) : "memory");
     }
+  } else {
+    // ---------------- epilogue (rows = block outputs, columns = rhs): lane r of the accumulator holds output
+    // row r of the weight image (r < 64: Re y_r, r >= 64: Im y_{r-64}; y_i is dof i % 16 of block site i / 16).
+    // Warp w owns lane quarter q = w % 4 and the items of parity (w - 2) / 4; x_B += inv_B r_B in 16-rhs steps.
+    const int q = warp & 3, par = (warp - TC_EPI_WARP0) >> 2;
+    const int oi = (q & 1) * 32 + lane;                 // complex output index of this thread
+    const int bj = oi >> 4, fo = 2 * (oi & 15) + (q >> 1);  // block site, float within its 32-float slab
+    const int nstep = vrows / 16;
+    // this thread's float of block site bj in the rhs-rhs0 row of item i's block
+    auto base_of = [&](int i) -> float* {
+      const int item = blockIdx.x + i * gridDim.x;
+      return out + (size_t)rhs0 * ncf + (size_t)block_site(item, bj, Ls, color) * TC_CHUNK + fo;
+    };
+    float cur[16];
+    float* pcur = nullptr;
+    auto fetch = [&](float* p, int t) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) cur[u] = s_live[16 * t + u] ? p[(size_t)(16 * t + u) * ncf] : 0.f;
+    };
+    if (par < n_my) {
+      pcur = base_of(par);
+      fetch(pcur, 0);
+    }
+    for (int i = par; i < n_my; i += 2) {
+      const int a = i % TC_NACC;
+      if (s_bad || !mbar_wait(&tfull_bar[a], (uint32_t)(i / TC_NACC) & 1u)) {
+        if (!s_bad) atomicExch(err, 4);
+        s_bad = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tq = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * acc_cols);
+      float* pnext = i + 2 < n_my ? base_of(i + 2) : nullptr;
+      for (int t = 0; t < nstep; ++t) {
+        float v[16];
+        tmem_ld8x2(tq + 16 * t, tq + 16 * t + 8, v);
+        float nx[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) nx[u] = cur[u] + v[u];
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (s_live[16 * t + u]) pcur[(size_t)(16 * t + u) * ncf] = nx[u];
+        if (t + 1 < nstep)
+          fetch(pcur, t + 1);
+        else if (pnext)
+          fetch(pnext, 0);
+      }
+      pcur = pnext;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[a])) : "memory");
+    }
   }
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"((uint32_t)NCOL)
-                 : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncol) : "memory");
   }
 }
 
@@ -467,15 +546,15 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-int box_rows(int nrhs) { return std::min(TC_M, ((nrhs + 7) / 8) * 8); }
-
-// 2D view [nrhs rows][nsite * 32 floats] of a coarse FP32 vector; box 32 floats x box_rows(nrhs) rows
-CUtensorMap make_map(const float2* v, int nsite, int nrhs) {
+// 2D view [nrhs rows][nsite * 32 floats] of a coarse FP32 vector; box 32 floats x `rows` rows (rows past
+// nrhs are filled with zeros by the copy engine)
+CUtensorMap make_map(const float2* v, int nsite, int nrhs, int rows) {
   MG_CHECK_ARG(((uintptr_t)v & 15) == 0, "tensor-core operand must be 16-byte aligned");
+  MG_CHECK_ARG(rows >= 8 && rows <= TC_M && rows % 8 == 0, "tensor-core box rows");
   CUtensorMap m;
   cuuint64_t dims[2] = {(cuuint64_t)nsite * TC_CHUNK, (cuuint64_t)nrhs};
   cuuint64_t strides[1] = {(cuuint64_t)nsite * TC_CHUNK * 4};
-  cuuint32_t box[2] = {TC_CHUNK, (cuuint32_t)box_rows(nrhs)};
+  cuuint32_t box[2] = {TC_CHUNK, (cuuint32_t)rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)v, dims, strides, box, es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -484,24 +563,31 @@ CUtensorMap make_map(const float2* v, int nsite, int nrhs) {
   return m;
 }
 
+// Launch shape of one tensor-core launch over nrhs right-hand sides:
+//   MODE 0: MMA M = 64 and 64 rhs per blockIdx.y (half the shared-memory operand reads of M = 128 and
+//           stages small enough for a deep pipeline); slab rows = rhs rounded up to 8 (at most 64).
+//   MODE 1: 128 rhs per blockIdx.y, slab rows = MMA N = rhs rounded up to 16 (at most 128).
 template <int MODE>
-void launch_tc(cudaStream_t st, const CUtensorMap& m, const float* W, float* out, const float* b, int Ls, int nitems,
+void launch_tc(cudaStream_t st, const float2* vin, const float* W, float* out, const float* b, int Ls, int nitems,
                int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops) {
   typedef TcCfg<MODE> CF;
   constexpr int SMEM_BUDGET = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
   ensure_max_smem((const void*)k_tc<MODE>, SMEM_BUDGET);
-  const int rows = box_rows(nrhs);
-  const int sbytes = tc_stage_bytes(CF::KC, CF::N, rows);
+  const int mm = MODE == 0 ? 64 : TC_M;
+  const int tile = MODE == 0 ? mm : TC_M;
+  const int vrows = MODE == 0 ? std::min(mm, ((nrhs + 7) / 8) * 8) : std::min(TC_M, ((nrhs + 15) / 16) * 16);
+  const CUtensorMap m = make_map(vin, Ls * Ls, nrhs, vrows);
+  const int sbytes = tc_stage_bytes(CF::KC, CF::NW, vrows);
   const int stages = std::max(1, std::min(TC_MAX_STAGES, (SMEM_BUDGET - 1024) / sbytes));
   const int sm = stages * sbytes + 1024;
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int tiles = (nrhs + TC_M - 1) / TC_M;
+  const int tiles = (nrhs + tile - 1) / tile;
   const int gx = std::max(1, std::min(nitems, (nsm + tiles - 1) / tiles));
   dim3 grid(gx, tiles);
-  MG_LAUNCH_W(bytes, flops, k_tc<MODE>, grid, TC_THREADS, sm, st, m, W, out, b, Ls, nitems, bmode, color, nrhs, rows,
-              stages, active, err);
+  MG_LAUNCH_W(bytes, flops, k_tc<MODE>, grid, TC_THREADS, sm, st, m, W, out, b, Ls, nitems, bmode, color, nrhs, vrows,
+              mm, stages, active, err);
 }
 
 }  // namespace
@@ -521,11 +607,10 @@ void tc_stencil_apply(cudaStream_t st, const float* W, int Ls, const float2* x, 
                       const int* active, int* err) {
   if (nrhs <= 0) return;
   const int ns = Ls * Ls;
-  CUtensorMap m = make_map(x, ns, nrhs);
   const double ar = act_rhs(nrhs);
   const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + ns * 5.0 * 2048;
   const double flops = ar * ns * 2.0 * 32 * 160;
-  launch_tc<0>(st, m, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
+  launch_tc<0>(st, x, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
 }
 
 // zero the sites of every colour-`color` 2x2 block of res ([rhs][site][16 complex])
@@ -551,10 +636,9 @@ void tc_residual_after_sap(cudaStream_t st, const float* Wst, int Ls, const floa
   if (nrhs <= 0) return;
   const int ns = Ls * Ls;
   const double ar = act_rhs(nrhs);
-  CUtensorMap m = make_map(x, ns, nrhs);
   const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 2048;
   const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
-  launch_tc<0>(st, m, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, 0, nrhs, active, err, bytes, flops);
+  launch_tc<0>(st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, 0, nrhs, active, err, bytes, flops);
   MG_LAUNCH_W(ar * (ns / 2) * 128.0, 0, k_zero_colour_blocks, 1024, 256, 0, st, res, Ls, 1, nrhs, active);
 }
 
@@ -564,16 +648,14 @@ void tc_sap_half(cudaStream_t st, const float* Wst, const float* Winv, int Ls, c
   const int ns = Ls * Ls, nblk = ns / 8;
   const double ar = act_rhs(nrhs);
   {  // residual on the sites of the colour's blocks
-    CUtensorMap m = make_map(x, ns, nrhs);
     const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 2048;
     const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
-    launch_tc<0>(st, m, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes, flops);
+    launch_tc<0>(st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes, flops);
   }
   {  // x_B += inv_B r_B
-    CUtensorMap m = make_map(res, ns, nrhs);
     const double bytes = ar * (ns / 2) * 128.0 * 3 + nblk * 32768.0;
     const double flops = ar * nblk * 2.0 * 128 * 128;
-    launch_tc<1>(st, m, Winv, (float*)x, nullptr, Ls, nblk, 0, color, nrhs, active, err, bytes, flops);
+    launch_tc<1>(st, res, Winv, (float*)x, nullptr, Ls, nblk, 0, color, nrhs, active, err, bytes, flops);
   }
 }
 
