@@ -28,10 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # V(2,2): of V(1,1) .. V(4,4), K-cycles and bootstrap 1-3 measured on this workload, the fastest set-up + estimate.
+# tensor_cores = 2: TF32 coarse-level tensor-core operands (measured faster here than BF16, = 1).
 # First batch of 8 samples per level (then batches sized from the variances, up to 256): the stop rule needs 6-8
 # samples on levels 0 and 1 here, so a first batch of 16 only computed samples that are discarded.
 WORKLOAD = dict(L=512, beta=5.0, seed=0, ntv=8, d=32, k=2, eps=1e-3, nrhs_max=256, nrhs_first=8,
-                bootstrap=2, bootstrap_its=6, kcycle_its=0, pre_smooth=2, post_smooth=2)
+                bootstrap=2, bootstrap_its=6, kcycle_its=0, pre_smooth=2, post_smooth=2, tensor_cores=2)
 FALLBACK_M0 = {512: -0.07, 128: -0.1199}
 
 
@@ -209,6 +210,8 @@ def main():
     ap.add_argument("--ref-L", type=int, default=32)
     ap.add_argument("--ref-eps", type=float, default=1e-3)
     ap.add_argument("--timing-filter", default="")
+    ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
+                    help="coarse-level tensor-core operands: 1 BF16, 2 TF32, 0 CUDA cores (default: the workload's)")
     ap.add_argument("--profile-case", choices=["solve", "stencil"], default=None,
                     help="run one small case for an ncu capture instead of the benchmark: 'solve' = one mixed "
                          "FGMRES solve on --profile-level with --profile-nrhs rhs on the workload hierarchy, "
@@ -246,13 +249,16 @@ def main():
 
     W = dict(WORKLOAD)
     W["L"], W["eps"] = args.L, args.eps
+    if args.tensor_cores is not None:
+        W["tensor_cores"] = args.tensor_cores
     L = W["L"]
     seed = W["seed"] + rank
     m0 = mass_for(L, W["beta"], W["seed"])
     U_host = gauge.links(gauge.field(L, W["beta"], seed))
     U = torch.from_numpy(U_host).cuda()
     mgp = dict(ntv=W["ntv"], bootstrap=W["bootstrap"], bootstrap_its=W["bootstrap_its"],
-               kcycle_its=W["kcycle_its"], pre_smooth=W["pre_smooth"], post_smooth=W["post_smooth"])
+               kcycle_its=W["kcycle_its"], pre_smooth=W["pre_smooth"], post_smooth=W["post_smooth"],
+               tensor_cores=W["tensor_cores"])
     estp = dict(eps=W["eps"], d=W["d"], k=W["k"], nrhs_max=W["nrhs_max"], nrhs_first=W["nrhs_first"], cost_mode=1,
                 seed=0)
     stream = torch.cuda.current_stream()

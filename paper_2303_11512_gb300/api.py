@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (ACCUMULATED, FP32, FP64, MIXED, NOISE_RADEMACHER, NOISE_Z4, OPTIMAL, REDUCED, TF32,
+from ._lib import (ACCUMULATED, BF16, FP32, FP64, MIXED, NOISE_RADEMACHER, NOISE_Z4, OPTIMAL, REDUCED, TF32,
                    TRACE_GAMMA5, TRACE_PLAIN, UNIFORM, EstParams, EstResult, HutchParams, HutchResult, MgParams,
                    SolveParams, SolveStats, check)
 
@@ -35,7 +35,7 @@ def _ptr(t: torch.Tensor, dtype=None) -> int:
 
 
 def _vec_dtype(prec: int):
-    return torch.complex64 if prec in (FP32, TF32) else torch.complex128
+    return torch.complex64 if prec in (FP32, TF32, BF16) else torch.complex128
 
 
 class Context:
@@ -157,7 +157,7 @@ class Hierarchy:
                                      prec), self.ctx.ptr)
 
     def smooth(self, level: int, f: torch.Tensor, x: torch.Tensor, prec: int = FP64, sweeps: int = 1):
-        """SAP sweeps for D_l x = f, x updated in place (prec FP64, FP32 or TF32)."""
+        """SAP sweeps for D_l x = f, x updated in place (prec FP64, FP32, or TF32 / BF16 on the tensor cores)."""
         dt = _vec_dtype(prec)
         check(_lib.load().mg_smooth(self.ctx.ptr, self.ptr, level, _ptr(f, dt), _ptr(x, dt), f.shape[0], prec,
                                     sweeps), self.ctx.ptr)

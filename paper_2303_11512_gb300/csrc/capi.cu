@@ -172,7 +172,7 @@ int mg_params_default(mg_params* p) {
   p->bootstrap_its = 6;
   p->kcycle_its = 0;
   p->kcycle_tol = 0.1;
-  p->tensor_cores = 1;
+  p->tensor_cores = 2;
   p->graphs = 1;
   return MGMLMC_OK;
 }
@@ -224,12 +224,15 @@ int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y,
     MG_CHECK_ARG(h && x && y && x != y, "null or aliased pointer");
     const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
-    MG_CHECK_ARG(prec == MGMLMC_TF32 ? h->use_tc(level) : true, "TF32 apply needs a coarse level with 16 dof");
-    if (prec != MGMLMC_TF32) check_prec(prec);
+    const bool tc = prec == MGMLMC_TF32 || prec == MGMLMC_BF16;
+    MG_CHECK_ARG(!tc || (h->use_tc(level) && h->lv[level].tc_bf == (prec == MGMLMC_BF16)),
+                 "tensor-core apply needs a coarse level with 16 dof whose images have this format "
+                 "(mg_params.tensor_cores: 1 BF16, 2 TF32)");
+    if (!tc) check_prec(prec);
     if (nrhs <= 0) return;
-    if (prec == MGMLMC_TF32)
-      tc_stencil_apply(ctx->stream, h->lv[level].tcW.as<float>(), h->lv[level].side, (const float2*)x, (float2*)y,
-                       nullptr, nrhs, nullptr, h->tc_err.as<int>());
+    if (tc)
+      tc_stencil_apply(ctx->stream, h->lv[level].tcW.p, h->lv[level].tc_bf, h->lv[level].side, (const float2*)x,
+                       (float2*)y, nullptr, nrhs, nullptr, h->tc_err.as<int>());
     else if (prec == MGMLMC_FP32)
       op_apply<float>(h, level, (const float2*)x, (float2*)y, nullptr, nrhs, nullptr);
     else
@@ -242,13 +245,14 @@ int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x
     MG_CHECK_ARG(h && f && x && f != x, "null or aliased pointer");
     h->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "the coarsest level has no smoother");
-    MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32 || prec == MGMLMC_TF32, "FP64, FP32 or TF32");
-    MG_CHECK_ARG(prec != MGMLMC_TF32 || (h->use_tc(level) && h->lv[level].tcInv[0].p),
-                 "TF32 smoothing needs a coarse level with 16 dof and 2x2 SAP blocks");
+    const bool tc = prec == MGMLMC_TF32 || prec == MGMLMC_BF16;
+    MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32 || tc, "FP64, FP32, TF32 or BF16");
+    MG_CHECK_ARG(!tc || (h->use_tc(level) && h->lv[level].tcInv[0].p && h->lv[level].tc_bf == (prec == MGMLMC_BF16)),
+                 "tensor-core smoothing needs a coarse level with 16 dof, 2x2 SAP blocks and images of this format");
     MG_CHECK_ARG(sweeps >= 0, "sweeps must be >= 0");
     if (nrhs <= 0) return;
     const int saved = h->prm.tensor_cores;
-    h->prm.tensor_cores = prec == MGMLMC_TF32;
+    h->prm.tensor_cores = tc ? saved : 0;
     try {
       for (int s = 0; s < sweeps; ++s) {
         if (prec == MGMLMC_FP64)

@@ -60,7 +60,7 @@ void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>
     if (h->use_tc(l) && L.sap_bs == 2 && L.tcInv[0].p) {
       float2* res = (float2*)h->work("tc_res", l, sizeof(float2) * L.n * nrhs);
       for (int color = 0; color < 2; ++color)
-        tc_sap_half(st, L.tcW.as<float>(), L.tcInv[color].as<float>(), L.side, f, x, res, color, nrhs, active,
+        tc_sap_half(st, L.tcW.p, L.tcInv[color].p, L.tc_bf, L.side, f, x, res, color, nrhs, active,
                     h->tc_err.as<int>());
       return;
     }
@@ -106,9 +106,9 @@ void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T
   if constexpr (sizeof(R) == 4) {
     if (h->use_tc(l)) {  // res = r - D e on the tensor cores (preconditioner accuracy)
       if (h->prm.pre_smooth > 0 && L.sap_bs == 2 && L.tcInv[0].p)  // zero on the blocks the sweep solved last
-        tc_residual_after_sap(st, L.tcW.as<float>(), L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
+        tc_residual_after_sap(st, L.tcW.p, L.tc_bf, L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
       else
-        tc_stencil_apply(st, L.tcW.as<float>(), L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
+        tc_stencil_apply(st, L.tcW.p, L.tc_bf, L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
       done = true;
     }
   }

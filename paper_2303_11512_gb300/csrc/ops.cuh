@@ -151,19 +151,21 @@ void proj_coeffs(cudaStream_t st, const double2* Q, int d, const double2* x, lon
 size_t proj_work_bytes(int d, long n, int nrhs);
 
 // ---------------------------------------------------------------- tensor cores (coarse levels, d = 16)
-// pre-swizzled TF32 weights: stencil [site][dir 5][32 x 32]; SAP block inverses of one colour [item][4][128 x 32]
-size_t tc_stencil_weight_floats(int nsite);
-size_t tc_blockinv_weight_floats(int Ls);
-void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, float* W);
-void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color, float* W);
-// y = D x (b == nullptr) or y = b - D x, FP32 vectors, TF32 products
-void tc_stencil_apply(cudaStream_t st, const float* W, int Ls, const float2* x, float2* y, const float2* b, int nrhs,
-                      const int* active, int* err);
+// Pre-swizzled weight images of the real-embedded coarse operators, Re rows only, in TF32 (bf = 0) or BF16
+// (bf = 1): stencil [site][dir 5][16 x 32]; SAP block inverses of one colour [item][4][64 x 32].
+size_t tc_stencil_weight_bytes(int nsite, int bf);
+size_t tc_blockinv_weight_bytes(int Ls, int bf);  // the blocks of one colour
+void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, void* W, int bf);
+void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color, void* W, int bf);
+// y = D x (b == nullptr) or y = b - D x, FP32 vectors, TF32 or BF16 products with FP32 accumulation
+void tc_stencil_apply(cudaStream_t st, const void* W, int bf, int Ls, const float2* x, float2* y, const float2* b,
+                      int nrhs, const int* active, int* err);
+// res = f - D x on colour-0 block sites, 0 on colour-1 block sites (the residual right after a SAP sweep: it
+// vanishes on the blocks solved last up to the rounding of the tensor-core products)
+void tc_residual_after_sap(cudaStream_t st, const void* Wst, int bf, int Ls, const float2* x, float2* res,
+                           const float2* f, int nrhs, const int* active, int* err);
 // one SAP colour half sweep with 2x2-site blocks: res = f - D x on the colour's sites, x_B += inv_B res_B
-// res = f - D x on colour-0 block sites, 0 on colour-1 block sites (valid right after a SAP sweep)
-void tc_residual_after_sap(cudaStream_t st, const float* Wst, int Ls, const float2* x, float2* res, const float2* f,
-                           int nrhs, const int* active, int* err);
-void tc_sap_half(cudaStream_t st, const float* Wst, const float* Winv, int Ls, const float2* f, float2* x,
+void tc_sap_half(cudaStream_t st, const void* Wst, const void* Winv, int bf, int Ls, const float2* f, float2* x,
                  float2* res, int color, int nrhs, const int* active, int* err);
 
 // ---------------------------------------------------------------- misc

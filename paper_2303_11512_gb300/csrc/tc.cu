@@ -27,6 +27,7 @@
 // an mbarrier is bounded: on expiry the kernel records an error code, stops, waits
 // (bounded) for its own copies and frees its TMEM.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include "ops.cuh"
 
@@ -113,9 +114,36 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;            // 128-byte swizzle
   return d;
 }
+// K-major operand tile with 64-byte swizzle: rows of 64 B, 8-row groups 512 B apart (BF16 tiles of 32 elements
+// per row; 16-byte chunk c of row r sits at chunk c ^ ((r >> 1) & 3))
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;           // descriptor version of tcgen05
+  d |= (uint64_t)4 << 61;           // 64-byte swizzle
+  return d;
+}
 // instruction descriptor: D f32, A/B tf32, both K-major, M x N
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// instruction descriptor of kind::f16: D f32, A/B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// two floats as a bf16 pair (round to nearest even), the first in the low half
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
@@ -160,10 +188,15 @@ __device__ __forceinline__ int block_site(int k, int j, int Ls, int color) {
   return (2 * BT + (j >> 1)) * Ls + 2 * BX + (j & 1);
 }
 
-// MODE 0: KC = 5 site slabs; the vectors are the A operand (rows = rhs, M = 64 or 128), the weights B (N = 32).
+// MODE 0: KC = 5 site slabs; the vectors are the A operand (rows = rhs, M = 64), the weights B (N = 32).
 // MODE 1: KC = 4 site slabs; the block inverse is the A operand (M = 128 outputs), the residual slabs B
 //         (rows = rhs, N = the launch's rhs count rounded up to 16): the transposed product, so a small batch
 //         is not padded to 128 MMA rows.
+// BF = 0: TF32 operands (kind::tf32, K = 8 per instruction); the FP32 vector slabs that TMA brings in are the
+//         MMA operand directly (128-byte rows, 128-byte swizzle).
+// BF = 1: BF16 operands (kind::f16, K = 16 per instruction, FP32 accumulation): half the weight bytes and half
+//         the MMA instructions; converter warps turn each staged FP32 slab into a BF16 operand tile
+//         (64-byte rows, 64-byte swizzle) before the MMA reads it.
 template <int MODE>
 struct TcCfg;
 template <>
@@ -176,38 +209,47 @@ struct TcCfg<1> {
 };
 constexpr int TC_MAX_STAGES = 8;
 constexpr int TC_PROD_WARPS = 5;  // one producer warp per chunk: the copies of an item are issued in parallel
-constexpr int TC_MMA_WARPS = 1;   // one MMA-issuing thread
+constexpr int TC_MMA_WARPS = 1;   // one MMA-issuing thread (two issuing warps faulted the GPU)
 constexpr int TC_EPI_WARPS = 8;   // two epilogue warps per TMEM lane quarter, alternating items
-constexpr int TC_EXP_WARPS = 2;   // expander warps: build the Im rows of each weight tile in shared memory
+constexpr int TC_EXP_WARPS = 4;   // expander/converter warps: Im rows of the weight tiles (and BF16 vector tiles)
 constexpr int TC_MMA_WARP0 = TC_PROD_WARPS;
 constexpr int TC_EPI_WARP0 = TC_MMA_WARP0 + TC_MMA_WARPS;
 constexpr int TC_EXP_WARP0 = TC_EPI_WARP0 + TC_EPI_WARPS;
-// producer warps, MMA warps, epilogue warps, expander warps
+// producer warps, MMA warp, epilogue warps, expander warps
 constexpr int TC_THREADS = 32 * (TC_EXP_WARP0 + TC_EXP_WARPS);
 constexpr int TC_NACC = 4;       // TMEM accumulators in flight
 
-// bytes of one pipeline stage: KC vector slabs of `vrows` rhs rows and KC weight tiles of NW rows (128 B each).
-// In MODE 0 the MMA reads M >= vrows A rows from a vector slab; rows past `vrows` land in the next slab or the
-// stage's weight tiles (never outside the stage) and only feed accumulator rows that are never stored.
-__host__ __device__ constexpr int tc_stage_bytes(int KC, int NW, int vrows) { return KC * (vrows + NW) * 128; }
+// Shared-memory layout of one pipeline stage (every tile base 1024-byte aligned):
+//   TF32: KC FP32 vector slabs (vrows rows x 128 B, the MMA operand), KC weight tiles (NW rows x 128 B);
+//   BF16: KC FP32 staging slabs (vrows x 128 B, TMA), KC BF16 vector tiles (vt rows x 64 B), KC weight tiles
+//         (NW rows x 64 B); vt = 64 in MODE 0 (the MMA reads M = 64 rows), vrows in MODE 1.
+// In MODE 0 the MMA reads 64 A rows from a vector tile of `vrows` rows (TF32) or from a 64-row BF16 tile; rows
+// past the converted/loaded ones only feed accumulator rows that are never stored.
+__host__ __device__ constexpr int tc_vt(int MODE, int vrows) { return MODE == 0 ? 64 : vrows; }
+__host__ __device__ constexpr int tc_stage_bytes(int MODE, int BF, int KC, int NW, int vrows) {
+  return BF ? KC * (vrows * 128 + tc_vt(MODE, vrows) * 64 + NW * 64) : KC * (vrows + NW) * 128;
+}
 
 // items: MODE 0 with bmode = 0: every site; bmode = 1: the 4 sites of every colour-`color` 2x2 block.
 //        MODE 1: every colour-`color` 2x2 block.
-// mm: MMA M of MODE 0 (64 when the launch has <= 64 rhs, else 128; it is also the rhs tile of blockIdx.y);
-// vrows: rows of a vector slab (MODE 0: rhs rounded up to 8; MODE 1: to 16, the MMA N).
-// Warp-specialised pipeline: the producer keeps up to `stages` items in flight in shared memory (full/empty
-// mbarriers), the MMA thread rotates over TC_NACC TMEM accumulators (tmem_full/tmem_empty mbarriers), the
-// epilogue warps drain one accumulator while the next item is multiplied.
-template <int MODE>
+// vrows: rows of a vector slab (MODE 0: rhs of the 64-rhs tile rounded up to 8; MODE 1: up to 16, the MMA N).
+// Warp-specialised pipeline: the producers keep up to `stages` items in flight in shared memory (full/empty
+// mbarriers), the expander/converter warps complete each stage (xfull), the MMA thread rotates over TC_NACC
+// TMEM accumulators (tmem_full/tmem_empty mbarriers), the epilogue warps drain one accumulator while the next
+// item is multiplied.
+template <int MODE, int BF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc(const __grid_constant__ CUtensorMap amap, const float* __restrict__ W, float* __restrict__ out,
-         const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int vrows, int mm,
-         int stages, const int* __restrict__ active, int* err) {
+    k_tc(const __grid_constant__ CUtensorMap amap, const void* __restrict__ Wv, float* __restrict__ out,
+         const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int vrows, int stages,
+         const int* __restrict__ active, int* err) {
   typedef TcCfg<MODE> CF;
   constexpr int KC = CF::KC, NW = CF::NW;
-  const int acc_cols = MODE == 0 ? NW : vrows;  // TMEM columns of one accumulator
-  const int tile_rhs = MODE == 0 ? mm : TC_M;   // rhs covered by one blockIdx.y
-  const uint32_t idesc = MODE == 0 ? idesc_tf32(mm, NW) : idesc_tf32(TC_M, vrows);
+  constexpr int MM = MODE == 0 ? 64 : TC_M;       // MMA M
+  constexpr int WROW = BF ? 64 : 128;             // bytes of one weight / operand row
+  const int acc_cols = MODE == 0 ? NW : vrows;    // TMEM columns of one accumulator
+  const int vt = tc_vt(MODE, vrows);
+  const uint32_t idesc = MODE == 0 ? (BF ? idesc_bf16(MM, NW) : idesc_tf32(MM, NW))
+                                   : (BF ? idesc_bf16(MM, vrows) : idesc_tf32(MM, vrows));
   uint32_t ncol = 32;
   while (ncol < (uint32_t)(TC_NACC * acc_cols)) ncol <<= 1;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -219,7 +261,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ volatile int s_bad;
   __shared__ unsigned char s_live[TC_M];  // MODE 1: rhs rhs0 + c exists and is active
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int rhs0 = blockIdx.y * tile_rhs;
+  const int rhs0 = blockIdx.y * (MODE == 0 ? MM : TC_M);
   if (tid == 0) s_skip = *(volatile int*)err;  // an earlier launch gave up: do nothing until the host sees it
   if (MODE == 1 && tid < TC_M) {
     const int r = rhs0 + tid;
@@ -228,23 +270,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   if (s_skip) return;
   const long ncf = (long)Ls * Ls * TC_CHUNK;  // floats per rhs row
-  const int sbytes = tc_stage_bytes(KC, NW, vrows);
-  const uint32_t chunk_tx = (uint32_t)((vrows + NW / 2) * 128);  // one vector slab + one stored (Re) weight half
-  // vector slab and weight tile of chunk kc in stage st (MODE 0: slabs first; MODE 1: weight tiles first)
-  auto sV = [&](int st, int kc) {
-    return MODE == 0 ? base + st * sbytes + kc * vrows * 128 : base + st * sbytes + KC * NW * 128 + kc * vrows * 128;
-  };
+  const int sbytes = tc_stage_bytes(MODE, BF, KC, NW, vrows);
+  const uint32_t chunk_tx = (uint32_t)(vrows * 128 + (NW / 2) * WROW);  // one vector slab + one stored weight half
+  // staged FP32 slab, MMA vector operand and weight tile of chunk kc in stage st
+  auto sS = [&](int st, int kc) { return base + st * sbytes + kc * vrows * 128; };
+  auto sV = [&](int st, int kc) { return BF ? base + st * sbytes + KC * vrows * 128 + kc * vt * 64 : sS(st, kc); };
   auto sW = [&](int st, int kc) {
-    return MODE == 0 ? base + st * sbytes + KC * vrows * 128 + kc * NW * 128 : base + st * sbytes + kc * NW * 128;
+    return base + st * sbytes + KC * vrows * 128 + (BF ? KC * vt * 64 : 0) + kc * NW * WROW;
   };
   auto center = [&](int item) -> int { return bmode ? block_site(item >> 2, item & 3, Ls, color) : item; };
   auto site_of = [&](int item, int kc) -> int {
     if (MODE == 1) return block_site(item, kc, Ls, color);
     return nbr_site_tc(center(item), kc, Ls);
   };
-  auto w_of = [&](int item, int kc) -> const float* {
-    if (MODE == 1) return W + ((size_t)item * KC + kc) * (NW / 2) * TC_CHUNK;
-    return W + ((size_t)center(item) * KC + kc) * (NW / 2) * TC_CHUNK;
+  auto w_of = [&](int item, int kc) -> const unsigned char* {
+    const size_t wi = MODE == 1 ? (size_t)item * KC + kc : (size_t)center(item) * KC + kc;
+    return reinterpret_cast<const unsigned char*>(Wv) + wi * (NW / 2) * WROW;
   };
 
   if (tid == 0) {
@@ -296,9 +337,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) mbar_expect_tx(&full_bar[s], chunk_tx);
         __syncwarp();
         if (lane == 0)
-          tma_load_2d(sV(s, kc), &amap, site_of(item, kc) * TC_CHUNK, rhs0, &full_bar[s]);
+          tma_load_2d(sS(s, kc), &amap, site_of(item, kc) * TC_CHUNK, rhs0, &full_bar[s]);
         else if (lane == 1)
-          bulk_load(sW(s, kc), w_of(item, kc), (NW / 2) * 128, &full_bar[s]);
+          bulk_load(sW(s, kc), w_of(item, kc), (NW / 2) * WROW, &full_bar[s]);
         issued = i + 1;
       }
       // let the last loads (of every producer warp) land before the CTA can exit (bounded)
@@ -324,26 +365,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
         const uint32_t d = taddr + (uint32_t)(a * acc_cols);
         for (int kc = 0; kc < KC; ++kc) {
-          const uint64_t vd = sw128_desc(smem_u32(sV(s, kc)));
-          const uint64_t wd = sw128_desc(smem_u32(sW(s, kc)));
+          const uint64_t vd = BF ? sw64_desc(smem_u32(sV(s, kc))) : sw128_desc(smem_u32(sV(s, kc)));
+          const uint64_t wd = BF ? sw64_desc(smem_u32(sW(s, kc))) : sw128_desc(smem_u32(sW(s, kc)));
           const uint64_t ad = MODE == 0 ? vd : wd, bd = MODE == 0 ? wd : vd;
+          if (BF) {
 #pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4)  // K = 8 tf32 = 32 B per instruction
-            mma_tf32(d, ad + 2 * k4, bd + 2 * k4, idesc, (kc | k4) != 0);
+            for (int k2 = 0; k2 < 2; ++k2)  // K = 16 bf16 = 32 B per instruction
+              mma_bf16(d, ad + 2 * k2, bd + 2 * k2, idesc, (kc | k2) != 0);
+          } else {
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4)  // K = 8 tf32 = 32 B per instruction
+              mma_tf32(d, ad + 2 * k4, bd + 2 * k4, idesc, (kc | k4) != 0);
+          }
         }
         mma_commit(&empty_bar[s]);  // smem stage free once these MMAs completed
         mma_commit(&tfull_bar[a]);  // accumulator a ready for the epilogue
       }
     }
   } else if (warp >= TC_EXP_WARP0) {
-    // ---------------- expander: the Im rows of every weight tile from its stored Re rows, (a, b) -> (-b, a);
-    // row n + NW/2 has the swizzle phase of row n, so each 16-byte chunk keeps its position
+    // ---------------- expander / converter.  Weight tiles: the Im rows from the stored Re rows, (a, b) ->
+    // (-b, a) per complex pair; row n + NW/2 has the swizzle phase of row n, so each 16-byte chunk keeps its
+    // position.  BF16: every staged FP32 slab (128-byte swizzle) becomes a BF16 operand tile (64-byte
+    // swizzle, round to nearest even).
     const int et = (warp - TC_EXP_WARP0) * 32 + lane;
-    constexpr int HALF4 = (NW / 2) * 8;  // float4 per stored half tile
-    constexpr int TILE4 = NW * 8;        // float4 per full tile
-    constexpr int PER = KC * HALF4 / (32 * TC_EXP_WARPS);
-    constexpr int BATCH = PER % 8 == 0 ? 8 : PER % 5 == 0 ? 5 : PER % 4 == 0 ? 4 : PER % 2 == 0 ? 2 : 1;
-    static_assert(KC * HALF4 % (32 * TC_EXP_WARPS) == 0, "expander work must divide evenly");
+    constexpr int NT = 32 * TC_EXP_WARPS;
+    constexpr int CPR = WROW / 16;           // 16-byte chunks per row
+    constexpr int HALF = (NW / 2) * CPR;     // chunks per stored half tile
+    constexpr int TILE = NW * CPR;           // chunks per full tile
     for (int i = 0; i < n_my; ++i) {
       const int s = i % stages;
       if (s_bad || !mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1u)) {
@@ -351,19 +399,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         s_bad = 1;
         break;
       }
-      float4* sb0 = reinterpret_cast<float4*>(sW(s, 0));  // element e: tile e / HALF4, offset e % HALF4
-#pragma unroll
-      for (int u0 = 0; u0 < PER; u0 += BATCH) {
-        float4 v[BATCH];
-#pragma unroll
-        for (int u = 0; u < BATCH; ++u) {
-          const int e = et + (u0 + u) * 32 * TC_EXP_WARPS, kc = e / HALF4;
-          v[u] = sb0[kc * TILE4 + (e - kc * HALF4)];
+      uint4* w0 = reinterpret_cast<uint4*>(sW(s, 0));  // chunk e: tile e / HALF, offset e % HALF
+      for (int e = et; e < KC * HALF; e += NT) {
+        const int kc = e / HALF, o = kc * TILE + (e - kc * HALF);
+        const uint4 v = w0[o];
+        uint4 r;
+        if (BF) {  // four bf16 pairs (a, b) -> (-b, a)
+          r.x = ((v.x & 0xFFFFu) << 16) | ((v.x >> 16) ^ 0x8000u);
+          r.y = ((v.y & 0xFFFFu) << 16) | ((v.y >> 16) ^ 0x8000u);
+          r.z = ((v.z & 0xFFFFu) << 16) | ((v.z >> 16) ^ 0x8000u);
+          r.w = ((v.w & 0xFFFFu) << 16) | ((v.w >> 16) ^ 0x8000u);
+        } else {  // two fp32 pairs (a, b) -> (-b, a)
+          r.x = v.y ^ 0x80000000u;
+          r.y = v.x;
+          r.z = v.w ^ 0x80000000u;
+          r.w = v.z;
         }
-#pragma unroll
-        for (int u = 0; u < BATCH; ++u) {
-          const int e = et + (u0 + u) * 32 * TC_EXP_WARPS, kc = e / HALF4;
-          sb0[kc * TILE4 + (e - kc * HALF4) + HALF4] = make_float4(-v[u].y, v[u].x, -v[u].w, v[u].z);
+        w0[o + HALF] = r;
+      }
+      if (BF) {
+        // output chunk (kc, row, c) holds k = 8c .. 8c+7 of that row: FP32 chunks 2c and 2c+1 of the staged row
+        for (int e = et; e < KC * vrows * 4; e += NT) {
+          const int kc = e / (vrows * 4), rem = e - kc * vrows * 4, row = rem >> 2, c = rem & 3;
+          const float4* src = reinterpret_cast<const float4*>(sS(s, kc)) + row * 8;
+          const float4 f0 = src[(2 * c) ^ (row & 7)], f1 = src[(2 * c + 1) ^ (row & 7)];
+          uint4 o;
+          o.x = bf16x2_rn(f0.x, f0.y);
+          o.y = bf16x2_rn(f0.z, f0.w);
+          o.z = bf16x2_rn(f1.x, f1.y);
+          o.w = bf16x2_rn(f1.z, f1.w);
+          reinterpret_cast<uint4*>(sV(s, kc))[row * 4 + (c ^ ((row >> 1) & 3))] = o;
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> MMA reads
@@ -372,14 +437,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (MODE == 0) {
     // ---------------- epilogue (rows = rhs): warp w owns TMEM lane quarter w % 4 and the items of parity
-    // (w - 2) / 4.  With M = 128 accumulator row r sits in lane r; with M = 64 row r sits in lane
-    // 32 (r / 16) + r % 16, so the quarter's lanes 16..31 are unused.
+    // (w - first epilogue warp) / 4.  With M = 64 accumulator row r sits in lane 32 (r / 16) + r % 16, so
+    // lanes 16..31 of each quarter are unused.
     const int q = warp & 3, par = (warp - TC_EPI_WARP0) >> 2;
-    const bool valid_lane = mm == 128 || lane < 16;
-    const int row = mm == 128 ? q * 32 + lane : q * 16 + lane;
+    const int row = q * 16 + lane;
     const int rhs = rhs0 + row;
-    const bool live = valid_lane && rhs < nrhs && !(active && !active[rhs]);
-    const bool quarter_live = rhs0 + q * (mm == 128 ? 32 : 16) < nrhs;  // warp-uniform
+    const bool live = lane < 16 && rhs < nrhs && !(active && !active[rhs]);
+    const bool quarter_live = rhs0 + q * 16 < nrhs;  // warp-uniform
     // with bvec the output is b - D x; the work of an item is split in steps of 8 complex outputs (half a site
     // slab); the additive input of step t + RD is fetched at step t.
     const float* in = bvec;
@@ -495,27 +559,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-// Weight images.  The real embedding of a complex output row i is the pair of B rows
+// Weight images.  The real embedding of a complex output row i is the pair of rows
 //   Re y_i:  k = 2j + b ->  (Re w_ij, -Im w_ij)        Im y_i:  k = 2j + b -> (Im w_ij, Re w_ij),
-// the second a fixed rearrangement of the first.  Only the Re rows are stored (N/2 rows per K chunk,
-// swizzled K-major: element (n, k) at n * 32 + (((k >> 2) ^ (n & 7)) << 2) + (k & 3)); the kernel's
-// expander warps build the Im rows in shared memory, so TMEM columns [0, N/2) hold Re y, [N/2, N) Im y.
+// the second a fixed rearrangement of the first.  Only the Re rows are stored (NW/2 rows per K chunk of 32
+// reals), pre-swizzled K-major: TF32 element (n, k) at n * 32 + (((k >> 2) ^ (n & 7)) << 2) + (k & 3) (128-byte
+// rows), BF16 element (n, k) at n * 32 + (((k >> 3) ^ ((n >> 1) & 3)) << 3) + (k & 7) (64-byte rows); the
+// kernel's expander warps build the Im rows in shared memory, so accumulator columns (MODE 0) or lanes
+// (MODE 1) [0, NW/2) hold Re y and [NW/2, NW) Im y.
 __device__ __forceinline__ int sw_index(int n, int k) { return n * 32 + ((((k >> 2) ^ (n & 7)) << 2) | (k & 3)); }
+__device__ __forceinline__ int sw64_index(int n, int k) {
+  return n * 32 + ((((k >> 3) ^ ((n >> 1) & 3)) << 3) | (k & 7));
+}
+template <int BF>
+__device__ __forceinline__ void put_w(void* W, size_t tile, int rows, int n, int k, float v) {
+  if (BF)
+    reinterpret_cast<__nv_bfloat16*>(W)[tile * rows * 32 + sw64_index(n, k)] = __float2bfloat16_rn(v);
+  else
+    reinterpret_cast<float*>(W)[tile * rows * 32 + sw_index(n, k)] = v;
+}
 
-__global__ void k_tc_stencil_weights(const float2* __restrict__ st, int nsite, float* __restrict__ W) {
-  // st[site][dir][16][16] complex -> W[site][dir][16 x 32]
+template <int BF>
+__global__ void k_tc_stencil_weights(const float2* __restrict__ st, int nsite, void* __restrict__ W) {
+  // st[site][dir][16][16] complex -> W[site][dir][16 stored rows x 32]
   const size_t total = (size_t)nsite * 5 * 16 * 32;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int k = e % 32, i = (e / 32) % 16;
     const size_t sd = e / 512;  // site * 5 + dir
     const int j = k >> 1, b = k & 1;
     const float2 z = st[sd * 256 + i * 16 + j];
-    W[sd * 512 + sw_index(i, k)] = b ? -z.y : z.x;
+    put_w<BF>(W, sd, 16, i, k, b ? -z.y : z.x);
   }
 }
 
-__global__ void k_tc_blockinv_weights(const float2* __restrict__ inv, int Ls, int color, int nblk, float* __restrict__ W) {
-  // colour-`color` blocks only, in their item order: inv[block][64][64] -> W[item][kc 4][64 x 32]
+template <int BF>
+__global__ void k_tc_blockinv_weights(const float2* __restrict__ inv, int Ls, int color, int nblk, void* __restrict__ W) {
+  // colour-`color` blocks only, in their item order: inv[block][64][64] -> W[item][kc 4][64 stored rows x 32]
   const size_t total = (size_t)nblk * 4 * 64 * 32;
   const int nbx = Ls / 2, half = nbx / 2;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -526,7 +604,7 @@ __global__ void k_tc_blockinv_weights(const float2* __restrict__ inv, int Ls, in
     const int kg = kc * 32 + kk;  // real input index 2 * (16 * site_j + dof) + b
     const int j = kg >> 1, b = kg & 1;
     const float2 z = inv[(size_t)blk * 4096 + i * 64 + j];
-    W[((size_t)item * 4 + kc) * 2048 + sw_index(i, kk)] = b ? -z.y : z.x;
+    put_w<BF>(W, (size_t)item * 4 + kc, 64, i, kk, b ? -z.y : z.x);
   }
 }
 
@@ -567,17 +645,17 @@ CUtensorMap make_map(const float2* v, int nsite, int nrhs, int rows) {
 //   MODE 0: MMA M = 64 and 64 rhs per blockIdx.y (half the shared-memory operand reads of M = 128 and
 //           stages small enough for a deep pipeline); slab rows = rhs rounded up to 8 (at most 64).
 //   MODE 1: 128 rhs per blockIdx.y, slab rows = MMA N = rhs rounded up to 16 (at most 128).
-template <int MODE>
-void launch_tc(cudaStream_t st, const float2* vin, const float* W, float* out, const float* b, int Ls, int nitems,
+template <int MODE, int BF>
+void launch_tc(cudaStream_t st, const float2* vin, const void* W, float* out, const float* b, int Ls, int nitems,
                int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops) {
   typedef TcCfg<MODE> CF;
   constexpr int SMEM_BUDGET = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
-  ensure_max_smem((const void*)k_tc<MODE>, SMEM_BUDGET);
-  const int mm = MODE == 0 ? 64 : TC_M;
-  const int tile = MODE == 0 ? mm : TC_M;
-  const int vrows = MODE == 0 ? std::min(mm, ((nrhs + 7) / 8) * 8) : std::min(TC_M, ((nrhs + 15) / 16) * 16);
+  auto* k_tc_kernel = &k_tc<MODE, BF>;
+  ensure_max_smem((const void*)k_tc_kernel, SMEM_BUDGET);
+  const int tile = MODE == 0 ? 64 : TC_M;
+  const int vrows = MODE == 0 ? std::min(64, ((nrhs + 7) / 8) * 8) : std::min(TC_M, ((nrhs + 15) / 16) * 16);
   const CUtensorMap m = make_map(vin, Ls * Ls, nrhs, vrows);
-  const int sbytes = tc_stage_bytes(CF::KC, CF::NW, vrows);
+  const int sbytes = tc_stage_bytes(MODE, BF, CF::KC, CF::NW, vrows);
   const int stages = std::max(1, std::min(TC_MAX_STAGES, (SMEM_BUDGET - 1024) / sbytes));
   const int sm = stages * sbytes + 1024;
   int dev = 0, nsm = 152;
@@ -586,31 +664,49 @@ void launch_tc(cudaStream_t st, const float2* vin, const float* W, float* out, c
   const int tiles = (nrhs + tile - 1) / tile;
   const int gx = std::max(1, std::min(nitems, (nsm + tiles - 1) / tiles));
   dim3 grid(gx, tiles);
-  MG_LAUNCH_W(bytes, flops, k_tc<MODE>, grid, TC_THREADS, sm, st, m, W, out, b, Ls, nitems, bmode, color, nrhs, vrows,
-              mm, stages, active, err);
+  MG_LAUNCH_W(bytes, flops, k_tc_kernel, grid, TC_THREADS, sm, st, m, W, out, b, Ls, nitems, bmode, color, nrhs,
+              vrows, stages, active, err);
+}
+
+template <int MODE>
+void launch_tc_fmt(int bf, cudaStream_t st, const float2* vin, const void* W, float* out, const float* b, int Ls,
+                   int nitems, int bmode, int color, int nrhs, const int* active, int* err, double bytes,
+                   double flops) {
+  if (bf)
+    launch_tc<MODE, 1>(st, vin, W, out, b, Ls, nitems, bmode, color, nrhs, active, err, bytes, flops);
+  else
+    launch_tc<MODE, 0>(st, vin, W, out, b, Ls, nitems, bmode, color, nrhs, active, err, bytes, flops);
 }
 
 }  // namespace
 
-size_t tc_stencil_weight_floats(int nsite) { return (size_t)nsite * 5 * 512; }
-size_t tc_blockinv_weight_floats(int Ls) { return (size_t)(Ls / 2) * (Ls / 2) / 2 * 4 * 2048; }
+// stored weight bytes: stencil 5 dirs x 16 Re rows x 32 reals per site; block inverses 4 chunks x 64 Re rows x
+// 32 reals per 2x2 block, for the (Ls/2)^2 / 2 blocks of one colour
+size_t tc_stencil_weight_bytes(int nsite, int bf) { return (size_t)nsite * 5 * 16 * 32 * (bf ? 2 : 4); }
+size_t tc_blockinv_weight_bytes(int Ls, int bf) { return (size_t)(Ls / 2) * (Ls / 2) / 2 * 4 * 64 * 32 * (bf ? 2 : 4); }
 
-void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, float* W) {
-  MG_LAUNCH(k_tc_stencil_weights, 1024, 256, 0, st, st32, nsite, W);
+void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, void* W, int bf) {
+  if (bf)
+    MG_LAUNCH(k_tc_stencil_weights<1>, 1024, 256, 0, st, st32, nsite, W);
+  else
+    MG_LAUNCH(k_tc_stencil_weights<0>, 1024, 256, 0, st, st32, nsite, W);
 }
-void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color, float* W) {
+void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color, void* W, int bf) {
   const int nblk = (Ls / 2) * (Ls / 2) / 2;
-  MG_LAUNCH(k_tc_blockinv_weights, 1024, 256, 0, st, inv32, Ls, color, nblk, W);
+  if (bf)
+    MG_LAUNCH(k_tc_blockinv_weights<1>, 1024, 256, 0, st, inv32, Ls, color, nblk, W);
+  else
+    MG_LAUNCH(k_tc_blockinv_weights<0>, 1024, 256, 0, st, inv32, Ls, color, nblk, W);
 }
 
-void tc_stencil_apply(cudaStream_t st, const float* W, int Ls, const float2* x, float2* y, const float2* b, int nrhs,
-                      const int* active, int* err) {
+void tc_stencil_apply(cudaStream_t st, const void* W, int bf, int Ls, const float2* x, float2* y, const float2* b,
+                      int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
   const int ns = Ls * Ls;
   const double ar = act_rhs(nrhs);
-  const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + ns * 5.0 * 2048;
+  const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + (double)tc_stencil_weight_bytes(ns, bf);
   const double flops = ar * ns * 2.0 * 32 * 160;
-  launch_tc<0>(st, x, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
+  launch_tc_fmt<0>(bf, st, x, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
 }
 
 // zero the sites of every colour-`color` 2x2 block of res ([rhs][site][16 complex])
@@ -631,31 +727,32 @@ __global__ void k_zero_colour_blocks(float2* __restrict__ res, int Ls, int color
 // res = f - D x on the sites of the colour-0 blocks and 0 on the colour-1 blocks: the V-cycle residual after
 // a SAP sweep whose last half sweep solved the colour-1 blocks, where it vanishes (the blocks of one colour do
 // not couple to each other, so their solves leave f - D x = 0 on them)
-void tc_residual_after_sap(cudaStream_t st, const float* Wst, int Ls, const float2* x, float2* res, const float2* f,
-                           int nrhs, const int* active, int* err) {
+void tc_residual_after_sap(cudaStream_t st, const void* Wst, int bf, int Ls, const float2* x, float2* res,
+                           const float2* f, int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
   const int ns = Ls * Ls;
   const double ar = act_rhs(nrhs);
-  const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 2048;
+  const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_stencil_weight_bytes(ns / 2, bf);
   const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
-  launch_tc<0>(st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, 0, nrhs, active, err, bytes, flops);
+  launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, 0, nrhs, active, err, bytes, flops);
   MG_LAUNCH_W(ar * (ns / 2) * 128.0, 0, k_zero_colour_blocks, 1024, 256, 0, st, res, Ls, 1, nrhs, active);
 }
 
-void tc_sap_half(cudaStream_t st, const float* Wst, const float* Winv, int Ls, const float2* f, float2* x,
+void tc_sap_half(cudaStream_t st, const void* Wst, const void* Winv, int bf, int Ls, const float2* f, float2* x,
                  float2* res, int color, int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
   const int ns = Ls * Ls, nblk = ns / 8;
   const double ar = act_rhs(nrhs);
   {  // residual on the sites of the colour's blocks
-    const double bytes = ar * (ns / 2) * 128.0 * 3 + (ns / 2) * 5.0 * 2048;
+    const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_stencil_weight_bytes(ns / 2, bf);
     const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
-    launch_tc<0>(st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes, flops);
+    launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes,
+                     flops);
   }
   {  // x_B += inv_B r_B
-    const double bytes = ar * (ns / 2) * 128.0 * 3 + nblk * 32768.0;
+    const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_blockinv_weight_bytes(Ls, bf);
     const double flops = ar * nblk * 2.0 * 128 * 128;
-    launch_tc<1>(st, res, Winv, (float*)x, nullptr, Ls, nblk, 0, color, nrhs, active, err, bytes, flops);
+    launch_tc_fmt<1>(bf, st, res, Winv, (float*)x, nullptr, Ls, nblk, 0, color, nrhs, active, err, bytes, flops);
   }
 }
 

@@ -2,8 +2,9 @@
 Z4 noise streams (bit-exact), the accumulated-form level difference on fine-size vectors
 (eq. mlmc_decomp_matrix), gamma5-weighted traces with Z4 vectors through Algorithm 2, plain Hutchinson
 (Algorithm 1) with unpreconditioned GMRES(30) on the L = 16 workload, and the V-cycle (FP64, FP32, and FP32
-with the TF32 tensor-core coarse levels) against the oracle's V-cycle.  Tolerances as in test_gpu_parity:
-samples and estimates 1e-8 at solver residual 1e-12, V-cycles 1e-12 (FP64) / 2e-5 (FP32) / 5e-3 (TF32)."""
+with the TF32 or BF16 tensor-core coarse levels) against the oracle's V-cycle.  Tolerances as in
+test_gpu_parity: samples and estimates 1e-8 at solver residual 1e-12, V-cycles 1e-12 (FP64) / 2e-5 (FP32) /
+5e-3 (TF32) / 2e-2 (BF16)."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla  # noqa: F401
@@ -128,14 +129,15 @@ def test_plain_hutchinson_gmres30(api, ctx):
         h.close()
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp32", "tf32"])
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "tf32", "bf16"])
 def test_vcycle_parity(api, ctx, h64, mode):
     """mg_vcycle against the oracle's V(1,1) cycle on the same (deterministic) hierarchy; with tensor cores
-    the coarse level's SAP sweeps and the residual after pre-smoothing run as TF32 tcgen05 GEMMs."""
+    the coarse level's SAP sweeps and the residual after pre-smoothing run as tcgen05 GEMMs (TF32 or BF16)."""
     h, H, U, m0 = h64
     hh = h
-    if mode == "fp32":   # the same hierarchy without the tensor-core coarse kernels
-        hh = api.mg_setup(ctx, torch.from_numpy(U).cuda(), 64, m0, ntv=8, setup_sweeps=4, seed=3, tensor_cores=0)
+    if mode != "fp64":   # the same hierarchy without / with TF32 / with BF16 tensor-core coarse kernels
+        hh = api.mg_setup(ctx, torch.from_numpy(U).cuda(), 64, m0, ntv=8, setup_sweeps=4, seed=3,
+                          tensor_cores={"fp32": 0, "tf32": 2, "bf16": 1}[mode])
     try:
         rs = np.random.default_rng(3)
         b = rs.standard_normal((5, H.n[0])) + 1j * rs.standard_normal((5, H.n[0]))
@@ -147,8 +149,9 @@ def test_vcycle_parity(api, ctx, h64, mode):
         else:
             x = torch.empty((5, H.n[0]), dtype=torch.complex64, device="cuda")
             hh.vcycle(0, torch.from_numpy(b.astype(np.complex64)).cuda(), x, api.FP32)
-            tol = 2e-5 if mode == "fp32" else 5e-3
-        assert relerr(x.cpu().numpy(), ref) < tol
+            tol = {"fp32": 2e-5, "tf32": 5e-3, "bf16": 2e-2}[mode]
+        err = relerr(x.cpu().numpy(), ref)
+        assert err < tol, err
         assert hh.tc_status() == 0
     finally:
         if hh is not h:

@@ -121,11 +121,12 @@ def test_stencil_full_size_sampled(api, ctx, prec):
 _HIER = {}
 
 
-def hierarchies(api, ctx, L, m0=-0.05, ntv=8, seed=3):
-    key = (L, m0, ntv, seed)
+def hierarchies(api, ctx, L, m0=-0.05, ntv=8, seed=3, tensor_cores=2):
+    """GPU hierarchy and the oracle's; tensor_cores: 2 = TF32 coarse images (the library default), 1 = BF16."""
+    key = (L, m0, ntv, seed, tensor_cores)
     if key not in _HIER:
         U = field(L, 3.0, 2)
-        h = api.mg_setup(ctx, cuda(U), L, m0, ntv=ntv, setup_sweeps=4, seed=seed)
+        h = api.mg_setup(ctx, cuda(U), L, m0, ntv=ntv, setup_sweeps=4, seed=seed, tensor_cores=tensor_cores)
         H = omg.Hierarchy(osch.dirac_sparse(U, m0), L, ntv=ntv, setup_sweeps=4, seed=seed)
         _HIER[key] = (h, H)
     return _HIER[key]
@@ -177,13 +178,14 @@ def test_level_operators_and_transfers(api, ctx):
             assert relerr(xf.cpu().numpy(), (P @ v.T).T) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
 def test_smoother_parity(api, ctx, prec):
-    """SAP sweeps (the smoother of the V-cycle) against the oracle's SAP on the same level operator."""
-    h, H = hierarchies(api, ctx, 64)
-    tol = {"fp64": 1e-12, "fp32": 2e-5, "tf32": 5e-3}[prec]
+    """SAP sweeps (the smoother of the V-cycle) against the oracle's SAP on the same level operator; TF32 and
+    BF16 tensor-core sweeps on the coarse levels (BF16: 8-bit significands, FP32 accumulation)."""
+    h, H = hierarchies(api, ctx, 64, tensor_cores=1 if prec == "bf16" else 2)
+    tol = {"fp64": 1e-12, "fp32": 2e-5, "tf32": 5e-3, "bf16": 2e-2}[prec]
     for l in range(H.levels - 1):
-        if prec == "tf32" and l == 0:
+        if prec in ("tf32", "bf16") and l == 0:
             continue  # tensor-core smoother runs on coarse levels
         f = rand_vecs(H.n[l], 3, 40 + l)
         x0 = rand_vecs(H.n[l], 3, 50 + l)
@@ -191,21 +193,26 @@ def test_smoother_parity(api, ctx, prec):
         ref = sap.sweep(f.T.copy(), sap.sweep(f.T.copy(), x0.T.copy())).T
         dt = np.complex128 if prec == "fp64" else np.complex64
         xd = cuda(x0.astype(dt))
-        h.smooth(l, cuda(f.astype(dt)), xd, {"fp64": api.FP64, "fp32": api.FP32, "tf32": api.TF32}[prec], 2)
-        assert relerr(xd.cpu().numpy(), ref) < tol
+        h.smooth(l, cuda(f.astype(dt)), xd, {"fp64": api.FP64, "fp32": api.FP32, "tf32": api.TF32,
+                                             "bf16": api.BF16}[prec], 2)
+        err = relerr(xd.cpu().numpy(), ref)
+        assert err < tol, (l, err)
     assert h.tc_status() == 0
 
 
-def test_tensor_core_stencil(api, ctx):
-    """TF32 tcgen05 coarse stencil against the oracle's Galerkin operator; ragged rhs counts."""
-    h, H = hierarchies(api, ctx, 64)
+@pytest.mark.parametrize("fmt", ["tf32", "bf16"])
+def test_tensor_core_stencil(api, ctx, fmt):
+    """tcgen05 coarse stencil (TF32 or BF16 operands, FP32 accumulation) against the oracle's Galerkin
+    operator; ragged rhs counts."""
+    h, H = hierarchies(api, ctx, 64, tensor_cores=2 if fmt == "tf32" else 1)
     for l in range(1, H.levels):
         for nrhs in (1, 37, 130):
             x = rand_vecs(H.n[l], nrhs, 60 + nrhs)
             ref = (H.D[l] @ x.T).T
             y = torch.zeros((nrhs, H.n[l]), dtype=torch.complex64, device="cuda")
-            h.apply(l, cuda(x.astype(np.complex64)), y, api.TF32)
-            assert relerr(y.cpu().numpy(), ref) < 5e-3
+            h.apply(l, cuda(x.astype(np.complex64)), y, api.TF32 if fmt == "tf32" else api.BF16)
+            err = relerr(y.cpu().numpy(), ref)
+            assert err < (5e-3 if fmt == "tf32" else 2e-2), (l, nrhs, err)
     assert h.tc_status() == 0
 
 

@@ -2,7 +2,7 @@
 
 The benchmark times MG-MLMC++ with the set-up and estimator of bench.WORKLOAD: bootstrap set-up (2 rounds of
 6 FGMRES iterations on top of the smoothed test vectors), 8 test vectors per chirality, V(2,2) SAP cycles with
-the TF32 tensor-core kernels on the coarse levels, mixed precision (FP32 inner FGMRES, FP64 true-residual
+the tensor-core kernels on the coarse levels (TF32 operands), mixed precision (FP32 inner FGMRES, FP64 true-residual
 refinement to 1e-10), d = 32 Hutch++ vectors with k = 2 power sweeps, accumulated form, first batch 8, counted
 flops as the sample cost.  Here the same configuration runs at L = 256 (4 levels, 256 -> 64 -> 16 -> 4, the
 same depth and coarse dof as L = 512) on a beta = 5 field with the tuned near-critical mass.
@@ -10,7 +10,8 @@ same depth and coarse dof as L = 512) on a beta = 5 field with the tuned near-cr
 The bootstrap set-up is adaptive (many prolongators are valid), so the GPU's P_l are imported as data and
 checked for their defining properties; the oracle then builds its own Galerkin operators P^H D P from its own
 fine operator and solves with sparse LU.  Tolerances: P^H P = I to 1e-12, stencils and tau_L 1e-10,
-tau_lr and per-sample tau 1e-8 (solver residual 1e-10), Q 1e-6, tensor-core (TF32) kernels 5e-3.
+tau_lr and per-sample tau 1e-8 (solver residual 1e-10), Q 1e-6, the tensor-core kernels 5e-3 with TF32
+operands (2e-2 with BF16: 8-bit significands, FP32 accumulation).
 """
 import json
 import os
@@ -49,7 +50,7 @@ def setup():
     ctx = api.Context()
     h = api.mg_setup(ctx, torch.from_numpy(U).cuda(), L, m0, ntv=W["ntv"], bootstrap=W["bootstrap"],
                      bootstrap_its=W["bootstrap_its"], kcycle_its=W["kcycle_its"], pre_smooth=W["pre_smooth"],
-                     post_smooth=W["post_smooth"])
+                     post_smooth=W["post_smooth"], tensor_cores=W["tensor_cores"])
     assert h.levels == 4 and h.side == [256, 64, 16, 4]
     Ps = [omg.prolongator_from_blocks(h.get_prolongator(l, 4, W["ntv"]), h.side[l], h.dof[l], 4, W["ntv"])
           for l in range(h.levels - 1)]
@@ -117,8 +118,9 @@ def test_estimate_of_the_benchmark_configuration(setup):
 
 def test_tensor_core_kernels_on_the_workload_level(setup):
     """Level 1 (64 x 64 coarse sites, 16 dof): every CTA of the tcgen05 kernels walks many sites and blocks.
-    TF32 stencil and TF32 SAP sweeps against the oracle's Galerkin operator and SAP on the same level."""
-    api, h, H = setup["api"], setup["h"], setup["H"]
+    Tensor-core stencil and SAP sweeps against the oracle's Galerkin operator and SAP on the same level."""
+    api, h, H, W = setup["api"], setup["h"], setup["H"], setup["W"]
+    prec, tol = (api.BF16, 2e-2) if W["tensor_cores"] == 1 else (api.TF32, 5e-3)
     l = 1
     n = h.n[l]
     sap = omg.SAP(H.D[l], h.side[l], h.dof[l], 2)
@@ -126,18 +128,20 @@ def test_tensor_core_kernels_on_the_workload_level(setup):
     for nrhs in (8, 200):
         x = rs.standard_normal((nrhs, n)) + 1j * rs.standard_normal((nrhs, n))
         y = torch.zeros((nrhs, n), dtype=torch.complex64, device="cuda")
-        h.apply(l, torch.from_numpy(x.astype(np.complex64)).cuda(), y, api.TF32)
-        assert relerr(y.cpu().numpy(), (H.D[l] @ x.T).T) < 5e-3
+        h.apply(l, torch.from_numpy(x.astype(np.complex64)).cuda(), y, prec)
+        err = relerr(y.cpu().numpy(), (H.D[l] @ x.T).T)
+        assert err < tol, err
         f = rs.standard_normal((nrhs, n)) + 1j * rs.standard_normal((nrhs, n))
         xd = torch.from_numpy(x.astype(np.complex64)).cuda()
-        h.smooth(l, torch.from_numpy(f.astype(np.complex64)).cuda(), xd, api.TF32, 2)
+        h.smooth(l, torch.from_numpy(f.astype(np.complex64)).cuda(), xd, prec, 2)
         ref = sap.sweep(f.T.copy(), sap.sweep(f.T.copy(), x.T.copy())).T
-        assert relerr(xd.cpu().numpy(), ref) < 5e-3
+        err = relerr(xd.cpu().numpy(), ref)
+        assert err < tol, err
     assert h.tc_status() == 0
 
 
 def test_vcycle_of_the_workload(setup):
-    """One V(2,2) cycle from the fine level, FP32 with the TF32 coarse kernels (the preconditioner the
+    """One V(2,2) cycle from the fine level, FP32 with the tensor-core coarse kernels (the preconditioner the
     benchmark's inner FGMRES applies) and FP64, against the oracle's V-cycle on the same hierarchy."""
     api, h, H, W = setup["api"], setup["h"], setup["H"], setup["W"]
     rs = np.random.default_rng(8)
@@ -148,5 +152,6 @@ def test_vcycle_of_the_workload(setup):
     assert relerr(x64.cpu().numpy(), ref) < 1e-11
     x32 = torch.empty((4, h.n[0]), dtype=torch.complex64, device="cuda")
     h.vcycle(0, torch.from_numpy(b.astype(np.complex64)).cuda(), x32, api.FP32)
-    assert relerr(x32.cpu().numpy(), ref) < 5e-3
+    err = relerr(x32.cpu().numpy(), ref)
+    assert err < (2e-2 if W["tensor_cores"] == 1 else 5e-3), err
     assert h.tc_status() == 0
