@@ -277,14 +277,14 @@ int mg_restrict_to_level(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const doubl
  * accumulated form), k block power sweeps Y = A_l S, Q = qr(Y) (CholeskyQR2 in
  * FP64, R with real positive diagonal), S = Q; then the low-rank part
  * tau_lr = sum_i q_i^H A_l q_i.  Q is kept at level size (Q_fine = Phat_l Q).
- * tau_lr: host complex128.  *out owns Q (n_l x d, FP64). */
+ * 1 <= d <= 64, k >= 1.  tau_lr: host complex128.  *out owns Q (n_l x d, FP64). */
 int hutchpp_sketch_qr(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, int d, int k, uint64_t seed,
                       int form, const solve_params* sp, mgmlmc_sketch** out, double* tau_lr);
 void hutchpp_sketch_destroy(mgmlmc_sketch* s);
 /* The QR step of the sketch (Algorithm 2, "Compute QR-factoriz. Y_l = Q_l K_l") in place on a caller's
  * basis: Y (device complex128 [d][n], vector i at Y + i n) becomes Q with Q^H Q = I by CholeskyQR2 (Gram
  * matrix G = Y^H Y in FP64, Cholesky G = R^H R with real positive diagonal, Y <- Y R^{-1}, done twice).
- * 1 <= d <= 32, n >= d.  Returns MGMLMC_ERR_NOT_POSDEF when a Gram matrix is not positive definite (Y of
+ * 1 <= d <= 64, n >= d.  Returns MGMLMC_ERR_NOT_POSDEF when a Gram matrix is not positive definite (Y of
  * rank < d); Y is then left partly transformed. */
 int hutchpp_cholqr2(mgmlmc_ctx* ctx, double* Y, int d, int64_t n);
 /* Copy Q to a device buffer complex128 [d][n_l]. */
@@ -359,7 +359,7 @@ int mg_attach_nn(mgmlmc_ctx* ctx, mgmlmc_hier* h, mgmlmc_nn* nn);
 
 typedef struct {
   double eps;                       /* target relative 1-sigma accuracy */
-  int d[MGMLMC_MAX_LEVELS];         /* deflation vectors per level difference (0 = plain MG-MLMC) */
+  int d[MGMLMC_MAX_LEVELS];         /* deflation vectors per level difference, 0..64 (0 = plain MG-MLMC) */
   int k;                            /* block power sweeps (2) */
   int nrhs_max;                     /* largest batch of samples per level (256) */
   int nrhs_first;                   /* first batch per level (32) */

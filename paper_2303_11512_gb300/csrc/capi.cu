@@ -459,7 +459,7 @@ void hutchpp_sketch_destroy(mgmlmc_sketch* s) {
 int hutchpp_cholqr2(mgmlmc_ctx* ctx, double* Y, int d, int64_t n) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(Y, "null pointer");
-    MG_CHECK_ARG(d >= 1 && d <= 32, "d must be 1..32");
+    MG_CHECK_ARG(d >= 1 && d <= SK_MAXD, "d must be 1..64");
     MG_CHECK_ARG(n >= d, "need n >= d");
     cholesky_qr2(ctx, (double2*)Y, d, (long)n);
   });

@@ -729,7 +729,7 @@ void cholesky_qr2(mgmlmc_ctx* ctx, double2* Y, int d, long n) {
 
 mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int form, const solve_params& sp,
                          double2* tau_lr) {
-  MG_CHECK_ARG(d >= 1 && d <= 32, "sketch size d must be 1..32");
+  MG_CHECK_ARG(d >= 1 && d <= SK_MAXD, "sketch size d must be 1..64");
   MG_CHECK_ARG(k >= 1, "at least one power sweep");
   cudaStream_t st = h->ctx->stream;
   const long n = h->lv[l].n;
@@ -779,7 +779,7 @@ void sketch_qr_all(mgmlmc_hier* h, const int* d, int k, uint64_t seed, int form,
   std::vector<double2*> S(nd, nullptr), Y(nd, nullptr);
   for (int l = 0; l < nd; ++l) {
     if (d[l] <= 0) continue;
-    MG_CHECK_ARG(d[l] <= 32, "sketch size d must be 1..32");
+    MG_CHECK_ARG(d[l] <= SK_MAXD, "sketch size d must be 1..64");
     const long n = h->lv[l].n;
     out[l].reset(new mgmlmc_sketch);
     out[l]->level = l; out[l]->d = d[l]; out[l]->n = n; out[l]->st = st;

@@ -138,6 +138,7 @@ void noise_fill(cudaStream_t st, int kind, uint64_t seed, int level, int phase, 
 void gamma5_apply(cudaStream_t st, double2* y, int dof, long n, int nrhs);
 
 // ---------------------------------------------------------------- Hutch++ (FP64)
+constexpr int SK_MAXD = 64;  // largest sketch size d (deflation vectors per level difference)
 // G = Y^H Y, Y = [d][n]; out d x d (row-major, G[i][j] = y_i^H y_j)
 void gram(cudaStream_t st, const double2* Y, int d, long n, double2* G, void* work);
 size_t gram_work_bytes(int d, long n);

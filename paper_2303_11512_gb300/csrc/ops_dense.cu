@@ -418,21 +418,27 @@ size_t gram_work_bytes(int d, long n) {
   return sizeof(double2) * (size_t)GBLK * d * d;
 }
 
-// G is Hermitian: thread t < d(d+1)/2 accumulates the upper-triangle entry (i, j), i <= j (packed so that the
-// working threads fill whole warps), and writes it and its conjugate mirror.
+// G is Hermitian: the upper-triangle entries (i, j), i <= j, are packed in order (t = 0 .. d(d+1)/2 - 1) and
+// thread tid accumulates entries tid, tid + blockDim.x, ... (at most GACC of them), writing each and its
+// conjugate mirror.
+constexpr int GACC = (SK_MAXD * (SK_MAXD + 1) / 2 + 1023) / 1024;
 __global__ void __launch_bounds__(1024) k_gram_part(const double2* __restrict__ Y, int d, long n,
                                                     double2* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* Ys = reinterpret_cast<double2*>(smem_raw);  // [GCH][d]
-  const int tid = threadIdx.x;
-  int i = 0, j = 0;
-  {
-    int t = tid;
-    while (i < d && t >= d - i) { t -= d - i; ++i; }
-    j = i + t;
+  const int tid = threadIdx.x, ntri = d * (d + 1) / 2;
+  int ii[GACC], jj[GACC];
+#pragma unroll
+  for (int u = 0; u < GACC; ++u) {
+    int t = tid + u * (int)blockDim.x, i = 0;
+    if (t >= ntri) { ii[u] = -1; jj[u] = 0; continue; }
+    while (t >= d - i) { t -= d - i; ++i; }
+    ii[u] = i;
+    jj[u] = i + t;
   }
-  const bool on = i < d;
-  double2 acc = make_double2(0, 0);
+  double2 acc[GACC];
+#pragma unroll
+  for (int u = 0; u < GACC; ++u) acc[u] = make_double2(0, 0);
   for (long e0 = (long)blockIdx.x * GCH; e0 < n; e0 += (long)gridDim.x * GCH) {
     __syncthreads();
     for (int q = tid; q < GCH * d; q += blockDim.x) {
@@ -440,13 +446,18 @@ __global__ void __launch_bounds__(1024) k_gram_part(const double2* __restrict__ 
       Ys[e * d + c] = (e0 + e < n) ? Y[(size_t)c * n + e0 + e] : make_double2(0, 0);
     }
     __syncthreads();
-    if (on)
+#pragma unroll
+    for (int u = 0; u < GACC; ++u)
+      if (ii[u] >= 0)
 #pragma unroll 8
-      for (int e = 0; e < GCH; ++e) acc = cfmac(Ys[e * d + i], Ys[e * d + j], acc);
+        for (int e = 0; e < GCH; ++e) acc[u] = cfmac(Ys[e * d + ii[u]], Ys[e * d + jj[u]], acc[u]);
   }
-  if (on) {
-    part[((size_t)blockIdx.x * d + i) * d + j] = acc;
-    if (i != j) part[((size_t)blockIdx.x * d + j) * d + i] = cconj(acc);
+#pragma unroll
+  for (int u = 0; u < GACC; ++u) {
+    if (ii[u] < 0) continue;
+    const int i = ii[u], j = jj[u];
+    part[((size_t)blockIdx.x * d + i) * d + j] = acc[u];
+    if (i != j) part[((size_t)blockIdx.x * d + j) * d + i] = cconj(acc[u]);
   }
 }
 
@@ -459,17 +470,18 @@ __global__ void k_gram_final(const double2* __restrict__ part, int d, int nb, do
 }
 
 void gram(cudaStream_t st, const double2* Y, int d, long n, double2* G, void* work) {
-  MG_CHECK_ARG(d <= 32, "sketch size d limited to 32");
+  MG_CHECK_ARG(d >= 1 && d <= SK_MAXD, "sketch size d limited to 64");
   const int nb = (int)std::min<long>(GBLK, cdiv(n, GCH));
   double2* part = reinterpret_cast<double2*>(work);
   MG_LAUNCH(k_gram_part, nb, 1024, sizeof(double2) * GCH * d, st, Y, d, n, part);
   MG_LAUNCH(k_gram_final, cdiv(d * d, 256), 256, 0, st, part, d, nb, G);
 }
 
-// G = R^H R (R upper, real positive diagonal), Rinv = R^{-1}.
+// G = R^H R (R upper, real positive diagonal), Rinv = R^{-1}; R and its inverse in dynamic shared memory
 __global__ void k_chol_inv(const double2* __restrict__ Gg, int d, double2* __restrict__ Rinv, int* fail) {
-  __shared__ double2 R[32 * 32];
-  __shared__ double2 X[32 * 32];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* R = reinterpret_cast<double2*>(smem_raw);
+  double2* X = R + d * d;
   __shared__ int bad;
   const int tid = threadIdx.x;
   for (int e = tid; e < d * d; e += blockDim.x) { R[e] = Gg[e]; X[e] = make_double2(0, 0); }
@@ -506,39 +518,49 @@ __global__ void k_chol_inv(const double2* __restrict__ Gg, int d, double2* __res
 }
 
 void chol_inv_upper(cudaStream_t st, const double2* G, int d, double2* Rinv, int* fail) {
-  MG_CHECK_ARG(d <= 32, "sketch size d limited to 32");
-  MG_LAUNCH(k_chol_inv, 1, 128, 0, st, G, d, Rinv, fail);
+  MG_CHECK_ARG(d >= 1 && d <= SK_MAXD, "sketch size d limited to 64");
+  const int sm = (int)sizeof(double2) * 2 * d * d;
+  ensure_max_smem((const void*)k_chol_inv, sizeof(double2) * 2 * SK_MAXD * SK_MAXD);
+  MG_LAUNCH(k_chol_inv, 1, 128, sm, st, G, d, Rinv, fail);
 }
 
-__global__ void k_right_mul_upper(double2* __restrict__ Y, int d, long n, const double2* __restrict__ Rinv) {
-  __shared__ double2 Rs[32 * 32];
+// Y <- Y Rinv for Y = [d][n]: a block takes RMT consecutive elements e of all d vectors into shared memory and
+// each thread forms new_j(e) = sum_{i <= j} Y_i(e) Rinv_ij for several (e, j)
+constexpr int RMT = 32;
+__global__ void __launch_bounds__(256) k_right_mul_upper(double2* __restrict__ Y, int d, long n,
+                                                         const double2* __restrict__ Rinv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* Rs = reinterpret_cast<double2*>(smem_raw);  // [d][d]
+  double2* Ys = Rs + d * d;                             // [RMT][d + 1]
   for (int e = threadIdx.x; e < d * d; e += blockDim.x) Rs[e] = Rinv[e];
-  __syncthreads();
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-    double2 v[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < d) v[i] = Y[(size_t)i * n + e];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j < d) {
-        double2 s = make_double2(0, 0);
-#pragma unroll
-        for (int i = 0; i <= j; ++i) s = cfma(v[i], Rs[i * d + j], s);
-        Y[(size_t)j * n + e] = s;
-      }
+  for (long e0 = (long)blockIdx.x * RMT; e0 < n; e0 += (long)gridDim.x * RMT) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < RMT * d; q += blockDim.x) {
+      const int i = q / RMT, e = q % RMT;
+      Ys[e * (d + 1) + i] = (e0 + e < n) ? Y[(size_t)i * n + e0 + e] : make_double2(0, 0);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < RMT * d; q += blockDim.x) {
+      const int j = q / RMT, e = q % RMT;
+      if (e0 + e >= n) continue;
+      double2 acc = make_double2(0, 0);
+      for (int i = 0; i <= j; ++i) acc = cfma(Ys[e * (d + 1) + i], Rs[i * d + j], acc);
+      Y[(size_t)j * n + e0 + e] = acc;
     }
   }
 }
 
 void right_mul_upper(cudaStream_t st, double2* Y, int d, long n, const double2* Rinv) {
-  MG_CHECK_ARG(d <= 32, "sketch size d limited to 32");
-  MG_LAUNCH(k_right_mul_upper, std::min<long>(cdiv(n, 128), 2048), 128, 0, st, Y, d, n, Rinv);
+  MG_CHECK_ARG(d >= 1 && d <= SK_MAXD, "sketch size d limited to 64");
+  const size_t sm = sizeof(double2) * ((size_t)d * d + (size_t)RMT * (d + 1));
+  ensure_max_smem((const void*)k_right_mul_upper,
+                  (int)(sizeof(double2) * ((size_t)SK_MAXD * SK_MAXD + (size_t)RMT * (SK_MAXD + 1))));
+  MG_LAUNCH(k_right_mul_upper, std::min<long>(cdiv(n, RMT), 2048), 256, sm, st, Y, d, n, Rinv);
 }
 
 // ---- projection coefficients c[i][r] = Q_i^H x_r -----------------------------------------------------
 namespace {
-constexpr int PCH = 64;    // rows per chunk
+constexpr int PCH = 32;    // rows per chunk (the Q tile of up to 64 vectors stays under 48 KB)
 constexpr int PRG = 8;     // rhs per block
 constexpr int PBLK = 96;   // chunks (partials)
 }
@@ -548,19 +570,20 @@ size_t proj_work_bytes(int d, long n, int nrhs) {
   return sizeof(double2) * (size_t)PBLK * d * nrhs;
 }
 
+// 32 x 8 threads: lane i accumulates basis vectors i and i + 32 (d <= 64) against rhs r0 + g
 __global__ void __launch_bounds__(256) k_proj_part(const double2* __restrict__ Q, int d, const double2* __restrict__ x,
                                                    long n, int nrhs, double2* __restrict__ part) {
-  __shared__ double2 Qs[PCH * 33];
+  __shared__ double2 Qs[PCH * (SK_MAXD + 1)];
   __shared__ double2 Xs[PRG * PCH];
   const int tid = threadIdx.x;
   const int r0 = blockIdx.y * PRG;
-  const int i = tid % 32, g = tid / 32;  // 32 x 8 threads
-  double2 acc = make_double2(0, 0);
+  const int i = tid % 32, g = tid / 32;
+  double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
   for (long e0 = (long)blockIdx.x * PCH; e0 < n; e0 += (long)gridDim.x * PCH) {
     __syncthreads();
     for (int q = tid; q < d * PCH; q += blockDim.x) {
       const int c = q / PCH, e = q % PCH;
-      Qs[e * 33 + c] = (e0 + e < n) ? Q[(size_t)c * n + e0 + e] : make_double2(0, 0);
+      Qs[e * (SK_MAXD + 1) + c] = (e0 + e < n) ? Q[(size_t)c * n + e0 + e] : make_double2(0, 0);
     }
     for (int q = tid; q < PRG * PCH; q += blockDim.x) {
       const int rr = q / PCH, e = q % PCH;
@@ -569,9 +592,16 @@ __global__ void __launch_bounds__(256) k_proj_part(const double2* __restrict__ Q
     __syncthreads();
     if (i < d)
 #pragma unroll 8
-      for (int e = 0; e < PCH; ++e) acc = cfmac(Qs[e * 33 + i], Xs[g * PCH + e], acc);
+      for (int e = 0; e < PCH; ++e) {
+        const double2 xv = Xs[g * PCH + e];
+        acc0 = cfmac(Qs[e * (SK_MAXD + 1) + i], xv, acc0);
+        if (i + 32 < d) acc1 = cfmac(Qs[e * (SK_MAXD + 1) + i + 32], xv, acc1);
+      }
   }
-  if (i < d && r0 + g < nrhs) part[((size_t)blockIdx.x * d + i) * nrhs + r0 + g] = acc;
+  if (r0 + g < nrhs) {
+    if (i < d) part[((size_t)blockIdx.x * d + i) * nrhs + r0 + g] = acc0;
+    if (i + 32 < d) part[((size_t)blockIdx.x * d + i + 32) * nrhs + r0 + g] = acc1;
+  }
 }
 
 __global__ void k_proj_final(const double2* __restrict__ part, int cnt, int nb, double2* __restrict__ c) {
@@ -583,7 +613,7 @@ __global__ void k_proj_final(const double2* __restrict__ part, int cnt, int nb, 
 }
 
 void proj_coeffs(cudaStream_t st, const double2* Q, int d, const double2* x, long n, int nrhs, double2* c, void* work) {
-  MG_CHECK_ARG(d <= 32, "sketch size d limited to 32");
+  MG_CHECK_ARG(d >= 1 && d <= SK_MAXD, "sketch size d limited to 64");
   const int nb = (int)std::min<long>(PBLK, cdiv(n, PCH));
   double2* part = reinterpret_cast<double2*>(work);
   MG_LAUNCH(k_proj_part, dim3(nb, cdiv(nrhs, PRG)), 256, 0, st, Q, d, x, n, nrhs, part);

@@ -48,10 +48,11 @@ def test_nan_gauge_link_and_nan_rhs(env):
         h.close()
 
 
-def test_cholqr2_parity_and_rank_deficiency(env):
+@pytest.mark.parametrize("d", [24, 50, 64])
+def test_cholqr2_parity_and_rank_deficiency(env, d):
     api, _lib, ctx = env
     rs = np.random.default_rng(2)
-    n, d = 5000, 24
+    n = 5000
     Y = rs.standard_normal((n, d)) + 1j * rs.standard_normal((n, d))
     Yd = torch.from_numpy(np.ascontiguousarray(Y.T)).cuda()
     api.hutchpp_cholqr2(ctx, Yd)

@@ -289,7 +289,7 @@ def test_level_sample_parity(api, ctx, form):
         assert relerr(tau, tau_ref) < 1e-8
 
 
-@pytest.mark.parametrize("L,d", [(32, 8), (64, 8)])
+@pytest.mark.parametrize("L,d", [(32, 8), (64, 8), (32, 48)])
 def test_sketch_parity(api, ctx, L, d):
     h, H = hierarchies(api, ctx, L)
     ld = oest.LevelDifference(H)
