@@ -419,6 +419,8 @@ typedef struct {
   solve_params solve;  /* solves on level 0 (e.g. precond = 0, m = 30: unpreconditioned GMRES(30)) */
   double* sample_out;  /* optional host buffer, complex128 [sample_cap] */
   int64_t sample_cap;
+  const mgmlmc_sketch* deflate; /* NULL, or a deflation basis from deflation_basis: the samples become
+                                   zeta^H (I - V V^H) D^{-1} zeta and the basis's direct part is added */
 } hutch_params;
 
 typedef struct {
@@ -428,6 +430,7 @@ typedef struct {
   int64_t computed;    /* samples computed (>= N) */
   int64_t solves;
   int64_t inner_iters;
+  double tau_defl[2];  /* the deflation basis's direct part tr(V^H D^{-1} V) (0 without deflation) */
 } hutch_result;
 
 int hutch_params_default(hutch_params* p);
@@ -436,6 +439,18 @@ int hutch_params_default(hutch_params* p);
  * stop once V/s <= (eps |tau|)^2.  Samples are solved in batches; the host replays the per-sample stop, so
  * N is that of the per-sample algorithm and surplus samples are discarded. */
 int hutchinson_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const hutch_params* p, hutch_result* r);
+
+/* Deflation basis of the exactly deflated Hutchinson estimator (Section 2, "Exact Deflation"; the paper's
+ * comparator in Section 4): the right singular vectors of the fine operator D with the k smallest singular
+ * values, i.e. the eigenvectors of the Hermitian gamma5 D with the smallest |mu|, approximated by `sweeps`
+ * steps of the block power method on D^{-1} gamma5 (V <- CholeskyQR2(D^{-1} gamma5 V), k Rademacher start
+ * vectors from the stream (seed, level 0, phase 4, samples 0..k-1)), solves with sp.  *out owns V (fine size,
+ * [k][n_0]); tau_defl (host complex128) = tr(V^H D^{-1} V) = tr(Pi D^{-1}) for Pi = V V^H (k more solves; exact
+ * for any orthonormal V, so the deflated estimator is unbiased however far the iteration converged);
+ * residual (host, may be NULL) = ||Y - V V^H Y||_F / ||Y||_F for Y = D^{-1} gamma5 V (0 for an invariant
+ * subspace).  1 <= k <= 64.  Use the basis with hutchinson_estimate (hutch_params.deflate). */
+int deflation_basis(mgmlmc_ctx* ctx, mgmlmc_hier* h, int k, int sweeps, uint64_t seed, const solve_params* sp,
+                    mgmlmc_sketch** out, double* tau_defl, double* residual);
 
 /* The target-accuracy update of Algorithm 2 for one step (host only, no GPU):
  * active[l] (in/out, 0/1) becomes 0 when V[l]/N[l] <= rho_l^2 with

@@ -60,12 +60,13 @@ class EstResult(C.Structure):
 class HutchParams(C.Structure):
     _fields_ = [("eps", C.c_double), ("nrhs_first", C.c_int), ("nrhs_max", C.c_int), ("seed", C.c_uint64),
                 ("noise", C.c_int), ("weight", C.c_int), ("min_samples", C.c_int), ("max_samples", C.c_int64),
-                ("solve", SolveParams), ("sample_out", C.POINTER(C.c_double)), ("sample_cap", C.c_int64)]
+                ("solve", SolveParams), ("sample_out", C.POINTER(C.c_double)), ("sample_cap", C.c_int64),
+                ("deflate", C.c_void_p)]
 
 
 class HutchResult(C.Structure):
     _fields_ = [("tau", C.c_double * 2), ("sigma", C.c_double), ("N", C.c_int64), ("computed", C.c_int64),
-                ("solves", C.c_int64), ("inner_iters", C.c_int64)]
+                ("solves", C.c_int64), ("inner_iters", C.c_int64), ("tau_defl", C.c_double * 2)]
 
 
 vp = C.c_void_p
@@ -122,6 +123,7 @@ SIGNATURES = {
     "trace_estimate": (ip, [vp, vp, C.POINTER(EstParams), C.POINTER(EstResult)]),
     "hutch_params_default": (ip, [C.POINTER(HutchParams)]),
     "hutchinson_estimate": (ip, [vp, vp, C.POINTER(HutchParams), C.POINTER(HutchResult)]),
+    "deflation_basis": (ip, [vp, vp, ip, ip, C.c_uint64, C.POINTER(SolveParams), C.POINTER(vp), dp, dp]),
     "mlmc_update_active": (ip, [ip, C.POINTER(ip), dp, C.POINTER(C.c_int64), dp, C.c_double, C.c_double, ip, ip]),
 }
 

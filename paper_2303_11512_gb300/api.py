@@ -461,16 +461,31 @@ def trace_estimate(ctx: Context, h: Hierarchy, eps: float = 1e-3, d=32, k: int =
     return out
 
 
+def deflation_basis(ctx: Context, h: Hierarchy, k: int, sweeps: int, seed: int = 0, **solve):
+    """Deflation basis of the exactly deflated Hutchinson comparator: (Sketch with V [k, n_0], tau_defl,
+    residual of the subspace)."""
+    sp = solve_params(**solve)
+    s = C.c_void_p()
+    t = (C.c_double * 2)()
+    res = C.c_double()
+    check(_lib.load().deflation_basis(ctx.ptr, h.ptr, k, sweeps, seed, C.byref(sp), C.byref(s), t, C.byref(res)),
+          ctx.ptr)
+    return Sketch(ctx, s), complex(t[0], t[1]), res.value
+
+
 def hutchinson_estimate(ctx: Context, h: Hierarchy, eps: float = 1e-2, seed: int = 0, nrhs_first: int = 32,
                         nrhs_max: int = 256, noise: int = NOISE_RADEMACHER, weight: int = TRACE_PLAIN,
-                        min_samples: int = 2, max_samples: int = 1 << 20, keep_samples: int = 0, **solve) -> dict:
-    """Plain Hutchinson (Algorithm 1) on the fine operator of h."""
+                        min_samples: int = 2, max_samples: int = 1 << 20, keep_samples: int = 0,
+                        deflate: "Sketch | None" = None, **solve) -> dict:
+    """Plain Hutchinson (Algorithm 1) on the fine operator of h; with `deflate` (a deflation_basis) the exactly
+    deflated estimator."""
     p = HutchParams()
     lib = _lib.load()
     lib.hutch_params_default(C.byref(p))
     p.eps, p.seed, p.nrhs_first, p.nrhs_max = eps, seed, nrhs_first, nrhs_max
     p.noise, p.weight, p.min_samples, p.max_samples = noise, weight, min_samples, max_samples
     p.solve = solve_params(**solve)
+    p.deflate = deflate.ptr if deflate is not None else None
     buf = None
     if keep_samples:
         buf = np.zeros(2 * keep_samples, dtype=np.float64)
@@ -479,7 +494,7 @@ def hutchinson_estimate(ctx: Context, h: Hierarchy, eps: float = 1e-2, seed: int
     r = HutchResult()
     check(lib.hutchinson_estimate(ctx.ptr, h.ptr, C.byref(p), C.byref(r)), ctx.ptr)
     out = dict(tau=complex(r.tau[0], r.tau[1]), sigma=r.sigma, N=r.N, computed=r.computed, solves=r.solves,
-               inner_iters=r.inner_iters)
+               inner_iters=r.inner_iters, tau_defl=complex(r.tau_defl[0], r.tau_defl[1]))
     if keep_samples:
         out["samples"] = buf.view(np.complex128)[: min(keep_samples, r.computed)]
     return out

@@ -524,6 +524,21 @@ int hutch_params_default(hutch_params* p) {
   return MGMLMC_OK;
 }
 
+int deflation_basis(mgmlmc_ctx* ctx, mgmlmc_hier* h, int k, int sweeps, uint64_t seed, const solve_params* sp,
+                    mgmlmc_sketch** out, double* tau_defl, double* residual) {
+  if (out) *out = nullptr;
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && sp && out && tau_defl, "null pointer");
+    h->ctx = ctx;
+    MG_CHECK_ARG(sp->tol > 0 && sp->maxit > 0, "tol and maxit must be positive");
+    check_prec(sp->prec);
+    mgmlmc_sketch* s = deflation_basis(h, k, sweeps, seed, *sp, residual, nullptr);
+    tau_defl[0] = s->tau.x;
+    tau_defl[1] = s->tau.y;
+    *out = s;
+  });
+}
+
 int hutchinson_estimate(mgmlmc_ctx* ctx, mgmlmc_hier* h, const hutch_params* p, hutch_result* r) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && p && r, "null pointer");

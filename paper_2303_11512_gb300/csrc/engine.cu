@@ -756,6 +756,78 @@ mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int
   double2 t = make_double2(0, 0);
   for (int i = 0; i < d; ++i) t = cadd(t, hd[i]);
   *tau_lr = t;
+  sk->tau = t;
+  return sk.release();
+}
+
+// Exactly deflated Hutchinson (the paper's comparator, Section 2): the deflating subspace approximates the right
+// singular vectors of D with the smallest singular values, i.e. the eigenvectors of the Hermitian gamma5 D with
+// the smallest |mu|: block power method on Q^{-1} = D^{-1} gamma5, V <- CholeskyQR2(D^{-1} gamma5 V), from k
+// Rademacher vectors (stream: seed, level 0, phase 4).  The direct part tr(V^H D^{-1} V) takes k more solves and
+// is exact for any orthonormal V, so the estimator stays unbiased however far the iteration converged.
+// residual = ||Y - V (V^H Y)||_F / ||Y||_F with Y = D^{-1} gamma5 V after the last sweep (0 for an invariant
+// subspace), from ||Y||^2 - ||V^H Y||^2 (V orthonormal).
+mgmlmc_sketch* deflation_basis(mgmlmc_hier* h, int k, int sweeps, uint64_t seed, const solve_params& sp0,
+                               double* residual, int64_t* solves) {
+  MG_CHECK_ARG(k >= 1 && k <= SK_MAXD, "deflation basis size must be 1..64");
+  MG_CHECK_ARG(sweeps >= 1, "at least one sweep");
+  mgmlmc_ctx* ctx = h->ctx;
+  cudaStream_t st = ctx->stream;
+  const long n = h->lv[0].n;
+  solve_params sp = sp0;
+  if (sp.prec == MGMLMC_FP32) sp.prec = MGMLMC_MIXED;  // FP64 basis
+  std::unique_ptr<mgmlmc_sketch> sk(new mgmlmc_sketch);
+  sk->level = 0; sk->d = k; sk->n = n; sk->st = st;
+  sk->Q.alloc(sizeof(double2) * n * k, st);
+  double2* V = sk->Q.as<double2>();
+  double2* T = (double2*)h->work("df_T", 0, sizeof(double2) * n * k);
+  double2* Y = (double2*)h->work("df_Y", 0, sizeof(double2) * n * k);
+  rademacher_fill(st, seed, 0, 4, 0, n, k, V);
+  int64_t ns = 0;
+  auto solve_g5 = [&](const double2* in, double2* out) {  // out = D^{-1} gamma5 in
+    vcopy<double2>(st, in, T, n, k);
+    gamma5_apply(st, T, h->lv[0].dof, n, k);
+    SolveOut o = solve(h, 0, T, out, k, sp);
+    if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "deflation-basis solves did not converge");
+    ns += k;
+  };
+  for (int it = 0; it < sweeps; ++it) {
+    solve_g5(V, Y);
+    cholesky_qr2(ctx, Y, k, n);
+    vcopy<double2>(st, Y, V, n, k);
+  }
+  // residual of the subspace
+  solve_g5(V, Y);
+  {
+    double* yn = (double*)h->work("df_yn", 0, sizeof(double) * k);
+    double2* G = (double2*)h->work("df_G", 0, sizeof(double2) * k * k);
+    vnorm2<double2>(st, Y, n, k, yn, h->work("df_red", 0, reduce_work_bytes(n, k, 1)), nullptr);
+    proj_coeffs(st, V, k, Y, n, k, G, h->work("df_pw", 0, proj_work_bytes(k, n, k)));
+    std::vector<double> hy(k);
+    std::vector<double2> hg((size_t)k * k);
+    MG_CUDA(cudaMemcpyAsync(hy.data(), yn, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaMemcpyAsync(hg.data(), G, sizeof(double2) * k * k, cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+    double ty = 0, tg = 0;
+    for (double v : hy) ty += v;
+    for (const double2& g : hg) tg += g.x * g.x + g.y * g.y;
+    if (residual) *residual = ty > 0 ? std::sqrt(std::max(0.0, ty - tg) / ty) : 0.0;
+  }
+  // direct part tr(V^H D^{-1} V)
+  {
+    SolveOut o = solve(h, 0, V, Y, k, sp);
+    if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "deflation-trace solves did not converge");
+    ns += k;
+    double2* dots = (double2*)h->work("df_dots", 0, sizeof(double2) * k);
+    vdot<double2>(st, V, Y, n, k, dots, h->work("df_red", 0, reduce_work_bytes(n, k, 1)), nullptr);
+    std::vector<double2> hd(k);
+    MG_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double2) * k, cudaMemcpyDeviceToHost, st));
+    MG_CUDA(cudaStreamSynchronize(st));
+    double2 t = make_double2(0, 0);
+    for (int i = 0; i < k; ++i) t = cadd(t, hd[i]);
+    sk->tau = t;
+  }
+  if (solves) *solves = ns;
   return sk.release();
 }
 
@@ -818,6 +890,7 @@ void sketch_qr_all(mgmlmc_hier* h, const int* d, int k, uint64_t seed, int form,
     double2 t = make_double2(0, 0);
     for (int i = 0; i < d[l]; ++i) t = cadd(t, hd[i]);
     tau_lr[l] = t;
+    out[l]->tau = t;
   }
 }
 
@@ -1036,6 +1109,10 @@ void hutchinson(mgmlmc_hier* h, const hutch_params& p, hutch_result* res) {
   solve_params sp = p.solve;
   if (sp.prec == MGMLMC_FP32) sp.prec = MGMLMC_MIXED;  // samples are FP64 vectors
   const long n = h->lv[0].n;
+  const mgmlmc_sketch* df = p.deflate;
+  MG_CHECK_ARG(!df || (df->level == 0 && df->n == n), "deflation basis must be of the fine level");
+  MG_CHECK_ARG(!df || p.weight == MGMLMC_TRACE_PLAIN, "deflation with the plain trace only");
+  const double2 tdf = df ? df->tau : make_double2(0, 0);
   const int64_t maxs = p.max_samples > 0 ? p.max_samples : (int64_t)1 << 40;
   std::vector<double2> samp;
   LevelStats S;
@@ -1043,7 +1120,7 @@ void hutchinson(mgmlmc_hier* h, const hutch_params& p, hutch_result* res) {
   while (!done && (int64_t)samp.size() < maxs) {
     int64_t want = p.nrhs_first;
     if (S.N >= 2) {  // samples still needed by the current variance: V / (eps |tau|)^2
-      const double t = std::hypot(S.mr, S.mi) * p.eps;
+      const double t = std::hypot(S.mr + tdf.x, S.mi + tdf.y) * p.eps;
       if (t > 0) want = (int64_t)std::ceil(1.15 * S.var() / (t * t)) - S.N + 1;
       want = std::max<int64_t>(want, 8);
       want = ((want + 7) / 8) * 8;
@@ -1057,20 +1134,22 @@ void hutchinson(mgmlmc_hier* h, const hutch_params& p, hutch_result* res) {
     if (!o.converged) throw Error(MGMLMC_ERR_NOT_CONVERGED, "Hutchinson solves did not converge");
     if (p.weight == MGMLMC_TRACE_GAMMA5) gamma5_apply(st, x, h->lv[0].dof, n, b);
     std::vector<double2> t(b);
-    project(ctx, nullptr, z, x, n, b, t.data());
+    project(ctx, df, z, x, n, b, t.data());  // with a deflation basis: zeta^H (I - V V^H) D^{-1} zeta
     res->solves += b;
     res->inner_iters += o.total_iters;
     samp.insert(samp.end(), t.begin(), t.end());
     for (int r = 0; r < b && !done; ++r) {  // Algorithm 1, one sample at a time
       S.add(t[r], 0.0);
       if (S.N >= p.min_samples) {
-        const double tol = std::hypot(S.mr, S.mi) * p.eps;
+        const double tol = std::hypot(S.mr + tdf.x, S.mi + tdf.y) * p.eps;
         if (S.var() / S.N <= tol * tol) done = true;
       }
     }
   }
-  res->tau[0] = S.mr;
-  res->tau[1] = S.mi;
+  res->tau[0] = S.mr + tdf.x;
+  res->tau[1] = S.mi + tdf.y;
+  res->tau_defl[0] = tdf.x;
+  res->tau_defl[1] = tdf.y;
   res->sigma = S.N >= 2 ? std::sqrt(S.var() / S.N) : NAN;
   res->N = S.N;
   res->computed = res->solves;

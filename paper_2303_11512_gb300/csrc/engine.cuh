@@ -111,6 +111,7 @@ struct mgmlmc_sketch {
   long n = 0;
   mg::DBuf Q;  // [d][n] complex128
   cudaStream_t st = 0;
+  double2 tau = make_double2(0, 0);  // direct part: tau_lr of a Hutch++ sketch, tr(Q^H D^{-1} Q) of a deflation basis
 };
 
 namespace mg {
@@ -178,6 +179,10 @@ void make_level_vectors(mgmlmc_hier* h, int l, int form, uint64_t seed, int phas
 SolveOut level_sample_accumulated(mgmlmc_hier* h, int l, const double2* zeta_fine, double2* y_fine, int nrhs,
                                   const solve_params& sp);
 void hutchinson(mgmlmc_hier* h, const hutch_params& p, hutch_result* r);
+// block subspace iteration on D^{-1} gamma5 (fine level): the deflation basis of the exactly deflated Hutchinson
+// comparator, its direct part tr(Q^H D^{-1} Q) in sk->tau and the relative residual of the invariant subspace
+mgmlmc_sketch* deflation_basis(mgmlmc_hier* h, int k, int sweeps, uint64_t seed, const solve_params& sp,
+                               double* residual, int64_t* solves);
 // in-place CholeskyQR2 of Y = [d][n] (FP64): Y <- Q with Q^H Q = I, R with real positive diagonal
 void cholesky_qr2(mgmlmc_ctx* ctx, double2* Y, int d, long n);
 mgmlmc_sketch* sketch_qr(mgmlmc_hier* h, int l, int d, int k, uint64_t seed, int form, const solve_params& sp,
