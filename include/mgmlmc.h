@@ -163,6 +163,8 @@ typedef struct {
                             0.836 s per estimate, BF16 0.866 s with 2.5 % more inner iterations) */
   int graphs;            /* 1: the V-cycle preconditioner is captured once per shape as a CUDA graph
                             and replayed (not while the kernel timer runs or with K-cycles) (1) */
+  int autotune;          /* 1: at the end of mg_setup, run mg_autotune for batches of 8..256 rhs unless the
+                            process-wide tuning table already holds this hierarchy's shapes (0) */
 } mg_params;
 
 int mg_params_default(mg_params* p);
@@ -201,6 +203,21 @@ int mg_get_stencil(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* hos
  * and updated in place.  prec FP64, FP32, or TF32 (tensor cores, coarse levels
  * with 16 dof only). */
 int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x, int nrhs, int prec, int sweeps);
+
+/* Launch-shape autotuner (measurement of this machine, not part of the paper's method).  Several kernels have
+ * launch variants that compute the same result: the tensor-core coarse stencil (MMA tile of 64 or 128
+ * right-hand sides, pipeline depth), the tensor-core SAP block update (pipeline depth) and the FP32 fine
+ * stencil (1, 2 or 4 right-hand sides per thread).  The library keeps one process-wide table
+ * (device, kernel, lattice side, batch bucket, weight format) -> variant, consulted by every launch (batch
+ * bucket: the power of two >= nrhs in 8..256; keys without an entry take the default variant).  mg_autotune
+ * times every variant of h's kernels (CUDA events, median of 5, on scratch vectors) for each of the `count`
+ * batch sizes and records the fastest; force = 0 keeps entries already present.  Synchronous. */
+int mg_autotune(mgmlmc_ctx* ctx, mgmlmc_hier* h, const int* nrhs_list, int count, int force);
+/* The table as text, one line per entry "device kind side bucket format variant microseconds\n" (kind 0 = FP32
+ * fine stencil, 1 = tensor-core stencil, 2 = tensor-core SAP block update); buf: host, len bytes. */
+int mgmlmc_tune_report(char* buf, int64_t len);
+/* Set one entry (for instance from a saved report) on the current device. */
+int mgmlmc_tune_set(int kind, int side, int bucket, int format, int variant);
 
 /* MGMLMC_ERR_TIMEOUT if a tensor-core kernel of this hierarchy ran out of a
  * bounded wait (it then stopped early and freed its tensor memory), else OK. */

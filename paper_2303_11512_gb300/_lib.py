@@ -27,7 +27,7 @@ class MgParams(C.Structure):
                 ("sap_block_coarse", C.c_int), ("setup_sweeps", C.c_int), ("pre_smooth", C.c_int),
                 ("post_smooth", C.c_int), ("seed", C.c_uint64), ("bootstrap", C.c_int),
                 ("bootstrap_its", C.c_int), ("kcycle_its", C.c_int), ("kcycle_tol", C.c_double),
-                ("tensor_cores", C.c_int), ("graphs", C.c_int)]
+                ("tensor_cores", C.c_int), ("graphs", C.c_int), ("autotune", C.c_int)]
 
 
 class SolveParams(C.Structure):
@@ -101,6 +101,9 @@ SIGNATURES = {
     "hutchpp_cholqr2": (ip, [vp, vp, ip, C.c_int64]),
     "mg_smooth": (ip, [vp, vp, ip, vp, vp, ip, ip, ip]),
     "mg_tc_status": (ip, [vp, vp]),
+    "mg_autotune": (ip, [vp, vp, C.POINTER(ip), ip, ip]),
+    "mgmlmc_tune_report": (ip, [C.c_char_p, C.c_int64]),
+    "mgmlmc_tune_set": (ip, [ip, ip, ip, ip, ip]),
     "solve_params_default": (ip, [C.POINTER(SolveParams)]),
     "fgmres_batched": (ip, [vp, vp, ip, vp, vp, ip, C.POINTER(SolveParams), C.POINTER(SolveStats), vp]),
     "mlmc_level_sample": (ip, [vp, vp, ip, ip, vp, vp, ip, C.POINTER(SolveParams), C.POINTER(SolveStats)]),

@@ -165,6 +165,11 @@ class Hierarchy:
     def tc_status(self) -> int:
         return _lib.load().mg_tc_status(self.ctx.ptr, self.ptr)
 
+    def autotune(self, nrhs_list=(8, 16, 32, 64, 128, 256), force: bool = False):
+        """Time the launch variants of this hierarchy's tunable kernels and record the fastest (mg_autotune)."""
+        arr = (C.c_int * len(nrhs_list))(*nrhs_list)
+        check(_lib.load().mg_autotune(self.ctx.ptr, self.ptr, arr, len(nrhs_list), int(force)), self.ctx.ptr)
+
     def vcycle(self, level: int, b: torch.Tensor, x: torch.Tensor, prec: int = FP64):
         dt = _vec_dtype(prec)
         check(_lib.load().mg_vcycle(self.ctx.ptr, self.ptr, level, _ptr(b, dt), _ptr(x, dt), b.shape[0], prec),
@@ -193,6 +198,27 @@ class Hierarchy:
             self.close()
         except Exception:
             pass
+
+
+TUNE_KINDS = {0: "fine stencil (FP32)", 1: "tensor-core stencil", 2: "tensor-core SAP block update"}
+
+
+def tune_table() -> list:
+    """The process-wide launch-variant table: [dict(device, kind, side, bucket, format, variant, us)]."""
+    buf = C.create_string_buffer(1 << 16)
+    check(_lib.load().mgmlmc_tune_report(buf, len(buf)))
+    out = []
+    for line in buf.value.decode().splitlines():
+        dev, kind, side, bucket, fmt, var, us = line.split("\t")
+        out.append(dict(device=int(dev), kind=int(kind), side=int(side), bucket=int(bucket), format=int(fmt),
+                        variant=int(var), us=float(us)))
+    return out
+
+
+def tune_set(entries):
+    """Load entries (as tune_table returns them) into the table of the current device."""
+    for e in entries:
+        check(_lib.load().mgmlmc_tune_set(e["kind"], e["side"], e["bucket"], e["format"], e["variant"]))
 
 
 def mg_setup(ctx: Context, U: torch.Tensor, L: int, m0: float, **params) -> Hierarchy:

@@ -174,6 +174,7 @@ int mg_params_default(mg_params* p) {
   p->kcycle_tol = 0.1;
   p->tensor_cores = 2;
   p->graphs = 1;
+  p->autotune = 0;
   return MGMLMC_OK;
 }
 
@@ -192,6 +193,7 @@ int mg_setup(mgmlmc_ctx* ctx, const double* U, int L, double m0, const mg_params
     else
       mg_params_default(&h->prm);
     build_hierarchy(ctx, h.get(), (const double2*)U);
+    if (h->prm.autotune) autotune(h.get(), {8, 16, 32, 64, 128, 256}, false);
     *out = h.release();
   });
 }
@@ -266,6 +268,33 @@ int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x
     }
     h->prm.tensor_cores = saved;
   });
+}
+
+int mg_autotune(mgmlmc_ctx* ctx, mgmlmc_hier* h, const int* nrhs_list, int count, int force) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && nrhs_list && count > 0, "null pointer or empty list");
+    h->ctx = ctx;
+    std::vector<int> v(nrhs_list, nrhs_list + count);
+    for (int n : v) MG_CHECK_ARG(n >= 1, "batch sizes must be positive");
+    autotune(h, v, force != 0);
+  });
+}
+
+int mgmlmc_tune_report(char* buf, int64_t len) {
+  if (!buf || len <= 0) return MGMLMC_ERR_INVALID_ARG;
+  const std::string t = tune_table_text();
+  if ((int64_t)t.size() >= len) return MGMLMC_ERR_INVALID_ARG;
+  std::memcpy(buf, t.c_str(), t.size() + 1);
+  return MGMLMC_OK;
+}
+
+int mgmlmc_tune_set(int kind, int side, int bucket, int format, int variant) {
+  if (kind < 0 || kind > 2 || side < 1 || bucket < 8 || bucket > 256 || (bucket & (bucket - 1)) || format < 0 ||
+      format > 1 || variant < 0 || variant > 15)
+    return MGMLMC_ERR_INVALID_ARG;
+  if (kind == TUNE_WILSON32 && variant != 1 && variant != 2 && variant != 4) return MGMLMC_ERR_INVALID_ARG;
+  tune_store(kind, side, bucket, format, variant, 0.f);
+  return MGMLMC_OK;
 }
 
 int mg_tc_status(mgmlmc_ctx* ctx, mgmlmc_hier* h) {

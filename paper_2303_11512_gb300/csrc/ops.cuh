@@ -169,6 +169,15 @@ void tc_residual_after_sap(cudaStream_t st, const void* Wst, int bf, int Ls, con
 void tc_sap_half(cudaStream_t st, const void* Wst, const void* Winv, int bf, int Ls, const float2* f, float2* x,
                  float2* res, int color, int nrhs, const int* active, int* err);
 
+// ---------------------------------------------------------------- launch-shape tuning table (tune.cu)
+enum { TUNE_WILSON32 = 0, TUNE_TC0 = 1, TUNE_TC1 = 2 };
+int tune_bucket(int nrhs);  // batch bucket: the power of two >= nrhs in 8..256
+// variant of (kernel kind, lattice side, bucket of nrhs, weight format) or dflt when the table has none
+int tune_lookup(int kind, int shape, int nrhs, int fmt, int dflt);
+void tune_store(int kind, int shape, int bucket, int fmt, int variant, float us);
+bool tune_known(int kind, int shape, int bucket, int fmt);
+std::string tune_table_text();  // lines "device kind side bucket fmt variant microseconds"
+
 // ---------------------------------------------------------------- misc
 void fill_int(cudaStream_t st, int* p, int v, int n);
 

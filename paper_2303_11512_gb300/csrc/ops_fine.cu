@@ -106,43 +106,64 @@ __device__ __forceinline__ void wilson_site(const typename CT<R>::T* __restrict_
   }
 }
 
-template <typename R, bool RES>
+// One thread per site and RPT right-hand sides (blockIdx.y * RPT + j): the RPT sites' neighbour loads are
+// independent, so each thread keeps RPT times as many loads in flight (the tuner picks RPT per batch size).
+template <typename R, bool RES, int RPT>
 __global__ void __launch_bounds__(256) k_wilson(const typename CT<R>::T* __restrict__ lk, R diag, int L,
                                                 const typename CT<R>::T* __restrict__ x,
                                                 typename CT<R>::T* __restrict__ y,
                                                 const typename CT<R>::T* __restrict__ b,
-                                                const int* __restrict__ active) {
+                                                const int* __restrict__ active, int nrhs) {
   typedef typename CT<R>::T C;
-  const int rhs = blockIdx.y;
-  if (active && !active[rhs]) return;
   const int V = L * L;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
-  const size_t off = (size_t)rhs * 2 * V;
-  C o0, o1;
-  wilson_site<R>(lk, diag, L, x + off, s, o0, o1);
-  if (RES) {
-    C b0, b1;
-    ld_sp(b + off, s, b0, b1);
-    o0 = csub(b0, o0);
-    o1 = csub(b1, o1);
+  C o0[RPT], o1[RPT];
+  bool on[RPT];
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) {
+    const int rhs = blockIdx.y * RPT + j;
+    on[j] = rhs < nrhs && !(active && !active[rhs]);
+    if (on[j]) wilson_site<R>(lk, diag, L, x + (size_t)rhs * 2 * V, s, o0[j], o1[j]);
   }
-  st_sp(y + off, s, o0, o1);
+#pragma unroll
+  for (int j = 0; j < RPT; ++j) {
+    if (!on[j]) continue;
+    const size_t off = (size_t)(blockIdx.y * RPT + j) * 2 * V;
+    if (RES) {
+      C b0, b1;
+      ld_sp(b + off, s, b0, b1);
+      o0[j] = csub(b0, o0[j]);
+      o1[j] = csub(b1, o1[j]);
+    }
+    st_sp(y + off, s, o0[j], o1[j]);
+  }
 }
 
 template <typename R>
 void wilson_apply(cudaStream_t st, const typename CT<R>::T* links, R diag, int L, const typename CT<R>::T* x,
                   typename CT<R>::T* y, const typename CT<R>::T* b, int nrhs, const int* active) {
   if (nrhs <= 0) return;
-  dim3 grid(cdiv((long)L * L, 256), nrhs);
+  const int rpt = sizeof(R) == 4 ? tune_lookup(TUNE_WILSON32, L, nrhs, 0, 1) : 1;
+  dim3 grid(cdiv((long)L * L, 256), cdiv(nrhs, rpt));
   // algorithmic traffic: x read + y written once per site and rhs (+ b), links once per launch
   const double V = (double)L * L, sp = 2.0 * sizeof(typename CT<R>::T), ar = act_rhs(nrhs);
   const double bytes = ar * V * sp * (b ? 3 : 2) + V * sp;
   const double flops = ar * V * (b ? 56.0 : 52.0);
-  if (b)
-    MG_LAUNCH_W(bytes, flops, (k_wilson<R, true>), grid, 256, 0, st, links, diag, L, x, y, b, active);
+#define MG_WILSON_LAUNCH(RPT_)                                                                                  \
+  do {                                                                                                          \
+    if (b)                                                                                                      \
+      MG_LAUNCH_W(bytes, flops, (k_wilson<R, true, RPT_>), grid, 256, 0, st, links, diag, L, x, y, b, active, nrhs); \
+    else                                                                                                        \
+      MG_LAUNCH_W(bytes, flops, (k_wilson<R, false, RPT_>), grid, 256, 0, st, links, diag, L, x, y, b, active, nrhs); \
+  } while (0)
+  if (rpt == 4)
+    MG_WILSON_LAUNCH(4);
+  else if (rpt == 2)
+    MG_WILSON_LAUNCH(2);
   else
-    MG_LAUNCH_W(bytes, flops, (k_wilson<R, false>), grid, 256, 0, st, links, diag, L, x, y, b, active);
+    MG_WILSON_LAUNCH(1);
+#undef MG_WILSON_LAUNCH
 }
 template void wilson_apply<float>(cudaStream_t, const float2*, float, int, const float2*, float2*, const float2*,
                                   int, const int*);

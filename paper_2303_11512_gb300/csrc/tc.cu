@@ -222,17 +222,18 @@ constexpr int TC_NACC = 4;       // TMEM accumulators in flight
 // Shared-memory layout of one pipeline stage (every tile base 1024-byte aligned):
 //   TF32: KC FP32 vector slabs (vrows rows x 128 B, the MMA operand), KC weight tiles (NW rows x 128 B);
 //   BF16: KC FP32 staging slabs (vrows x 128 B, TMA), KC BF16 vector tiles (vt rows x 64 B), KC weight tiles
-//         (NW rows x 64 B); vt = 64 in MODE 0 (the MMA reads M = 64 rows), vrows in MODE 1.
-// In MODE 0 the MMA reads 64 A rows from a vector tile of `vrows` rows (TF32) or from a 64-row BF16 tile; rows
+//         (NW rows x 64 B); vt = mm in MODE 0 (the MMA reads M = mm rows), vrows in MODE 1.
+// In MODE 0 the MMA reads mm A rows from a vector tile of `vrows` rows (TF32) or from an mm-row BF16 tile; rows
 // past the converted/loaded ones only feed accumulator rows that are never stored.
-__host__ __device__ constexpr int tc_vt(int MODE, int vrows) { return MODE == 0 ? 64 : vrows; }
-__host__ __device__ constexpr int tc_stage_bytes(int MODE, int BF, int KC, int NW, int vrows) {
-  return BF ? KC * (vrows * 128 + tc_vt(MODE, vrows) * 64 + NW * 64) : KC * (vrows + NW) * 128;
+__host__ __device__ constexpr int tc_vt(int MODE, int vrows, int mm) { return MODE == 0 ? mm : vrows; }
+__host__ __device__ constexpr int tc_stage_bytes(int MODE, int BF, int KC, int NW, int vrows, int mm) {
+  return BF ? KC * (vrows * 128 + tc_vt(MODE, vrows, mm) * 64 + NW * 64) : KC * (vrows + NW) * 128;
 }
 
 // items: MODE 0 with bmode = 0: every site; bmode = 1: the 4 sites of every colour-`color` 2x2 block.
 //        MODE 1: every colour-`color` 2x2 block.
-// vrows: rows of a vector slab (MODE 0: rhs of the 64-rhs tile rounded up to 8; MODE 1: up to 16, the MMA N).
+// vrows: rows of a vector slab (MODE 0: rhs of the mm-rhs tile rounded up to 8; MODE 1: up to 16, the MMA N);
+// mm: MMA M of MODE 0 (64 or 128, also the rhs covered by one blockIdx.y; a tuned launch variant).
 // Warp-specialised pipeline: the producers keep up to `stages` items in flight in shared memory (full/empty
 // mbarriers), the expander/converter warps complete each stage (xfull), the MMA thread rotates over TC_NACC
 // TMEM accumulators (tmem_full/tmem_empty mbarriers), the epilogue warps drain one accumulator while the next
@@ -240,14 +241,14 @@ __host__ __device__ constexpr int tc_stage_bytes(int MODE, int BF, int KC, int N
 template <int MODE, int BF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc(const __grid_constant__ CUtensorMap amap, const void* __restrict__ Wv, float* __restrict__ out,
-         const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int vrows, int stages,
-         const int* __restrict__ active, int* err) {
+         const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int vrows, int mm,
+         int stages, const int* __restrict__ active, int* err) {
   typedef TcCfg<MODE> CF;
   constexpr int KC = CF::KC, NW = CF::NW;
-  constexpr int MM = MODE == 0 ? 64 : TC_M;       // MMA M
+  const int MM = MODE == 0 ? mm : TC_M;           // MMA M
   constexpr int WROW = BF ? 64 : 128;             // bytes of one weight / operand row
   const int acc_cols = MODE == 0 ? NW : vrows;    // TMEM columns of one accumulator
-  const int vt = tc_vt(MODE, vrows);
+  const int vt = tc_vt(MODE, vrows, MM);
   const uint32_t idesc = MODE == 0 ? (BF ? idesc_bf16(MM, NW) : idesc_tf32(MM, NW))
                                    : (BF ? idesc_bf16(MM, vrows) : idesc_tf32(MM, vrows));
   uint32_t ncol = 32;
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   if (s_skip) return;
   const long ncf = (long)Ls * Ls * TC_CHUNK;  // floats per rhs row
-  const int sbytes = tc_stage_bytes(MODE, BF, KC, NW, vrows);
+  const int sbytes = tc_stage_bytes(MODE, BF, KC, NW, vrows, MM);
   const uint32_t chunk_tx = (uint32_t)(vrows * 128 + (NW / 2) * WROW);  // one vector slab + one stored weight half
   // staged FP32 slab, MMA vector operand and weight tile of chunk kc in stage st
   auto sS = [&](int st, int kc) { return base + st * sbytes + kc * vrows * 128; };
@@ -437,13 +438,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (MODE == 0) {
     // ---------------- epilogue (rows = rhs): warp w owns TMEM lane quarter w % 4 and the items of parity
-    // (w - first epilogue warp) / 4.  With M = 64 accumulator row r sits in lane 32 (r / 16) + r % 16, so
-    // lanes 16..31 of each quarter are unused.
+    // (w - first epilogue warp) / 4.  With M = 128 accumulator row r sits in lane r; with M = 64 in lane
+    // 32 (r / 16) + r % 16, so lanes 16..31 of each quarter are unused.
     const int q = warp & 3, par = (warp - TC_EPI_WARP0) >> 2;
-    const int row = q * 16 + lane;
+    const int qrows = MM == 128 ? 32 : 16;
+    const int row = q * qrows + lane;
     const int rhs = rhs0 + row;
-    const bool live = lane < 16 && rhs < nrhs && !(active && !active[rhs]);
-    const bool quarter_live = rhs0 + q * 16 < nrhs;  // warp-uniform
+    const bool live = lane < qrows && rhs < nrhs && !(active && !active[rhs]);
+    const bool quarter_live = rhs0 + q * qrows < nrhs;  // warp-uniform
     // with bvec the output is b - D x; the work of an item is split in steps of 8 complex outputs (half a site
     // slab); the additive input of step t + RD is fetched at step t.
     const float* in = bvec;
@@ -612,8 +614,10 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-EncodeTiledFn encode_fn() {
+EncodeTiledFn encode_fn() {  // looked up once, thread-safe (several host threads may drive the library)
+  static std::mutex mu;
   static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -652,11 +656,16 @@ void launch_tc(cudaStream_t st, const float2* vin, const void* W, float* out, co
   constexpr int SMEM_BUDGET = 225 * 1024;  // dynamic shared memory per CTA (one CTA per SM)
   auto* k_tc_kernel = &k_tc<MODE, BF>;
   ensure_max_smem((const void*)k_tc_kernel, SMEM_BUDGET);
-  const int tile = MODE == 0 ? 64 : TC_M;
-  const int vrows = MODE == 0 ? std::min(64, ((nrhs + 7) / 8) * 8) : std::min(TC_M, ((nrhs + 15) / 16) * 16);
+  // tuned variant: MODE 0 bit 0 = MMA M 128 (else 64), bits 1.. = pipeline-depth cap (0 = as deep as fits);
+  // MODE 1: the depth cap
+  const int var = tune_lookup(MODE == 0 ? TUNE_TC0 : TUNE_TC1, Ls, nrhs, BF, 0);
+  const int mm = MODE == 0 ? ((var & 1) ? TC_M : 64) : TC_M;
+  const int cap = MODE == 0 ? (var >> 1) : var;
+  const int tile = mm;
+  const int vrows = MODE == 0 ? std::min(mm, ((nrhs + 7) / 8) * 8) : std::min(TC_M, ((nrhs + 15) / 16) * 16);
   const CUtensorMap m = make_map(vin, Ls * Ls, nrhs, vrows);
-  const int sbytes = tc_stage_bytes(MODE, BF, CF::KC, CF::NW, vrows);
-  const int stages = std::max(1, std::min(TC_MAX_STAGES, (SMEM_BUDGET - 1024) / sbytes));
+  const int sbytes = tc_stage_bytes(MODE, BF, CF::KC, CF::NW, vrows, mm);
+  const int stages = std::max(1, std::min(cap > 0 ? cap : TC_MAX_STAGES, (SMEM_BUDGET - 1024) / sbytes));
   const int sm = stages * sbytes + 1024;
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
@@ -665,7 +674,7 @@ void launch_tc(cudaStream_t st, const float2* vin, const void* W, float* out, co
   const int gx = std::max(1, std::min(nitems, (nsm + tiles - 1) / tiles));
   dim3 grid(gx, tiles);
   MG_LAUNCH_W(bytes, flops, k_tc_kernel, grid, TC_THREADS, sm, st, m, W, out, b, Ls, nitems, bmode, color, nrhs,
-              vrows, stages, active, err);
+              vrows, mm, stages, active, err);
 }
 
 template <int MODE>

@@ -27,3 +27,27 @@ def test_admission_largest_first_and_rejection():
     ok, no = ens.admit(f, free)
     assert [x.L for x in ok] == [512, 128, 64]
     assert [x.L for x in no] == [1024]
+
+
+def test_concurrent_groups_fit_memory_and_width():
+    f = [ens.Field(np.zeros((L, L, 2), complex), L, -0.05, "f%d" % i) for i, L in enumerate((512, 512, 256, 128, 128))]
+    m512, m256, m128 = ens.memory_estimate(512), ens.memory_estimate(256), ens.memory_estimate(128)
+    g = ens.group_fields(f, m512 + m256 + 1, 2)
+    assert [[x.name for x in grp] for grp in g] == [["f0"], ["f1", "f2"], ["f3", "f4"]]
+    for grp in g:
+        assert len(grp) <= 2 and sum(ens.memory_estimate(x.L) for x in grp) <= m512 + m256 + 1
+    assert [len(grp) for grp in ens.group_fields(f, 10 ** 15, 1)] == [1] * 5
+
+
+def test_tuning_table_round_trip():
+    pytest.importorskip("torch")
+    import __graft_entry__ as gentry
+    gentry.build()
+    from paper_2303_11512_gb300 import _lib, api
+    api.tune_set([dict(kind=1, side=32, bucket=64, format=0, variant=5)])
+    rows = [r for r in api.tune_table() if r["kind"] == 1 and r["side"] == 32 and r["bucket"] == 64]
+    assert rows and rows[0]["variant"] == 5
+    with pytest.raises(_lib.MgmlmcError):
+        api.tune_set([dict(kind=0, side=32, bucket=64, format=0, variant=3)])   # 3 rhs per thread: no such variant
+    with pytest.raises(_lib.MgmlmcError):
+        api.tune_set([dict(kind=1, side=32, bucket=48, format=0, variant=0)])   # not a bucket
