@@ -237,14 +237,44 @@ def profile_case(args):
             api.schwinger_apply(ctx, U, L, m0, x, y, api.FP32)
     else:
         h = api.mg_setup(ctx, U, L, m0, ntv=W["ntv"], bootstrap=args.profile_bootstrap,
-                         bootstrap_its=W["bootstrap_its"], pre_smooth=W["pre_smooth"], post_smooth=W["post_smooth"])
-        b = api.mgmlmc_rademacher(ctx, 1, 0, 0, 0, h.n[args.profile_level], args.profile_nrhs)
-        x = torch.empty_like(b)
-        st = api.fgmres_batched(ctx, h, args.profile_level, b, x, prec=api.MIXED, tol=1e-10)
-        print("iters", st["iters"], "relres", st["max_relres"])
+                         bootstrap_its=W["bootstrap_its"], pre_smooth=W["pre_smooth"], post_smooth=W["post_smooth"],
+                         tensor_cores=W["tensor_cores"])
+        lv = args.profile_level
+        if args.profile_case == "coarse":
+            # ten tensor-core stencil applications y = D_l x on level lv (no additive input, every rhs active)
+            prec = api.BF16 if W["tensor_cores"] == 1 else api.TF32
+            x = torch.randn((args.profile_nrhs, h.n[lv]), dtype=torch.complex64, device="cuda")
+            y = torch.empty_like(x)
+            for _ in range(10):
+                h.apply(lv, x, y, prec)
+            ns = h.side[lv] ** 2
+            wbytes = ns * 5 * 16 * 32 * (2 if W["tensor_cores"] == 1 else 4)
+            print("algorithmic bytes per launch", ns * 256 * args.profile_nrhs + wbytes, "sites", ns)
+        else:
+            b = api.mgmlmc_rademacher(ctx, 1, 0, 0, 0, h.n[lv], args.profile_nrhs)
+            x = torch.empty_like(b)
+            st = api.fgmres_batched(ctx, h, lv, b, x, prec=api.MIXED, tol=1e-10)
+            print("iters", st["iters"], "relres", st["max_relres"])
         h.close()
     torch.cuda.synchronize()
     ctx.close()
+    return 0
+
+
+def ensemble_record(args):
+    """Ensemble record: time to eps of every field (set-up included) and the whole-ensemble throughput."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_2303_11512_gb300 import ensemble
+    out = ensemble.run_c4(n=16, eps=args.eps, concurrency=args.ensemble, workload=WORKLOAD)
+    fields = [dict(name=r["name"], L=r["L"], m0=r["m0"], N=r["N"], solves=r["solves"],
+                   setup_s=round(r["setup_s"], 4), time_to_eps_s=round(r["time_s"], 4),
+                   rel_sigma=r["sigma"] / abs(complex(*r["tau"]))) for r in out["runs"]]
+    print(json.dumps({"metric": "ensemble_wall_time_to_eps", "value": out["wall_s"], "unit": "s",
+                      "higher_is_better": False, "eps": args.eps, "concurrency": args.ensemble,
+                      "fields_per_s": out["fields_per_s"], "solves_per_s": out["solves_per_s"],
+                      "admitted": len(out["runs"]), "rejected": out["rejected"], "groups": out["groups"],
+                      "data": "synthetic quenched U(1), beta 3", "fields": fields}), flush=True)
     return 0
 
 
@@ -263,19 +293,25 @@ def main():
     ap.add_argument("--timing-filter", default="")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                     help="coarse-level tensor-core operands: 1 BF16, 2 TF32, 0 CUDA cores (default: the workload's)")
-    ap.add_argument("--profile-case", choices=["solve", "stencil"], default=None,
+    ap.add_argument("--profile-case", choices=["solve", "stencil", "coarse"], default=None,
                     help="run one small case for an ncu capture instead of the benchmark: 'solve' = one mixed "
                          "FGMRES solve on --profile-level with --profile-nrhs rhs on the workload hierarchy, "
-                         "'stencil' = ten FP32 fine-stencil applications to --profile-nrhs vectors")
+                         "'stencil' = ten FP32 fine-stencil applications to --profile-nrhs vectors, 'coarse' = ten "
+                         "tensor-core stencil applications on --profile-level")
     ap.add_argument("--profile-level", type=int, default=1)
     ap.add_argument("--profile-nrhs", type=int, default=64)
     ap.add_argument("--profile-bootstrap", type=int, default=WORKLOAD["bootstrap"],
                     help="bootstrap rounds of the profiled hierarchy (0: no tensor-core launches before the solve)")
+    ap.add_argument("--ensemble", type=int, default=0, metavar="CONCURRENCY",
+                    help="instead of the benchmark, run the 16-field ensemble (L 128..1024, three masses) with up "
+                         "to CONCURRENCY fields at a time and print its record as one JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_case:
         return profile_case(args)
+    if args.ensemble:
+        return ensemble_record(args)
 
     import numpy as np
     import torch
@@ -451,7 +487,9 @@ def main():
             stencil_fp32=stencil,
             estimate=dict(tau=[r["tau"].real, r["tau"].imag], sigma=r["sigma"], rel_sigma=r["sigma"] / abs(r["tau"]),
                           N=r["N"], computed=r["computed"], solves=r["solves"], inner_iters=r["inner_iters"]),
-            kernels=kernels)
+            kernels=kernels,
+            tuning=[[api.TUNE_KINDS.get(e["kind"], e["kind"]), e["side"], e["bucket"], e["format"], e["variant"],
+                     round(e["us"], 1)] for e in api.tune_table()])
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

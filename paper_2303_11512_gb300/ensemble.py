@@ -178,6 +178,21 @@ def ensemble_fields(Ls=(128, 256, 512, 1024), masses=(-0.02, -0.05, -0.08), n=16
             for i, ((L, _, _), U) in enumerate(zip(specs, links))]
 
 
+def run_c4(n: int = 16, eps: float = 1e-3, concurrency: int = 2, workload: dict | None = None) -> dict:
+    """The 16-field ensemble (L 128..1024, m0 in {-0.02, -0.05, -0.08}, beta 3) with the benchmark workload's
+    hierarchy and estimator parameters, autotuned launch variants and batches of up to 64 rhs."""
+    W = dict(workload or {})
+    fields = ensemble_fields(n=n)
+    mg_params = dict(ntv=W.get("ntv", 8), bootstrap=W.get("bootstrap", 2), bootstrap_its=W.get("bootstrap_its", 6),
+                     pre_smooth=W.get("pre_smooth", 2), post_smooth=W.get("post_smooth", 2),
+                     tensor_cores=W.get("tensor_cores", 2), autotune=1)
+    est_params = dict(d=W.get("d", 32), k=W.get("k", 2), nrhs_max=64, nrhs_first=W.get("nrhs_first", 8), cost_mode=1)
+    out = run_ensemble(fields, eps=eps, mg_params=mg_params, est_params=est_params, concurrency=concurrency)
+    out["runs"] = [dict(r, tau=[r["tau"].real, r["tau"].imag]) for r in sorted(out["runs"], key=lambda r: r["name"])]
+    out["concurrency"] = concurrency
+    return out
+
+
 def main():
     import argparse
     import json
@@ -192,24 +207,15 @@ def main():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
         sys.path.insert(0, root)
-    fields = ensemble_fields(n=a.n)
     import __graft_entry__ as g
     g.build()
     import bench
-    W = bench.WORKLOAD
-    mg_params = dict(ntv=W["ntv"], bootstrap=W["bootstrap"], bootstrap_its=W["bootstrap_its"],
-                     pre_smooth=W["pre_smooth"], post_smooth=W["post_smooth"], tensor_cores=W["tensor_cores"],
-                     autotune=1)
-    est_params = dict(d=W["d"], k=W["k"], nrhs_max=64, nrhs_first=W["nrhs_first"], cost_mode=1)
-    out = run_ensemble(fields, eps=a.eps, mg_params=mg_params, est_params=est_params, concurrency=a.concurrency)
-    for r in sorted(out["runs"], key=lambda r: r["name"]):
-        r = dict(r, tau=[r["tau"].real, r["tau"].imag])
+    out = run_c4(n=a.n, eps=a.eps, concurrency=a.concurrency, workload=bench.WORKLOAD)
+    for r in out["runs"]:
         print(json.dumps(r), flush=True)
-    summary = {k: v for k, v in out.items() if k != "runs"}
-    print(json.dumps(summary), flush=True)
+    print(json.dumps({k: v for k, v in out.items() if k != "runs"}), flush=True)
     if a.out:
-        json.dump(dict(out, runs=[dict(r, tau=[r["tau"].real, r["tau"].imag]) for r in out["runs"]]),
-                  open(a.out, "w"), indent=1)
+        json.dump(out, open(a.out, "w"), indent=1)
 
 
 if __name__ == "__main__":
