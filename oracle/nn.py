@@ -25,6 +25,18 @@ Definition
                 y = W u  ->  g_W += g_y conj(u),  g_u += conj(W) g_y.
 Offsets are enumerated d = 3 * (dt + 1) + (dx + 1).
 Arrays: fields a[nrhs, L*L, C] (site = t * L + x), links U[t, x, mu].
+
+Tensor-core number format (tc=True), the arithmetic of the library's tcgen05 layers with BF16 operands:
+  forward       every layer input a (the residual r included) is rounded to bfloat16 (real and imaginary
+                parts) before the channel mixing; the mixing sums, transports, activation and the output
+                stay exact here (FP32 in the library).
+  backward      the gradient w.r.t. each layer's pre-activation, gz, is rounded to bfloat16 before it enters
+                the weight gradient and the input gradient; the transported inputs u = T_d a are rounded to
+                bfloat16 for the weight gradient.  The rounding steps are passed through unchanged in the
+                derivative (the gradient is that of the same formulas without them).
+  The library's input gradient uses the identity conj(T_d(y - d)) = T_(-d)(y) (the reversed path), so it
+  is the same gathered mixing as the forward with the weights conj(W[-d])^T; that identity is pinned by the
+  tests of this module.
 """
 from __future__ import annotations
 
@@ -44,6 +56,11 @@ def bf16_round(a: np.ndarray) -> np.ndarray:
 
 def round_weights(W: np.ndarray) -> np.ndarray:
     return bf16_round(W.real) + 1j * bf16_round(W.imag)
+
+
+def bf16_complex(a: np.ndarray) -> np.ndarray:
+    """Real and imaginary parts rounded to the nearest bfloat16."""
+    return bf16_round(np.real(a)) + 1j * bf16_round(np.imag(a))
 
 
 def transporters(U: np.ndarray) -> np.ndarray:
@@ -79,9 +96,11 @@ def neighbour_index(L: int) -> np.ndarray:
 
 
 class Net:
-    def __init__(self, U, weights, biases, round_bf16=True):
-        """weights: list of complex arrays [9, c_out, c_in]; biases: list (len = layers - 1) of real [c_out]."""
+    def __init__(self, U, weights, biases, round_bf16=True, tc=False):
+        """weights: list of complex arrays [9, c_out, c_in]; biases: list (len = layers - 1) of real [c_out];
+        tc: the tensor-core number format (module docstring)."""
         self.L = U.shape[0]
+        self.tc = tc
         self.T = transporters(U)
         self.nb = neighbour_index(self.L)
         self.W = [round_weights(w) if round_bf16 else np.asarray(w, complex) for w in weights]
@@ -96,6 +115,8 @@ class Net:
         self.tape = []
         a = r
         for l, W in enumerate(self.W):
+            if self.tc:
+                a = bf16_complex(a)
             u = self._gather(a)
             z = np.einsum("dkc,rxdc->rxk", W, u)
             if l < len(self.W) - 1:
@@ -133,6 +154,9 @@ class Net:
                 gb[l] = np.sum(np.where(on, rad, 0), axis=(0, 1))
             else:
                 gz = g
+            if self.tc:
+                gz = bf16_complex(gz)
+                u = bf16_complex(u)
             gW[l] = np.einsum("rxk,rxdc->dkc", gz, np.conj(u))
             gu = np.einsum("dkc,rxk->rxdc", np.conj(self.W[l]), gz)
             # u = T_d(x) a(x + d): g_a(y) += conj(T_d(x)) g_u(x, d) for y = x + d

@@ -36,6 +36,7 @@ PHASE_STOCH = 0     # stochastic samples zeta_s (Algorithm 2, stochastic part)
 PHASE_SKETCH = 1    # sketch vectors S_l (Algorithm 2, deflation part)
 PHASE_TESTVEC = 2   # multigrid set-up test vectors
 PHASE_HUTCH = 3     # plain Hutchinson samples (Algorithm 1)
+PHASE_HARVEST = 5   # right-hand sides of the learned preconditioner's training pairs
 
 
 def mix64(z):
