@@ -79,7 +79,9 @@ enum mgmlmc_weight { /* the matrix whose trace is estimated (Section 1: traces "
 };
 
 enum mgmlmc_phase { /* streams of the counter-based Rademacher generator */
-  MGMLMC_PHASE_STOCH = 0, MGMLMC_PHASE_SKETCH = 1, MGMLMC_PHASE_TESTVEC = 2, MGMLMC_PHASE_HUTCH = 3
+  MGMLMC_PHASE_STOCH = 0, MGMLMC_PHASE_SKETCH = 1, MGMLMC_PHASE_TESTVEC = 2, MGMLMC_PHASE_HUTCH = 3,
+  MGMLMC_PHASE_DEFL = 4,   /* start block of the deflation subspace iteration */
+  MGMLMC_PHASE_HARVEST = 5 /* right-hand sides of the learned preconditioner's training pairs */
 };
 
 #define MGMLMC_MAX_LEVELS 8
@@ -371,6 +373,31 @@ int nn_loss_grad(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, const void* e, i
 int nn_train_step(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, const void* e, int nrhs, double lr, double* loss);
 /* use nn in the fine-level preconditioner of h (precond = 2); NULL detaches. nn must outlive the attachment. */
 int mg_attach_nn(mgmlmc_ctx* ctx, mgmlmc_hier* h, mgmlmc_nn* nn);
+/* Number format of the layers.  0: FP32 CUDA-core kernels (layer inputs FP32).  1 (the default where L is a
+ * multiple of 16): tcgen05 tensor-core kernels with BF16 operands and FP32 accumulation: every layer input
+ * (the residual included) is rounded to bfloat16, the channel mixing of each of the 9 offsets is one MMA whose
+ * FP32 result is multiplied by the transporter in the epilogue (T_d(x) is a scalar per site and offset, so it
+ * commutes with the mixing); in the backward pass the pre-activation gradients and, for the weight gradient,
+ * the transported inputs T_d a are rounded to bfloat16 as well.  Returns MGMLMC_ERR_INVALID_ARG for format 1
+ * on other lattices.  A tensor-core layer whose bounded wait expires makes nn_forward / nn_loss_grad /
+ * nn_train_step return MGMLMC_ERR_TIMEOUT (inside FGMRES the hierarchy's tensor-core status reports it). */
+int nn_set_format(mgmlmc_ctx* ctx, mgmlmc_nn* nn, int format);
+int nn_get_format(const mgmlmc_nn* nn);
+/* Rebinds nn to another gauge field U (device complex128 [L][L][2], any even L >= 4; a multiple of 16 in
+ * format 1): the transporters are recomputed, the weights and the Adam state kept, so one network trains on
+ * pairs from several lattices and serves any of them (the layers are local and gauge covariant).  Detach it
+ * from hierarchies of the old lattice first. */
+int nn_set_field(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const double* U, int L);
+/* Training pairs from the method's own fine-level solves (the learned correction's data): for the Rademacher
+ * right-hand sides zeta_s of stream (seed, level 0, MGMLMC_PHASE_HARVEST, s), s = sample0 .. sample0+count-1,
+ * with v = V(zeta) one FP32 V-cycle of h, r = zeta - D v and x = D^{-1} zeta by FP32 FGMRES (V-cycle
+ * preconditioned) to relative residual tol:
+ *   R[s] = r / ||r||,   E[s] = (x - v) / ||r||     (so D E = R up to the solver tolerance).
+ * R, E: device complex64 [count][n_0], caller-owned; the call blocks until they are written.  Errors:
+ * MGMLMC_ERR_INVALID_ARG (null / aliased pointers, count < 0, tol outside (0, 1)), MGMLMC_ERR_NOT_CONVERGED is
+ * not raised (a solve that stops at the iteration limit still yields a pair), CUDA errors as elsewhere. */
+int nn_harvest_pairs(mgmlmc_ctx* ctx, mgmlmc_hier* h, uint64_t seed, int64_t sample0, int count, double tol,
+                     void* R, void* E);
 
 /* ---- Algorithm 2 end to end --------------------------------------------- */
 

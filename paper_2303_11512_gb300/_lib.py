@@ -121,6 +121,10 @@ SIGNATURES = {
     "nn_forward": (ip, [vp, vp, vp, vp, ip]),
     "nn_loss_grad": (ip, [vp, vp, vp, vp, ip, dp, vp]),
     "nn_train_step": (ip, [vp, vp, vp, vp, ip, C.c_double, dp]),
+    "nn_set_format": (ip, [vp, vp, ip]),
+    "nn_get_format": (ip, [vp]),
+    "nn_set_field": (ip, [vp, vp, vp, ip]),
+    "nn_harvest_pairs": (ip, [vp, vp, C.c_uint64, C.c_int64, ip, C.c_double, vp, vp]),
     "mg_attach_nn": (ip, [vp, vp, vp]),
     "est_params_default": (ip, [C.POINTER(EstParams)]),
     "trace_estimate": (ip, [vp, vp, C.POINTER(EstParams), C.POINTER(EstResult)]),

@@ -335,13 +335,30 @@ def hutchpp_project(ctx: Context, sketch: Sketch | None, zeta: torch.Tensor, y: 
 class Net:
     """Learned gauge-covariant correction M ~ D^{-1} (see include/mgmlmc.h, nn_*)."""
 
-    def __init__(self, ctx: Context, U: torch.Tensor, L: int, layers: int = 4, channels: int = 16, seed: int = 0):
+    def __init__(self, ctx: Context, U: torch.Tensor, L: int, layers: int = 4, channels: int = 16, seed: int = 0,
+                 tensor_cores: bool | None = None):
+        """tensor_cores: True = BF16 tcgen05 layers, False = FP32 CUDA-core layers, None = the library's
+        default (tensor cores where L is a multiple of 16)."""
         self.ctx, self.L = ctx, L
         h = C.c_void_p()
         check(_lib.load().nn_create(ctx.ptr, _ptr(U, torch.complex128), L, layers, channels, seed, C.byref(h)),
               ctx.ptr)
         self.ptr = h
         self.nparams = int(_lib.load().nn_num_params(h))
+        if tensor_cores is not None:
+            self.set_format(1 if tensor_cores else 0)
+
+    def set_format(self, fmt: int):
+        check(_lib.load().nn_set_format(self.ctx.ptr, self.ptr, fmt), self.ctx.ptr)
+
+    @property
+    def format(self) -> int:
+        return int(_lib.load().nn_get_format(self.ptr))
+
+    def set_field(self, U: torch.Tensor, L: int):
+        """Rebind to another gauge field (weights and Adam state kept)."""
+        check(_lib.load().nn_set_field(self.ctx.ptr, self.ptr, _ptr(U, torch.complex128), L), self.ctx.ptr)
+        self.L = L
 
     def set_params(self, p: np.ndarray):
         p = np.ascontiguousarray(p, dtype=np.float32)
@@ -385,6 +402,18 @@ class Net:
             self.close()
         except Exception:
             pass
+
+
+def nn_harvest_pairs(ctx: Context, h: "Hierarchy", count: int, seed: int = 3, sample0: int = 0,
+                     tol: float = 1e-6):
+    """Training pairs (R, E) [count, n_0] complex64 from the hierarchy's own V-cycle and FP32 solves
+    (R = (zeta - D V zeta)/|.|, E = (D^{-1} zeta - V zeta)/|.|; see nn_harvest_pairs in the header)."""
+    n = h.n[0]
+    R = torch.empty((count, n), dtype=torch.complex64, device="cuda")
+    E = torch.empty_like(R)
+    check(_lib.load().nn_harvest_pairs(ctx.ptr, h.ptr, seed, sample0, count, tol, _ptr(R, torch.complex64),
+                                       _ptr(E, torch.complex64)), ctx.ptr)
+    return R, E
 
 
 def pack_params(W, b) -> np.ndarray:

@@ -639,6 +639,61 @@ int nn_forward(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, void* y, int nrhs)
     MG_CHECK_ARG(nn && r && y && r != y, "null or aliased pointer");
     if (nrhs <= 0) return;
     mg::nn_forward(&nn->net, (const float2*)r, (float2*)y, nrhs, false, ctx->stream);
+    if (nn->net.tc) mg::nn_check(&nn->net, ctx->stream);
+  });
+}
+
+int nn_set_format(mgmlmc_ctx* ctx, mgmlmc_nn* nn, int format) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(nn, "null pointer");
+    MG_CHECK_ARG(format == 0 || format == 1, "format: 0 FP32 CUDA cores, 1 BF16 tensor cores");
+    MG_CHECK_ARG(format == 0 || mg::nn_tc_supported(nn->net.L), "tensor-core layers need L a multiple of 16");
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    nn->net.tc = format;
+  });
+}
+
+int nn_get_format(const mgmlmc_nn* nn) { return nn ? nn->net.tc : MGMLMC_ERR_INVALID_ARG; }
+
+int nn_set_field(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const double* U, int L) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(nn && U, "null pointer");
+    mg::nn_bind_field(&nn->net, (const double2*)U, L, ctx->stream);
+  });
+}
+
+int nn_harvest_pairs(mgmlmc_ctx* ctx, mgmlmc_hier* h, uint64_t seed, int64_t sample0, int count, double tol,
+                     void* R, void* E) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(h && R && E && R != E, "null or aliased pointer");
+    MG_CHECK_ARG(count >= 0 && sample0 >= 0, "negative count or sample index");
+    MG_CHECK_ARG(tol > 0 && tol < 1, "tol must lie in (0, 1)");
+    h->ctx = ctx;
+    if (count == 0) return;
+    cudaStream_t st = ctx->stream;
+    const long n = h->lv[0].n;
+    const int B = std::min(count, 64);
+    DBuf z64(sizeof(double2) * n * B, st), z(sizeof(float2) * n * B, st), v(sizeof(float2) * n * B, st),
+        x(sizeof(float2) * n * B, st), nrm(sizeof(double) * B, st), red(reduce_work_bytes(n, B, 1), st);
+    solve_params sp;
+    solve_params_default(&sp);
+    sp.prec = MGMLMC_FP32;
+    sp.tol = tol;
+    sp.precond = 1;
+    for (int s0 = 0; s0 < count; s0 += B) {
+      const int nb = std::min(B, count - s0);
+      float2* Rb = (float2*)R + (size_t)s0 * n;
+      float2* Eb = (float2*)E + (size_t)s0 * n;
+      rademacher_fill(st, seed, 0, MGMLMC_PHASE_HARVEST, sample0 + s0, n, nb, z64.as<double2>());
+      vconvert<float2, double2>(st, z64.as<double2>(), z.as<float2>(), n, nb, nullptr, nullptr);
+      vcycle<float>(h, 0, z.as<float2>(), v.as<float2>(), nb, nullptr);           // v = V(zeta)
+      op_apply<float>(h, 0, v.as<float2>(), Rb, z.as<float2>(), nb, nullptr);    // r = zeta - D v
+      solve(h, 0, z.p, x.p, nb, sp);                                              // x = D^{-1} zeta (FP32, tol)
+      vnorm2<float2>(st, Rb, n, nb, nrm.as<double>(), red.p, nullptr);
+      sqrt_inplace(st, nrm.as<double>(), nb);
+      mg::nn_pair_finish(st, Rb, Eb, x.as<float2>(), v.as<float2>(), nrm.as<double>(), n, nb);
+    }
+    MG_CUDA(cudaStreamSynchronize(st));
   });
 }
 
@@ -647,6 +702,7 @@ int nn_loss_grad(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, const void* e, i
   return guarded(ctx, [&] {
     MG_CHECK_ARG(nn && r && e && loss && nrhs > 0, "null pointer or empty batch");
     *loss = mg::nn_backward(&nn->net, (const float2*)r, (const float2*)e, nrhs, ctx->stream, ctx->pinned);
+    if (nn->net.tc) mg::nn_check(&nn->net, ctx->stream);
     if (host_grad) {
       MG_CUDA(cudaMemcpyAsync(host_grad, nn->net.grad.p, sizeof(float) * nn->net.nparams, cudaMemcpyDeviceToHost,
                               ctx->stream));
@@ -659,6 +715,7 @@ int nn_train_step(mgmlmc_ctx* ctx, mgmlmc_nn* nn, const void* r, const void* e, 
   return guarded(ctx, [&] {
     MG_CHECK_ARG(nn && r && e && loss && nrhs > 0 && lr > 0, "bad arguments");
     *loss = mg::nn_backward(&nn->net, (const float2*)r, (const float2*)e, nrhs, ctx->stream, ctx->pinned);
+    if (nn->net.tc) mg::nn_check(&nn->net, ctx->stream);
     mg::nn_adam(&nn->net, lr, ctx->stream);
   });
 }

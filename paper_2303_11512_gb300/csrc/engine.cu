@@ -391,6 +391,7 @@ void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<
         vcycle_maybe_graph<R>(h, l, Vj, Zj, nrhs, s.iact);
         if constexpr (sizeof(R) == 4) {
           if (precond == 2 && l == 0 && h->nn) {  // learned correction: z += |t| M(t / |t|), t = v - D z
+            MG_CHECK_ARG(h->nn->L == h->L, "the attached network is bound to another lattice");
             C* tt = (C*)h->work("nn_t", l, sizeof(C) * n * nrhs);
             C* cc = (C*)h->work("nn_c", l, sizeof(C) * n * nrhs);
             double* tn = (double*)h->work("nn_n", l, sizeof(double) * nrhs);
@@ -398,8 +399,12 @@ void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<
             op_apply<R>(h, l, Zj, tt, Vj, nrhs, s.iact);
             vnorm2<C>(st, tt, n, nrhs, tn, red, s.iact);
             sqrt_inplace(st, tn, nrhs);
-            vscale_inv<C>(st, tn, tt, tt, n, nrhs, s.iact);
-            nn_forward(h->nn, tt, cc, nrhs, false, st);
+            if (h->nn->tc) {  // the tensor-core net scales while rounding its input to BF16
+              nn_tc_forward(h->nn, tt, tn, cc, nrhs, false, h->tc_err.as<int>(), st);
+            } else {
+              vscale_inv<C>(st, tn, tt, tt, n, nrhs, s.iact);
+              nn_forward(h->nn, tt, cc, nrhs, false, st);
+            }
             nn_add(st, Zj, cc, n, nrhs, tn);
           }
         }

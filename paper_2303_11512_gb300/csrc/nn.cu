@@ -330,8 +330,34 @@ void nn_init(NNet* net, const double2* U, int L, int layers, int channels, uint6
   MG_CUDA(cudaMemcpyAsync(net->params.p, p.data(), sizeof(float) * net->nparams, cudaMemcpyHostToDevice, st));
   MG_CUDA(cudaMemsetAsync(net->m.p, 0, sizeof(float) * net->nparams, st));
   MG_CUDA(cudaMemsetAsync(net->v.p, 0, sizeof(float) * net->nparams, st));
+  net->err.alloc(sizeof(int), st);
+  MG_CUDA(cudaMemsetAsync(net->err.p, 0, sizeof(int), st));
   MG_CUDA(cudaStreamSynchronize(st));
   net->step = 0;
+  net->tc = nn_tc_supported(L) ? 1 : 0;
+}
+
+void nn_check(NNet* net, cudaStream_t st) {
+  int flag = 0;
+  MG_CUDA(cudaMemcpyAsync(&flag, net->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+  if (flag) {
+    MG_CUDA(cudaMemsetAsync(net->err.p, 0, sizeof(int), st));
+    throw Error(MGMLMC_ERR_TIMEOUT, "tensor-core layer: a bounded wait expired (code " + std::to_string(flag) + ")");
+  }
+}
+
+void nn_bind_field(NNet* net, const double2* U, int L, cudaStream_t st) {
+  MG_CHECK_ARG(L >= 4 && L % 2 == 0, "L must be even and >= 4");
+  MG_CHECK_ARG(!net->tc || nn_tc_supported(L), "tensor-core layers need L a multiple of 16");
+  MG_CUDA(cudaStreamSynchronize(net->st));
+  net->L = L;
+  net->st = st;
+  net->T.alloc(sizeof(float2) * 9 * L * L, st);
+  MG_LAUNCH(k_nn_transport, cdiv(L * L, 128), 128, 0, st, U, L, net->T.as<float2>());
+  net->acts.clear();
+  net->zs.clear();
+  net->acts16.clear();
 }
 
 static void nn_round(NNet* net, cudaStream_t st) {
@@ -341,6 +367,7 @@ static void nn_round(NNet* net, cudaStream_t st) {
 
 // forward; with a tape (training) the inputs of every layer and hidden pre-activations are kept
 void nn_forward(NNet* net, const float2* r, float2* y, int nrhs, bool tape, cudaStream_t st) {
+  if (net->tc) return nn_tc_forward(net, r, nullptr, y, nrhs, tape, net->err.as<int>(), st);
   const int L = net->L, V = L * L;
   nn_round(net, st);
   const size_t fsz = (size_t)nrhs * V * 16;
@@ -402,6 +429,10 @@ double nn_backward(NNet* net, const float2* r, const float2* e, int nrhs, cudaSt
   for (int i = 0; i < nrhs; ++i) loss += hn[nrhs + i] / hn[i];
   loss /= nrhs;
   MG_LAUNCH(k_nn_scale, dim3(cdiv(n, 256), nrhs), 256, 0, st, g.as<float2>(), n, nrm.as<double>(), nrhs);
+  if (net->tc) {
+    nn_tc_backward(net, g.as<float2>(), nrhs, net->err.as<int>(), st);
+    return loss;
+  }
   // walk the layers backwards; g holds the gradient w.r.t. the current layer's output
   DBuf gprev;
   for (int l = net->layers - 1; l >= 0; --l) {

@@ -1,13 +1,18 @@
 """Training and evaluation of the learned gauge-covariant correction (C ABI nn_*).
 
-    python -m paper_2303_11512_gb300.learned --L-train 128 --L-eval 256 --pairs 4096 --steps 1500
+    python -m paper_2303_11512_gb300.learned                       # 20k pairs from L=128/256, eval L=256/512
+    python -m paper_2303_11512_gb300.learned --pairs 4096 --steps 600 --eval 256:3
 
-Pairs (r, e) come from the library's own V-cycle and solves on the training field: r = zeta - D V(zeta),
-e = D^{-1} zeta - V(zeta), both divided by ||r|| (the net is applied to unit-norm residuals).  The net is
-trained with the library's forward/backward/Adam kernels, then its weights are loaded into a net built on
-the evaluation field (the layers are local and gauge covariant, so one set of weights serves any lattice) and
-FGMRES to the FP64 true residual 1e-10 is timed with the V-cycle alone (precond 1) and with V-cycle + net
-(precond 2).  Prints one JSON line.
+Pairs (R, E) come from the library's own V-cycle and solves (nn_harvest_pairs): R = (zeta - D V zeta)/s,
+E = (D^{-1} zeta - V zeta)/s, s = |zeta - D V zeta|.  One network is trained on the pairs of every training field
+(nn_set_field rebinds it to a field's transporters, keeping weights and Adam state; the layers are local and
+gauge covariant, so one set of weights serves any lattice) with the library's forward/backward/Adam kernels
+(tensor-core layers by default).  Then, on every evaluation field, FGMRES to the FP64 true residual 1e-10 is
+timed with the V-cycle alone (precond 1) and with the V-cycle + net (precond 2), and optionally MG-MLMC++ to the
+target accuracy with either preconditioner.  Prints one JSON line.
+
+Hierarchies use the benchmark workload's set-up (bootstrap 2, V(2,2) SAP, TF32 coarse tensor cores).  Masses:
+the tuned near-critical ones where the mass table has them, else -0.10 at beta 3 and -0.075 at beta 5.
 """
 from __future__ import annotations
 
@@ -21,30 +26,18 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-
-def harvest(api, ctx, h, n_pairs: int, batch: int, seed: int):
-    """n_pairs (r, e) pairs at the fine level of hierarchy h, FP32 complex [n_pairs, n]."""
-    import torch
-    n = h.n[0]
-    R = torch.empty((n_pairs, n), dtype=torch.complex64, device="cuda")
-    E = torch.empty_like(R)
-    for s0 in range(0, n_pairs, batch):
-        nb = min(batch, n_pairs - s0)
-        z = api.mgmlmc_rademacher(ctx, seed, 0, 0, s0, n, nb).to(torch.complex64)
-        v = torch.empty_like(z)
-        h.vcycle(0, z, v, api.FP32)
-        dv = torch.empty_like(z)
-        h.apply(0, v, dv, api.FP32)
-        r1 = z - dv
-        x = torch.empty_like(z)
-        api.fgmres_batched(ctx, h, 0, z, x, prec=api.FP32, tol=1e-6)
-        s = torch.linalg.vector_norm(r1, dim=1, keepdim=True)
-        R[s0:s0 + nb] = r1 / s
-        E[s0:s0 + nb] = (x - v) / s
-    return R, E
+MG = dict(ntv=8, bootstrap=2, bootstrap_its=6, pre_smooth=2, post_smooth=2, tensor_cores=2)
 
 
-def timed_solves(api, ctx, h, precond: int, nrhs: int, seed: int, reps: int = 2):
+def field_mass(L: int, beta: float, seed: int) -> float:
+    try:
+        data = json.load(open(os.path.join(ROOT, "tests", "golden", "masses.json")))
+        return float(data["L%d_beta%g_seed%d" % (L, beta, seed)]["m0"])
+    except Exception:
+        return -0.10 if beta < 4 else -0.075
+
+
+def timed_solves(api, ctx, h, precond: int, nrhs: int, seed: int, reps: int = 3):
     import torch
     b = api.mgmlmc_rademacher(ctx, seed, 0, 0, 0, h.n[0], nrhs)
     x = torch.empty_like(b)
@@ -58,67 +51,131 @@ def timed_solves(api, ctx, h, precond: int, nrhs: int, seed: int, reps: int = 2)
                 s_per_solve=(time.perf_counter() - t0) / reps), x
 
 
-def main():
+def net_apply_time(api, net, n: int, nrhs: int, reps: int = 5) -> float:
+    """Seconds per application of the net to nrhs fine-level vectors (CUDA events)."""
+    import torch
+    r = torch.randn((nrhs, n), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(r)
+    net.forward(r, y)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        net.forward(r, y)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps / 1e3
+
+
+def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--L-train", type=int, default=128)
-    ap.add_argument("--L-eval", type=int, default=256)
-    ap.add_argument("--beta", type=float, default=3.0)
-    ap.add_argument("--m0", type=float, default=-0.08)
-    ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--train", default="128:3,256:3", help="training fields L:beta, comma separated")
+    ap.add_argument("--eval", default="256:3,256:5,512:3,512:5", help="evaluation fields L:beta")
+    ap.add_argument("--pairs", type=int, default=20480, help="training pairs in total (split over the fields)")
     ap.add_argument("--batch", type=int, default=32)
-    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--block", type=int, default=50, help="Adam steps on one field before switching")
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--layers", type=int, default=4)
     ap.add_argument("--channels", type=int, default=16)
     ap.add_argument("--nrhs", type=int, default=16)
-    a = ap.parse_args()
+    ap.add_argument("--tensor-cores", type=int, default=1)
+    ap.add_argument("--estimate", default="512:5", help="fields L:beta of an MG-MLMC++ run with each preconditioner")
+    ap.add_argument("--eps", type=float, default=1e-3)
+    a = ap.parse_args(argv)
     import torch
 
     from paper_2303_11512_gb300 import api, build
     from synthetic import gauge
     build.build()
     ctx = api.Context()
-    out = dict(L_train=a.L_train, L_eval=a.L_eval, beta=a.beta, m0=a.m0, layers=a.layers, channels=a.channels)
-    # training field and pairs
-    Ut = torch.from_numpy(gauge.links(gauge.field(a.L_train, a.beta, 1))).cuda()
-    ht = api.mg_setup(ctx, Ut, a.L_train, a.m0)
+    spec = lambda s: [(int(x.split(":")[0]), float(x.split(":")[1])) for x in s.split(",") if x]
+    out = dict(layers=a.layers, channels=a.channels, tensor_cores=a.tensor_cores, pairs=a.pairs, steps=a.steps,
+               batch=a.batch, mg=MG)
+    # ---- training fields and pairs
+    train = []
     t0 = time.perf_counter()
-    R, E = harvest(api, ctx, ht, a.pairs, 64, seed=3)
+    for i, (L, beta) in enumerate(spec(a.train)):
+        m0 = field_mass(L, beta, 1 + i)
+        U = torch.from_numpy(gauge.links(gauge.field(L, beta, 1 + i))).cuda()
+        h = api.mg_setup(ctx, U, L, m0, **MG)
+        npair = a.pairs // len(spec(a.train))
+        R, E = api.nn_harvest_pairs(ctx, h, npair, seed=3 + i)
+        Rv, Ev = api.nn_harvest_pairs(ctx, h, 64, seed=100 + i)     # held out
+        h.close()
+        train.append(dict(L=L, beta=beta, m0=m0, U=U, R=R, E=E, Rv=Rv, Ev=Ev))
     torch.cuda.synchronize()
     out["harvest_s"] = time.perf_counter() - t0
-    Rv, Ev = harvest(api, ctx, ht, 64, 64, seed=4)   # held out
-    net = api.Net(ctx, Ut, a.L_train, a.layers, a.channels, seed=2)
-    l0, _ = net.loss_grad(Rv, Ev)
-    t0 = time.perf_counter()
+    out["train_fields"] = [dict(L=f["L"], beta=f["beta"], m0=f["m0"], pairs=f["R"].shape[0]) for f in train]
+    net = api.Net(ctx, train[0]["U"], train[0]["L"], a.layers, a.channels, seed=2,
+                  tensor_cores=bool(a.tensor_cores))
+
+    def heldout():
+        ls = []
+        for f in train:
+            net.set_field(f["U"], f["L"])
+            ls.append(net.loss_grad(f["Rv"], f["Ev"])[0])
+        return ls
+
+    l0 = heldout()
     g = torch.Generator(device="cpu").manual_seed(0)
+    t0 = time.perf_counter()
+    cur = -1
     for it in range(a.steps):
-        idx = torch.randint(0, a.pairs, (a.batch,), generator=g).cuda()
-        net.train_step(R[idx].contiguous(), E[idx].contiguous(), a.lr)
+        fi = (it // a.block) % len(train)
+        f = train[fi]
+        if fi != cur:
+            net.set_field(f["U"], f["L"])
+            cur = fi
+        idx = torch.randint(0, f["R"].shape[0], (a.batch,), generator=g).cuda()
+        lr = a.lr if it < 2 * a.steps // 3 else a.lr / 4
+        net.train_step(f["R"][idx].contiguous(), f["E"][idx].contiguous(), lr)
     torch.cuda.synchronize()
     out["train_s"] = time.perf_counter() - t0
-    l1, _ = net.loss_grad(Rv, Ev)
-    out["heldout_loss"] = [l0, l1]
-    params = net.get_params()
-    del R, E
+    out["heldout_loss"] = dict(before=l0, after=heldout())
+    del train
+    torch.cuda.empty_cache()
+    # ---- evaluation: solves with either preconditioner
     res = {}
-    for L in sorted({a.L_train, a.L_eval}):
-        U = Ut if L == a.L_train else torch.from_numpy(gauge.links(gauge.field(L, a.beta, 5))).cuda()
-        h = ht if L == a.L_train else api.mg_setup(ctx, U, L, a.m0)
-        n2 = api.Net(ctx, U, L, a.layers, a.channels, seed=2)
-        n2.set_params(params)
-        n2.attach(h)
+    for L, beta in spec(a.eval):
+        m0 = field_mass(L, beta, 0)
+        U = torch.from_numpy(gauge.links(gauge.field(L, beta, 0))).cuda()
+        h = api.mg_setup(ctx, U, L, m0, **MG)
+        net.set_field(U, L)
+        net.attach(h)
         s1, x1 = timed_solves(api, ctx, h, 1, a.nrhs, seed=9)
         s2, x2 = timed_solves(api, ctx, h, 2, a.nrhs, seed=9)
-        s1["agree"] = float((torch.abs(x1 - x2).max() / torch.abs(x1).max()).item())
-        res[str(L)] = dict(vcycle=s1, vcycle_net=s2)
-        n2.close()
-        if h is not ht:
-            h.close()
+        agree = float((torch.abs(x1 - x2).max() / torch.abs(x1).max()).item())
+        res["L%d_beta%g" % (L, beta)] = dict(m0=m0, vcycle=s1, vcycle_net=s2, solutions_agree=agree,
+                                             net_apply_s=net_apply_time(api, net, h.n[0], a.nrhs))
+        h.close()
+        del U
     out["solves"] = res
-    ht.close()
+    # ---- MG-MLMC++ to eps with either preconditioner (the benchmark's estimator settings)
+    est = {}
+    for L, beta in spec(a.estimate):
+        m0 = field_mass(L, beta, 0)
+        U = torch.from_numpy(gauge.links(gauge.field(L, beta, 0))).cuda()
+        net.set_field(U, L)
+        row = {}
+        for pc in (1, 2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = api.mg_setup(ctx, U, L, m0, **MG)
+            net.attach(h)
+            r = api.trace_estimate(ctx, h, eps=a.eps, d=32, k=2, nrhs_max=256, nrhs_first=8, cost_mode=1, seed=0,
+                                   prec=api.MIXED, precond=pc)
+            torch.cuda.synchronize()
+            row["precond%d" % pc] = dict(time_to_eps_s=time.perf_counter() - t0, N=r["N"], solves=r["solves"],
+                                         inner_iters=r["inner_iters"], rel_sigma=r["sigma"] / abs(r["tau"]),
+                                         tau=[r["tau"].real, r["tau"].imag])
+            h.close()
+        est["L%d_beta%g" % (L, beta)] = row
+        del U
+    out["estimate"] = est
     net.close()
     ctx.close()
-    print(json.dumps(out))
+    print(json.dumps(out), flush=True)
+    return out
 
 
 if __name__ == "__main__":

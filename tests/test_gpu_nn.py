@@ -28,16 +28,16 @@ def ctx(api):
     c.close()
 
 
-def _setup(api, ctx, L=16, C=4, layers=4, seed=0):
+def _setup(api, ctx, L=16, C=4, layers=4, seed=0, tc=False):
     th = gauge.quenched_u1(L, 3.0, 20, seed)
     U = gauge.links(th)
     W, b = onn.init_params(C, layers, seed + 1)
     rs = np.random.default_rng(seed + 2)
     b = [0.2 * rs.standard_normal(bb.shape) for bb in b]
-    net = api.Net(ctx, torch.from_numpy(U).cuda(), L, layers, C, seed=3)
+    net = api.Net(ctx, torch.from_numpy(U).cuda(), L, layers, C, seed=3, tensor_cores=tc)
     net.set_params(api.pack_params(W, b))
     W32, b32 = api.unpack_params(net.get_params(), layers, C)   # the exact float32 values in use
-    ref = onn.Net(U, W32, [bb.astype(float) for bb in b32], round_bf16=True)
+    ref = onn.Net(U, W32, [bb.astype(float) for bb in b32], round_bf16=True, tc=tc)
     return th, U, net, ref
 
 
@@ -48,13 +48,96 @@ def _fields(L, nrhs, seed):
 
 
 def test_forward_matches_oracle(api, ctx):
+    """FP32 CUDA-core layers against the oracle with the same BF16 weights."""
     for C in (4, 8, 16):
         th, U, net, ref = _setup(api, ctx, L=16, C=C, layers=4, seed=C)
+        assert net.format == 0
         r = _fields(16, 3, 7)
         y = net.forward(torch.from_numpy(r.reshape(3, -1)).cuda()).cpu().numpy().reshape(3, -1, 2)
         yr = ref.forward(r.astype(complex))
         assert np.abs(y - yr).max() < 2e-5 * np.abs(yr).max(), C
         net.close()
+
+
+def _relerr(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max()), float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("L,C,nrhs", [(16, 4, 3), (16, 8, 3), (16, 16, 3), (128, 16, 4), (128, 4, 2), (256, 8, 1)])
+def test_tensor_core_forward_matches_oracle(api, ctx, L, C, nrhs):
+    """tcgen05 layers (BF16 operands, FP32 accumulation) against the oracle in the same number format (layer
+    inputs rounded to bfloat16).  The two round the same values to BF16 except where the FP32 and FP64 values
+    fall on different sides of a rounding midpoint (a 2^-8 change of one input, about one element in 2^16),
+    so the bound is 2e-3 of the largest output (4e-4 norm-wise) instead of FP32 rounding.  L = 16: gathered
+    tiles (a tile spans several lattice rows).  L = 128 and 256: the hidden and last layers stage row segments
+    by TMA (halo sites wrapped at both row ends at L = 128, interior at L = 256); 4 rhs at L = 128 give 512
+    tiles, several per CTA, with the TMEM accumulator ring and the stage ring wrapping many times."""
+    th, U, net, ref = _setup(api, ctx, L=L, C=C, layers=4, seed=C + L, tc=True)
+    assert net.format == 1
+    r = _fields(L, nrhs, 7 + L)
+    y = net.forward(torch.from_numpy(r.reshape(nrhs, -1)).cuda()).cpu().numpy().reshape(nrhs, -1, 2)
+    yr = ref.forward(r.astype(complex))
+    emax, enorm = _relerr(y, yr)
+    assert emax < 2e-3 and enorm < 4e-4, (emax, enorm)
+    # and it is the tensor-core format, not the FP32 one: the exact-input oracle is further away
+    y32 = onn.Net(U, ref.W, ref.b, round_bf16=False).forward(r.astype(complex))
+    assert _relerr(y, y32)[1] > 4 * enorm
+    net.close()
+
+
+@pytest.mark.parametrize("L,nrhs", [(64, 8), (128, 2)])
+def test_tensor_core_gradients_match_oracle(api, ctx, L, nrhs):
+    """Loss and gradients of the tensor-core layers (input gradient by the gathered mixing with the
+    conjugate-transposed weights, weight gradient as a tcgen05 GEMM over the sites) against the oracle's
+    hand-derived backward in the same number format.  L = 64 with 8 rhs: 512 chunks of 64 sites for the
+    weight gradient, several per CTA (the stage ring wraps and TMEM accumulates across chunks); L = 128: the
+    row-segment staging in the forward and the input gradient."""
+    C, layers = 16, 4
+    th, U, net, ref = _setup(api, ctx, L=L, C=C, layers=layers, seed=41, tc=True)
+    r = _fields(L, nrhs, 11)
+    e = _fields(L, nrhs, 12)
+    loss, g = net.loss_grad(torch.from_numpy(r.reshape(nrhs, -1)).cuda(), torch.from_numpy(e.reshape(nrhs, -1)).cuda())
+    lref, gW, gb = ref.backward(r.astype(complex), e.astype(complex))
+    assert abs(loss - lref) < 1e-4 * abs(lref)
+    gref = api.pack_params(gW, gb).astype(np.float64)
+    Wg, bg = api.unpack_params(g, layers, C)
+    for l in range(layers):
+        emax, enorm = _relerr(Wg[l], gW[l])
+        assert emax < 5e-3 and enorm < 1e-3, (l, emax, enorm)
+    for l in range(layers - 1):
+        emax, enorm = _relerr(bg[l], gb[l])
+        assert enorm < 1e-3, (l, emax, enorm)
+    assert np.linalg.norm(g - gref) < 1e-3 * np.linalg.norm(gref)
+    net.close()
+
+
+def test_harvested_pairs(api, ctx):
+    """nn_harvest_pairs: R = (zeta - D V zeta)/s, E = (D^{-1} zeta - V zeta)/s with s = |zeta - D V zeta|, for
+    the Rademacher stream (seed, 0, PHASE_HARVEST, s).  Checked against the oracle operator: |R| = 1,
+    D E = R to the solver tolerance, and R equal to the residual of the library's own FP32 V-cycle."""
+    from oracle import rng as orng
+    from oracle import schwinger as osch
+    L, m0 = 32, -0.05
+    U = gauge.links(gauge.field(L, 3.0, 2, sweeps=40))
+    Ut = torch.from_numpy(U).cuda()
+    h = api.mg_setup(ctx, Ut, L, m0)
+    count, seed, s0 = 5, 3, 2
+    R, E = api.nn_harvest_pairs(ctx, h, count, seed=seed, sample0=s0, tol=1e-6)
+    R, E = R.cpu().numpy().astype(complex), E.cpu().numpy().astype(complex)
+    D = osch.dirac_sparse(U, m0)
+    assert np.allclose(np.linalg.norm(R, axis=1), 1.0, atol=1e-6)
+    Z = np.ascontiguousarray(orng.rademacher_block(seed, 0, orng.PHASE_HARVEST, s0, h.n[0], count).T)
+    v = torch.empty((count, h.n[0]), dtype=torch.complex64, device="cuda")
+    h.vcycle(0, torch.from_numpy(Z.astype(np.complex64)).cuda(), v, api.FP32)
+    r1 = Z - (D @ v.cpu().numpy().astype(complex).T).T
+    s = np.linalg.norm(r1, axis=1)
+    assert np.abs(r1 / s[:, None] - R).max() < 1e-5
+    # D E - R = (D x - zeta) / s: the FP32 solve's residual, at most tol |zeta| / s (plus FP32 rounding)
+    res = np.linalg.norm((D @ E.T).T - R, axis=1)
+    bound = 1e-6 * np.linalg.norm(Z, axis=1) / s
+    assert np.all(res < 1.5 * bound + 1e-6), (res, bound)
+    assert np.linalg.norm(E, axis=1).min() > 1e-3
+    h.close()
 
 
 def test_gradients_match_oracle(api, ctx):
@@ -73,11 +156,11 @@ def test_gradients_match_oracle(api, ctx):
 
 def test_gauge_covariance_on_gpu(api, ctx):
     L, C = 16, 4
-    th, U, net, _ = _setup(api, ctx, L=L, C=C, seed=5)
+    th, U, net, _ = _setup(api, ctx, L=L, C=C, seed=5)   # FP32 layers: covariant to rounding
     om = np.random.default_rng(1).uniform(-np.pi, np.pi, (L, L))
     Om = np.exp(1j * om).ravel()
     U2 = gauge.links(gauge.gauge_transform(th, om))
-    net2 = api.Net(ctx, torch.from_numpy(U2).cuda(), L, 4, C, seed=3)
+    net2 = api.Net(ctx, torch.from_numpy(U2).cuda(), L, 4, C, seed=3, tensor_cores=False)
     net2.set_params(net.get_params())
     r = _fields(L, 2, 3)
     y = net.forward(torch.from_numpy(r.reshape(2, -1)).cuda()).cpu().numpy().reshape(2, -1, 2)
