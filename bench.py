@@ -32,9 +32,18 @@ sys.path.insert(0, ROOT)
 # autotune = 1: launch variants timed in the first set-up (a warm-up step) and reused from the tuning table.
 # First batch of 8 samples per level (then batches sized from the variances, up to 256): the stop rule needs 6-8
 # samples on levels 0 and 1 here, so a first batch of 16 only computed samples that are discarded.
+# Sketch d = 32, k = 2 (the workload's configuration).  A d x k scan on this workload finds smaller sketches faster
+# (the deflated part removes little variance on these fields); the benchmark line also reports one estimate with
+# d = 16, k = 1 (32 difference-operator applications per level) as `sketch_d16_k1`.
 WORKLOAD = dict(L=512, beta=5.0, seed=0, ntv=8, d=32, k=2, eps=1e-3, nrhs_max=256, nrhs_first=8,
                 bootstrap=2, bootstrap_its=6, kcycle_its=0, pre_smooth=2, post_smooth=2, tensor_cores=2, autotune=1)
 FALLBACK_M0 = {512: -0.07, 128: -0.1199}
+
+
+# DRAM bytes per algorithmic byte of the tensor-core coarse stencil (k_tc, MODE 0, TF32): one ncu capture of
+# the level-1 launch with 32 rhs of the L = 512 hierarchy read 235.99 MB and wrote 48.96 MB against 301.99 MB of
+# algorithmic traffic (weights 167.8 MB + 32 rhs x 16384 sites x 256 B)
+K_TC0_DRAM_PER_ALG_BYTE = (235.987 + 48.964) / 301.990
 
 
 def mass_for(L: int, beta: float, seed: int) -> float:
@@ -54,8 +63,8 @@ def peaks() -> dict:
                  bf16_tflops_sustained=float(m.get("bf16_tflops_sustained", m["bf16_tflops"])), src="measured")
     except Exception:
         pass
-    # CUDA-core peaks from unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes x 2 flops,
-    # FP64 at the nominal 1.25 TFLOP/s of the part
+    # CUDA-core peaks from unit counts and the maximum SM clock (152 SMs x 128 FP32 lanes x 2 flops) and the
+    # nominal FP64 rate; the benchmark replaces both by the library's measurement (mgmlmc_alu_peak)
     p["fp32_alu_tflops"] = 152 * 128 * 2 * 2.070e9 / 1e12
     p["fp64_alu_tflops"] = 1.25
     # dense TF32 tensor rate: the measured sustained bf16 rate times the nominal tf32 / bf16 ratio (1.1 / 2.25)
@@ -217,7 +226,8 @@ def workload_name(W, L, m0=None, nlev=4):
 # ------------------------------------------------------------------ profiling cases (ncu captures)
 def profile_case(args):
     """Small self-contained GPU cases whose kernels an ncu capture can select (-k, -s, -c): the workload's
-    hierarchy and one solve on a level, or the fine stencil alone.  Prints nothing timed."""
+    hierarchy and one solve on a level, the fine stencil alone, the coarse tensor-core stencil alone, or the
+    learned preconditioner's forward.  Prints nothing timed."""
     import torch
 
     import __graft_entry__ as g
@@ -229,7 +239,17 @@ def profile_case(args):
     m0 = mass_for(L, W["beta"], W["seed"])
     U = torch.from_numpy(gauge.links(gauge.field(L, W["beta"], W["seed"]))).cuda()
     ctx = api.Context()
-    if args.profile_case == "stencil":
+    if args.profile_case == "nn":
+        # five forward applications of the learned preconditioner (4 layers, 16 channels, tensor-core layers,
+        # seeded initial weights) to --profile-nrhs fine-level vectors
+        net = api.Net(ctx, U, L, 4, 16, seed=2, tensor_cores=True)
+        r = torch.randn((args.profile_nrhs, 2 * L * L), dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(r)
+        for _ in range(5):
+            net.forward(r, y)
+        torch.cuda.synchronize()
+        net.close()
+    elif args.profile_case == "stencil":
         n = 2 * L * L
         x = torch.randn((args.profile_nrhs, n), dtype=torch.complex64, device="cuda")
         y = torch.empty_like(x)
@@ -257,6 +277,69 @@ def profile_case(args):
             print("iters", st["iters"], "relres", st["max_relres"])
         h.close()
     torch.cuda.synchronize()
+    ctx.close()
+    return 0
+
+
+def config_records(args):
+    """Records of the small configurations: plain Hutchinson (Algorithm 1, unpreconditioned GMRES(30) to 1e-10)
+    at L = 16 against the exact trace from the library's dense inverse of D, and MG-MLMC at L = 128 (3 levels, 64
+    rhs per launch) in the FP64 and the FP32 / FP64-refinement form.  Times with CUDA events after one untimed
+    run; one JSON line."""
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2303_11512_gb300 import api
+    from synthetic import gauge
+    ctx = api.Context()
+    stream = ctx.stream
+
+    def timed(fn, reps=3):
+        fn()
+        ts, out = [], None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return sorted(ts)[len(ts) // 2], out
+
+    # C0: L = 16, beta 3, m0 -0.05, Rademacher, at most 1000 samples
+    L0, m00 = 16, -0.05
+    U0 = torch.from_numpy(gauge.links(gauge.field(L0, 3.0, 0))).cuda()
+    n0 = 2 * L0 * L0
+    I = torch.eye(n0, dtype=torch.complex128, device="cuda")
+    Dm = torch.empty_like(I)
+    api.schwinger_apply(ctx, U0, L0, m00, I, Dm, api.FP64)      # rows = D e_j, i.e. D^T
+    Dinv = Dm.transpose(0, 1).contiguous()
+    api.mg_dense_inverse(ctx, Dinv, api.FP64)
+    exact = complex(torch.diagonal(Dinv).sum().item())
+    h0 = api.mg_setup(ctx, U0, L0, m00, ntv=4, setup_sweeps=2)
+    t0, r0 = timed(lambda: api.hutchinson_estimate(ctx, h0, eps=0.02, seed=4, precond=0, m=30, tol=1e-10,
+                                                   maxit=20000, prec=api.FP64, max_samples=1000))
+    h0.close()
+    c0 = dict(L=16, time_to_eps_s=t0, eps=0.02, N=r0["N"], tau=[r0["tau"].real, r0["tau"].imag], sigma=r0["sigma"],
+              exact=[exact.real, exact.imag], deviation_in_sigma=abs(r0["tau"] - exact) / r0["sigma"])
+    # C1: L = 128, beta 3, tuned m0, MG-MLMC (d = 0), 64 rhs per launch, FP64 vs mixed
+    L1 = 128
+    m01 = mass_for(L1, 3.0, 0)
+    U1 = torch.from_numpy(gauge.links(gauge.field(L1, 3.0, 0))).cuda()
+    c1 = dict(L=128, m0=m01, eps=1e-3)
+    for name, prec in (("fp64", api.FP64), ("mixed", api.MIXED)):
+        def run():
+            h = api.mg_setup(ctx, U1, L1, m01, ntv=8)
+            r = api.trace_estimate(ctx, h, eps=1e-3, d=0, k=1, nrhs_max=64, nrhs_first=16, cost_mode=1, seed=3,
+                                   prec=prec)
+            h.close()
+            return r
+        t, r = timed(run)
+        c1[name] = dict(time_to_eps_s=t, N=r["N"], solves=r["solves"], tau=[r["tau"].real, r["tau"].imag],
+                        rel_sigma=r["sigma"] / abs(r["tau"]))
+    c1["speedup_mixed_vs_fp64"] = c1["fp64"]["time_to_eps_s"] / c1["mixed"]["time_to_eps_s"]
+    print(json.dumps({"record": "configs", "hutchinson_L16": c0, "mlmc_L128": c1}), flush=True)
     ctx.close()
     return 0
 
@@ -293,15 +376,19 @@ def main():
     ap.add_argument("--timing-filter", default="")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                     help="coarse-level tensor-core operands: 1 BF16, 2 TF32, 0 CUDA cores (default: the workload's)")
-    ap.add_argument("--profile-case", choices=["solve", "stencil", "coarse"], default=None,
+    ap.add_argument("--profile-case", choices=["solve", "stencil", "coarse", "nn"], default=None,
                     help="run one small case for an ncu capture instead of the benchmark: 'solve' = one mixed "
                          "FGMRES solve on --profile-level with --profile-nrhs rhs on the workload hierarchy, "
                          "'stencil' = ten FP32 fine-stencil applications to --profile-nrhs vectors, 'coarse' = ten "
-                         "tensor-core stencil applications on --profile-level")
+                         "tensor-core stencil applications on --profile-level, 'nn' = five forward applications "
+                         "of the learned preconditioner")
     ap.add_argument("--profile-level", type=int, default=1)
     ap.add_argument("--profile-nrhs", type=int, default=64)
     ap.add_argument("--profile-bootstrap", type=int, default=WORKLOAD["bootstrap"],
                     help="bootstrap rounds of the profiled hierarchy (0: no tensor-core launches before the solve)")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the benchmark, print the records of the L = 16 plain Hutchinson and the L = 128 "
+                         "MG-MLMC (FP64 vs mixed) configurations")
     ap.add_argument("--ensemble", type=int, default=0, metavar="CONCURRENCY",
                     help="instead of the benchmark, run the 16-field ensemble (L 128..1024, three masses) with up "
                          "to CONCURRENCY fields at a time and print its record as one JSON line")
@@ -312,6 +399,8 @@ def main():
         return profile_case(args)
     if args.ensemble:
         return ensemble_record(args)
+    if args.configs:
+        return config_records(args)
 
     import numpy as np
     import torch
@@ -351,9 +440,9 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = api.Context(stream)
 
-    def step(prec=api.MIXED):
+    def step(prec=api.MIXED, **over):
         h = api.mg_setup(ctx, U, L, m0, **mgp)
-        r = api.trace_estimate(ctx, h, prec=prec, **estp)
+        r = api.trace_estimate(ctx, h, prec=prec, **dict(estp, **over))
         h.close()
         return r
 
@@ -382,8 +471,10 @@ def main():
         ms = float(t.item())
     value = ms / 1e3
 
-    # dominant kernel -> roofline
+    # dominant kernel -> roofline (CUDA-core FMA peaks measured on this GPU by the library)
     P = peaks()
+    P["fp64_alu_tflops"] = api.alu_peak(ctx, True)
+    P["fp32_alu_tflops"] = api.alu_peak(ctx, False)
     dom, info = max(rpt.items(), key=lambda kv: kv[1]["ms"])
     tot_ms = sum(v["ms"] for v in rpt.values())
     avg_ms = info["ms"] / info["launches"]
@@ -402,8 +493,16 @@ def main():
     else:
         roof = dict(bound=comp_bound, achieved=flops_l / (avg_ms * 1e-3) / 1e12, peak=comp_peak, unit="TFLOP/s")
     roof["frac"] = roof["achieved"] / roof["peak"]
+    # DRAM traffic of the dominant kernel: the ncu capture of one launch (dram__bytes_read + _write) relative to
+    # that launch's algorithmic bytes, scaled to this run's average launch (the bench's launches mix levels and
+    # batch sizes; the capture is the level-1, 32-rhs stencil of profiles/k_tc_stencil_level1_32rhs_L512.md)
+    traffic = None
+    if "MODE = 0" in dom and "BF = 0" in dom:
+        traffic = K_TC0_DRAM_PER_ALG_BYTE * bytes_l
     roof.update(kernel=dom, launches=info["launches"], avg_launch_ms=avg_ms, share=info["ms"] / max(tot_ms, 1e-9),
-                bytes_per_launch=bytes_l, flops_per_launch=flops_l, peak_src=P["src"], traffic=None)
+                bytes_per_launch=bytes_l, flops_per_launch=flops_l, peak_src=P["src"], traffic=traffic,
+                traffic_src=("ncu capture of one launch (level 1, 32 rhs): 284.95 MB DRAM / 301.99 MB algorithmic, "
+                             "scaled to the average launch" if traffic else None))
     kernels = {k: dict(launches=v["launches"], ms=round(v["ms"], 3), share=round(v["ms"] / max(tot_ms, 1e-9), 4),
                        gbs=round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
                        tflops=round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 3))
@@ -447,6 +546,21 @@ def main():
         e2e = dict(value=sum(e2e_t) / len(e2e_t), unit="s", h2d_bytes_per_step=int(U_host.nbytes),
                    d2h_bytes_per_step=int(16 * 2))
 
+    # the same time to eps with a smaller sketch (d = 16, k = 1: 32 difference-operator applications per level),
+    # median of three after one untimed run
+    alt_runs = []
+    barrier()
+    step(d=16, k=1)
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ra = step(d=16, k=1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        alt_runs.append(a.elapsed_time(b) / 1e3)
+    sketch_alt = dict(d=16, k=1, time_to_eps_s=sorted(alt_runs)[1], runs_s=alt_runs, N=ra["N"], solves=ra["solves"],
+                      rel_sigma=ra["sigma"] / abs(ra["tau"]))
+
     # plain FP64 batched MG form of the same estimator (the comparator of the metric): one untimed run, then the
     # median of three
     fp64_s, fp64_runs = None, []
@@ -484,6 +598,9 @@ def main():
             roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
             clocks=clk, fp64_reference_s=fp64_s, fp64_reference_runs_s=fp64_runs,
             speedup_vs_fp64=(fp64_s / value) if fp64_s else None,
+            sketch_d16_k1=sketch_alt,
+            alu_peaks=dict(fp64_tflops=P["fp64_alu_tflops"], fp32_tflops=P["fp32_alu_tflops"],
+                           src="measured: mgmlmc_alu_peak (8 FMA chains per thread, full grid)"),
             stencil_fp32=stencil,
             estimate=dict(tau=[r["tau"].real, r["tau"].imag], sigma=r["sigma"], rel_sigma=r["sigma"] / abs(r["tau"]),
                           N=r["N"], computed=r["computed"], solves=r["solves"], inner_iters=r["inner_iters"]),

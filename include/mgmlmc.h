@@ -110,6 +110,10 @@ int mgmlmc_version(void);
  * the records. */
 int mgmlmc_timing_enable(mgmlmc_ctx* ctx, int on, const char* filter);
 int mgmlmc_timing_report(mgmlmc_ctx* ctx, char* buf, int64_t len);
+/* Measured FMA throughput of the CUDA cores (fp64 != 0: FP64, else FP32) in TFLOP/s: eight independent FMA
+ * chains per thread over a grid of 8 x 256-thread blocks per SM, best of three launches (CUDA events on the
+ * context stream).  The roofline of ALU-bound kernels is taken against it. */
+int mgmlmc_alu_peak(mgmlmc_ctx* ctx, int fp64, double* tflops);
 
 /* ---- operator ----------------------------------------------------------- */
 

@@ -123,6 +123,7 @@ SIGNATURES = {
     "nn_train_step": (ip, [vp, vp, vp, vp, ip, C.c_double, dp]),
     "nn_set_format": (ip, [vp, vp, ip]),
     "nn_get_format": (ip, [vp]),
+    "mgmlmc_alu_peak": (ip, [vp, ip, dp]),
     "nn_set_field": (ip, [vp, vp, vp, ip]),
     "nn_harvest_pairs": (ip, [vp, vp, C.c_uint64, C.c_int64, ip, C.c_double, vp, vp]),
     "mg_attach_nn": (ip, [vp, vp, vp]),

@@ -203,6 +203,13 @@ class Hierarchy:
 TUNE_KINDS = {0: "fine stencil (FP32)", 1: "tensor-core stencil", 2: "tensor-core SAP block update"}
 
 
+def alu_peak(ctx: Context, fp64: bool) -> float:
+    """Measured CUDA-core FMA throughput (TFLOP/s) of the current device, FP64 or FP32."""
+    v = C.c_double()
+    check(_lib.load().mgmlmc_alu_peak(ctx.ptr, 1 if fp64 else 0, C.byref(v)), ctx.ptr)
+    return v.value
+
+
 def tune_table() -> list:
     """The process-wide launch-variant table: [dict(device, kind, side, bucket, format, variant, us)]."""
     buf = C.create_string_buffer(1 << 16)

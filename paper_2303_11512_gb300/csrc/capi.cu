@@ -68,6 +68,13 @@ const char* mgmlmc_last_error(const mgmlmc_ctx* ctx) { return ctx ? ctx->err.c_s
 
 int64_t mgmlmc_launch_count(const mgmlmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int mgmlmc_alu_peak(mgmlmc_ctx* ctx, int fp64, double* tflops) {
+  return guarded(ctx, [&] {
+    MG_CHECK_ARG(tflops, "null pointer");
+    *tflops = mg::alu_peak_tflops(ctx->stream, fp64 != 0);
+  });
+}
+
 int mgmlmc_timing_enable(mgmlmc_ctx* ctx, int on, const char* filter) {
   if (!ctx) return MGMLMC_ERR_INVALID_ARG;
   ctx->timer.on = on != 0;

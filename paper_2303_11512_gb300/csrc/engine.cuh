@@ -181,6 +181,8 @@ SolveOut level_sample_accumulated(mgmlmc_hier* h, int l, const double2* zeta_fin
 void hutchinson(mgmlmc_hier* h, const hutch_params& p, hutch_result* r);
 // time the launch variants of h's tunable kernels for these batch sizes and record the fastest (tune.cu)
 void autotune(mgmlmc_hier* h, const std::vector<int>& nrhs_list, bool force);
+// FMA throughput of the CUDA cores (FP64 or FP32), TFLOP/s, measured on the current device
+double alu_peak_tflops(cudaStream_t st, bool fp64);
 // block subspace iteration on D^{-1} gamma5 (fine level): the deflation basis of the exactly deflated Hutchinson
 // comparator, its direct part tr(Q^H D^{-1} Q) in sk->tau and the relative residual of the invariant subspace
 mgmlmc_sketch* deflation_basis(mgmlmc_hier* h, int k, int sweeps, uint64_t seed, const solve_params& sp,

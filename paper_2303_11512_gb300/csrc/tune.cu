@@ -150,4 +150,40 @@ void autotune(mgmlmc_hier* h, const std::vector<int>& nrhs_list, bool force) {
   MG_CUDA(cudaStreamSynchronize(st));
 }
 
+// ---- measured ALU peaks -------------------------------------------------------------------------------------
+// Eight independent FMA chains per thread, a full grid of resident warps: the CUDA-core FMA throughput that the
+// roofline of ALU-bound kernels (FP64 refinement residual, Galerkin products) is taken against.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T* out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = (T)(threadIdx.x + 1) * (T)(j + 1) * (T)1e-7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fma(x[j], a, b);
+  }
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  if (s == (T)12345.678) out[blockIdx.x] = s;  // never true: keeps the chains from being removed
+}
+
+double alu_peak_tflops(cudaStream_t st, bool fp64) {
+  int dev = 0, nsm = 152;
+  MG_CUDA(cudaGetDevice(&dev));
+  MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = nsm * 8, iters = fp64 ? 2048 : 65536;
+  DBuf out(sizeof(double) * grid, st);
+  auto launch = [&] {
+    if (fp64)
+      MG_LAUNCH(k_fma_peak<double>, grid, 256, 0, st, out.as<double>(), iters, 0.999, 0.001);
+    else
+      MG_LAUNCH(k_fma_peak<float>, grid, 256, 0, st, out.as<float>(), iters, 0.999f, 0.001f);
+  };
+  launch();
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) best = std::min(best, time_us(st, launch, 1));
+  return 2.0 * 8.0 * iters * (double)grid * 256 / (best * 1e-6) / 1e12;
+}
+
 }  // namespace mg

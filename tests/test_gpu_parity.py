@@ -336,3 +336,55 @@ def test_trace_estimate_parity(api, ctx, L, d, form):
     assert abs(r["tau"] - ro["tau"]) < 1e-8 * abs(ro["tau"])
     assert abs(r["sigma"] - ro["sigma"]) < 1e-6 * ro["sigma"]
     assert r["sigma"] <= eps * abs(r["tau"]) * (1 + 1e-9)
+
+
+# ---------------------------------------------------------------- fewer test vectors (Table 1)
+@pytest.mark.parametrize("ntv", [2, 4])
+def test_fewer_test_vectors(api, ctx, ntv):
+    """Table 1's 2 and 4 test vectors per chirality (4 and 8 coarse dof per site; runtime-shape transfer, coarse
+    stencil and SAP kernels, no tensor cores): prolongators, Galerkin stencils and the coarsest trace against the
+    oracle's own hierarchy, level operators, a V-cycle, and level-difference samples in both forms."""
+    h, H = hierarchies(api, ctx, 64, ntv=ntv)
+    assert h.levels == H.levels and h.dof[1] == 2 * ntv
+    for l in range(H.levels - 1):
+        Pg = h.get_prolongator(l, 4, ntv)
+        blocks = omg.aggregate_blocks(H.side[l], H.dof[l], 4)
+        Po = H.P[l].tocsr()
+        Lc, dc = H.side[l + 1], H.dof[l + 1]
+        ref = np.empty_like(Pg)
+        for T in range(Lc):
+            for X in range(Lc):
+                for c in range(2):
+                    cols = (T * Lc + X) * dc + c * ntv + np.arange(ntv)
+                    ref[T * Lc + X, c] = Po[blocks[X, T, c]][:, cols].toarray()
+        assert relerr(Pg, ref) < 1e-10
+    for l in range(1, H.levels):
+        Sg = h.get_stencil(l)
+        So = omg.stencil_blocks(H.D[l], H.side[l], H.dof[l]).reshape(Sg.shape)
+        assert relerr(Sg, So) < 1e-10
+        x = rand_vecs(H.n[l], 3, 40 + l)
+        y = torch.empty((3, H.n[l]), dtype=torch.complex128, device="cuda")
+        h.apply(l, cuda(x), y, api.FP64)
+        assert relerr(y.cpu().numpy(), (H.D[l] @ x.T).T) < 1e-12
+    tL = np.trace(np.linalg.inv(H.D[-1].toarray()))
+    assert abs(h.coarsest_trace() - tL) < 1e-10 * abs(tL)
+    b = rand_vecs(H.n[0], 3, 8)
+    ref = H.vcycle(0, b.T, 1, 1).T
+    x64 = torch.empty((3, H.n[0]), dtype=torch.complex128, device="cuda")
+    h.vcycle(0, cuda(b), x64, api.FP64)
+    assert relerr(x64.cpu().numpy(), ref) < 1e-11
+    x32 = torch.empty((3, H.n[0]), dtype=torch.complex64, device="cuda")
+    h.vcycle(0, cuda(b.astype(np.complex64)), x32, api.FP32)
+    assert relerr(x32.cpu().numpy(), ref) < 1e-4
+    for form in ("accumulated", "reduced"):
+        ld = oest.LevelDifference(H, form)
+        for l in range(H.levels - 1):
+            nv = ld.vec_size(l)
+            Z = np.stack([orng.rademacher(5, l, orng.PHASE_STOCH, s, nv) for s in range(4)], axis=1)
+            tau_ref = np.einsum("ij,ij->j", Z, ld.apply(l, Z.astype(complex)))
+            zf = api.mgmlmc_rademacher(ctx, 5, l, orng.PHASE_STOCH, 0, nv, 4)
+            zl = api.mg_restrict_to_level(ctx, h, l, zf) if form == "accumulated" else zf
+            yy = torch.empty_like(zl)
+            st = api.mlmc_level_sample(ctx, h, l, zl, yy, tol=1e-12, prec=api.MIXED)
+            assert st["converged"]
+            assert relerr(api.hutchpp_project(ctx, None, zl, yy), tau_ref) < 1e-8, (form, l)

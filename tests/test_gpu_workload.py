@@ -3,8 +3,8 @@
 The benchmark times MG-MLMC++ with the set-up and estimator of bench.WORKLOAD: bootstrap set-up (2 rounds of
 6 FGMRES iterations on top of the smoothed test vectors), 8 test vectors per chirality, V(2,2) SAP cycles with
 the tensor-core kernels on the coarse levels (TF32 operands), mixed precision (FP32 inner FGMRES, FP64 true-residual
-refinement to 1e-10), d = 32 Hutch++ vectors with k = 2 power sweeps, accumulated form, first batch 8, counted
-flops as the sample cost.  Here the same configuration runs at L = 256 (4 levels, 256 -> 64 -> 16 -> 4, the
+refinement to 1e-10), the workload's Hutch++ sketch (W["d"] vectors, W["k"] sketch applications), accumulated
+form, first batch 8, counted flops as the sample cost.  Here the same configuration runs at L = 256 (4 levels, 256 -> 64 -> 16 -> 4, the
 same depth and coarse dof as L = 512) on a beta = 5 field with the tuned near-critical mass.
 
 The bootstrap set-up is adaptive (many prolongators are valid), so the GPU's P_l are imported as data and
