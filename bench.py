@@ -262,13 +262,13 @@ def profile_case(args):
         lv = args.profile_level
         if args.profile_case == "coarse":
             # ten tensor-core stencil applications y = D_l x on level lv (no additive input, every rhs active)
-            prec = api.BF16 if W["tensor_cores"] == 1 else api.TF32
+            prec = {1: api.BF16, 3: api.FP16}.get(W["tensor_cores"], api.TF32)
             x = torch.randn((args.profile_nrhs, h.n[lv]), dtype=torch.complex64, device="cuda")
             y = torch.empty_like(x)
             for _ in range(10):
                 h.apply(lv, x, y, prec)
             ns = h.side[lv] ** 2
-            wbytes = ns * 5 * 16 * 32 * (2 if W["tensor_cores"] == 1 else 4)
+            wbytes = ns * 5 * 16 * 32 * (2 if W["tensor_cores"] in (1, 3) else 4)
             print("algorithmic bytes per launch", ns * 256 * args.profile_nrhs + wbytes, "sites", ns)
         else:
             b = api.mgmlmc_rademacher(ctx, 1, 0, 0, 0, h.n[lv], args.profile_nrhs)
@@ -374,8 +374,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--timing-filter", default="")
-    ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
-                    help="coarse-level tensor-core operands: 1 BF16, 2 TF32, 0 CUDA cores (default: the workload's)")
+    ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="coarse-level tensor-core operands: 1 BF16, 2 TF32, 3 FP16, 0 CUDA cores (default: the workload's)")
     ap.add_argument("--profile-case", choices=["solve", "stencil", "coarse", "nn"], default=None,
                     help="run one small case for an ncu capture instead of the benchmark: 'solve' = one mixed "
                          "FGMRES solve on --profile-level with --profile-nrhs rhs on the workload hierarchy, "

@@ -56,8 +56,10 @@ enum mgmlmc_prec {
   MGMLMC_MIXED = 2,  /* FP64 vectors and true residuals, FP32 inner Krylov + V-cycle */
   MGMLMC_TF32 = 3,   /* FP32 vectors, TF32 tensor-core products (mg_apply / mg_smooth on coarse levels of a
                         hierarchy set up with tensor_cores = 2) */
-  MGMLMC_BF16 = 4    /* FP32 vectors, BF16 tensor-core products with FP32 accumulation (same calls, a hierarchy
+  MGMLMC_BF16 = 4,   /* FP32 vectors, BF16 tensor-core products with FP32 accumulation (same calls, a hierarchy
                         set up with tensor_cores = 1) */
+  MGMLMC_FP16 = 5    /* FP32 vectors, FP16 tensor-core products with FP32 accumulation (same calls, a hierarchy
+                        set up with tensor_cores = 3) */
 };
 
 enum mgmlmc_form {
@@ -165,7 +167,8 @@ typedef struct {
   double kcycle_tol;     /* relative residual at which a K-cycle stops early (0.1) */
   int tensor_cores;      /* inside the FP32 V-cycle, coarse levels with 16 dof per site run their SAP sweeps
                             and residuals as tcgen05 GEMMs over the rhs: 1 = BF16 operands (FP32 accumulation),
-                            2 = TF32 operands, 0 = CUDA cores only (2: on the L = 512 workload TF32 took
+                            2 = TF32 operands, 3 = FP16 operands (11-bit significands like TF32 at the 16-bit
+                            instruction rate), 0 = CUDA cores only (2: on the L = 512 workload TF32 took
                             0.836 s per estimate, BF16 0.866 s with 2.5 % more inner iterations) */
   int graphs;            /* 1: the V-cycle preconditioner is captured once per shape as a CUDA graph
                             and replayed (not while the kernel timer runs or with K-cycles) (1) */

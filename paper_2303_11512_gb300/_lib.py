@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libmgmlmc.so")
 
 MAX_LEVELS = 8
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_NAN, ERR_NOT_POSDEF = 0, -1, -2, -3, -4, -5, -6, -7
-FP64, FP32, MIXED, TF32, BF16 = 0, 1, 2, 3, 4
+FP64, FP32, MIXED, TF32, BF16, FP16 = 0, 1, 2, 3, 4, 5
 ACCUMULATED, REDUCED = 0, 1
 OPTIMAL, UNIFORM = 0, 1
 PHASE_STOCH, PHASE_SKETCH, PHASE_TESTVEC, PHASE_HUTCH = 0, 1, 2, 3

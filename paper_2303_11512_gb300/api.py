@@ -13,14 +13,14 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (ACCUMULATED, BF16, FP32, FP64, MIXED, NOISE_RADEMACHER, NOISE_Z4, OPTIMAL, REDUCED, TF32,
+from ._lib import (ACCUMULATED, BF16, FP16, FP32, FP64, MIXED, NOISE_RADEMACHER, NOISE_Z4, OPTIMAL, REDUCED, TF32,
                    TRACE_GAMMA5, TRACE_PLAIN, UNIFORM, EstParams, EstResult, HutchParams, HutchResult, MgParams,
                    SolveParams, SolveStats, check)
 
 __all__ = ["Context", "Hierarchy", "Sketch", "schwinger_apply", "mgmlmc_rademacher", "mg_setup",
            "fgmres_batched", "mlmc_level_sample", "mg_restrict_to_level", "hutchpp_sketch_qr",
            "hutchpp_project", "trace_estimate", "hutchinson_estimate", "mgmlmc_noise", "mlmc_update_active",
-           "FP64", "FP32", "MIXED", "ACCUMULATED", "REDUCED", "OPTIMAL", "UNIFORM", "NOISE_RADEMACHER", "NOISE_Z4",
+           "FP64", "FP32", "FP16", "MIXED", "ACCUMULATED", "REDUCED", "OPTIMAL", "UNIFORM", "NOISE_RADEMACHER", "NOISE_Z4",
            "TRACE_PLAIN", "TRACE_GAMMA5"]
 
 
@@ -35,7 +35,7 @@ def _ptr(t: torch.Tensor, dtype=None) -> int:
 
 
 def _vec_dtype(prec: int):
-    return torch.complex64 if prec in (FP32, TF32, BF16) else torch.complex128
+    return torch.complex64 if prec in (FP32, TF32, BF16, FP16) else torch.complex128
 
 
 class Context:

@@ -228,15 +228,18 @@ int mg_coarsest_trace(const mgmlmc_hier* h, double* tau_L) {
   return MGMLMC_OK;
 }
 
+// image format of a tensor-core precision: 0 TF32, 1 BF16, 2 FP16
+static int tc_format_of(int prec) { return prec == MGMLMC_BF16 ? 1 : prec == MGMLMC_FP16 ? 2 : 0; }
+
 int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y, int nrhs, int prec) {
   return guarded(ctx, [&] {
     MG_CHECK_ARG(h && x && y && x != y, "null or aliased pointer");
     const_cast<mgmlmc_hier*>(h)->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level < h->nlev, "level out of range");
-    const bool tc = prec == MGMLMC_TF32 || prec == MGMLMC_BF16;
-    MG_CHECK_ARG(!tc || (h->use_tc(level) && h->lv[level].tc_bf == (prec == MGMLMC_BF16)),
+    const bool tc = prec == MGMLMC_TF32 || prec == MGMLMC_BF16 || prec == MGMLMC_FP16;
+    MG_CHECK_ARG(!tc || (h->use_tc(level) && h->lv[level].tc_bf == tc_format_of(prec)),
                  "tensor-core apply needs a coarse level with 16 dof whose images have this format "
-                 "(mg_params.tensor_cores: 1 BF16, 2 TF32)");
+                 "(mg_params.tensor_cores: 1 BF16, 2 TF32, 3 FP16)");
     if (!tc) check_prec(prec);
     if (nrhs <= 0) return;
     if (tc)
@@ -254,9 +257,9 @@ int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x
     MG_CHECK_ARG(h && f && x && f != x, "null or aliased pointer");
     h->ctx = ctx;
     MG_CHECK_ARG(level >= 0 && level + 1 < h->nlev, "the coarsest level has no smoother");
-    const bool tc = prec == MGMLMC_TF32 || prec == MGMLMC_BF16;
-    MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32 || tc, "FP64, FP32, TF32 or BF16");
-    MG_CHECK_ARG(!tc || (h->use_tc(level) && h->lv[level].tcInv[0].p && h->lv[level].tc_bf == (prec == MGMLMC_BF16)),
+    const bool tc = prec == MGMLMC_TF32 || prec == MGMLMC_BF16 || prec == MGMLMC_FP16;
+    MG_CHECK_ARG(prec == MGMLMC_FP64 || prec == MGMLMC_FP32 || tc, "FP64, FP32, TF32, BF16 or FP16");
+    MG_CHECK_ARG(!tc || (h->use_tc(level) && h->lv[level].tcInv[0].p && h->lv[level].tc_bf == tc_format_of(prec)),
                  "tensor-core smoothing needs a coarse level with 16 dof, 2x2 SAP blocks and images of this format");
     MG_CHECK_ARG(sweeps >= 0, "sweeps must be >= 0");
     if (nrhs <= 0) return;

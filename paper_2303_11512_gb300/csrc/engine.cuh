@@ -45,7 +45,7 @@ struct LevelData {
   DBuf P64, P32;
   // tensor-core images (coarse levels with 16 dof): stencil and per-colour SAP block inverses
   DBuf tcW, tcInv[2];
-  int tc_bf = 0;  // format of the tensor-core images: 1 BF16, 0 TF32
+  int tc_bf = 0;  // format of the tensor-core images: 0 TF32, 1 BF16, 2 FP16
   // coarsest level: dense inverse
   DBuf inv64, inv32;
   double2 trace = make_double2(0, 0);     // coarsest level: tr(D_L^{-1})

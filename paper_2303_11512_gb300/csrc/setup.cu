@@ -51,7 +51,7 @@ static void build_sap(mgmlmc_hier* h, int l, int* dfail, bool fp64) {
   }
   lv.sap64_ok = fp64;
   if (h->prm.tensor_cores && l >= 1 && d == 16 && bs == 2) {
-    lv.tc_bf = h->prm.tensor_cores == 1;
+    lv.tc_bf = h->prm.tensor_cores == 1 ? 1 : h->prm.tensor_cores == 3 ? 2 : 0;
     for (int c = 0; c < 2; ++c) {
       lv.tcInv[c].alloc(tc_blockinv_weight_bytes(Ls, lv.tc_bf), st);
       tc_blockinv_weights(st, lv.sapinv32.as<float2>(), Ls, c, lv.tcInv[c].p, lv.tc_bf);
@@ -113,7 +113,7 @@ static void build_from_tv(mgmlmc_hier* h, int l, int* dfail, bool sap64, bool co
       galerkin(st, lv.st64.as<double2>(), false, 0.0, Ls, d, p.agg, ntv, lv.P64.as<double2>(), lc.st64.as<double2>());
     to_fp32(st, lc.st64, lc.st32, scount);
     if (p.tensor_cores && dc == 16) {
-      lc.tc_bf = p.tensor_cores == 1;
+      lc.tc_bf = p.tensor_cores == 1 ? 1 : p.tensor_cores == 3 ? 2 : 0;
       lc.tcW.alloc(tc_stencil_weight_bytes(Lc * Lc, lc.tc_bf), st);
       tc_stencil_weights(st, lc.st32.as<float2>(), Lc * Lc, lc.tcW.p, lc.tc_bf);
     }

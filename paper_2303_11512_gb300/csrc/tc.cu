@@ -28,6 +28,7 @@
 // (bounded) for its own copies and frees its TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "ops.cuh"
 #include "tcgen05.cuh"
@@ -62,7 +63,7 @@ __device__ __forceinline__ int block_site(int k, int j, int Ls, int color) {
 //         is not padded to 128 MMA rows.
 // BF = 0: TF32 operands (kind::tf32, K = 8 per instruction); the FP32 vector slabs that TMA brings in are the
 //         MMA operand directly (128-byte rows, 128-byte swizzle).
-// BF = 1: BF16 operands (kind::f16, K = 16 per instruction, FP32 accumulation): half the weight bytes and half
+// BF = 1 / 2: BF16 / FP16 operands (kind::f16, K = 16 per instruction, FP32 accumulation): half the weight bytes and half
 //         the MMA instructions; converter warps turn each staged FP32 slab into a BF16 operand tile
 //         (64-byte rows, 64-byte swizzle) before the MMA reads it.
 template <int MODE>
@@ -117,8 +118,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr int WROW = BF ? 64 : 128;             // bytes of one weight / operand row
   const int acc_cols = MODE == 0 ? NW : vrows;    // TMEM columns of one accumulator
   const int vt = tc_vt(MODE, vrows, MM);
-  const uint32_t idesc = MODE == 0 ? (BF ? idesc_bf16(MM, NW) : idesc_tf32(MM, NW))
-                                   : (BF ? idesc_bf16(MM, vrows) : idesc_tf32(MM, vrows));
+  const int NI = MODE == 0 ? NW : vrows;  // MMA N
+  const uint32_t idesc = BF == 2 ? idesc_f16(MM, NI) : BF == 1 ? idesc_bf16(MM, NI) : idesc_tf32(MM, NI);
   uint32_t ncol = 32;
   while (ncol < (uint32_t)(TC_NACC * acc_cols)) ncol <<= 1;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -218,6 +219,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp < TC_EPI_WARP0) {
     // ---------------- MMA issuer
+    const uint64_t vdesc0 = BF ? sw64_desc(smem_u32(sV(0, 0))) : sw128_desc(smem_u32(sV(0, 0)));
+    const uint64_t wdesc0 = BF ? sw64_desc(smem_u32(sW(0, 0))) : sw128_desc(smem_u32(sW(0, 0)));
+    const uint32_t stage16 = (uint32_t)sbytes >> 4;
+    const uint32_t vstep16 = (uint32_t)(BF ? vt * 64 : vrows * 128) >> 4, wstep16 = (uint32_t)(NW * WROW) >> 4;
     if (lane == 0) {
       for (int i = 0; i < n_my && !s_bad; ++i) {
         const int s = i % stages, a = i % TC_NACC;
@@ -233,9 +238,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t d = taddr + (uint32_t)(a * acc_cols);
+        // descriptors of this stage: the first chunk's plus fixed steps (address field in 16-byte units)
+        const uint64_t vds = vdesc0 + (uint64_t)(s * stage16), wds = wdesc0 + (uint64_t)(s * stage16);
+#pragma unroll
         for (int kc = 0; kc < KC; ++kc) {
-          const uint64_t vd = BF ? sw64_desc(smem_u32(sV(s, kc))) : sw128_desc(smem_u32(sV(s, kc)));
-          const uint64_t wd = BF ? sw64_desc(smem_u32(sW(s, kc))) : sw128_desc(smem_u32(sW(s, kc)));
+          const uint64_t vd = vds + (uint64_t)(kc * vstep16), wd = wds + (uint64_t)(kc * wstep16);
           const uint64_t ad = MODE == 0 ? vd : wd, bd = MODE == 0 ? wd : vd;
           if (BF) {
 #pragma unroll
@@ -268,36 +275,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         s_bad = 1;
         break;
       }
-      uint4* w0 = reinterpret_cast<uint4*>(sW(s, 0));  // chunk e: tile e / HALF, offset e % HALF
-      for (int e = et; e < KC * HALF; e += NT) {
-        const int kc = e / HALF, o = kc * TILE + (e - kc * HALF);
-        const uint4 v = w0[o];
-        uint4 r;
-        if (BF) {  // four bf16 pairs (a, b) -> (-b, a)
-          r.x = ((v.x & 0xFFFFu) << 16) | ((v.x >> 16) ^ 0x8000u);
-          r.y = ((v.y & 0xFFFFu) << 16) | ((v.y >> 16) ^ 0x8000u);
-          r.z = ((v.z & 0xFFFFu) << 16) | ((v.z >> 16) ^ 0x8000u);
-          r.w = ((v.w & 0xFFFFu) << 16) | ((v.w >> 16) ^ 0x8000u);
-        } else {  // two fp32 pairs (a, b) -> (-b, a)
-          r.x = v.y ^ 0x80000000u;
-          r.y = v.x;
-          r.z = v.w ^ 0x80000000u;
-          r.w = v.z;
+      // weight tiles: the KC chunks of one (row, 16-byte chunk) position are independent, so each thread handles
+      // a position of all KC tiles at once (KC loads in flight, no index division)
+      uint4* w0 = reinterpret_cast<uint4*>(sW(s, 0));
+      for (int e = et; e < HALF; e += NT) {
+        uint4 v[KC];
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc) v[kc] = w0[kc * TILE + e];
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc) {
+          uint4 r;
+          if (BF) {  // four 16-bit pairs (a, b) -> (-b, a)
+            r.x = ((v[kc].x & 0xFFFFu) << 16) | ((v[kc].x >> 16) ^ 0x8000u);
+            r.y = ((v[kc].y & 0xFFFFu) << 16) | ((v[kc].y >> 16) ^ 0x8000u);
+            r.z = ((v[kc].z & 0xFFFFu) << 16) | ((v[kc].z >> 16) ^ 0x8000u);
+            r.w = ((v[kc].w & 0xFFFFu) << 16) | ((v[kc].w >> 16) ^ 0x8000u);
+          } else {  // two fp32 pairs (a, b) -> (-b, a)
+            r.x = v[kc].y ^ 0x80000000u;
+            r.y = v[kc].x;
+            r.z = v[kc].w ^ 0x80000000u;
+            r.w = v[kc].z;
+          }
+          w0[kc * TILE + e + HALF] = r;
         }
-        w0[o + HALF] = r;
       }
       if (BF) {
-        // output chunk (kc, row, c) holds k = 8c .. 8c+7 of that row: FP32 chunks 2c and 2c+1 of the staged row
-        for (int e = et; e < KC * vrows * 4; e += NT) {
-          const int kc = e / (vrows * 4), rem = e - kc * vrows * 4, row = rem >> 2, c = rem & 3;
-          const float4* src = reinterpret_cast<const float4*>(sS(s, kc)) + row * 8;
-          const float4 f0 = src[(2 * c) ^ (row & 7)], f1 = src[(2 * c + 1) ^ (row & 7)];
-          uint4 o;
-          o.x = bf16x2_rn(f0.x, f0.y);
-          o.y = bf16x2_rn(f0.z, f0.w);
-          o.z = bf16x2_rn(f1.x, f1.y);
-          o.w = bf16x2_rn(f1.z, f1.w);
-          reinterpret_cast<uint4*>(sV(s, kc))[row * 4 + (c ^ ((row >> 1) & 3))] = o;
+        // output chunk (kc, row, c) holds k = 8c .. 8c+7 of that row: FP32 chunks 2c and 2c+1 of the staged row;
+        // a thread converts position (row, c) of all KC slabs
+        for (int u = et; u < vrows * 4; u += NT) {
+          const int row = u >> 2, c = u & 3;
+          float4 f[KC][2];
+#pragma unroll
+          for (int kc = 0; kc < KC; ++kc) {
+            const float4* src = reinterpret_cast<const float4*>(sS(s, kc)) + row * 8;
+            f[kc][0] = src[(2 * c) ^ (row & 7)];
+            f[kc][1] = src[(2 * c + 1) ^ (row & 7)];
+          }
+#pragma unroll
+          for (int kc = 0; kc < KC; ++kc) {
+            uint4 o;
+            if (BF == 2) {
+              o.x = f16x2_rn(f[kc][0].x, f[kc][0].y);
+              o.y = f16x2_rn(f[kc][0].z, f[kc][0].w);
+              o.z = f16x2_rn(f[kc][1].x, f[kc][1].y);
+              o.w = f16x2_rn(f[kc][1].z, f[kc][1].w);
+            } else {
+              o.x = bf16x2_rn(f[kc][0].x, f[kc][0].y);
+              o.y = bf16x2_rn(f[kc][0].z, f[kc][0].w);
+              o.z = bf16x2_rn(f[kc][1].x, f[kc][1].y);
+              o.w = bf16x2_rn(f[kc][1].z, f[kc][1].w);
+            }
+            reinterpret_cast<uint4*>(sV(s, kc))[row * 4 + (c ^ ((row >> 1) & 3))] = o;
+          }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> MMA reads
@@ -442,7 +471,9 @@ __device__ __forceinline__ int sw64_index(int n, int k) {
 }
 template <int BF>
 __device__ __forceinline__ void put_w(void* W, size_t tile, int rows, int n, int k, float v) {
-  if (BF)
+  if (BF == 2)
+    reinterpret_cast<__half*>(W)[tile * rows * 32 + sw64_index(n, k)] = __float2half_rn(v);
+  else if (BF == 1)
     reinterpret_cast<__nv_bfloat16*>(W)[tile * rows * 32 + sw64_index(n, k)] = __float2bfloat16_rn(v);
   else
     reinterpret_cast<float*>(W)[tile * rows * 32 + sw_index(n, k)] = v;
@@ -531,7 +562,9 @@ template <int MODE>
 void launch_tc_fmt(int bf, cudaStream_t st, const float2* vin, const void* W, float* out, const float* b, int Ls,
                    int nitems, int bmode, int color, int nrhs, const int* active, int* err, double bytes,
                    double flops) {
-  if (bf)
+  if (bf == 2)
+    launch_tc<MODE, 2>(st, vin, W, out, b, Ls, nitems, bmode, color, nrhs, active, err, bytes, flops);
+  else if (bf == 1)
     launch_tc<MODE, 1>(st, vin, W, out, b, Ls, nitems, bmode, color, nrhs, active, err, bytes, flops);
   else
     launch_tc<MODE, 0>(st, vin, W, out, b, Ls, nitems, bmode, color, nrhs, active, err, bytes, flops);
@@ -545,14 +578,18 @@ size_t tc_stencil_weight_bytes(int nsite, int bf) { return (size_t)nsite * 5 * 1
 size_t tc_blockinv_weight_bytes(int Ls, int bf) { return (size_t)(Ls / 2) * (Ls / 2) / 2 * 4 * 64 * 32 * (bf ? 2 : 4); }
 
 void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, void* W, int bf) {
-  if (bf)
+  if (bf == 2)
+    MG_LAUNCH(k_tc_stencil_weights<2>, 1024, 256, 0, st, st32, nsite, W);
+  else if (bf == 1)
     MG_LAUNCH(k_tc_stencil_weights<1>, 1024, 256, 0, st, st32, nsite, W);
   else
     MG_LAUNCH(k_tc_stencil_weights<0>, 1024, 256, 0, st, st32, nsite, W);
 }
 void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color, void* W, int bf) {
   const int nblk = (Ls / 2) * (Ls / 2) / 2;
-  if (bf)
+  if (bf == 2)
+    MG_LAUNCH(k_tc_blockinv_weights<2>, 1024, 256, 0, st, inv32, Ls, color, nblk, W);
+  else if (bf == 1)
     MG_LAUNCH(k_tc_blockinv_weights<1>, 1024, 256, 0, st, inv32, Ls, color, nblk, W);
   else
     MG_LAUNCH(k_tc_blockinv_weights<0>, 1024, 256, 0, st, inv32, Ls, color, nblk, W);

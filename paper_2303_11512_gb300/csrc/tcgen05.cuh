@@ -5,6 +5,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <mutex>
 
@@ -121,12 +122,21 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// instruction descriptor of kind::f16: D f32, A/B f16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
           dtmem),
       "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
+}
+// two floats as an fp16 pair (round to nearest even), the first in the low half
+__device__ __forceinline__ uint32_t f16x2_rn(float lo, float hi) {
+  const __half2 v = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 // two floats as a bf16 pair (round to nearest even), the first in the low half
 __device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {

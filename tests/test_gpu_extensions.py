@@ -129,7 +129,7 @@ def test_plain_hutchinson_gmres30(api, ctx):
         h.close()
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "tf32", "bf16", "fp16"])
 def test_vcycle_parity(api, ctx, h64, mode):
     """mg_vcycle against the oracle's V(1,1) cycle on the same (deterministic) hierarchy; with tensor cores
     the coarse level's SAP sweeps and the residual after pre-smoothing run as tcgen05 GEMMs (TF32 or BF16)."""
@@ -137,7 +137,7 @@ def test_vcycle_parity(api, ctx, h64, mode):
     hh = h
     if mode != "fp64":   # the same hierarchy without / with TF32 / with BF16 tensor-core coarse kernels
         hh = api.mg_setup(ctx, torch.from_numpy(U).cuda(), 64, m0, ntv=8, setup_sweeps=4, seed=3,
-                          tensor_cores={"fp32": 0, "tf32": 2, "bf16": 1}[mode])
+                          tensor_cores={"fp32": 0, "tf32": 2, "bf16": 1, "fp16": 3}[mode])
     try:
         rs = np.random.default_rng(3)
         b = rs.standard_normal((5, H.n[0])) + 1j * rs.standard_normal((5, H.n[0]))
@@ -149,7 +149,7 @@ def test_vcycle_parity(api, ctx, h64, mode):
         else:
             x = torch.empty((5, H.n[0]), dtype=torch.complex64, device="cuda")
             hh.vcycle(0, torch.from_numpy(b.astype(np.complex64)).cuda(), x, api.FP32)
-            tol = {"fp32": 2e-5, "tf32": 5e-3, "bf16": 2e-2}[mode]
+            tol = {"fp32": 2e-5, "tf32": 5e-3, "bf16": 2e-2, "fp16": 5e-3}[mode]
         err = relerr(x.cpu().numpy(), ref)
         assert err < tol, err
         assert hh.tc_status() == 0

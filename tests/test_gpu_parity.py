@@ -178,14 +178,18 @@ def test_level_operators_and_transfers(api, ctx):
             assert relerr(xf.cpu().numpy(), (P @ v.T).T) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
+TC_MODE = {"tf32": 2, "bf16": 1, "fp16": 3}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "fp16"])
 def test_smoother_parity(api, ctx, prec):
-    """SAP sweeps (the smoother of the V-cycle) against the oracle's SAP on the same level operator; TF32 and
-    BF16 tensor-core sweeps on the coarse levels (BF16: 8-bit significands, FP32 accumulation)."""
-    h, H = hierarchies(api, ctx, 64, tensor_cores=1 if prec == "bf16" else 2)
-    tol = {"fp64": 1e-12, "fp32": 2e-5, "tf32": 5e-3, "bf16": 2e-2}[prec]
+    """SAP sweeps (the smoother of the V-cycle) against the oracle's SAP on the same level operator; TF32, BF16
+    and FP16 tensor-core sweeps on the coarse levels (BF16: 8-bit significands; TF32 and FP16: 11-bit; FP32
+    accumulation)."""
+    h, H = hierarchies(api, ctx, 64, tensor_cores=TC_MODE.get(prec, 2))
+    tol = {"fp64": 1e-12, "fp32": 2e-5, "tf32": 5e-3, "bf16": 2e-2, "fp16": 5e-3}[prec]
     for l in range(H.levels - 1):
-        if prec in ("tf32", "bf16") and l == 0:
+        if prec in TC_MODE and l == 0:
             continue  # tensor-core smoother runs on coarse levels
         f = rand_vecs(H.n[l], 3, 40 + l)
         x0 = rand_vecs(H.n[l], 3, 50 + l)
@@ -194,25 +198,25 @@ def test_smoother_parity(api, ctx, prec):
         dt = np.complex128 if prec == "fp64" else np.complex64
         xd = cuda(x0.astype(dt))
         h.smooth(l, cuda(f.astype(dt)), xd, {"fp64": api.FP64, "fp32": api.FP32, "tf32": api.TF32,
-                                             "bf16": api.BF16}[prec], 2)
+                                             "bf16": api.BF16, "fp16": api.FP16}[prec], 2)
         err = relerr(xd.cpu().numpy(), ref)
         assert err < tol, (l, err)
     assert h.tc_status() == 0
 
 
-@pytest.mark.parametrize("fmt", ["tf32", "bf16"])
+@pytest.mark.parametrize("fmt", ["tf32", "bf16", "fp16"])
 def test_tensor_core_stencil(api, ctx, fmt):
-    """tcgen05 coarse stencil (TF32 or BF16 operands, FP32 accumulation) against the oracle's Galerkin
+    """tcgen05 coarse stencil (TF32, BF16 or FP16 operands, FP32 accumulation) against the oracle's Galerkin
     operator; ragged rhs counts."""
-    h, H = hierarchies(api, ctx, 64, tensor_cores=2 if fmt == "tf32" else 1)
+    h, H = hierarchies(api, ctx, 64, tensor_cores=TC_MODE[fmt])
     for l in range(1, H.levels):
         for nrhs in (1, 37, 130):
             x = rand_vecs(H.n[l], nrhs, 60 + nrhs)
             ref = (H.D[l] @ x.T).T
             y = torch.zeros((nrhs, H.n[l]), dtype=torch.complex64, device="cuda")
-            h.apply(l, cuda(x.astype(np.complex64)), y, api.TF32 if fmt == "tf32" else api.BF16)
+            h.apply(l, cuda(x.astype(np.complex64)), y, {"tf32": api.TF32, "bf16": api.BF16, "fp16": api.FP16}[fmt])
             err = relerr(y.cpu().numpy(), ref)
-            assert err < (5e-3 if fmt == "tf32" else 2e-2), (l, nrhs, err)
+            assert err < (2e-2 if fmt == "bf16" else 5e-3), (l, nrhs, err)
     assert h.tc_status() == 0
 
 
