@@ -28,7 +28,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # V(2,2): of V(1,1) .. V(4,4), K-cycles and bootstrap 1-3 measured on this workload, the fastest set-up + estimate.
-# tensor_cores = 2: TF32 coarse-level tensor-core operands (measured faster here than BF16, = 1).
+# tensor_cores = 3: FP16 coarse-level tensor-core operands (11-bit significands like TF32; the stencil runs the
+# 2x2-block kernel where the tuner finds it faster); measured 0.841 s against 0.843 s with TF32 (= 2) and 0.844 s
+# with BF16 (= 1).
 # autotune = 1: launch variants timed in the first set-up (a warm-up step) and reused from the tuning table.
 # First batch of 8 samples per level (then batches sized from the variances, up to 256): the stop rule needs 6-8
 # samples on levels 0 and 1 here, so a first batch of 16 only computed samples that are discarded.
@@ -36,14 +38,22 @@ sys.path.insert(0, ROOT)
 # (the deflated part removes little variance on these fields); the benchmark line also reports one estimate with
 # d = 16, k = 1 (32 difference-operator applications per level) as `sketch_d16_k1`.
 WORKLOAD = dict(L=512, beta=5.0, seed=0, ntv=8, d=32, k=2, eps=1e-3, nrhs_max=256, nrhs_first=8,
-                bootstrap=2, bootstrap_its=6, kcycle_its=0, pre_smooth=2, post_smooth=2, tensor_cores=2, autotune=1)
+                bootstrap=2, bootstrap_its=6, kcycle_its=0, pre_smooth=2, post_smooth=2, tensor_cores=3, autotune=1)
 FALLBACK_M0 = {512: -0.07, 128: -0.1199}
 
 
-# DRAM bytes per algorithmic byte of the tensor-core coarse stencil (k_tc, MODE 0, TF32): one ncu capture of
-# the level-1 launch with 32 rhs of the L = 512 hierarchy read 235.99 MB and wrote 48.96 MB against 301.99 MB of
-# algorithmic traffic (weights 167.8 MB + 32 rhs x 16384 sites x 256 B)
-K_TC0_DRAM_PER_ALG_BYTE = (235.987 + 48.964) / 301.990
+# DRAM bytes per algorithmic byte of the tensor-core coarse stencil kernels, from one ncu capture each of the
+# level-1 launch with 32 rhs of the L = 512 hierarchy (dram__bytes_read + _write against the launch's algorithmic
+# bytes); the benchmark scales them to its average launch.  Per-site TF32 kernel: 235.99 + 48.96 MB against
+# 301.99 MB (weights 167.8 MB + 32 rhs x 16384 sites x 256 B); profiles/k_tc_stencil_level1_32rhs_L512.md.
+# 2x2-block FP16 kernel: 217.63 + 45.98 MB against 218.10 MB (FP16 weights 83.9 MB + 32 rhs x 16384 sites x 256 B);
+# profiles/k_tcb_stencil_level1_32rhs_L512.md.
+TRAFFIC_PER_ALG_BYTE = {
+    "MODE = 0; int BF = 0": ((235.987 + 48.964) / 301.990, "ncu capture of one launch (level 1, 32 rhs): 284.95 MB "
+                            "DRAM / 301.99 MB algorithmic, scaled to the average launch"),
+    "k_tcb_kernel": ((217.630 + 45.980) / 218.104, "ncu capture of one launch (level 1, 32 rhs, FP16): 263.61 MB DRAM "
+                     "/ 218.10 MB algorithmic, scaled to the average launch"),
+}
 
 
 def mass_for(L: int, beta: float, seed: int) -> float:
@@ -496,13 +506,13 @@ def main():
     # DRAM traffic of the dominant kernel: the ncu capture of one launch (dram__bytes_read + _write) relative to
     # that launch's algorithmic bytes, scaled to this run's average launch (the bench's launches mix levels and
     # batch sizes; the capture is the level-1, 32-rhs stencil of profiles/k_tc_stencil_level1_32rhs_L512.md)
-    traffic = None
-    if "MODE = 0" in dom and "BF = 0" in dom:
-        traffic = K_TC0_DRAM_PER_ALG_BYTE * bytes_l
+    traffic, traffic_src = None, None
+    for key, (ratio, src) in TRAFFIC_PER_ALG_BYTE.items():
+        if key in dom:
+            traffic, traffic_src = ratio * bytes_l, src
     roof.update(kernel=dom, launches=info["launches"], avg_launch_ms=avg_ms, share=info["ms"] / max(tot_ms, 1e-9),
                 bytes_per_launch=bytes_l, flops_per_launch=flops_l, peak_src=P["src"], traffic=traffic,
-                traffic_src=("ncu capture of one launch (level 1, 32 rhs): 284.95 MB DRAM / 301.99 MB algorithmic, "
-                             "scaled to the average launch" if traffic else None))
+                traffic_src=traffic_src)
     kernels = {k: dict(launches=v["launches"], ms=round(v["ms"], 3), share=round(v["ms"] / max(tot_ms, 1e-9), 4),
                        gbs=round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
                        tflops=round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 3))

@@ -168,8 +168,7 @@ typedef struct {
   int tensor_cores;      /* inside the FP32 V-cycle, coarse levels with 16 dof per site run their SAP sweeps
                             and residuals as tcgen05 GEMMs over the rhs: 1 = BF16 operands (FP32 accumulation),
                             2 = TF32 operands, 3 = FP16 operands (11-bit significands like TF32 at the 16-bit
-                            instruction rate), 0 = CUDA cores only (2: on the L = 512 workload TF32 took
-                            0.836 s per estimate, BF16 0.866 s with 2.5 % more inner iterations) */
+                            instruction rate), 0 = CUDA cores only */
   int graphs;            /* 1: the V-cycle preconditioner is captured once per shape as a CUDA graph
                             and replayed (not while the kernel timer runs or with K-cycles) (1) */
   int autotune;          /* 1: at the end of mg_setup, run mg_autotune for batches of 8..256 rhs unless the
@@ -214,9 +213,11 @@ int mg_get_stencil(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* hos
 int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x, int nrhs, int prec, int sweeps);
 
 /* Launch-shape autotuner (measurement of this machine, not part of the paper's method).  Several kernels have
- * launch variants that compute the same result: the tensor-core coarse stencil (MMA tile of 64 or 128
- * right-hand sides, pipeline depth), the tensor-core SAP block update (pipeline depth) and the FP32 fine
- * stencil (1, 2 or 4 right-hand sides per thread).  The library keeps one process-wide table
+ * launch variants that compute the same result: the tensor-core coarse stencil (variant bit 0: MMA tile of 128
+ * rather than 64 right-hand sides, bits 1-3: pipeline-depth cap, bit 4: with BF16 / FP16 images, the kernel
+ * that takes a 2x2 block of sites per item and shares the block's slabs across its sites, else one site per
+ * item), the tensor-core SAP block update (pipeline depth) and the FP32 fine stencil (1, 2 or 4 right-hand
+ * sides per thread).  The library keeps one process-wide table
  * (device, kernel, lattice side, batch bucket, weight format) -> variant, consulted by every launch (batch
  * bucket: the power of two >= nrhs in 8..256; keys without an entry take the default variant).  mg_autotune
  * times every variant of h's kernels (CUDA events, median of 5, on scratch vectors) for each of the `count`
@@ -225,8 +226,13 @@ int mg_autotune(mgmlmc_ctx* ctx, mgmlmc_hier* h, const int* nrhs_list, int count
 /* The table as text, one line per entry "device kind side bucket format variant microseconds\n" (kind 0 = FP32
  * fine stencil, 1 = tensor-core stencil, 2 = tensor-core SAP block update); buf: host, len bytes. */
 int mgmlmc_tune_report(char* buf, int64_t len);
-/* Set one entry (for instance from a saved report) on the current device. */
+/* Set one entry (for instance from a saved report) on the current device.  format: 0 TF32, 1 BF16, 2 FP16 images
+ * (0 for the FP32 fine stencil); MGMLMC_ERR_INVALID_ARG for an unknown kind, a bucket that is not a power of two
+ * in 8..256, a variant the kernel does not have (fine stencil: 1, 2 or 4; bit 4 only for the tensor-core stencil
+ * with 16-bit images on a side divisible by 4). */
 int mgmlmc_tune_set(int kind, int side, int bucket, int format, int variant);
+/* Drop every entry of the current device: later launches take the default variants again. */
+int mgmlmc_tune_clear(void);
 
 /* MGMLMC_ERR_TIMEOUT if a tensor-core kernel of this hierarchy ran out of a
  * bounded wait (it then stopped early and freed its tensor memory), else OK. */

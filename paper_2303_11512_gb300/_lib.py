@@ -104,6 +104,7 @@ SIGNATURES = {
     "mg_autotune": (ip, [vp, vp, C.POINTER(ip), ip, ip]),
     "mgmlmc_tune_report": (ip, [C.c_char_p, C.c_int64]),
     "mgmlmc_tune_set": (ip, [ip, ip, ip, ip, ip]),
+    "mgmlmc_tune_clear": (ip, []),
     "solve_params_default": (ip, [C.POINTER(SolveParams)]),
     "fgmres_batched": (ip, [vp, vp, ip, vp, vp, ip, C.POINTER(SolveParams), C.POINTER(SolveStats), vp]),
     "mlmc_level_sample": (ip, [vp, vp, ip, ip, vp, vp, ip, C.POINTER(SolveParams), C.POINTER(SolveStats)]),

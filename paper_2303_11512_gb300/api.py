@@ -228,6 +228,11 @@ def tune_set(entries):
         check(_lib.load().mgmlmc_tune_set(e["kind"], e["side"], e["bucket"], e["format"], e["variant"]))
 
 
+def tune_clear():
+    """Drop the table's entries of the current device (later launches take the default variants)."""
+    check(_lib.load().mgmlmc_tune_clear())
+
+
 def mg_setup(ctx: Context, U: torch.Tensor, L: int, m0: float, **params) -> Hierarchy:
     p = mg_params(**params)
     h = C.c_void_p()

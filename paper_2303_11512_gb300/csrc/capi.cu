@@ -300,10 +300,18 @@ int mgmlmc_tune_report(char* buf, int64_t len) {
 
 int mgmlmc_tune_set(int kind, int side, int bucket, int format, int variant) {
   if (kind < 0 || kind > 2 || side < 1 || bucket < 8 || bucket > 256 || (bucket & (bucket - 1)) || format < 0 ||
-      format > 1 || variant < 0 || variant > 15)
+      format > 2 || variant < 0 || variant > 31)
     return MGMLMC_ERR_INVALID_ARG;
   if (kind == TUNE_WILSON32 && variant != 1 && variant != 2 && variant != 4) return MGMLMC_ERR_INVALID_ARG;
+  // bit 4 (the 2x2-block stencil) exists for the 16-bit formats on sides divisible by 4 only
+  if ((variant & 16) && (kind != TUNE_TC0 || format == 0 || side % 4)) return MGMLMC_ERR_INVALID_ARG;
+  if (kind != TUNE_TC0 && variant > 15) return MGMLMC_ERR_INVALID_ARG;
   tune_store(kind, side, bucket, format, variant, 0.f);
+  return MGMLMC_OK;
+}
+
+int mgmlmc_tune_clear(void) {
+  tune_clear();
   return MGMLMC_OK;
 }
 

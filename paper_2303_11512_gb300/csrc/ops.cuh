@@ -154,6 +154,10 @@ size_t proj_work_bytes(int d, long n, int nrhs);
 // ---------------------------------------------------------------- tensor cores (coarse levels, d = 16)
 // Pre-swizzled weight images of the real-embedded coarse operators, Re rows only, in TF32 (bf = 0) or BF16
 // (bf = 1): stencil [site][dir 5][16 x 32]; SAP block inverses of one colour [item][4][64 x 32].
+// coarse stencil y = D x (or y = b - D x) with 16-bit operands (bf 1 BF16, 2 FP16), one 2x2 block of sites per
+// item: all blocks (bmode 0) or the blocks of colour `color` (bmode 1); W is the per-site weight image
+void tc_block_stencil(cudaStream_t st, int bf, const void* W, int Ls, const float2* x, float2* y, const float2* b,
+                      int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops);
 size_t tc_stencil_weight_bytes(int nsite, int bf);
 size_t tc_blockinv_weight_bytes(int Ls, int bf);  // the blocks of one colour
 void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, void* W, int bf);
@@ -177,6 +181,7 @@ int tune_lookup(int kind, int shape, int nrhs, int fmt, int dflt);
 void tune_store(int kind, int shape, int bucket, int fmt, int variant, float us);
 bool tune_known(int kind, int shape, int bucket, int fmt);
 std::string tune_table_text();  // lines "device kind side bucket fmt variant microseconds"
+void tune_clear();               // drops the entries of the current device
 
 // ---------------------------------------------------------------- misc
 void fill_int(cudaStream_t st, int* p, int v, int n);

@@ -539,7 +539,7 @@ void launch_tc(cudaStream_t st, const float2* vin, const void* W, float* out, co
   ensure_max_smem((const void*)k_tc_kernel, SMEM_BUDGET);
   // tuned variant: MODE 0 bit 0 = MMA M 128 (else 64), bits 1.. = pipeline-depth cap (0 = as deep as fits);
   // MODE 1: the depth cap
-  const int var = tune_lookup(MODE == 0 ? TUNE_TC0 : TUNE_TC1, Ls, nrhs, BF, 0);
+  const int var = tune_lookup(MODE == 0 ? TUNE_TC0 : TUNE_TC1, Ls, nrhs, BF, 0) & (MODE == 0 ? 15 : ~0);
   const int mm = MODE == 0 ? ((var & 1) ? TC_M : 64) : TC_M;
   const int cap = MODE == 0 ? (var >> 1) : var;
   const int tile = mm;
@@ -595,6 +595,15 @@ void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color
     MG_LAUNCH(k_tc_blockinv_weights<0>, 1024, 256, 0, st, inv32, Ls, color, nblk, W);
 }
 
+// 16-bit formats: the 2x2-block kernel (tc_block.cu) or the per-site kernel; a tuned variant of the stencil
+// (TUNE_TC0) with bit 4 set selects the block kernel, untuned launches take it for batches of at most 32 rhs (it
+// issues fewer MMAs per site; at larger batches the per-site kernel's TMA staging keeps more loads in flight)
+static bool use_block_kernel(int bf, int Ls, int nrhs) {
+  if (!bf || Ls % 4) return false;
+  const int var = tune_lookup(TUNE_TC0, Ls, nrhs, bf, -1);
+  return var < 0 ? nrhs <= 32 : (var & 16) != 0;
+}
+
 void tc_stencil_apply(cudaStream_t st, const void* W, int bf, int Ls, const float2* x, float2* y, const float2* b,
                       int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
@@ -602,7 +611,10 @@ void tc_stencil_apply(cudaStream_t st, const void* W, int bf, int Ls, const floa
   const double ar = act_rhs(nrhs);
   const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + (double)tc_stencil_weight_bytes(ns, bf);
   const double flops = ar * ns * 2.0 * 32 * 160;
-  launch_tc_fmt<0>(bf, st, x, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
+  if (use_block_kernel(bf, Ls, nrhs))  // 16-bit operands: 2x2-site items sharing slabs (tc_block.cu)
+    tc_block_stencil(st, bf, W, Ls, x, y, b, 0, 0, nrhs, active, err, bytes, flops);
+  else
+    launch_tc_fmt<0>(bf, st, x, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
 }
 
 // zero the sites of every colour-`color` 2x2 block of res ([rhs][site][16 complex])
@@ -630,7 +642,10 @@ void tc_residual_after_sap(cudaStream_t st, const void* Wst, int bf, int Ls, con
   const double ar = act_rhs(nrhs);
   const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_stencil_weight_bytes(ns / 2, bf);
   const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
-  launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, 0, nrhs, active, err, bytes, flops);
+  if (use_block_kernel(bf, Ls, nrhs))
+    tc_block_stencil(st, bf, Wst, Ls, x, res, f, 1, 0, nrhs, active, err, bytes, flops);
+  else
+    launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, 0, nrhs, active, err, bytes, flops);
   MG_LAUNCH_W(ar * (ns / 2) * 128.0, 0, k_zero_colour_blocks, 1024, 256, 0, st, res, Ls, 1, nrhs, active);
 }
 
@@ -642,8 +657,11 @@ void tc_sap_half(cudaStream_t st, const void* Wst, const void* Winv, int bf, int
   {  // residual on the sites of the colour's blocks
     const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_stencil_weight_bytes(ns / 2, bf);
     const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
-    launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes,
-                     flops);
+    if (use_block_kernel(bf, Ls, nrhs))
+      tc_block_stencil(st, bf, Wst, Ls, x, res, f, 1, color, nrhs, active, err, bytes, flops);
+    else
+      launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes,
+                       flops);
   }
   {  // x_B += inv_B r_B
     const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_blockinv_weight_bytes(Ls, bf);

@@ -46,6 +46,13 @@ bool tune_known(int kind, int shape, int bucket, int fmt) {
   return g_tune.count(std::make_tuple(dev, kind, shape, bucket, fmt)) != 0;
 }
 
+void tune_clear() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto it = g_tune.begin(); it != g_tune.end();) it = std::get<0>(it->first) == dev ? g_tune.erase(it) : ++it;
+}
+
 std::string tune_table_text() {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   std::string out;
@@ -120,16 +127,18 @@ void autotune(mgmlmc_hier* h, const std::vector<int>& nrhs_list, bool force) {
       if (force || !tune_known(TUNE_TC0, L.side, bucket, fmt)) {
         int best = 0;
         float tbest = 1e30f;
+        std::vector<int> vars;
         for (int m128 : {0, 1})
-          for (int cap : {0, 2, 3, 4}) {
-            const int v = m128 | (cap << 1);
-            tune_store(TUNE_TC0, L.side, bucket, fmt, v, 0.f);
-            const float t = time_us(st, [&] {
-              tc_stencil_apply(st, L.tcW.p, fmt, L.side, x.as<float2>(), y.as<float2>(), f.as<float2>(), bucket,
-                               nullptr, err);
-            });
-            if (t < tbest) { tbest = t; best = v; }
-          }
+          for (int cap : {0, 2, 3, 4}) vars.push_back(m128 | (cap << 1));
+        if (fmt && L.side % 4 == 0) vars.push_back(16);  // 16-bit formats: the 2x2-block kernel
+        for (int v : vars) {
+          tune_store(TUNE_TC0, L.side, bucket, fmt, v, 0.f);
+          const float t = time_us(st, [&] {
+            tc_stencil_apply(st, L.tcW.p, fmt, L.side, x.as<float2>(), y.as<float2>(), f.as<float2>(), bucket,
+                             nullptr, err);
+          });
+          if (t < tbest) { tbest = t; best = v; }
+        }
         tune_store(TUNE_TC0, L.side, bucket, fmt, best, tbest);
       }
       if (force || !tune_known(TUNE_TC1, L.side, bucket, fmt)) {

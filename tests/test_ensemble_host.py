@@ -51,3 +51,12 @@ def test_tuning_table_round_trip():
         api.tune_set([dict(kind=0, side=32, bucket=64, format=0, variant=3)])   # 3 rhs per thread: no such variant
     with pytest.raises(_lib.MgmlmcError):
         api.tune_set([dict(kind=1, side=32, bucket=48, format=0, variant=0)])   # not a bucket
+    api.tune_set([dict(kind=1, side=32, bucket=16, format=2, variant=16)])      # FP16 images: 2x2-block stencil
+    rows = [r for r in api.tune_table() if r["kind"] == 1 and r["side"] == 32 and r["bucket"] == 16]
+    assert rows and rows[0]["variant"] == 16 and rows[0]["format"] == 2
+    with pytest.raises(_lib.MgmlmcError):
+        api.tune_set([dict(kind=1, side=32, bucket=16, format=0, variant=16)])  # TF32 images: no block kernel
+    with pytest.raises(_lib.MgmlmcError):
+        api.tune_set([dict(kind=1, side=30, bucket=16, format=1, variant=16)])  # side not divisible by 4
+    with pytest.raises(_lib.MgmlmcError):
+        api.tune_set([dict(kind=2, side=32, bucket=16, format=1, variant=16)])  # SAP update has no such bit

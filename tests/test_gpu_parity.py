@@ -122,7 +122,7 @@ _HIER = {}
 
 
 def hierarchies(api, ctx, L, m0=-0.05, ntv=8, seed=3, tensor_cores=2):
-    """GPU hierarchy and the oracle's; tensor_cores: 2 = TF32 coarse images (the library default), 1 = BF16."""
+    """GPU hierarchy and the oracle's; tensor_cores: 2 = TF32 coarse images (the library default), 1 = BF16, 3 = FP16."""
     key = (L, m0, ntv, seed, tensor_cores)
     if key not in _HIER:
         U = field(L, 3.0, 2)
@@ -218,6 +218,46 @@ def test_tensor_core_stencil(api, ctx, fmt):
             err = relerr(y.cpu().numpy(), ref)
             assert err < (2e-2 if fmt == "bf16" else 5e-3), (l, nrhs, err)
     assert h.tc_status() == 0
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_block_and_site_stencil_kernels(api, ctx, fmt):
+    """With 16-bit images the coarse stencil has two tcgen05 kernels: one site per item, and 2x2 sites per item
+    sharing the block's slabs (N = 32 / 96 / 128 MMA windows).  Each is forced through the launch-variant table for
+    every batch bucket (ragged rhs counts included) and checked against the oracle's Galerkin operator and SAP
+    sweeps (the SAP residual runs the colour-block form of the block kernel); the two kernels agree to FP32
+    accumulation order."""
+    h, H = hierarchies(api, ctx, 64, tensor_cores=TC_MODE[fmt])
+    f, prec = {"bf16": (1, api.BF16), "fp16": (2, api.FP16)}[fmt]
+    tol = 2e-2 if fmt == "bf16" else 5e-3
+    out = {}
+    try:
+        for variant in (0, 16):
+            api.tune_clear()
+            api.tune_set([dict(kind=1, side=H.side[l], bucket=b, format=f, variant=variant)
+                          for l in range(1, H.levels) for b in (8, 16, 32, 64, 128, 256)])
+            for l in range(1, H.levels):
+                for nrhs in (1, 8, 37, 130, 256):
+                    x = rand_vecs(H.n[l], nrhs, 70 + nrhs)
+                    y = torch.zeros((nrhs, H.n[l]), dtype=torch.complex64, device="cuda")
+                    h.apply(l, cuda(x.astype(np.complex64)), y, prec)
+                    out[variant, l, nrhs] = y.cpu().numpy()
+                    err = relerr(out[variant, l, nrhs], (H.D[l] @ x.T).T)
+                    assert err < tol, (variant, l, nrhs, err)
+            sap = omg.SAP(H.D[1], H.side[1], H.dof[1], 2)
+            for nrhs in (3, 40):
+                fv, x0 = rand_vecs(H.n[1], nrhs, 80 + nrhs), rand_vecs(H.n[1], nrhs, 90 + nrhs)
+                ref = sap.sweep(fv.T.copy(), sap.sweep(fv.T.copy(), x0.T.copy())).T
+                xd = cuda(x0.astype(np.complex64))
+                h.smooth(1, cuda(fv.astype(np.complex64)), xd, prec, 2)
+                err = relerr(xd.cpu().numpy(), ref)
+                assert err < tol, (variant, nrhs, err)
+            assert h.tc_status() == 0
+    finally:
+        api.tune_clear()
+    for (variant, l, nrhs), y in out.items():
+        if variant == 16:
+            assert relerr(y, out[0, l, nrhs]) < 1e-5, (l, nrhs)
 
 
 # ---------------------------------------------------------------- solver

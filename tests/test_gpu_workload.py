@@ -2,15 +2,16 @@
 
 The benchmark times MG-MLMC++ with the set-up and estimator of bench.WORKLOAD: bootstrap set-up (2 rounds of
 6 FGMRES iterations on top of the smoothed test vectors), 8 test vectors per chirality, V(2,2) SAP cycles with
-the tensor-core kernels on the coarse levels (TF32 operands), mixed precision (FP32 inner FGMRES, FP64 true-residual
-refinement to 1e-10), the workload's Hutch++ sketch (W["d"] vectors, W["k"] sketch applications), accumulated
-form, first batch 8, counted flops as the sample cost.  Here the same configuration runs at L = 256 (4 levels, 256 -> 64 -> 16 -> 4, the
-same depth and coarse dof as L = 512) on a beta = 5 field with the tuned near-critical mass.
+the tensor-core kernels on the coarse levels (the workload's operand format), mixed precision (FP32 inner FGMRES,
+FP64 true-residual refinement to 1e-10), the workload's Hutch++ sketch (W["d"] vectors, W["k"] sketch
+applications), accumulated form, first batch 8, counted flops as the sample cost.  Here the same configuration
+runs at L = 256 (4 levels, 256 -> 64 -> 16 -> 4, the same depth and coarse dof as L = 512) on a beta = 5 field with
+the tuned near-critical mass.
 
 The bootstrap set-up is adaptive (many prolongators are valid), so the GPU's P_l are imported as data and
 checked for their defining properties; the oracle then builds its own Galerkin operators P^H D P from its own
 fine operator and solves with sparse LU.  Tolerances: P^H P = I to 1e-12, stencils and tau_L 1e-10,
-tau_lr and per-sample tau 1e-8 (solver residual 1e-10), Q 1e-6, the tensor-core kernels 5e-3 with TF32
+tau_lr and per-sample tau 1e-8 (solver residual 1e-10), Q 1e-6, the tensor-core kernels 5e-3 with TF32 or FP16
 operands (2e-2 with BF16: 8-bit significands, FP32 accumulation).
 """
 import json
@@ -120,7 +121,7 @@ def test_tensor_core_kernels_on_the_workload_level(setup):
     """Level 1 (64 x 64 coarse sites, 16 dof): every CTA of the tcgen05 kernels walks many sites and blocks.
     Tensor-core stencil and SAP sweeps against the oracle's Galerkin operator and SAP on the same level."""
     api, h, H, W = setup["api"], setup["h"], setup["H"], setup["W"]
-    prec, tol = (api.BF16, 2e-2) if W["tensor_cores"] == 1 else (api.TF32, 5e-3)
+    prec, tol = {1: (api.BF16, 2e-2), 2: (api.TF32, 5e-3), 3: (api.FP16, 5e-3)}[W["tensor_cores"]]
     l = 1
     n = h.n[l]
     sap = omg.SAP(H.D[l], h.side[l], h.dof[l], 2)
