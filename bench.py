@@ -46,13 +46,9 @@ FALLBACK_M0 = {512: -0.07, 128: -0.1199}
 # level-1 launch with 32 rhs of the L = 512 hierarchy (dram__bytes_read + _write against the launch's algorithmic
 # bytes); the benchmark scales them to its average launch.  Per-site TF32 kernel: 235.99 + 48.96 MB against
 # 301.99 MB (weights 167.8 MB + 32 rhs x 16384 sites x 256 B); profiles/k_tc_stencil_level1_32rhs_L512.md.
-# 2x2-block FP16 kernel: 217.63 + 45.98 MB against 218.10 MB (FP16 weights 83.9 MB + 32 rhs x 16384 sites x 256 B);
-# profiles/k_tcb_stencil_level1_32rhs_L512.md.
 TRAFFIC_PER_ALG_BYTE = {
     "MODE = 0; int BF = 0": ((235.987 + 48.964) / 301.990, "ncu capture of one launch (level 1, 32 rhs): 284.95 MB "
                             "DRAM / 301.99 MB algorithmic, scaled to the average launch"),
-    "k_tcb_kernel": ((217.630 + 45.980) / 218.104, "ncu capture of one launch (level 1, 32 rhs, FP16): 263.61 MB DRAM "
-                     "/ 218.10 MB algorithmic, scaled to the average launch"),
 }
 
 
@@ -270,7 +266,15 @@ def profile_case(args):
                          bootstrap_its=W["bootstrap_its"], pre_smooth=W["pre_smooth"], post_smooth=W["post_smooth"],
                          tensor_cores=W["tensor_cores"])
         lv = args.profile_level
-        if args.profile_case == "coarse":
+        if args.profile_case == "smooth":
+            # ten tensor-core SAP sweeps on level lv (block stencil residuals and block-inverse updates)
+            prec = {1: api.BF16, 3: api.FP16}.get(W["tensor_cores"], api.TF32)
+            f = torch.randn((args.profile_nrhs, h.n[lv]), dtype=torch.complex64, device="cuda")
+            x = torch.zeros_like(f)
+            h.smooth(lv, f, x, prec, 10)
+            ns = h.side[lv] ** 2
+            print("sites", ns, "blocks per colour", ns // 8)
+        elif args.profile_case == "coarse":
             # ten tensor-core stencil applications y = D_l x on level lv (no additive input, every rhs active)
             prec = {1: api.BF16, 3: api.FP16}.get(W["tensor_cores"], api.TF32)
             x = torch.randn((args.profile_nrhs, h.n[lv]), dtype=torch.complex64, device="cuda")
@@ -386,12 +390,12 @@ def main():
     ap.add_argument("--timing-filter", default="")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2, 3],
                     help="coarse-level tensor-core operands: 1 BF16, 2 TF32, 3 FP16, 0 CUDA cores (default: the workload's)")
-    ap.add_argument("--profile-case", choices=["solve", "stencil", "coarse", "nn"], default=None,
+    ap.add_argument("--profile-case", choices=["solve", "stencil", "coarse", "smooth", "nn"], default=None,
                     help="run one small case for an ncu capture instead of the benchmark: 'solve' = one mixed "
                          "FGMRES solve on --profile-level with --profile-nrhs rhs on the workload hierarchy, "
                          "'stencil' = ten FP32 fine-stencil applications to --profile-nrhs vectors, 'coarse' = ten "
-                         "tensor-core stencil applications on --profile-level, 'nn' = five forward applications "
-                         "of the learned preconditioner")
+                         "tensor-core stencil applications on --profile-level, 'smooth' = ten tensor-core SAP sweeps "
+                         "on --profile-level, 'nn' = five forward applications of the learned preconditioner")
     ap.add_argument("--profile-level", type=int, default=1)
     ap.add_argument("--profile-nrhs", type=int, default=64)
     ap.add_argument("--profile-bootstrap", type=int, default=WORKLOAD["bootstrap"],

@@ -242,9 +242,16 @@ int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y,
                  "(mg_params.tensor_cores: 1 BF16, 2 TF32, 3 FP16)");
     if (!tc) check_prec(prec);
     if (nrhs <= 0) return;
-    if (tc)
-      tc_stencil_apply(ctx->stream, h->lv[level].tcW.p, h->lv[level].tc_bf, h->lv[level].side, (const float2*)x,
-                       (float2*)y, nullptr, nrhs, nullptr, h->tc_err.as<int>());
+    if (tc) {
+      const LevelData& L = h->lv[level];
+      void* x16 = nullptr;
+      if (tc_block_selected(L.tc_bf, L.side, nrhs)) {  // the block stencil reads a 16-bit copy of x
+        x16 = h->work("ap_x16", level, sizeof(uint32_t) * L.n * nrhs);
+        tc_round16(ctx->stream, L.tc_bf, (const float2*)x, x16, L.side * L.side, nrhs);
+      }
+      tc_stencil_apply(ctx->stream, L.tcW.p, L.tc_bf, L.side, (const float2*)x, x16, (float2*)y, nullptr, nrhs,
+                       nullptr, h->tc_err.as<int>());
+    }
     else if (prec == MGMLMC_FP32)
       op_apply<float>(h, level, (const float2*)x, (float2*)y, nullptr, nrhs, nullptr);
     else

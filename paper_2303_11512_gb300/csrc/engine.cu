@@ -52,15 +52,19 @@ void op_apply(mgmlmc_hier* h, int l, const typename CT<R>::T* x, typename CT<R>:
 
 template <typename R>
 void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>::T* x, int nrhs,
-               const int* active) {
+               const int* active, void* x16) {
   const LevelData& L = h->lv[l];
   cudaStream_t st = h->ctx->stream;
   if (sizeof(R) == 8 && !L.sap64_ok) throw Error(MGMLMC_ERR_INVALID_ARG, "FP64 SAP inverse not built at this level");
   if constexpr (sizeof(R) == 4) {
     if (h->use_tc(l) && L.sap_bs == 2 && L.tcInv[0].p) {
       float2* res = (float2*)h->work("tc_res", l, sizeof(float2) * L.n * nrhs);
+      if (!x16 && tc_block_selected(L.tc_bf, L.side, nrhs)) {  // the block stencil reads a 16-bit copy of x
+        x16 = h->work("sap_x16", l, sizeof(uint32_t) * L.n * nrhs);
+        tc_round16(st, L.tc_bf, x, x16, L.side * L.side, nrhs);
+      }
       for (int color = 0; color < 2; ++color)
-        tc_sap_half(st, L.tcW.p, L.tcInv[color].p, L.tc_bf, L.side, f, x, res, color, nrhs, active,
+        tc_sap_half(st, L.tcW.p, L.tcInv[color].p, L.tc_bf, L.side, f, x, x16, res, color, nrhs, active,
                     h->tc_err.as<int>());
       return;
     }
@@ -100,15 +104,23 @@ void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T
   C* res = (C*)h->work(pr ? "vc_res64" : "vc_res32", l, sizeof(C) * L.n * nrhs);
   C* rc = (C*)h->work(pr ? "vc_rc64" : "vc_rc32", l, sizeof(C) * Lc.n * nrhs);
   C* ec = (C*)h->work(pr ? "vc_ec64" : "vc_ec32", l, sizeof(C) * Lc.n * nrhs);
+  // the 16-bit copy of e that the 2x2-block tensor-core stencil reads, kept up to date by every kernel that
+  // writes e below (SAP block updates, the coarse-grid correction)
+  void* e16 = nullptr;
+  if constexpr (sizeof(R) == 4) {
+    if (h->use_tc(l) && tc_block_selected(L.tc_bf, L.side, nrhs))
+      e16 = h->work("vc_e16", l, sizeof(uint32_t) * L.n * nrhs);
+  }
   vzero<C>(st, e, L.n, nrhs);
-  for (int s = 0; s < h->prm.pre_smooth; ++s) sap_sweep<R>(h, l, r, e, nrhs, active);
+  if (e16) MG_CUDA(cudaMemsetAsync(e16, 0, sizeof(uint32_t) * L.n * nrhs, st));
+  for (int s = 0; s < h->prm.pre_smooth; ++s) sap_sweep<R>(h, l, r, e, nrhs, active, e16);
   bool done = false;
   if constexpr (sizeof(R) == 4) {
     if (h->use_tc(l)) {  // res = r - D e on the tensor cores (preconditioner accuracy)
       if (h->prm.pre_smooth > 0 && L.sap_bs == 2 && L.tcInv[0].p)  // zero on the blocks the sweep solved last
-        tc_residual_after_sap(st, L.tcW.p, L.tc_bf, L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
+        tc_residual_after_sap(st, L.tcW.p, L.tc_bf, L.side, e, e16, res, r, nrhs, active, h->tc_err.as<int>());
       else
-        tc_stencil_apply(st, L.tcW.p, L.tc_bf, L.side, e, res, r, nrhs, active, h->tc_err.as<int>());
+        tc_stencil_apply(st, L.tcW.p, L.tc_bf, L.side, e, e16, res, r, nrhs, active, h->tc_err.as<int>());
       done = true;
     }
   }
@@ -119,12 +131,12 @@ void vcycle(mgmlmc_hier* h, int l, const typename CT<R>::T* r, typename CT<R>::T
                    nullptr, nullptr, nullptr);
   else
     vcycle<R>(h, l + 1, rc, ec, nrhs, active);
-  prolong_op<R>(st, P_of<R>(L), L.side, L.dof, h->prm.agg, h->prm.ntv, ec, e, true, nrhs, active);
-  for (int s = 0; s < h->prm.post_smooth; ++s) sap_sweep<R>(h, l, r, e, nrhs, active);
+  prolong_op<R>(st, P_of<R>(L), L.side, L.dof, h->prm.agg, h->prm.ntv, ec, e, true, nrhs, active, e16, L.tc_bf);
+  for (int s = 0; s < h->prm.post_smooth; ++s) sap_sweep<R>(h, l, r, e, nrhs, active, e16);
 }
 
-template void sap_sweep<float>(mgmlmc_hier*, int, const float2*, float2*, int, const int*);
-template void sap_sweep<double>(mgmlmc_hier*, int, const double2*, double2*, int, const int*);
+template void sap_sweep<float>(mgmlmc_hier*, int, const float2*, float2*, int, const int*, void*);
+template void sap_sweep<double>(mgmlmc_hier*, int, const double2*, double2*, int, const int*, void*);
 template void op_apply<float>(mgmlmc_hier*, int, const float2*, float2*, const float2*, int, const int*);
 template void op_apply<double>(mgmlmc_hier*, int, const double2*, double2*, const double2*, int, const int*);
 template void vcycle<float>(mgmlmc_hier*, int, const float2*, float2*, int, const int*);

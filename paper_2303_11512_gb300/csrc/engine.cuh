@@ -132,9 +132,12 @@ struct LaunchScope {
 
 void build_hierarchy(mgmlmc_ctx* ctx, mgmlmc_hier* h, const double2* U);
 
-// One SAP sweep (colour 0 then 1) for D_l x = f.
+// One SAP sweep (colour 0 then 1) for D_l x = f.  x16: the planar 16-bit copy of x that the tensor-core sweep
+// keeps up to date where the 2x2-block stencil is selected (tc_block_selected); nullptr makes the sweep derive
+// one from x first.
 template <typename R>
-void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>::T* x, int nrhs, const int* active);
+void sap_sweep(mgmlmc_hier* h, int l, const typename CT<R>::T* f, typename CT<R>::T* x, int nrhs, const int* active,
+               void* x16 = nullptr);
 // Batched flexible GMRES(m) in precision R, x0 = 0; see engine.cu.
 template <typename R>
 void fgmres_core(mgmlmc_hier* h, int l, const typename CT<R>::T* b, typename CT<R>::T* x, int nrhs, int m,

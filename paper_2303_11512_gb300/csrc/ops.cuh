@@ -50,7 +50,7 @@ void restrict_op(cudaStream_t st, const typename CT<R>::T* P, int Ls, int d, int
 template <typename R>
 void prolong_op(cudaStream_t st, const typename CT<R>::T* P, int Ls, int d, int agg, int ntv,
                 const typename CT<R>::T* xc, typename CT<R>::T* xf, bool add, int nrhs,
-                const int* active);
+                const int* active, void* xf16 = nullptr, int bf = 0);  // xf16: planar 16-bit copy of xf (d 16)
 // gather test-vector blocks from V[m][n] into P layout
 void gather_tv_blocks(cudaStream_t st, const double2* V, int Ls, int d, int agg, int ntv, double2* P);
 // orthonormalise every (aggregate, chirality) block of P (bsz x ntv): QR with real positive diag
@@ -152,26 +152,42 @@ void proj_coeffs(cudaStream_t st, const double2* Q, int d, const double2* x, lon
 size_t proj_work_bytes(int d, long n, int nrhs);
 
 // ---------------------------------------------------------------- tensor cores (coarse levels, d = 16)
-// Pre-swizzled weight images of the real-embedded coarse operators, Re rows only, in TF32 (bf = 0) or BF16
-// (bf = 1): stencil [site][dir 5][16 x 32]; SAP block inverses of one colour [item][4][64 x 32].
+// Pre-swizzled weight images of the real-embedded coarse operators, Re rows only, in TF32 (bf = 0, K in the
+// interleaved Re/Im order of the FP32 vectors) or BF16 / FP16 (bf = 1 / 2, planar K: 16 Re then 16 Im parts per
+// site): stencil [site][dir 5][16 x 32]; SAP block inverses of one colour [item][4][64 x 32].
+// The 16-bit copy x16 of a coarse FP32 vector x ([rhs][site][16 complex]) is [rhs][site][16 Re | 16 Im] in the
+// operand format, rounded to nearest even; the 2x2-block stencil reads it by TMA.
 // coarse stencil y = D x (or y = b - D x) with 16-bit operands (bf 1 BF16, 2 FP16), one 2x2 block of sites per
-// item: all blocks (bmode 0) or the blocks of colour `color` (bmode 1); W is the per-site weight image
-void tc_block_stencil(cudaStream_t st, int bf, const void* W, int Ls, const float2* x, float2* y, const float2* b,
-                      int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops);
+// item: all blocks (bmode 0) or the blocks of colour `color` (bmode 1); W is the per-site weight image, x16 the
+// 16-bit copy of x; y FP32 (y16 = 0) or, for bmode 1, the planar 16-bit form of y (y16 = 1)
+void tc_block_stencil(cudaStream_t st, int bf, const void* W, int Ls, const void* x16, void* y, int y16,
+                      const float2* b, int bmode, int color, int nrhs, const int* active, int* err, double bytes,
+                      double flops);
+// SAP block update x_B += inv_B r_B on the colour-`color` 2x2 blocks, rhs on the MMA M dimension: r16 the planar
+// 16-bit residual tiles (tc_block_stencil with y16 = 1), Winv the colour's block-inverse image; x (FP32) and its
+// 16-bit copy x16 are updated on the colour's sites
+void tc_block_update(cudaStream_t st, int bf, const void* Winv, int Ls, const void* r16, float2* x, void* x16,
+                     int color, int nrhs, const int* active, int* err, double bytes, double flops);
 size_t tc_stencil_weight_bytes(int nsite, int bf);
 size_t tc_blockinv_weight_bytes(int Ls, int bf);  // the blocks of one colour
 void tc_stencil_weights(cudaStream_t st, const float2* st32, int nsite, void* W, int bf);
 void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color, void* W, int bf);
-// y = D x (b == nullptr) or y = b - D x, FP32 vectors, TF32 or BF16 products with FP32 accumulation
-void tc_stencil_apply(cudaStream_t st, const void* W, int bf, int Ls, const float2* x, float2* y, const float2* b,
-                      int nrhs, const int* active, int* err);
+// true where the stencil launches for (bf, Ls, nrhs) take the 2x2-block kernel: their callers then pass x16
+bool tc_block_selected(int bf, int Ls, int nrhs);
+// x16 = the 16-bit copy of x (all rhs rows)
+void tc_round16(cudaStream_t st, int bf, const float2* x, void* x16, int nsite, int nrhs);
+// y = D x (b == nullptr) or y = b - D x, FP32 vectors, TF32, BF16 or FP16 products with FP32 accumulation;
+// x16 (the 16-bit copy of x) is required where tc_block_selected, else unused
+void tc_stencil_apply(cudaStream_t st, const void* W, int bf, int Ls, const float2* x, const void* x16, float2* y,
+                      const float2* b, int nrhs, const int* active, int* err);
 // res = f - D x on colour-0 block sites, 0 on colour-1 block sites (the residual right after a SAP sweep: it
 // vanishes on the blocks solved last up to the rounding of the tensor-core products)
-void tc_residual_after_sap(cudaStream_t st, const void* Wst, int bf, int Ls, const float2* x, float2* res,
-                           const float2* f, int nrhs, const int* active, int* err);
-// one SAP colour half sweep with 2x2-site blocks: res = f - D x on the colour's sites, x_B += inv_B res_B
+void tc_residual_after_sap(cudaStream_t st, const void* Wst, int bf, int Ls, const float2* x, const void* x16,
+                           float2* res, const float2* f, int nrhs, const int* active, int* err);
+// one SAP colour half sweep with 2x2-site blocks: res = f - D x on the colour's sites, x_B += inv_B res_B; where
+// tc_block_selected, x16 is read by the residual and updated with x_B (res then holds the 16-bit residual)
 void tc_sap_half(cudaStream_t st, const void* Wst, const void* Winv, int bf, int Ls, const float2* f, float2* x,
-                 float2* res, int color, int nrhs, const int* active, int* err);
+                 void* x16, float2* res, int color, int nrhs, const int* active, int* err);
 
 // ---------------------------------------------------------------- launch-shape tuning table (tune.cu)
 enum { TUNE_WILSON32 = 0, TUNE_TC0 = 1, TUNE_TC1 = 2 };

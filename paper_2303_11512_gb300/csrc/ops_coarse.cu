@@ -6,6 +6,9 @@
 // Stencil layout: st[site][dir][i][j], dir = 0 self, 1 +x, 2 -x, 3 +t, 4 -t;
 // (D x)(s)_i = sum_dir sum_j st[s][dir][i][j] x(s + dir)_j, periodic (the
 // fermion boundary sign is already inside the Galerkin blocks).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ops.cuh"
 
 namespace mg {
@@ -276,7 +279,8 @@ __global__ void __launch_bounds__(256) k_restrict(const typename CT<R>::T* __res
 template <typename R, bool ADD, int DT, int AT, int NT>
 __global__ void __launch_bounds__(256) k_prolong(const typename CT<R>::T* __restrict__ P, int Ls, int d_, int agg_,
                                                  int ntv_, const typename CT<R>::T* __restrict__ xc,
-                                                 typename CT<R>::T* __restrict__ xf, int nrhs,
+                                                 typename CT<R>::T* __restrict__ xf,
+                                                 unsigned short* __restrict__ xf16, int bf, int nrhs,
                                                  const int* __restrict__ active) {
   typedef typename CT<R>::T C;
   const int d = DT ? DT : d_, agg = AT ? AT : agg_, ntv = NT ? NT : ntv_;
@@ -314,7 +318,15 @@ __global__ void __launch_bounds__(256) k_prolong(const typename CT<R>::T* __rest
         const int jt = js / agg, jx = js - jt * agg;
         const size_t site = (size_t)(agg * T + jt) * Ls + agg * X + jx;
         C* p = xf + rhs * n + site * d + k;
-        *p = ADD ? cadd(*p, acc) : acc;
+        const C v = ADD ? cadd(*p, acc) : acc;
+        *p = v;
+        if constexpr (sizeof(R) == 4) {
+          if (xf16) {  // planar 16-bit copy of an FP32 coarse vector: Re parts of the site's d dofs, then Im
+            unsigned short* p16 = xf16 + 2 * (rhs * n + site * d) + k;
+            p16[0] = bf == 2 ? __half_as_ushort(__float2half_rn(v.x)) : __bfloat16_as_ushort(__float2bfloat16_rn(v.x));
+            p16[d] = bf == 2 ? __half_as_ushort(__float2half_rn(v.y)) : __bfloat16_as_ushort(__float2bfloat16_rn(v.y));
+          }
+        }
       }
     }
   }
@@ -359,51 +371,55 @@ void restrict_op(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, in
 
 template <typename R, bool ADD>
 static void prolong_launch(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, int agg, int ntv,
-                           const typename CT<R>::T* xc, typename CT<R>::T* xf, int nrhs, const int* active,
-                           size_t sm, double bytes, double flops) {
+                           const typename CT<R>::T* xc, typename CT<R>::T* xf, unsigned short* xf16, int bf,
+                           int nrhs, const int* active, size_t sm, double bytes, double flops) {
   const int Lc = Ls / agg;
   switch (transfer_shape(d, agg, ntv)) {
     case SHAPE_FINE:
       set_smem_attr(k_prolong<R, ADD, 2, 4, 8>);
       MG_LAUNCH_W(bytes, flops, (k_prolong<R, ADD, 2, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf,
-                  nrhs, active);
+                  xf16, bf, nrhs, active);
       break;
     case SHAPE_COARSE:
       set_smem_attr(k_prolong<R, ADD, 16, 4, 8>);
       MG_LAUNCH_W(bytes, flops, (k_prolong<R, ADD, 16, 4, 8>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf,
-                  nrhs, active);
+                  xf16, bf, nrhs, active);
       break;
     default:
       set_smem_attr(k_prolong<R, ADD, 0, 0, 0>);
       MG_LAUNCH_W(bytes, flops, (k_prolong<R, ADD, 0, 0, 0>), Lc * Lc, 256, sm, stm, P, Ls, d, agg, ntv, xc, xf,
-                  nrhs, active);
+                  xf16, bf, nrhs, active);
   }
 }
 
 template <typename R>
 void prolong_op(cudaStream_t stm, const typename CT<R>::T* P, int Ls, int d, int agg, int ntv,
-                const typename CT<R>::T* xc, typename CT<R>::T* xf, bool add, int nrhs, const int* active) {
+                const typename CT<R>::T* xc, typename CT<R>::T* xf, bool add, int nrhs, const int* active,
+                void* xf16, int bf) {
+  MG_CHECK_ARG(!xf16 || (sizeof(R) == 4 && (bf == 1 || bf == 2)), "16-bit copy: FP32 vectors, BF16 or FP16");
   typedef typename CT<R>::T C;
   const int na = agg * agg, bsz = na * d / 2, dc = 2 * ntv, fa = na * d;
   const int G = std::max(1, 256 / fa);
   size_t sm = sizeof(C) * ((size_t)2 * bsz * ntv + (size_t)G * dc);
   const int Lc = Ls / agg;
   const double nag = (double)Lc * Lc, cs = sizeof(C), ar = act_rhs(nrhs);
-  const double bytes = nag * (ar * ((add ? 2.0 : 1.0) * fa + dc) * cs + 2.0 * bsz * ntv * cs);
+  const double bytes = nag * (ar * ((add ? 2.0 : 1.0) * fa + dc) * cs + 2.0 * bsz * ntv * cs) +
+                       (xf16 ? nag * ar * fa * 4.0 : 0.0);
   const double flops = nag * ar * 8.0 * 2.0 * bsz * ntv;
+  unsigned short* x16 = (unsigned short*)xf16;
   if (add)
-    prolong_launch<R, true>(stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active, sm, bytes, flops);
+    prolong_launch<R, true>(stm, P, Ls, d, agg, ntv, xc, xf, x16, bf, nrhs, active, sm, bytes, flops);
   else
-    prolong_launch<R, false>(stm, P, Ls, d, agg, ntv, xc, xf, nrhs, active, sm, bytes, flops);
+    prolong_launch<R, false>(stm, P, Ls, d, agg, ntv, xc, xf, x16, bf, nrhs, active, sm, bytes, flops);
 }
 template void restrict_op<float>(cudaStream_t, const float2*, int, int, int, int, const float2*, float2*, int,
                                  const int*);
 template void restrict_op<double>(cudaStream_t, const double2*, int, int, int, int, const double2*, double2*, int,
                                   const int*);
 template void prolong_op<float>(cudaStream_t, const float2*, int, int, int, int, const float2*, float2*, bool, int,
-                                const int*);
+                                const int*, void*, int);
 template void prolong_op<double>(cudaStream_t, const double2*, int, int, int, int, const double2*, double2*, bool,
-                                 int, const int*);
+                                 int, const int*, void*, int);
 
 // ---- test vectors -> prolongator blocks --------------------------------------------
 __global__ void k_gather_tv(const double2* __restrict__ V, int Ls, int d, int agg, int ntv, double2* __restrict__ P) {

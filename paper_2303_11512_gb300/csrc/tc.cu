@@ -259,10 +259,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   } else if (warp >= TC_EXP_WARP0) {
-    // ---------------- expander / converter.  Weight tiles: the Im rows from the stored Re rows, (a, b) ->
-    // (-b, a) per complex pair; row n + NW/2 has the swizzle phase of row n, so each 16-byte chunk keeps its
-    // position.  BF16: every staged FP32 slab (128-byte swizzle) becomes a BF16 operand tile (64-byte
-    // swizzle, round to nearest even).
+    // ---------------- expander / converter.  Weight tiles: the Im rows from the stored Re rows; row n + NW/2
+    // has the swizzle phase of row n.  TF32: (a, b) -> (-b, a) per complex pair, each 16-byte chunk keeps its
+    // position.  16-bit (planar K): logical chunk c of the Im row is chunk c ^ 2 of the Re row, negated for
+    // c < 2 (the -Im half becomes the leading Im half).  16-bit formats: every staged FP32 slab (128-byte
+    // swizzle, interleaved Re/Im) becomes a planar operand tile (64-byte swizzle, round to nearest even).
     const int et = (warp - TC_EXP_WARP0) * 32 + lane;
     constexpr int NT = 32 * TC_EXP_WARPS;
     constexpr int CPR = WROW / 16;           // 16-byte chunks per row
@@ -279,17 +280,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // a position of all KC tiles at once (KC loads in flight, no index division)
       uint4* w0 = reinterpret_cast<uint4*>(sW(s, 0));
       for (int e = et; e < HALF; e += NT) {
+        // 16-bit: position e ^ 2 holds logical chunk c ^ 2; the sign flips where the Im row's logical chunk < 2
+        const uint32_t neg = BF && !(((e & 3) ^ ((e >> 3) & 3)) & 2) ? 0x80008000u : 0u;
         uint4 v[KC];
 #pragma unroll
-        for (int kc = 0; kc < KC; ++kc) v[kc] = w0[kc * TILE + e];
+        for (int kc = 0; kc < KC; ++kc) v[kc] = w0[kc * TILE + (BF ? e ^ 2 : e)];
 #pragma unroll
         for (int kc = 0; kc < KC; ++kc) {
           uint4 r;
-          if (BF) {  // four 16-bit pairs (a, b) -> (-b, a)
-            r.x = ((v[kc].x & 0xFFFFu) << 16) | ((v[kc].x >> 16) ^ 0x8000u);
-            r.y = ((v[kc].y & 0xFFFFu) << 16) | ((v[kc].y >> 16) ^ 0x8000u);
-            r.z = ((v[kc].z & 0xFFFFu) << 16) | ((v[kc].z >> 16) ^ 0x8000u);
-            r.w = ((v[kc].w & 0xFFFFu) << 16) | ((v[kc].w >> 16) ^ 0x8000u);
+          if (BF) {
+            r = make_uint4(v[kc].x ^ neg, v[kc].y ^ neg, v[kc].z ^ neg, v[kc].w ^ neg);
           } else {  // two fp32 pairs (a, b) -> (-b, a)
             r.x = v[kc].y ^ 0x80000000u;
             r.y = v[kc].x;
@@ -300,10 +300,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       if (BF) {
-        // output chunk (kc, row, c) holds k = 8c .. 8c+7 of that row: FP32 chunks 2c and 2c+1 of the staged row;
-        // a thread converts position (row, c) of all KC slabs
+        // unit (row, c): complex dofs 4c .. 4c+3 = FP32 chunks 2c and 2c+1 of the staged row; their Re parts go
+        // to half c & 1 of logical output chunk c >> 1, their Im parts to the same half of chunk 2 + (c >> 1).
+        // A thread converts position (row, c) of all KC slabs.
         for (int u = et; u < vrows * 4; u += NT) {
-          const int row = u >> 2, c = u & 3;
+          const int row = u >> 2, c = u & 3, ph = (row >> 1) & 3;
           float4 f[KC][2];
 #pragma unroll
           for (int kc = 0; kc < KC; ++kc) {
@@ -311,21 +312,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             f[kc][0] = src[(2 * c) ^ (row & 7)];
             f[kc][1] = src[(2 * c + 1) ^ (row & 7)];
           }
+          const int ore = row * 8 + ((((c >> 1)) ^ ph) << 1) + (c & 1);      // uint2 index of the Re half
+          const int oim = row * 8 + (((2 + (c >> 1)) ^ ph) << 1) + (c & 1);  // uint2 index of the Im half
 #pragma unroll
           for (int kc = 0; kc < KC; ++kc) {
-            uint4 o;
+            uint2 re, im;
             if (BF == 2) {
-              o.x = f16x2_rn(f[kc][0].x, f[kc][0].y);
-              o.y = f16x2_rn(f[kc][0].z, f[kc][0].w);
-              o.z = f16x2_rn(f[kc][1].x, f[kc][1].y);
-              o.w = f16x2_rn(f[kc][1].z, f[kc][1].w);
+              re = make_uint2(f16x2_rn(f[kc][0].x, f[kc][0].z), f16x2_rn(f[kc][1].x, f[kc][1].z));
+              im = make_uint2(f16x2_rn(f[kc][0].y, f[kc][0].w), f16x2_rn(f[kc][1].y, f[kc][1].w));
             } else {
-              o.x = bf16x2_rn(f[kc][0].x, f[kc][0].y);
-              o.y = bf16x2_rn(f[kc][0].z, f[kc][0].w);
-              o.z = bf16x2_rn(f[kc][1].x, f[kc][1].y);
-              o.w = bf16x2_rn(f[kc][1].z, f[kc][1].w);
+              re = make_uint2(bf16x2_rn(f[kc][0].x, f[kc][0].z), bf16x2_rn(f[kc][1].x, f[kc][1].z));
+              im = make_uint2(bf16x2_rn(f[kc][0].y, f[kc][0].w), bf16x2_rn(f[kc][1].y, f[kc][1].w));
             }
-            reinterpret_cast<uint4*>(sV(s, kc))[row * 4 + (c ^ ((row >> 1) & 3))] = o;
+            reinterpret_cast<uint2*>(sV(s, kc))[ore] = re;
+            reinterpret_cast<uint2*>(sV(s, kc))[oim] = im;
           }
         }
       }
@@ -459,10 +459,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // Weight images.  The real embedding of a complex output row i is the pair of rows
-//   Re y_i:  k = 2j + b ->  (Re w_ij, -Im w_ij)        Im y_i:  k = 2j + b -> (Im w_ij, Re w_ij),
+//   TF32 (k = 2j + b, the interleaved order of the FP32 vectors):
+//     Re y_i:  (Re w_ij, -Im w_ij)        Im y_i:  (Im w_ij, Re w_ij)
+//   16-bit (k = 16b + j, planar: the 16-bit operand tiles hold the 16 Re parts of a site, then the 16 Im parts):
+//     Re y_i:  [Re w_i. | -Im w_i.]       Im y_i:  [Im w_i. | Re w_i.]
 // the second a fixed rearrangement of the first.  Only the Re rows are stored (NW/2 rows per K chunk of 32
 // reals), pre-swizzled K-major: TF32 element (n, k) at n * 32 + (((k >> 2) ^ (n & 7)) << 2) + (k & 3) (128-byte
-// rows), BF16 element (n, k) at n * 32 + (((k >> 3) ^ ((n >> 1) & 3)) << 3) + (k & 7) (64-byte rows); the
+// rows), 16-bit element (n, k) at n * 32 + (((k >> 3) ^ ((n >> 1) & 3)) << 3) + (k & 7) (64-byte rows); the
 // kernel's expander warps build the Im rows in shared memory, so accumulator columns (MODE 0) or lanes
 // (MODE 1) [0, NW/2) hold Re y and [NW/2, NW) Im y.
 __device__ __forceinline__ int sw_index(int n, int k) { return n * 32 + ((((k >> 2) ^ (n & 7)) << 2) | (k & 3)); }
@@ -488,7 +491,7 @@ __global__ void k_tc_stencil_weights(const float2* __restrict__ st, int nsite, v
     const size_t sd = e / 512;  // site * 5 + dir
     const int j = k >> 1, b = k & 1;
     const float2 z = st[sd * 256 + i * 16 + j];
-    put_w<BF>(W, sd, 16, i, k, b ? -z.y : z.x);
+    put_w<BF>(W, sd, 16, i, BF ? 16 * b + j : k, b ? -z.y : z.x);
   }
 }
 
@@ -505,7 +508,7 @@ __global__ void k_tc_blockinv_weights(const float2* __restrict__ inv, int Ls, in
     const int kg = kc * 32 + kk;  // real input index 2 * (16 * site_j + dof) + b
     const int j = kg >> 1, b = kg & 1;
     const float2 z = inv[(size_t)blk * 4096 + i * 64 + j];
-    put_w<BF>(W, (size_t)item * 4 + kc, 64, i, kk, b ? -z.y : z.x);
+    put_w<BF>(W, (size_t)item * 4 + kc, 64, i, BF ? 16 * b + (kk >> 1) : kk, b ? -z.y : z.x);
   }
 }
 
@@ -570,6 +573,27 @@ void launch_tc_fmt(int bf, cudaStream_t st, const float2* vin, const void* W, fl
     launch_tc<MODE, 0>(st, vin, W, out, b, Ls, nitems, bmode, color, nrhs, active, err, bytes, flops);
 }
 
+// FP32 coarse vectors [rhs][site][16 complex] -> the planar 16-bit copy [rhs][site][16 Re | 16 Im] (round to
+// nearest even); one thread per 4 complex dofs
+template <int BF>
+__global__ void k_round16(const float4* __restrict__ x, uint2* __restrict__ x16, size_t nquad) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nquad; e += (size_t)gridDim.x * blockDim.x) {
+    const float4 a = x[2 * e], b = x[2 * e + 1];
+    const size_t site = e >> 2;  // 4 quads per site
+    const int c = (int)(e & 3);
+    uint2 re, im;
+    if (BF == 2) {
+      re = make_uint2(f16x2_rn(a.x, a.z), f16x2_rn(b.x, b.z));
+      im = make_uint2(f16x2_rn(a.y, a.w), f16x2_rn(b.y, b.w));
+    } else {
+      re = make_uint2(bf16x2_rn(a.x, a.z), bf16x2_rn(b.x, b.z));
+      im = make_uint2(bf16x2_rn(a.y, a.w), bf16x2_rn(b.y, b.w));
+    }
+    x16[site * 8 + c] = re;      // uint2 units: Re dofs 4c .. 4c+3
+    x16[site * 8 + 4 + c] = im;  // Im dofs 4c .. 4c+3
+  }
+}
+
 }  // namespace
 
 // stored weight bytes: stencil 5 dirs x 16 Re rows x 32 reals per site; block inverses 4 chunks x 64 Re rows x
@@ -598,23 +622,38 @@ void tc_blockinv_weights(cudaStream_t st, const float2* inv32, int Ls, int color
 // 16-bit formats: the 2x2-block kernel (tc_block.cu) or the per-site kernel; a tuned variant of the stencil
 // (TUNE_TC0) with bit 4 set selects the block kernel, untuned launches take it for batches of at most 32 rhs (it
 // issues fewer MMAs per site; at larger batches the per-site kernel's TMA staging keeps more loads in flight)
-static bool use_block_kernel(int bf, int Ls, int nrhs) {
+bool tc_block_selected(int bf, int Ls, int nrhs) {
   if (!bf || Ls % 4) return false;
   const int var = tune_lookup(TUNE_TC0, Ls, nrhs, bf, -1);
   return var < 0 ? nrhs <= 32 : (var & 16) != 0;
 }
 
-void tc_stencil_apply(cudaStream_t st, const void* W, int bf, int Ls, const float2* x, float2* y, const float2* b,
-                      int nrhs, const int* active, int* err) {
+void tc_round16(cudaStream_t st, int bf, const float2* x, void* x16, int nsite, int nrhs) {
+  MG_CHECK_ARG(bf == 1 || bf == 2, "16-bit copy of a coarse vector needs a 16-bit format");
+  if (nrhs <= 0) return;
+  const size_t nquad = (size_t)nsite * 4 * nrhs;
+  const double bytes = (double)nquad * 48.0;
+  const unsigned grid = (unsigned)std::min<size_t>((nquad + 255) / 256, 152 * 16);
+  if (bf == 2)
+    MG_LAUNCH_W(bytes, 0, k_round16<2>, grid, 256, 0, st, (const float4*)x, (uint2*)x16, nquad);
+  else
+    MG_LAUNCH_W(bytes, 0, k_round16<1>, grid, 256, 0, st, (const float4*)x, (uint2*)x16, nquad);
+}
+
+void tc_stencil_apply(cudaStream_t st, const void* W, int bf, int Ls, const float2* x, const void* x16, float2* y,
+                      const float2* b, int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
   const int ns = Ls * Ls;
   const double ar = act_rhs(nrhs);
-  const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + (double)tc_stencil_weight_bytes(ns, bf);
   const double flops = ar * ns * 2.0 * 32 * 160;
-  if (use_block_kernel(bf, Ls, nrhs))  // 16-bit operands: 2x2-site items sharing slabs (tc_block.cu)
-    tc_block_stencil(st, bf, W, Ls, x, y, b, 0, 0, nrhs, active, err, bytes, flops);
-  else
+  if (tc_block_selected(bf, Ls, nrhs)) {  // 16-bit operands: 2x2-site items sharing slabs (tc_block.cu)
+    MG_CHECK_ARG(x16, "the 2x2-block stencil reads the 16-bit copy of x");
+    const double bytes = ar * ns * (64.0 + 128.0 * (b ? 2 : 1)) + (double)tc_stencil_weight_bytes(ns, bf);
+    tc_block_stencil(st, bf, W, Ls, x16, y, 0, b, 0, 0, nrhs, active, err, bytes, flops);
+  } else {
+    const double bytes = ar * ns * 128.0 * (b ? 3 : 2) + (double)tc_stencil_weight_bytes(ns, bf);
     launch_tc_fmt<0>(bf, st, x, W, (float*)y, (const float*)b, Ls, ns, 0, 0, nrhs, active, err, bytes, flops);
+  }
 }
 
 // zero the sites of every colour-`color` 2x2 block of res ([rhs][site][16 complex])
@@ -635,39 +674,44 @@ __global__ void k_zero_colour_blocks(float2* __restrict__ res, int Ls, int color
 // res = f - D x on the sites of the colour-0 blocks and 0 on the colour-1 blocks: the V-cycle residual after
 // a SAP sweep whose last half sweep solved the colour-1 blocks, where it vanishes (the blocks of one colour do
 // not couple to each other, so their solves leave f - D x = 0 on them)
-void tc_residual_after_sap(cudaStream_t st, const void* Wst, int bf, int Ls, const float2* x, float2* res,
-                           const float2* f, int nrhs, const int* active, int* err) {
+void tc_residual_after_sap(cudaStream_t st, const void* Wst, int bf, int Ls, const float2* x, const void* x16,
+                           float2* res, const float2* f, int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
   const int ns = Ls * Ls;
   const double ar = act_rhs(nrhs);
-  const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_stencil_weight_bytes(ns / 2, bf);
   const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
-  if (use_block_kernel(bf, Ls, nrhs))
-    tc_block_stencil(st, bf, Wst, Ls, x, res, f, 1, 0, nrhs, active, err, bytes, flops);
-  else
-    launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, 0, nrhs, active, err, bytes, flops);
+  if (tc_block_selected(bf, Ls, nrhs)) {
+    MG_CHECK_ARG(x16, "the 2x2-block stencil reads the 16-bit copy of x");
+    const double bytes = ar * (ns / 2) * (64.0 + 128.0 * 2) + (double)tc_stencil_weight_bytes(ns / 2, bf);
+    tc_block_stencil(st, bf, Wst, Ls, x16, res, 0, f, 1, 0, nrhs, active, err, bytes, flops);
+  } else {
+    const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_stencil_weight_bytes(ns / 2, bf);
+    launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, 0, nrhs, active, err, bytes,
+                     flops);
+  }
   MG_LAUNCH_W(ar * (ns / 2) * 128.0, 0, k_zero_colour_blocks, 1024, 256, 0, st, res, Ls, 1, nrhs, active);
 }
 
 void tc_sap_half(cudaStream_t st, const void* Wst, const void* Winv, int bf, int Ls, const float2* f, float2* x,
-                 float2* res, int color, int nrhs, const int* active, int* err) {
+                 void* x16, float2* res, int color, int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
   const int ns = Ls * Ls, nblk = ns / 8;
   const double ar = act_rhs(nrhs);
-  {  // residual on the sites of the colour's blocks
-    const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_stencil_weight_bytes(ns / 2, bf);
-    const double flops = ar * (ns / 2) * 2.0 * 32 * 160;
-    if (use_block_kernel(bf, Ls, nrhs))
-      tc_block_stencil(st, bf, Wst, Ls, x, res, f, 1, color, nrhs, active, err, bytes, flops);
-    else
-      launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err, bytes,
-                       flops);
+  const double sflops = ar * (ns / 2) * 2.0 * 32 * 160, uflops = ar * nblk * 2.0 * 128 * 128;
+  if (tc_block_selected(bf, Ls, nrhs)) {
+    // 16-bit path: the block stencil writes r = f - D x of the colour's sites as planar 16-bit tiles (into res's
+    // memory), the rhs-on-M block update reads them by TMA and updates x and its 16-bit copy
+    MG_CHECK_ARG(x16, "the 2x2-block stencil reads the 16-bit copy of x");
+    tc_block_stencil(st, bf, Wst, Ls, x16, res, 1, f, 1, color, nrhs, active, err,
+                     ar * (ns / 2) * (64.0 + 128.0 + 64.0) + (double)tc_stencil_weight_bytes(ns / 2, bf), sflops);
+    tc_block_update(st, bf, Winv, Ls, res, x, x16, color, nrhs, active, err,
+                    ar * (ns / 2) * (64.0 + 128.0 * 2 + 64.0) + (double)tc_blockinv_weight_bytes(Ls, bf), uflops);
+    return;
   }
-  {  // x_B += inv_B r_B
-    const double bytes = ar * (ns / 2) * 128.0 * 3 + (double)tc_blockinv_weight_bytes(Ls, bf);
-    const double flops = ar * nblk * 2.0 * 128 * 128;
-    launch_tc_fmt<1>(bf, st, res, Winv, (float*)x, nullptr, Ls, nblk, 0, color, nrhs, active, err, bytes, flops);
-  }
+  launch_tc_fmt<0>(bf, st, x, Wst, (float*)res, (const float*)f, Ls, ns / 2, 1, color, nrhs, active, err,
+                   ar * (ns / 2) * 128.0 * 3 + (double)tc_stencil_weight_bytes(ns / 2, bf), sflops);
+  launch_tc_fmt<1>(bf, st, res, Winv, (float*)x, nullptr, Ls, nblk, 0, color, nrhs, active, err,
+                   ar * (ns / 2) * 128.0 * 3 + (double)tc_blockinv_weight_bytes(Ls, bf), uflops);
 }
 
 }  // namespace mg

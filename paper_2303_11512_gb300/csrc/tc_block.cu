@@ -8,10 +8,11 @@
 // the item's 4 x 32 accumulator columns) replaces three; the 8 halo slabs feed one site each.  12 slabs x 2 K
 // steps = 24 MMAs per block, 6 per site.
 //
-// Shared memory of a stage: 12 vector tiles (64 rhs rows x 32 16-bit values, 64-byte swizzle) converted from the
-// FP32 vectors by converter warps, and the weight windows: 22 sub-tiles of 32 rows (Re rows from the per-site
-// weight image by bulk copies, Im rows derived), two of them zero, arranged so that every slab's targets are
-// consecutive rows:
+// Shared memory of a stage: 12 vector tiles (64 rhs rows x 32 16-bit values, 64-byte swizzle), each one TMA box
+// of the planar 16-bit copy of x ([rhs][site][16 Re | 16 Im], kept up to date by the kernels that write x, rows
+// past nrhs filled with zeros by the copy engine), and the weight windows: 22 sub-tiles of 32 rows (Re rows from
+// the per-site weight image by bulk copies, Im rows derived by converter warps), two of them zero, arranged so
+// that every slab's targets are consecutive rows:
 //   slab s00: [W(s00,self) W(s01,-x) W(s10,-t)]            N =  96, columns  0..95
 //   slab s01: [W(s00,+x) W(s01,self) 0 W(s11,-t)]          N = 128, columns  0..127
 //   slab s10: [W(s00,+t) 0 W(s10,self) W(s11,-x)]          N = 128, columns  0..127
@@ -33,7 +34,8 @@ constexpr int TB_STAGE = TB_SLABS * TB_VTILE + TB_BROWS * 64;
 constexpr int TB_STAGES = 2;
 constexpr int TB_NACC = 4;                  // accumulators (128 columns each)
 constexpr int TB_PROD_WARP = 0, TB_MMA_WARP = 1, TB_EPI_WARP0 = 2, TB_EPI_WARPS = 8, TB_CONV_WARP0 = 10,
-              TB_CONV_WARPS = 8;
+              TB_CONV_WARPS = 4;
+constexpr uint32_t TB_TX = 20u * 1024u + TB_SLABS * TB_VTILE;  // bytes landing in a stage per item
 constexpr int TB_THREADS = 32 * (TB_CONV_WARP0 + TB_CONV_WARPS);
 static_assert(TB_CONV_WARP0 == TB_EPI_WARP0 + TB_EPI_WARPS, "warp roles: producer, MMA, epilogue, converters");
 constexpr int TB_SMEM = 1024 + TB_STAGES * TB_STAGE;
@@ -55,6 +57,11 @@ __constant__ signed char c_order[TB_SLABS] = {4, 6, 8, 10, 5, 7, 9, 11, 0, 1, 2,
 
 __device__ __forceinline__ int tb_wrap(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
+template <int BF>
+__device__ __forceinline__ uint32_t tb_pack(float a, float b) {
+  return BF == 2 ? f16x2_rn(a, b) : bf16x2_rn(a, b);
+}
+
 // corner (t0, x0) of item k: all blocks (bmode 0, colour-0 blocks then colour-1 blocks) or the blocks of colour
 // `color` (bmode 1), in the block order of the SAP sweeps
 __device__ __forceinline__ void tb_corner(int k, int Ls, int bmode, int color, int& t0, int& x0) {
@@ -72,14 +79,11 @@ __device__ __forceinline__ void tb_corner(int k, int Ls, int bmode, int color, i
   x0 = 2 * BX;
 }
 
-template <int BF>
-__device__ __forceinline__ uint32_t tb_pack(float a, float b) {
-  return BF == 2 ? f16x2_rn(a, b) : bf16x2_rn(a, b);
-}
-
-template <int BF>
+// O16 = 0: y (FP32, [rhs][site][16 complex]); O16 = 1: y as a planar 16-bit tile ([rhs][site][16 Re | 16 Im],
+// the A operand of the SAP block update k_tcs)
+template <int BF, int O16>
 __global__ void __launch_bounds__(TB_THREADS, 1)
-    k_tcb(const float* __restrict__ xin, const unsigned char* __restrict__ W, float* __restrict__ out,
+    k_tcb(const __grid_constant__ CUtensorMap xmap, const unsigned char* __restrict__ W, void* __restrict__ out,
           const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs,
           const int* __restrict__ active, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -91,14 +95,17 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
   __shared__ volatile int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rhs0 = blockIdx.y * TB_MM;
-  const int vrows = min(TB_MM, ((nrhs - rhs0 + 7) / 8) * 8);  // vector rows converted per tile
-  const long ncf = (long)Ls * Ls * 32;                          // floats per rhs row
+  const long ncf = (long)Ls * Ls * 32;  // floats per rhs row
   if (tid == 0) s_skip = *(volatile int*)err;
   __syncthreads();
   if (s_skip) return;
-  // zero both stages (the two zero weight sub-tiles are never written afterwards)
-  for (int i = tid; i < TB_STAGES * TB_STAGE / 16; i += TB_THREADS)
-    reinterpret_cast<uint4*>(base)[i] = make_uint4(0, 0, 0, 0);
+  // the two zero weight sub-tiles (rows 160..191 and 256..287 of every stage's weight windows) are never written
+  // by the pipeline: clear them once
+  for (int i = tid; i < TB_STAGES * 2 * 32 * 4; i += TB_THREADS) {
+    const int st = i / 256, z = (i >> 7) & 1, e = i & 127;
+    reinterpret_cast<uint4*>(base + st * TB_STAGE + TB_SLABS * TB_VTILE + (z ? 256 : 160) * 64)[e] =
+        make_uint4(0, 0, 0, 0);
+  }
   if (tid == 0) {
     for (int s = 0; s < TB_STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -124,7 +131,8 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
   auto sB = [&](int s) { return base + s * TB_STAGE + TB_SLABS * TB_VTILE; };
 
   if (warp == TB_PROD_WARP) {
-    // ---------------- producer: the 20 stored weight halves of the block (lane k issues copy k)
+    // ---------------- producer: lanes 0..19 the 20 stored weight halves of the block (lane 5 j + f: site j,
+    // direction f), lanes 20..31 the 12 vector slabs (TMA boxes of the 16-bit copy)
     for (int i = 0; i < n_my; ++i) {
       const int s = i % TB_STAGES;
       int ok = lane == 0 ? !s_bad : 0;
@@ -135,14 +143,18 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
         ok = 0;
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      if (lane == 0) mbar_expect_tx(&full_bar[s], 20u * 1024u);
+      if (lane == 0) mbar_expect_tx(&full_bar[s], TB_TX);
       __syncwarp();
+      int t0, x0;
+      tb_corner(blockIdx.x + i * gridDim.x, Ls, bmode, color, t0, x0);
       if (lane < 20) {
-        int t0, x0;
-        tb_corner(blockIdx.x + i * gridDim.x, Ls, bmode, color, t0, x0);
         const int j = lane / 5, f = lane % 5;
         const int site = (t0 + (j >> 1)) * Ls + x0 + (j & 1);
         bulk_load(sB(s) + c_rowpos[j][f] * 64, W + ((size_t)site * 5 + f) * 1024, 1024, &full_bar[s]);
+      } else {
+        const int q = lane - 20;
+        const int site = tb_wrap(t0 + c_sdt[q], Ls) * Ls + tb_wrap(x0 + c_sdx[q], Ls);
+        tma_load_2d(sV(s, q), &xmap, site * 32, rhs0, &full_bar[s]);
       }
     }
     // the last copies land before the CTA can exit (bounded)
@@ -182,7 +194,8 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
       }
     }
   } else if (warp >= TB_CONV_WARP0) {
-    // ---------------- converters: Im rows of the weight sub-tiles; FP32 vector rows -> 16-bit operand tiles
+    // ---------------- converters: the Im rows of the weight sub-tiles (planar K: logical chunk c of an Im row
+    // is chunk c ^ 2 of its Re row, negated for c < 2; rows n and n + 16 share the swizzle phase)
     const int ct = (warp - TB_CONV_WARP0) * 32 + lane;
     constexpr int NT = 32 * TB_CONV_WARPS;
     for (int i = 0; i < n_my; ++i) {
@@ -192,59 +205,14 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
         s_bad = 1;
         break;
       }
-      // Im rows: 20 sub-tiles x 16 rows x 4 chunks; (a, b) -> (-b, a) per 16-bit pair, same swizzle phase
       uint4* wb = reinterpret_cast<uint4*>(sB(s));
+#pragma unroll 2
       for (int e = ct; e < 20 * 64; e += NT) {
         const int t = e >> 6, r = e & 63;
-        const int row0 = c_rowpos[t / 5][t % 5];
-        const uint4 v = wb[row0 * 4 + r];
-        uint4 o;
-        o.x = ((v.x & 0xFFFFu) << 16) | ((v.x >> 16) ^ 0x8000u);
-        o.y = ((v.y & 0xFFFFu) << 16) | ((v.y >> 16) ^ 0x8000u);
-        o.z = ((v.z & 0xFFFFu) << 16) | ((v.z >> 16) ^ 0x8000u);
-        o.w = ((v.w & 0xFFFFu) << 16) | ((v.w >> 16) ^ 0x8000u);
-        wb[(row0 + 16) * 4 + r] = o;
-      }
-      // vector tiles: unit (slab q, row r, 16-byte output chunk c) from two float4 of the FP32 vector
-      int t0, x0;
-      tb_corner(blockIdx.x + i * gridDim.x, Ls, bmode, color, t0, x0);
-      const int units = TB_SLABS * vrows * 4;
-      // batches of UB units per thread: 2 UB global loads in flight (the loads come mostly from L2, so the
-      // converters are latency bound without them)
-      constexpr int UB = 6;
-      for (int u0 = ct; u0 < units; u0 += UB * NT) {
-        float4 f[UB][2];
-        int q2[UB], r2[UB], c2[UB];
-#pragma unroll
-        for (int h = 0; h < UB; ++h) {
-          const int u = u0 + h * NT;
-          const bool ok = u < units;
-          const int q = ok ? u / (vrows * 4) : 0, rem = u - q * vrows * 4;
-          const int r = rem >> 2, c = rem & 3;
-          q2[h] = ok ? q : -1;
-          r2[h] = r;
-          c2[h] = c;
-          const int rhs = rhs0 + r;
-          if (ok && rhs < nrhs) {
-            const int site = tb_wrap(t0 + c_sdt[q], Ls) * Ls + tb_wrap(x0 + c_sdx[q], Ls);
-            const float4* src = reinterpret_cast<const float4*>(xin + (size_t)rhs * ncf + (size_t)site * 32) + 2 * c;
-            f[h][0] = __ldg(src);
-            f[h][1] = __ldg(src + 1);
-          } else {
-            f[h][0] = f[h][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-        }
-#pragma unroll
-        for (int h = 0; h < UB; ++h) {
-          if (q2[h] < 0) continue;
-          uint4 o;
-          o.x = tb_pack<BF>(f[h][0].x, f[h][0].y);
-          o.y = tb_pack<BF>(f[h][0].z, f[h][0].w);
-          o.z = tb_pack<BF>(f[h][1].x, f[h][1].y);
-          o.w = tb_pack<BF>(f[h][1].z, f[h][1].w);
-          const int r = r2[h];
-          reinterpret_cast<uint4*>(sV(s, q2[h]))[r * 4 + (c2[h] ^ ((r >> 1) & 3))] = o;
-        }
+        const int c0 = c_rowpos[t / 5][t % 5] * 4 + r;  // chunk index of the Re row position
+        const uint32_t neg = (((c0 & 3) ^ ((c0 >> 3) & 3)) & 2) ? 0u : 0x80008000u;
+        const uint4 v = wb[c0 ^ 2];
+        wb[c0 + 64] = make_uint4(v.x ^ neg, v.y ^ neg, v.z ^ neg, v.w ^ neg);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> MMA reads
       __syncwarp();
@@ -259,6 +227,26 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
     const int rhs = rhs0 + row;
     const bool live = lane < 16 && rhs < nrhs && !(active && !active[rhs]);
     const bool quarter_live = rhs0 + q * 16 < nrhs;  // warp-uniform
+    // offset of step k (site j = k / 2, complex outputs 8 (k % 2) .. + 7) of item i in this thread's rhs row
+    auto step_off = [&](int i, int k) -> size_t {
+      int t0, x0;
+      tb_corner(blockIdx.x + i * gridDim.x, Ls, bmode, color, t0, x0);
+      const int j = k >> 1;
+      return (size_t)rhs * ncf + (size_t)((t0 + (j >> 1)) * Ls + x0 + (j & 1)) * 32 + 16 * (k & 1);
+    };
+    // the additive input b of step g + RD is fetched at step g (the steps of this warp's items in sequence), so
+    // its loads overlap the TMEM reads and stores of the steps before it
+    constexpr int NSTEP = 8, RD = 2;
+    float4 ring[RD][4];
+    auto prefetch = [&](float4 (&dst)[4], int i, int k) {
+      if (bvec && live && i < n_my) {
+        const float4* src = reinterpret_cast<const float4*>(bvec + step_off(i, k));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dst[u] = __ldg(src + u);
+      }
+    };
+#pragma unroll
+    for (int g = 0; g < RD; ++g) prefetch(ring[g], par, g);
     for (int i = par; i < n_my; i += 2) {
       const int a = i % TB_NACC;
       if (s_bad || !mbar_wait(&tfull_bar[a], (uint32_t)(i / TB_NACC) & 1u)) {
@@ -271,29 +259,47 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
       int t0, x0;
       tb_corner(blockIdx.x + i * gridDim.x, Ls, bmode, color, t0, x0);
       const uint32_t tq = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128);
-      if (quarter_live) {
+      float vs[32];  // site j's outputs: vs[0..15] Re, vs[16..31] Im of complex 0 .. 15
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+      for (int k = 0; k < NSTEP; ++k) {
+        const int j = k >> 1, t = k & 1;
+        float4 cur[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cur[u] = ring[k % RD][u];
+        prefetch(ring[k % RD], i + 2 * ((k + RD) / NSTEP), (k + RD) % NSTEP);
+        if (!quarter_live) continue;
+        if (t == 0) tmem_ld16x2(tq + 32 * j, tq + 32 * j + 16, vs);  // one TMEM wait per site
+        float v[16];  // v[0..7] Re, v[8..15] Im of complex outputs 8t .. 8t + 7 of block site j
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          v[e] = vs[8 * t + e];
+          v[8 + e] = vs[16 + 8 * t + e];
+        }
+        if (live) {
           const int site = (t0 + (j >> 1)) * Ls + x0 + (j & 1);
+          if (bvec) {  // y = b - D x: b's complex k at cur[k / 2] (x, y) or (z, w)
 #pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            float v[16];  // v[0..7] Re, v[8..15] Im of complex outputs 8t .. 8t + 7
-            tmem_ld8x2(tq + 32 * j + 8 * t, tq + 32 * j + 16 + 8 * t, v);
-            if (live) {
-              const size_t off = (size_t)rhs * ncf + (size_t)site * 32 + 16 * t;
-              float4* o = reinterpret_cast<float4*>(out + off);
-              if (bvec) {
-                const float4* bb = reinterpret_cast<const float4*>(bvec + off);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  const float4 c = bb[u];
-                  o[u] = make_float4(c.x - v[2 * u], c.y - v[8 + 2 * u], c.z - v[2 * u + 1], c.w - v[9 + 2 * u]);
-                }
-              } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) o[u] = make_float4(v[2 * u], v[8 + 2 * u], v[2 * u + 1], v[9 + 2 * u]);
-              }
+            for (int u = 0; u < 4; ++u) {
+              v[2 * u] = cur[u].x - v[2 * u];
+              v[8 + 2 * u] = cur[u].y - v[8 + 2 * u];
+              v[2 * u + 1] = cur[u].z - v[2 * u + 1];
+              v[9 + 2 * u] = cur[u].w - v[9 + 2 * u];
             }
+          }
+          if (O16) {  // Re parts of complex 8t .. 8t+7, then their Im parts 16 values later
+            uint16_t* o = reinterpret_cast<uint16_t*>(out) + (size_t)rhs * ncf + (size_t)site * 32 + 8 * t;
+            uint4 re, im;
+            re.x = tb_pack<BF>(v[0], v[1]), re.y = tb_pack<BF>(v[2], v[3]);
+            re.z = tb_pack<BF>(v[4], v[5]), re.w = tb_pack<BF>(v[6], v[7]);
+            im.x = tb_pack<BF>(v[8], v[9]), im.y = tb_pack<BF>(v[10], v[11]);
+            im.z = tb_pack<BF>(v[12], v[13]), im.w = tb_pack<BF>(v[14], v[15]);
+            *reinterpret_cast<uint4*>(o) = re;
+            *reinterpret_cast<uint4*>(o + 16) = im;
+          } else {
+            float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + (size_t)rhs * ncf +
+                                                  (size_t)site * 32 + 16 * t);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) o[u] = make_float4(v[2 * u], v[8 + 2 * u], v[2 * u + 1], v[9 + 2 * u]);
           }
         }
       }
@@ -309,28 +315,352 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
   }
 }
 
-}  // namespace
+// ---------------------------------------------------------------------------------------------------------------
+// SAP block update x_B += inv_B r_B for the 2x2 blocks of one colour, rhs on M: per block the A operand is the
+// block's 4 residual slabs (the planar 16-bit tiles that k_tcb<BF, 1> wrote, TMA boxes of 64 rhs rows x 32
+// values), the B operand the block inverse image (4 K chunks of 64 stored Re rows x 32 values, Im rows derived),
+// N = 128 outputs (accumulator columns 16 j + i: Re of dof i of block site j, 64 + 16 j + i: its Im part), 8 MMAs
+// of K = 16.  The old x of the block's sites comes by TMA too (FP32 boxes of 64 rhs rows x 32 floats, 128-byte
+// swizzle) into one shared-memory slot per epilogue parity, issued by a warp of its own as soon as the slot is
+// free; the epilogue adds the product in place (rows of inactive rhs keep their values) and one thread of the
+// parity writes the slot back with TMA stores (whole 128-byte rows, instead of 16-byte pieces of 16 rows per
+// warp instruction); the updated sites' planar 16-bit copy is stored from registers.
+constexpr int TS_STAGES = 3;
+constexpr int TS_ATILE = TB_MM * 64;                   // one residual slab
+constexpr int TS_BTILE = 128 * 64;                     // one K chunk of the inverse image (Re and Im rows)
+constexpr int TS_STAGE = 4 * TS_ATILE + 4 * TS_BTILE;  // 48 KB
+constexpr int TS_XBYTES = 2 * 4 * TB_MM * 128;         // old-x slots: 2 of 64 rows or 4 of 32 rows x 4 sites
+constexpr uint32_t TS_TX = 4u * TS_ATILE + 4u * 64u * 64u;
+constexpr int TS_XPROD_WARP = TB_CONV_WARP0 + TB_CONV_WARPS;
+constexpr int TS_THREADS = 32 * (TS_XPROD_WARP + 1);
+constexpr int TS_SMEM = 1024 + TS_STAGES * TS_STAGE + TS_XBYTES;
 
-void tc_block_stencil(cudaStream_t st, int bf, const void* W, int Ls, const float2* x, float2* y, const float2* b,
-                      int bmode, int color, int nrhs, const int* active, int* err, double bytes, double flops) {
-  MG_CHECK_ARG(bf == 1 || bf == 2, "the block stencil kernel takes 16-bit operands");
-  MG_CHECK_ARG(Ls >= 4 && Ls % 4 == 0, "the block stencil kernel needs a lattice side that is a multiple of 4");
-  const int nitems = bmode ? Ls * Ls / 8 : Ls * Ls / 4;
+template <int BF>
+__global__ void __launch_bounds__(TS_THREADS, 1)
+    k_tcs(const __grid_constant__ CUtensorMap rmap, const __grid_constant__ CUtensorMap xmap,
+          const unsigned char* __restrict__ Winv, float* __restrict__ x, uint16_t* __restrict__ x16, int Ls, int nitems,
+          int color, int nrhs, int xrows, const int* __restrict__ active, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[TS_STAGES], empty_bar[TS_STAGES], xfull_bar[TS_STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar[TB_NACC], tempty_bar[TB_NACC];
+  __shared__ __align__(8) uint64_t oxfull_bar[4], oxempty_bar[4];  // old-x slots (items i, i + nxs, ... share one)
+  __shared__ __align__(8) uint64_t edone_bar[4];                    // the parity's warps finished the slot
+  __shared__ uint32_t s_taddr;
+  __shared__ int s_skip;
+  __shared__ volatile int s_bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rhs0 = blockIdx.y * TB_MM;
+  const long ncf = (long)Ls * Ls * 32;  // floats (and 16-bit values) per rhs row
+  if (tid == 0) s_skip = *(volatile int*)err;
+  __syncthreads();
+  if (s_skip) return;
+  if (tid == 0) {
+    for (int s = 0; s < TS_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+      mbar_init(&xfull_bar[s], TB_CONV_WARPS);
+    }
+    for (int a = 0; a < TB_NACC; ++a) {
+      mbar_init(&tfull_bar[a], 1);
+      mbar_init(&tempty_bar[a], 4);
+    }
+    for (int p = 0; p < 4; ++p) {
+      mbar_init(&oxfull_bar[p], 1);
+      mbar_init(&oxempty_bar[p], 1);  // the storing thread of the parity, once its stores have read the slot
+      mbar_init(&edone_bar[p], 4);    // the four lane-quarter warps of the parity
+    }
+    s_bad = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 0) tmem_alloc(&s_taddr, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = s_taddr;
+  int n_my = 0;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) ++n_my;
+  auto sA = [&](int s, int kc) { return base + s * TS_STAGE + kc * TS_ATILE; };
+  auto sB = [&](int s, int kc) { return base + s * TS_STAGE + 4 * TS_ATILE + kc * TS_BTILE; };
+  // old-x slots: xrows rows per site slab (64, or 32 where the launch has at most 32 rhs: then 4 slots), the slot
+  // of item i is i % nxs, so each epilogue parity owns nxs / 2 of them
+  const int nxs = xrows == 32 ? 4 : 2, xtile = xrows * 128;
+  auto sX = [&](int sl, int j) { return base + TS_STAGES * TS_STAGE + (sl * 4 + j) * xtile; };
+  auto site_of = [&](int i, int j) -> int {
+    int t0, x0;
+    tb_corner(blockIdx.x + i * gridDim.x, Ls, 1, color, t0, x0);
+    return (t0 + (j >> 1)) * Ls + x0 + (j & 1);
+  };
+
+  if (warp == TB_PROD_WARP) {
+    // ---------------- producer: lanes 0..3 the stored Re rows of K chunk kc, lanes 4..7 the residual slab of
+    // block site kc
+    for (int i = 0; i < n_my; ++i) {
+      const int s = i % TS_STAGES;
+      int ok = lane == 0 ? !s_bad : 0;
+      if (lane == 0 && ok && i >= TS_STAGES &&
+          !mbar_wait(&empty_bar[s], (uint32_t)((i / TS_STAGES) - 1) & 1u)) {
+        atomicExch(err, 41);
+        s_bad = 1;
+        ok = 0;
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      if (lane == 0) mbar_expect_tx(&full_bar[s], TS_TX);
+      __syncwarp();
+      const int item = blockIdx.x + i * gridDim.x;
+      if (lane < 4)
+        bulk_load(sB(s, lane), Winv + ((size_t)item * 4 + lane) * 4096, 4096, &full_bar[s]);
+      else if (lane < 8)
+        tma_load_2d(sA(s, lane - 4), &rmap, site_of(i, lane - 4) * 32, rhs0, &full_bar[s]);
+    }
+    if (lane == 0)
+      for (int i = max(0, n_my - TS_STAGES); i < n_my && !s_bad; ++i)
+        mbar_wait(&full_bar[i % TS_STAGES], (uint32_t)(i / TS_STAGES) & 1u);
+  } else if (warp == TS_XPROD_WARP) {
+    // ---------------- old-x producer: item i's 4 site slabs into slot i % nxs once the epilogue warps released
+    // it (lane j issues site j)
+    for (int i = 0; i < n_my; ++i) {
+      const int sl = i % nxs;
+      int ok = lane == 0 ? !s_bad : 0;
+      if (lane == 0 && ok && i >= nxs && !mbar_wait(&oxempty_bar[sl], (uint32_t)((i / nxs) - 1) & 1u)) {
+        atomicExch(err, 46);
+        s_bad = 1;
+        ok = 0;
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      if (lane == 0) mbar_expect_tx(&oxfull_bar[sl], (uint32_t)(4 * xtile));
+      __syncwarp();
+      if (lane < 4) tma_load_2d(sX(sl, lane), &xmap, site_of(i, lane) * 32, rhs0, &oxfull_bar[sl]);
+    }
+    if (lane == 0)
+      for (int i = max(0, n_my - nxs); i < n_my && !s_bad; ++i)
+        mbar_wait(&oxfull_bar[i % nxs], (uint32_t)(i / nxs) & 1u);
+  } else if (warp == TB_MMA_WARP) {
+    // ---------------- MMA issuer: D[rhs][n] = sum_k r[rhs][k] inv[n][k], K chunk kc = block site kc
+    if (lane == 0) {
+      const uint32_t idesc = BF == 2 ? idesc_f16(TB_MM, 128) : idesc_bf16(TB_MM, 128);
+      const uint64_t ad0 = sw64_desc(smem_u32(sA(0, 0))), bd0 = sw64_desc(smem_u32(sB(0, 0)));
+      for (int i = 0; i < n_my && !s_bad; ++i) {
+        const int s = i % TS_STAGES, a = i % TB_NACC;
+        if (!mbar_wait(&xfull_bar[s], (uint32_t)(i / TS_STAGES) & 1u)) {
+          atomicExch(err, 42);
+          s_bad = 1;
+          break;
+        }
+        if (i >= TB_NACC && !mbar_wait(&tempty_bar[a], (uint32_t)((i / TB_NACC) - 1) & 1u)) {
+          atomicExch(err, 43);
+          s_bad = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = taddr + (uint32_t)(a * 128);
+        const uint64_t ads = ad0 + (uint64_t)((s * TS_STAGE) >> 4), bds = bd0 + (uint64_t)((s * TS_STAGE) >> 4);
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc)
+#pragma unroll
+          for (int k2 = 0; k2 < 2; ++k2)
+            mma_bf16(d, ads + (uint64_t)((kc * TS_ATILE) >> 4) + 2 * k2, bds + (uint64_t)((kc * TS_BTILE) >> 4) + 2 * k2,
+                     idesc, (kc | k2) ? 1u : 0u);
+        mma_commit(&empty_bar[s]);
+        mma_commit(&tfull_bar[a]);
+      }
+    }
+  } else if (warp >= TB_CONV_WARP0) {
+    // ---------------- converters: Im rows 64 + n of every K chunk from its stored Re row n (planar K: logical
+    // chunk c of the Im row is chunk c ^ 2 of the Re row, negated for c < 2; rows n and n + 64 share the phase)
+    const int ct = (warp - TB_CONV_WARP0) * 32 + lane;
+    constexpr int NT = 32 * TB_CONV_WARPS;
+    for (int i = 0; i < n_my; ++i) {
+      const int s = i % TS_STAGES;
+      if (s_bad || !mbar_wait(&full_bar[s], (uint32_t)(i / TS_STAGES) & 1u)) {
+        if (!s_bad) atomicExch(err, 45);
+        s_bad = 1;
+        break;
+      }
+#pragma unroll 2
+      for (int e = ct; e < 4 * 256; e += NT) {
+        uint4* wb = reinterpret_cast<uint4*>(sB(s, e >> 8));
+        const int c0 = e & 255;  // chunk index within the stored Re rows (64 rows x 4 chunks)
+        const uint32_t neg = (((c0 & 3) ^ ((c0 >> 3) & 3)) & 2) ? 0u : 0x80008000u;
+        const uint4 v = wb[c0 ^ 2];
+        wb[c0 + 256] = make_uint4(v.x ^ neg, v.y ^ neg, v.z ^ neg, v.w ^ neg);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&xfull_bar[s]);
+    }
+  } else {
+    // ---------------- epilogue: warp w owns TMEM lane quarter w % 4 (rhs row r in lane 32 (r / 16) + r % 16)
+    // and the items of parity p = (w - first epilogue warp) / 4 (item i's old x in slot i % nxs); step k =
+    // (block site j = k / 2, complex dofs 8 (k % 2) .. + 7): x += product
+    const int q = warp & 3, par = (warp - TB_EPI_WARP0) >> 2;
+    const int row = q * 16 + lane;
+    const int rhs = rhs0 + row;
+    const bool exists = lane < 16 && rhs < nrhs;
+    const bool live = exists && !(active && !active[rhs]);
+    const bool quarter_live = rhs0 + q * 16 < nrhs;
+    const bool storer = q == 0 && lane == 0;
+    for (int i = par; i < n_my; i += 2) {
+      const int a = i % TB_NACC;
+      if (s_bad || !mbar_wait(&tfull_bar[a], (uint32_t)(i / TB_NACC) & 1u) ||
+          !mbar_wait(&oxfull_bar[i % nxs], (uint32_t)(i / nxs) & 1u)) {
+        if (!s_bad) atomicExch(err, 44);
+        s_bad = 1;
+        break;
+      }
+      tc_fence_after();
+      __syncwarp();
+      const uint32_t tq = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128);
+      float vs[32];  // site j's product: vs[0..15] Re, vs[16..31] Im of dofs 0 .. 15
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int j = k >> 1, t = k & 1;
+        if (!quarter_live) continue;
+        if (t == 0) tmem_ld16x2(tq + 16 * j, tq + 64 + 16 * j, vs);  // one TMEM wait per site
+        float v[16];  // v[0..7] Re, v[8..15] Im of dofs 8t .. 8t + 7 of block site j
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          v[e] = vs[8 * t + e];
+          v[8 + e] = vs[16 + 8 * t + e];
+        }
+        if (exists) {
+          // old x: FP32 chunks 4t .. 4t+3 of this row of site j's slab (128-byte swizzle: chunk c at c ^ (row & 7)),
+          // updated in place
+          float4* xs = reinterpret_cast<float4*>(sX(i % nxs, j)) + row * 8;
+          float4 cur[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) cur[u] = xs[(4 * t + u) ^ (row & 7)];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {  // inactive rhs: x unchanged (their product rows may hold anything)
+            v[2 * u] = live ? v[2 * u] + cur[u].x : cur[u].x;
+            v[8 + 2 * u] = live ? v[8 + 2 * u] + cur[u].y : cur[u].y;
+            v[2 * u + 1] = live ? v[2 * u + 1] + cur[u].z : cur[u].z;
+            v[9 + 2 * u] = live ? v[9 + 2 * u] + cur[u].w : cur[u].w;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            xs[(4 * t + u) ^ (row & 7)] = make_float4(v[2 * u], v[8 + 2 * u], v[2 * u + 1], v[9 + 2 * u]);
+          const int site = site_of(i, j);
+          uint16_t* o16 = x16 + (size_t)rhs * ncf + (size_t)site * 32 + 8 * t;
+          uint4 re, im;
+          re.x = tb_pack<BF>(v[0], v[1]), re.y = tb_pack<BF>(v[2], v[3]);
+          re.z = tb_pack<BF>(v[4], v[5]), re.w = tb_pack<BF>(v[6], v[7]);
+          im.x = tb_pack<BF>(v[8], v[9]), im.y = tb_pack<BF>(v[10], v[11]);
+          im.z = tb_pack<BF>(v[12], v[13]), im.w = tb_pack<BF>(v[14], v[15]);
+          *reinterpret_cast<uint4*>(o16) = re;
+          *reinterpret_cast<uint4*>(o16 + 16) = im;
+        }
+      }
+      tc_fence_before();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // slot writes -> TMA store reads
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&tempty_bar[a]);
+        mbar_arrive(&edone_bar[i % nxs]);
+      }
+      if (q == 0) {  // the storing warp (warp-uniform wait; lane 0 issues the stores)
+        if (!mbar_wait(&edone_bar[i % nxs], (uint32_t)(i / nxs) & 1u)) {
+          if (lane == 0) atomicExch(err, 47);
+          s_bad = 1;
+          break;
+        }
+        if (storer) {
+          for (int j = 0; j < 4; ++j) tma_store_2d(&xmap, sX(i % nxs, j), site_of(i, j) * 32, rhs0);
+          bulk_commit();
+          bulk_wait_read0();  // the slot may be refilled once the stores have read it
+          mbar_arrive(&oxempty_bar[i % nxs]);
+        }
+        __syncwarp();
+      }
+    }
+    if (storer) bulk_wait0();  // the stores have landed before the CTA exits
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 512);
+  }
+}
+
+// 2D view [nrhs rows][ns x 32 16-bit values]; box 32 values (one site, 64 B) x 64 rows, 64-byte swizzle (rows
+// past nrhs are filled with zeros by the copy engine)
+CUtensorMap map16(const void* v, int ns, int nrhs) {
+  MG_CHECK_ARG(v && ((uintptr_t)v & 15) == 0, "16-bit coarse vector: 16-byte aligned device pointer");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)ns * 32, (cuuint64_t)nrhs};
+  cuuint64_t strides[1] = {(cuuint64_t)ns * 64};
+  cuuint32_t box[2] = {32, (cuuint32_t)TB_MM};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(v), dims, strides, box, es,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(MGMLMC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+dim3 grid_of(int nitems, int nrhs) {
   int dev = 0, nsm = 152;
   MG_CUDA(cudaGetDevice(&dev));
   MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int tiles = (nrhs + TB_MM - 1) / TB_MM;
-  const int gx = std::max(1, std::min(nitems, (nsm + tiles - 1) / tiles));
-  dim3 grid(gx, tiles);
+  return dim3(std::max(1, std::min(nitems, (nsm + tiles - 1) / tiles)), tiles);
+}
+
+}  // namespace
+
+void tc_block_stencil(cudaStream_t st, int bf, const void* W, int Ls, const void* x16, void* y, int y16,
+                      const float2* b, int bmode, int color, int nrhs, const int* active, int* err, double bytes,
+                      double flops) {
+  MG_CHECK_ARG(bf == 1 || bf == 2, "the block stencil kernel takes 16-bit operands");
+  MG_CHECK_ARG(Ls >= 4 && Ls % 4 == 0, "the block stencil kernel needs a lattice side that is a multiple of 4");
+  MG_CHECK_ARG(!y16 || bmode, "16-bit output: colour blocks only");
+  const CUtensorMap xmap = map16(x16, Ls * Ls, nrhs);
+  const int nitems = bmode ? Ls * Ls / 8 : Ls * Ls / 4;
+  const dim3 grid = grid_of(nitems, nrhs);
   auto go = [&](auto* k_tcb_kernel) {
     ensure_max_smem((const void*)k_tcb_kernel, TB_SMEM);
-    MG_LAUNCH_W(bytes, flops, k_tcb_kernel, grid, TB_THREADS, TB_SMEM, st, (const float*)x,
-                (const unsigned char*)W, (float*)y, (const float*)b, Ls, nitems, bmode, color, nrhs, active, err);
+    MG_LAUNCH_W(bytes, flops, k_tcb_kernel, grid, TB_THREADS, TB_SMEM, st, xmap, (const unsigned char*)W, y,
+                (const float*)b, Ls, nitems, bmode, color, nrhs, active, err);
   };
   if (bf == 2)
-    go(&k_tcb<2>);
+    y16 ? go(&k_tcb<2, 1>) : go(&k_tcb<2, 0>);
   else
-    go(&k_tcb<1>);
+    y16 ? go(&k_tcb<1, 1>) : go(&k_tcb<1, 0>);
+}
+
+void tc_block_update(cudaStream_t st, int bf, const void* Winv, int Ls, const void* r16, float2* x, void* x16,
+                     int color, int nrhs, const int* active, int* err, double bytes, double flops) {
+  MG_CHECK_ARG(bf == 1 || bf == 2, "the block update kernel takes 16-bit operands");
+  MG_CHECK_ARG(Ls >= 4 && Ls % 4 == 0, "the block update kernel needs a lattice side that is a multiple of 4");
+  MG_CHECK_ARG(x && x16, "block update: x and its 16-bit copy");
+  const CUtensorMap rmap = map16(r16, Ls * Ls, nrhs);
+  MG_CHECK_ARG(((uintptr_t)x & 15) == 0, "x: 16-byte aligned device pointer");
+  // 2D view [nrhs rows][Ls^2 x 32 floats] of x; box 32 floats (one site) x xrows rows, 128-byte swizzle
+  const int xrows = nrhs <= 32 ? 32 : TB_MM;
+  CUtensorMap xmap;
+  {
+    const int ns = Ls * Ls;
+    cuuint64_t dims[2] = {(cuuint64_t)ns * 32, (cuuint64_t)nrhs};
+    cuuint64_t strides[1] = {(cuuint64_t)ns * 128};
+    cuuint32_t box[2] = {32, (cuuint32_t)xrows};
+    cuuint32_t es[2] = {1, 1};
+    const CUresult r = encode_fn()(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)x, dims, strides, box, es,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error(MGMLMC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  }
+  const int nitems = Ls * Ls / 8;
+  const dim3 grid = grid_of(nitems, nrhs);
+  auto go = [&](auto* k_tcs_kernel) {
+    ensure_max_smem((const void*)k_tcs_kernel, TS_SMEM);
+    MG_LAUNCH_W(bytes, flops, k_tcs_kernel, grid, TS_THREADS, TS_SMEM, st, rmap, xmap, (const unsigned char*)Winv,
+                (float*)x, (uint16_t*)x16, Ls, nitems, color, nrhs, xrows, active, err);
+  };
+  if (bf == 2)
+    go(&k_tcs<2>);
+  else
+    go(&k_tcs<1>);
 }
 
 }  // namespace mg

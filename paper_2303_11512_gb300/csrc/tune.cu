@@ -121,9 +121,10 @@ void autotune(mgmlmc_hier* h, const std::vector<int>& nrhs_list, bool force) {
       if (!h->use_tc(l) || !L.tcInv[0].p) continue;
       const int fmt = L.tc_bf;
       DBuf x(sizeof(float2) * L.n * bucket, st), y(sizeof(float2) * L.n * bucket, st),
-          f(sizeof(float2) * L.n * bucket, st);
+          f(sizeof(float2) * L.n * bucket, st), x16(fmt ? sizeof(uint32_t) * L.n * bucket : 16, st);
       vzero<float2>(st, x.as<float2>(), L.n, bucket);
       vzero<float2>(st, f.as<float2>(), L.n, bucket);
+      if (fmt) MG_CUDA(cudaMemsetAsync(x16.p, 0, sizeof(uint32_t) * L.n * bucket, st));
       if (force || !tune_known(TUNE_TC0, L.side, bucket, fmt)) {
         int best = 0;
         float tbest = 1e30f;
@@ -134,8 +135,8 @@ void autotune(mgmlmc_hier* h, const std::vector<int>& nrhs_list, bool force) {
         for (int v : vars) {
           tune_store(TUNE_TC0, L.side, bucket, fmt, v, 0.f);
           const float t = time_us(st, [&] {
-            tc_stencil_apply(st, L.tcW.p, fmt, L.side, x.as<float2>(), y.as<float2>(), f.as<float2>(), bucket,
-                             nullptr, err);
+            tc_stencil_apply(st, L.tcW.p, fmt, L.side, x.as<float2>(), x16.p, y.as<float2>(), f.as<float2>(),
+                             bucket, nullptr, err);
           });
           if (t < tbest) { tbest = t; best = v; }
         }
@@ -147,8 +148,8 @@ void autotune(mgmlmc_hier* h, const std::vector<int>& nrhs_list, bool force) {
         for (int cap : {0, 1, 2, 4}) {
           tune_store(TUNE_TC1, L.side, bucket, fmt, cap, 0.f);
           const float t = time_us(st, [&] {
-            tc_sap_half(st, L.tcW.p, L.tcInv[0].p, fmt, L.side, f.as<float2>(), x.as<float2>(), y.as<float2>(), 0,
-                        bucket, nullptr, err);
+            tc_sap_half(st, L.tcW.p, L.tcInv[0].p, fmt, L.side, f.as<float2>(), x.as<float2>(), fmt ? x16.p : nullptr,
+                        y.as<float2>(), 0, bucket, nullptr, err);
           });
           if (t < tbest) { tbest = t; best = cap; }
         }

@@ -100,11 +100,14 @@ def test_estimate_of_the_benchmark_configuration(setup):
             S, _ = qr_positive(ld.apply(l, S))
         tlr = complex(np.sum(np.conj(S) * ld.apply(l, S)))
         assert abs(r["tau_lr"][l] - tlr) < 1e-8 * abs(tlr), (l, r["tau_lr"][l], tlr)
-        # the GPU's Q of this level (same seed, d, k: the basis the estimate projected with)
+        # the GPU's Q of this level (same seed, d, k: the basis the estimate projected with).  The estimate
+        # solves the sketches of neighbouring levels side by side (64 rhs per coarse launch) where this call
+        # solves one level's 32, so the launches may take the other tensor-core stencil kernel (another FP32
+        # summation order): the two agree to the solver tolerance (1e-10 residual), not bitwise
         sk, tlr1 = api.hutchpp_sketch_qr(ctx, h, l, W["d"], W["k"], 0, api.ACCUMULATED)
         Qf = ld.Phat[l] @ sk.Q().cpu().numpy().T
         sk.close()
-        assert abs(tlr1 - r["tau_lr"][l]) < 1e-10 * abs(tlr)
+        assert abs(tlr1 - r["tau_lr"][l]) < 1e-8 * abs(tlr)
         assert relerr(Qf, S) < 1e-6
         # every computed stochastic sample, projected with that Q
         nc = r["computed"][l]
