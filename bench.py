@@ -42,13 +42,20 @@ WORKLOAD = dict(L=512, beta=5.0, seed=0, ntv=8, d=32, k=2, eps=1e-3, nrhs_max=25
 FALLBACK_M0 = {512: -0.07, 128: -0.1199}
 
 
-# DRAM bytes per algorithmic byte of the tensor-core coarse stencil kernels, from one ncu capture each of the
-# level-1 launch with 32 rhs of the L = 512 hierarchy (dram__bytes_read + _write against the launch's algorithmic
-# bytes); the benchmark scales them to its average launch.  Per-site TF32 kernel: 235.99 + 48.96 MB against
-# 301.99 MB (weights 167.8 MB + 32 rhs x 16384 sites x 256 B); profiles/k_tc_stencil_level1_32rhs_L512.md.
+# DRAM bytes per algorithmic byte of the tensor-core coarse kernels, from one ncu capture each of a level-1 launch
+# with 32 rhs of the L = 512 hierarchy (dram__bytes_read + _write against the launch's algorithmic bytes); the
+# benchmark scales them to its average launch.  Per-site TF32 stencil: 235.99 + 48.96 MB against 301.99 MB
+# (profiles/k_tc_stencil_level1_32rhs_L512.md).  2x2-block FP16 stencil, SAP residual of one colour: 109.31 +
+# 5.99 MB against 109.05 MB (8192 sites x 32 rhs x 256 B + 41.94 MB of weights); SAP block update: 83.95 + 5.74
+# MB against 134.22 MB (its x and 16-bit copy writes stay in L2;
+# profiles/k_tcb_k_tcs_sap_level1_32rhs_L512.md).
 TRAFFIC_PER_ALG_BYTE = {
     "MODE = 0; int BF = 0": ((235.987 + 48.964) / 301.990, "ncu capture of one launch (level 1, 32 rhs): 284.95 MB "
                             "DRAM / 301.99 MB algorithmic, scaled to the average launch"),
+    "k_tcb_kernel": ((109.313 + 5.991) / 109.052, "ncu capture of one SAP-residual launch (level 1, 32 rhs, FP16): "
+                     "115.30 MB DRAM / 109.05 MB algorithmic, scaled to the average launch"),
+    "k_tcs_kernel": ((83.952 + 5.735) / 134.218, "ncu capture of one SAP block-update launch (level 1, 32 rhs, "
+                     "FP16): 89.69 MB DRAM / 134.22 MB algorithmic, scaled to the average launch"),
 }
 
 
@@ -509,7 +516,7 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     # DRAM traffic of the dominant kernel: the ncu capture of one launch (dram__bytes_read + _write) relative to
     # that launch's algorithmic bytes, scaled to this run's average launch (the bench's launches mix levels and
-    # batch sizes; the capture is the level-1, 32-rhs stencil of profiles/k_tc_stencil_level1_32rhs_L512.md)
+    # batch sizes; the captures are level-1, 32-rhs launches, TRAFFIC_PER_ALG_BYTE)
     traffic, traffic_src = None, None
     for key, (ratio, src) in TRAFFIC_PER_ALG_BYTE.items():
         if key in dom:

@@ -8,7 +8,8 @@
 // the item's 4 x 32 accumulator columns) replaces three; the 8 halo slabs feed one site each.  12 slabs x 2 K
 // steps = 24 MMAs per block, 6 per site.
 //
-// Shared memory of a stage: 12 vector tiles (64 rhs rows x 32 16-bit values, 64-byte swizzle), each one TMA box
+// Shared memory of a stage: 12 vector tiles (64 rhs rows, or 32 for launches of at most 32 rhs, x 32 16-bit
+// values, 64-byte swizzle), each one TMA box
 // of the planar 16-bit copy of x ([rhs][site][16 Re | 16 Im], kept up to date by the kernels that write x, rows
 // past nrhs filled with zeros by the copy engine), and the weight windows: 22 sub-tiles of 32 rows (Re rows from
 // the per-site weight image by bulk copies, Im rows derived by converter warps), two of them zero, arranged so
@@ -29,16 +30,25 @@ namespace {
 constexpr int TB_MM = 64;                   // rhs per tile (MMA M)
 constexpr int TB_SLABS = 12;
 constexpr int TB_BROWS = 704;               // weight rows per stage (22 sub-tiles of 32)
-constexpr int TB_VTILE = TB_MM * 64;        // bytes of one vector tile
-constexpr int TB_STAGE = TB_SLABS * TB_VTILE + TB_BROWS * 64;
-constexpr int TB_STAGES = 2;
+// a vector tile holds vrows_t = 64 rhs rows (32 where the launch has at most 32 rhs: the M = 64 MMA then also reads
+// the next 2 KB as rows 32..63, whose accumulator rows are never stored), so a stage is 92 KB or 68 KB and the
+// pipeline 2 or 3 stages deep
+constexpr int TB_MAXST = 3;
+__host__ __device__ constexpr int tb_stage_bytes(int vrows_t) { return TB_SLABS * vrows_t * 64 + TB_BROWS * 64; }
+__host__ __device__ constexpr int tb_stages(int vrows_t) { return vrows_t == 32 ? 3 : 2; }
 constexpr int TB_NACC = 4;                  // accumulators (128 columns each)
 constexpr int TB_PROD_WARP = 0, TB_MMA_WARP = 1, TB_EPI_WARP0 = 2, TB_EPI_WARPS = 8, TB_CONV_WARP0 = 10,
               TB_CONV_WARPS = 4;
-constexpr uint32_t TB_TX = 20u * 1024u + TB_SLABS * TB_VTILE;  // bytes landing in a stage per item
+
 constexpr int TB_THREADS = 32 * (TB_CONV_WARP0 + TB_CONV_WARPS);
 static_assert(TB_CONV_WARP0 == TB_EPI_WARP0 + TB_EPI_WARPS, "warp roles: producer, MMA, epilogue, converters");
-constexpr int TB_SMEM = 1024 + TB_STAGES * TB_STAGE;
+constexpr int TB_EBUF = 2048;  // per epilogue warp and slot: one site of its 16 rhs rows (b in, the output out)
+// epilogue buffers: two slots for each warp whose lane quarter can hold rhs (all 8 warps, or the 4 of quarters
+// 0 and 1 with 32-row tiles)
+__host__ __device__ constexpr int tb_smem_bytes(int vrows_t) {
+  return 1024 + tb_stages(vrows_t) * tb_stage_bytes(vrows_t) + (vrows_t == 32 ? 4 : 8) * 2 * TB_EBUF;
+}
+static_assert(tb_smem_bytes(32) <= 227 * 1024 && tb_smem_bytes(64) <= 227 * 1024, "shared memory per CTA");
 
 // weight sub-tile row of (block site j, direction f), f: 0 self, 1 +x, 2 -x, 3 +t, 4 -t
 __constant__ short c_rowpos[4][5] = {{0, 96, 448, 224, 480},
@@ -62,6 +72,14 @@ __device__ __forceinline__ uint32_t tb_pack(float a, float b) {
   return BF == 2 ? f16x2_rn(a, b) : bf16x2_rn(a, b);
 }
 
+// 16-byte global -> shared copy without a register round trip (completion by commit / wait groups)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // corner (t0, x0) of item k: all blocks (bmode 0, colour-0 blocks then colour-1 blocks) or the blocks of colour
 // `color` (bmode 1), in the block order of the SAP sweeps
 __device__ __forceinline__ void tb_corner(int k, int Ls, int bmode, int color, int& t0, int& x0) {
@@ -84,30 +102,32 @@ __device__ __forceinline__ void tb_corner(int k, int Ls, int bmode, int color, i
 template <int BF, int O16>
 __global__ void __launch_bounds__(TB_THREADS, 1)
     k_tcb(const __grid_constant__ CUtensorMap xmap, const unsigned char* __restrict__ W, void* __restrict__ out,
-          const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs,
+          const float* __restrict__ bvec, int Ls, int nitems, int bmode, int color, int nrhs, int vrows_t,
           const int* __restrict__ active, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[TB_STAGES], empty_bar[TB_STAGES], xfull_bar[TB_STAGES];
+  __shared__ __align__(8) uint64_t full_bar[TB_MAXST], empty_bar[TB_MAXST], xfull_bar[TB_MAXST];
   __shared__ __align__(8) uint64_t tfull_bar[TB_NACC], tempty_bar[TB_NACC];
   __shared__ uint32_t s_taddr;
   __shared__ int s_skip;
   __shared__ volatile int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rhs0 = blockIdx.y * TB_MM;
+  const int vtile = vrows_t * 64, stage = tb_stage_bytes(vrows_t), nst = tb_stages(vrows_t);
+  const uint32_t tx = 20u * 1024u + (uint32_t)(TB_SLABS * vtile);  // bytes landing in a stage per item
   const long ncf = (long)Ls * Ls * 32;  // floats per rhs row
   if (tid == 0) s_skip = *(volatile int*)err;
   __syncthreads();
   if (s_skip) return;
   // the two zero weight sub-tiles (rows 160..191 and 256..287 of every stage's weight windows) are never written
   // by the pipeline: clear them once
-  for (int i = tid; i < TB_STAGES * 2 * 32 * 4; i += TB_THREADS) {
+  for (int i = tid; i < nst * 2 * 32 * 4; i += TB_THREADS) {
     const int st = i / 256, z = (i >> 7) & 1, e = i & 127;
-    reinterpret_cast<uint4*>(base + st * TB_STAGE + TB_SLABS * TB_VTILE + (z ? 256 : 160) * 64)[e] =
+    reinterpret_cast<uint4*>(base + st * stage + TB_SLABS * vtile + (z ? 256 : 160) * 64)[e] =
         make_uint4(0, 0, 0, 0);
   }
   if (tid == 0) {
-    for (int s = 0; s < TB_STAGES; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
       mbar_init(&xfull_bar[s], TB_CONV_WARPS);
@@ -127,23 +147,22 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
   const uint32_t taddr = s_taddr;
   int n_my = 0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) ++n_my;
-  auto sV = [&](int s, int q) { return base + s * TB_STAGE + q * TB_VTILE; };
-  auto sB = [&](int s) { return base + s * TB_STAGE + TB_SLABS * TB_VTILE; };
+  auto sV = [&](int s, int q) { return base + s * stage + q * vtile; };
+  auto sB = [&](int s) { return base + s * stage + TB_SLABS * vtile; };
 
   if (warp == TB_PROD_WARP) {
     // ---------------- producer: lanes 0..19 the 20 stored weight halves of the block (lane 5 j + f: site j,
     // direction f), lanes 20..31 the 12 vector slabs (TMA boxes of the 16-bit copy)
     for (int i = 0; i < n_my; ++i) {
-      const int s = i % TB_STAGES;
+      const int s = i % nst;
       int ok = lane == 0 ? !s_bad : 0;
-      if (lane == 0 && ok && i >= TB_STAGES &&
-          !mbar_wait(&empty_bar[s], (uint32_t)((i / TB_STAGES) - 1) & 1u)) {
+      if (lane == 0 && ok && i >= nst && !mbar_wait(&empty_bar[s], (uint32_t)((i / nst) - 1) & 1u)) {
         atomicExch(err, 31);
         s_bad = 1;
         ok = 0;
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      if (lane == 0) mbar_expect_tx(&full_bar[s], TB_TX);
+      if (lane == 0) mbar_expect_tx(&full_bar[s], tx);
       __syncwarp();
       int t0, x0;
       tb_corner(blockIdx.x + i * gridDim.x, Ls, bmode, color, t0, x0);
@@ -159,14 +178,13 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
     }
     // the last copies land before the CTA can exit (bounded)
     if (lane == 0)
-      for (int i = max(0, n_my - TB_STAGES); i < n_my && !s_bad; ++i)
-        mbar_wait(&full_bar[i % TB_STAGES], (uint32_t)(i / TB_STAGES) & 1u);
+      for (int i = max(0, n_my - nst); i < n_my && !s_bad; ++i) mbar_wait(&full_bar[i % nst], (uint32_t)(i / nst) & 1u);
   } else if (warp == TB_MMA_WARP) {
     // ---------------- MMA issuer
     if (lane == 0) {
       for (int i = 0; i < n_my && !s_bad; ++i) {
-        const int s = i % TB_STAGES, a = i % TB_NACC;
-        if (!mbar_wait(&xfull_bar[s], (uint32_t)(i / TB_STAGES) & 1u)) {
+        const int s = i % nst, a = i % TB_NACC;
+        if (!mbar_wait(&xfull_bar[s], (uint32_t)(i / nst) & 1u)) {
           atomicExch(err, 32);
           s_bad = 1;
           break;
@@ -184,7 +202,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
           const int q = c_order[o];
           const int nn = c_ncol[q];
           const uint32_t idesc = BF == 2 ? idesc_f16(TB_MM, nn) : idesc_bf16(TB_MM, nn);
-          const uint64_t ad = vd0 + (uint64_t)((q * TB_VTILE) >> 4), bd = bd0 + (uint64_t)((c_brow[q] * 64) >> 4);
+          const uint64_t ad = vd0 + (uint64_t)((q * vtile) >> 4), bd = bd0 + (uint64_t)((c_brow[q] * 64) >> 4);
           const uint32_t d = d0 + (uint32_t)c_col0[q];
 #pragma unroll
           for (int k2 = 0; k2 < 2; ++k2) mma_bf16(d, ad + 2 * k2, bd + 2 * k2, idesc, (o >= 4 || k2 > 0) ? 1u : 0u);
@@ -199,8 +217,8 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
     const int ct = (warp - TB_CONV_WARP0) * 32 + lane;
     constexpr int NT = 32 * TB_CONV_WARPS;
     for (int i = 0; i < n_my; ++i) {
-      const int s = i % TB_STAGES;
-      if (s_bad || !mbar_wait(&full_bar[s], (uint32_t)(i / TB_STAGES) & 1u)) {
+      const int s = i % nst;
+      if (s_bad || !mbar_wait(&full_bar[s], (uint32_t)(i / nst) & 1u)) {
         if (!s_bad) atomicExch(err, 35);
         s_bad = 1;
         break;
@@ -220,34 +238,44 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
     }
   } else {
     // ---------------- epilogue: warp w owns TMEM lane quarter w % 4 (M = 64: rhs row r of the tile in lane
-    // 32 (r / 16) + r % 16) and the items of parity (w - first epilogue warp) / 4; per site, two steps of 8
-    // complex outputs (Re in columns 32 j + [0, 16), Im in 32 j + [16, 32))
-    const int q = warp & 3, par = (warp - TB_EPI_WARP0) >> 2;
+    // 32 (r / 16) + r % 16) and the items of parity (w - first epilogue warp) / 4; per site j, Re outputs in
+    // columns 32 j + [0, 16), Im in 32 j + [16, 32).  Memory traffic goes through two per-warp slots of one site
+    // x 16 rows: the additive input b of the next site is copied in (cp.async, each instruction 4 whole 128-byte
+    // rows) while the current one is used, and the outputs are staged in the slot just read and stored with
+    // each instruction covering whole row segments, instead of 16-byte pieces of 16 rows.
+    const int q = warp & 3, ew = warp - TB_EPI_WARP0, par = ew >> 2;
     const int row = q * 16 + lane;
     const int rhs = rhs0 + row;
     const bool live = lane < 16 && rhs < nrhs && !(active && !active[rhs]);
     const bool quarter_live = rhs0 + q * 16 < nrhs;  // warp-uniform
-    // offset of step k (site j = k / 2, complex outputs 8 (k % 2) .. + 7) of item i in this thread's rhs row
-    auto step_off = [&](int i, int k) -> size_t {
+    const unsigned live_mask = __ballot_sync(0xffffffffu, live);  // bit r: row r of the quarter is stored
+    const int rows_here = min(16, max(0, nrhs - (rhs0 + q * 16)));
+    unsigned char* ebuf = base + nst * stage + (vrows_t == 32 ? 2 * par + (q & 1) : ew) * 2 * TB_EBUF;
+    // the warp's site sequence g = 4 (k-th item of the parity) + j
+    const int n_par = n_my > par ? (n_my - par + 1) / 2 : 0;
+    auto site_g = [&](int g) -> int {
       int t0, x0;
-      tb_corner(blockIdx.x + i * gridDim.x, Ls, bmode, color, t0, x0);
-      const int j = k >> 1;
-      return (size_t)rhs * ncf + (size_t)((t0 + (j >> 1)) * Ls + x0 + (j & 1)) * 32 + 16 * (k & 1);
+      tb_corner(blockIdx.x + (par + 2 * (g >> 2)) * gridDim.x, Ls, bmode, color, t0, x0);
+      const int j = g & 3;
+      return (t0 + (j >> 1)) * Ls + x0 + (j & 1);
     };
-    // the additive input b of step g + RD is fetched at step g (the steps of this warp's items in sequence), so
-    // its loads overlap the TMEM reads and stores of the steps before it
-    constexpr int NSTEP = 8, RD = 2;
-    float4 ring[RD][4];
-    auto prefetch = [&](float4 (&dst)[4], int i, int k) {
-      if (bvec && live && i < n_my) {
-        const float4* src = reinterpret_cast<const float4*>(bvec + step_off(i, k));
+    auto fetch_b = [&](int g) {  // rows 4k + lane / 8, 16-byte chunk lane % 8 (swizzled by the row)
+      if (bvec && quarter_live && g < 4 * n_par) {
+        const int site = site_g(g);
+        unsigned char* slot = ebuf + (g & 1) * TB_EBUF;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) dst[u] = __ldg(src + u);
+        for (int k = 0; k < 4; ++k) {
+          const int r = 4 * k + (lane >> 3), c = lane & 7;
+          if (r < rows_here)
+            cp_async16(slot + r * 128 + ((c ^ (r & 7)) << 4),
+                       bvec + (size_t)(rhs0 + q * 16 + r) * ncf + (size_t)site * 32 + 4 * c);
+        }
       }
+      cp_async_commit();
     };
-#pragma unroll
-    for (int g = 0; g < RD; ++g) prefetch(ring[g], par, g);
-    for (int i = par; i < n_my; i += 2) {
+    fetch_b(0);
+    for (int ii = 0; ii < n_par; ++ii) {
+      const int i = par + 2 * ii;
       const int a = i % TB_NACC;
       if (s_bad || !mbar_wait(&tfull_bar[a], (uint32_t)(i / TB_NACC) & 1u)) {
         if (!s_bad) atomicExch(err, 34);
@@ -256,57 +284,76 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
       }
       tc_fence_after();
       __syncwarp();
-      int t0, x0;
-      tb_corner(blockIdx.x + i * gridDim.x, Ls, bmode, color, t0, x0);
       const uint32_t tq = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128);
-      float vs[32];  // site j's outputs: vs[0..15] Re, vs[16..31] Im of complex 0 .. 15
-#pragma unroll
-      for (int k = 0; k < NSTEP; ++k) {
-        const int j = k >> 1, t = k & 1;
-        float4 cur[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) cur[u] = ring[k % RD][u];
-        prefetch(ring[k % RD], i + 2 * ((k + RD) / NSTEP), (k + RD) % NSTEP);
+#pragma unroll 1
+      for (int j = 0; j < 4; ++j) {
+        const int g = 4 * ii + j;
+        fetch_b(g + 1);  // into the other slot, read two sites ago
+        cp_async_wait1();
+        __syncwarp();
         if (!quarter_live) continue;
-        if (t == 0) tmem_ld16x2(tq + 32 * j, tq + 32 * j + 16, vs);  // one TMEM wait per site
-        float v[16];  // v[0..7] Re, v[8..15] Im of complex outputs 8t .. 8t + 7 of block site j
+        unsigned char* slot = ebuf + (g & 1) * TB_EBUF;
+        float vs[32];  // vs[0..15] Re, vs[16..31] Im of the site's 16 complex outputs, this lane's row
+        tmem_ld16x2(tq + 32 * j, tq + 32 * j + 16, vs);
+        if (bvec && lane < 16) {  // y = b - D x; b's complex k at floats 2k, 2k + 1 of the row
+          const float4* bs = reinterpret_cast<const float4*>(slot + lane * 128);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          v[e] = vs[8 * t + e];
-          v[8 + e] = vs[16 + 8 * t + e];
+          for (int c = 0; c < 8; ++c) {
+            const float4 bb = bs[c ^ (lane & 7)];
+            vs[2 * c] = bb.x - vs[2 * c];
+            vs[16 + 2 * c] = bb.y - vs[16 + 2 * c];
+            vs[2 * c + 1] = bb.z - vs[2 * c + 1];
+            vs[17 + 2 * c] = bb.w - vs[17 + 2 * c];
+          }
         }
-        if (live) {
-          const int site = (t0 + (j >> 1)) * Ls + x0 + (j & 1);
-          if (bvec) {  // y = b - D x: b's complex k at cur[k / 2] (x, y) or (z, w)
+        __syncwarp();  // the slot's b is read: stage the outputs in it
+        if (lane < 16) {
+          if (O16) {  // 64-byte row: chunks Re 0..7, Re 8..15, Im 0..7, Im 8..15
+            uint4* os = reinterpret_cast<uint4*>(slot + lane * 64);
+            const int sw = (lane >> 1) & 3;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              v[2 * u] = cur[u].x - v[2 * u];
-              v[8 + 2 * u] = cur[u].y - v[8 + 2 * u];
-              v[2 * u + 1] = cur[u].z - v[2 * u + 1];
-              v[9 + 2 * u] = cur[u].w - v[9 + 2 * u];
+            for (int c = 0; c < 4; ++c) {
+              const float* h = vs + (c >> 1) * 16 + (c & 1) * 8;
+              os[c ^ sw] = make_uint4(tb_pack<BF>(h[0], h[1]), tb_pack<BF>(h[2], h[3]), tb_pack<BF>(h[4], h[5]),
+                                      tb_pack<BF>(h[6], h[7]));
+            }
+          } else {  // 128-byte row, interleaved (Re, Im)
+            float4* os = reinterpret_cast<float4*>(slot + lane * 128);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              os[c ^ (lane & 7)] = make_float4(vs[2 * c], vs[16 + 2 * c], vs[2 * c + 1], vs[17 + 2 * c]);
+          }
+        }
+        __syncwarp();
+        const int site = site_g(g);
+        if (O16) {  // 2 instructions of 8 rows x 64 bytes
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int r = 8 * k + (lane >> 2), c = lane & 3;
+            if ((live_mask >> r) & 1u) {
+              const uint4 v = reinterpret_cast<const uint4*>(slot + r * 64)[c ^ ((r >> 1) & 3)];
+              *reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(out) + (size_t)(rhs0 + q * 16 + r) * ncf +
+                                        (size_t)site * 32 + 8 * c) = v;
             }
           }
-          if (O16) {  // Re parts of complex 8t .. 8t+7, then their Im parts 16 values later
-            uint16_t* o = reinterpret_cast<uint16_t*>(out) + (size_t)rhs * ncf + (size_t)site * 32 + 8 * t;
-            uint4 re, im;
-            re.x = tb_pack<BF>(v[0], v[1]), re.y = tb_pack<BF>(v[2], v[3]);
-            re.z = tb_pack<BF>(v[4], v[5]), re.w = tb_pack<BF>(v[6], v[7]);
-            im.x = tb_pack<BF>(v[8], v[9]), im.y = tb_pack<BF>(v[10], v[11]);
-            im.z = tb_pack<BF>(v[12], v[13]), im.w = tb_pack<BF>(v[14], v[15]);
-            *reinterpret_cast<uint4*>(o) = re;
-            *reinterpret_cast<uint4*>(o + 16) = im;
-          } else {
-            float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + (size_t)rhs * ncf +
-                                                  (size_t)site * 32 + 16 * t);
+        } else {  // 4 instructions of 4 rows x 128 bytes
 #pragma unroll
-            for (int u = 0; u < 4; ++u) o[u] = make_float4(v[2 * u], v[8 + 2 * u], v[2 * u + 1], v[9 + 2 * u]);
+          for (int k = 0; k < 4; ++k) {
+            const int r = 4 * k + (lane >> 3), c = lane & 7;
+            if ((live_mask >> r) & 1u) {
+              const float4 v = reinterpret_cast<const float4*>(slot + r * 128)[c ^ (r & 7)];
+              *reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + (size_t)(rhs0 + q * 16 + r) * ncf +
+                                         (size_t)site * 32 + 4 * c) = v;
+            }
           }
         }
+        __syncwarp();  // the slot is refilled two sites later
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar[a]);
     }
+    cp_async_wait0();
   }
   __syncthreads();
   if (warp == 0) {
@@ -583,14 +630,14 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
   }
 }
 
-// 2D view [nrhs rows][ns x 32 16-bit values]; box 32 values (one site, 64 B) x 64 rows, 64-byte swizzle (rows
+// 2D view [nrhs rows][ns x 32 16-bit values]; box 32 values (one site, 64 B) x `rows` rows, 64-byte swizzle (rows
 // past nrhs are filled with zeros by the copy engine)
-CUtensorMap map16(const void* v, int ns, int nrhs) {
+CUtensorMap map16(const void* v, int ns, int nrhs, int rows) {
   MG_CHECK_ARG(v && ((uintptr_t)v & 15) == 0, "16-bit coarse vector: 16-byte aligned device pointer");
   CUtensorMap m;
   cuuint64_t dims[2] = {(cuuint64_t)ns * 32, (cuuint64_t)nrhs};
   cuuint64_t strides[1] = {(cuuint64_t)ns * 64};
-  cuuint32_t box[2] = {32, (cuuint32_t)TB_MM};
+  cuuint32_t box[2] = {32, (cuuint32_t)rows};
   cuuint32_t es[2] = {1, 1};
   const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(v), dims, strides, box, es,
                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -615,13 +662,16 @@ void tc_block_stencil(cudaStream_t st, int bf, const void* W, int Ls, const void
   MG_CHECK_ARG(bf == 1 || bf == 2, "the block stencil kernel takes 16-bit operands");
   MG_CHECK_ARG(Ls >= 4 && Ls % 4 == 0, "the block stencil kernel needs a lattice side that is a multiple of 4");
   MG_CHECK_ARG(!y16 || bmode, "16-bit output: colour blocks only");
-  const CUtensorMap xmap = map16(x16, Ls * Ls, nrhs);
+  const int vrows_t = nrhs <= 32 ? 32 : TB_MM;
+  const CUtensorMap xmap = map16(x16, Ls * Ls, nrhs, vrows_t);
   const int nitems = bmode ? Ls * Ls / 8 : Ls * Ls / 4;
   const dim3 grid = grid_of(nitems, nrhs);
+  const int smem = tb_smem_bytes(vrows_t);
   auto go = [&](auto* k_tcb_kernel) {
-    ensure_max_smem((const void*)k_tcb_kernel, TB_SMEM);
-    MG_LAUNCH_W(bytes, flops, k_tcb_kernel, grid, TB_THREADS, TB_SMEM, st, xmap, (const unsigned char*)W, y,
-                (const float*)b, Ls, nitems, bmode, color, nrhs, active, err);
+    ensure_max_smem((const void*)k_tcb_kernel, tb_smem_bytes(32) > tb_smem_bytes(64) ? tb_smem_bytes(32)
+                                                                                      : tb_smem_bytes(64));
+    MG_LAUNCH_W(bytes, flops, k_tcb_kernel, grid, TB_THREADS, smem, st, xmap, (const unsigned char*)W, y,
+                (const float*)b, Ls, nitems, bmode, color, nrhs, vrows_t, active, err);
   };
   if (bf == 2)
     y16 ? go(&k_tcb<2, 1>) : go(&k_tcb<2, 0>);
@@ -634,7 +684,7 @@ void tc_block_update(cudaStream_t st, int bf, const void* Winv, int Ls, const vo
   MG_CHECK_ARG(bf == 1 || bf == 2, "the block update kernel takes 16-bit operands");
   MG_CHECK_ARG(Ls >= 4 && Ls % 4 == 0, "the block update kernel needs a lattice side that is a multiple of 4");
   MG_CHECK_ARG(x && x16, "block update: x and its 16-bit copy");
-  const CUtensorMap rmap = map16(r16, Ls * Ls, nrhs);
+  const CUtensorMap rmap = map16(r16, Ls * Ls, nrhs, TB_MM);
   MG_CHECK_ARG(((uintptr_t)x & 15) == 0, "x: 16-byte aligned device pointer");
   // 2D view [nrhs rows][Ls^2 x 32 floats] of x; box 32 floats (one site) x xrows rows, 128-byte swizzle
   const int xrows = nrhs <= 32 ? 32 : TB_MM;
