@@ -192,7 +192,9 @@ int mg_level_info(const mgmlmc_hier* h, int level, int* side, int* dof, int64_t*
 /* tr(D_L^{-1}) of the coarsest level (= tau_L of Algorithm 2), host complex128. */
 int mg_coarsest_trace(const mgmlmc_hier* h, double* tau_L);
 
-/* y = D_l x on level l (vectors of n_l, precision prec). */
+/* y = D_l x on level l (vectors of n_l, precision prec).  With BF16 / FP16 (16-bit tensor-core images) the
+ * library rounds x to a 16-bit workspace copy first where the 2x2-block stencil kernel is selected for this
+ * level and batch (launch-shape table), so x itself is only read. */
 int mg_apply(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* x, void* y, int nrhs, int prec);
 /* xc = P_l^H xf  (level l -> l+1). */
 int mg_restrict(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* xf, void* xc, int nrhs, int prec);
@@ -208,8 +210,9 @@ int mg_get_stencil(mgmlmc_ctx* ctx, const mgmlmc_hier* h, int level, double* hos
 /* `sweeps` SAP sweeps for D_l x = f (the multigrid smoother): per sweep the
  * colour-0 blocks, then the colour-1 blocks, x_B += D_BB^{-1} (f - D_l x)_B
  * (block side sap_block_fine on level 0, sap_block_coarse above).  x is read
- * and updated in place.  prec FP64, FP32, or TF32 (tensor cores, coarse levels
- * with 16 dof only). */
+ * and updated in place.  prec FP64, FP32, or TF32 / BF16 / FP16 (tensor cores,
+ * coarse levels with 16 dof and images of that format only; the 16-bit forms keep
+ * a 16-bit workspace copy of x alongside the FP32 x for the 2x2-block kernels). */
 int mg_smooth(mgmlmc_ctx* ctx, mgmlmc_hier* h, int level, const void* f, void* x, int nrhs, int prec, int sweeps);
 
 /* Launch-shape autotuner (measurement of this machine, not part of the paper's method).  Several kernels have
