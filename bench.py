@@ -247,7 +247,9 @@ def profile_case(args):
     g.build()
     from paper_2303_11512_gb300 import api
     from synthetic import gauge
-    W = WORKLOAD
+    W = dict(WORKLOAD)
+    if args.tensor_cores is not None:
+        W["tensor_cores"] = args.tensor_cores
     L = args.L
     m0 = mass_for(L, W["beta"], W["seed"])
     U = torch.from_numpy(gauge.links(gauge.field(L, W["beta"], W["seed"]))).cuda()
