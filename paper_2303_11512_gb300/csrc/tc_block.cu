@@ -1,4 +1,7 @@
-// Coarse stencil on the tensor cores, one 2x2 block of sites per item (16-bit operands: BF16 or FP16).
+// The 16-bit (BF16 or FP16) coarse-level kernels on 2x2 blocks of sites: the stencil / SAP residual k_tcb and the
+// SAP block update k_tcs (at the end of the file).
+//
+// Coarse stencil on the tensor cores, one 2x2 block of sites per item.
 //
 // y_s = sum_f W_(s,f) x_(s+f) over f in {self, +x, -x, +t, -t}.  With the rhs on M, the per-site form issues one
 // N = 32 MMA chain per (site, slab): 20 MMAs of K = 8 (TF32) or 10 of K = 16 per site, and a tcgen05.mma costs its
@@ -9,11 +12,10 @@
 // steps = 24 MMAs per block, 6 per site.
 //
 // Shared memory of a stage: 12 vector tiles (64 rhs rows, or 32 for launches of at most 32 rhs, x 32 16-bit
-// values, 64-byte swizzle), each one TMA box
-// of the planar 16-bit copy of x ([rhs][site][16 Re | 16 Im], kept up to date by the kernels that write x, rows
-// past nrhs filled with zeros by the copy engine), and the weight windows: 22 sub-tiles of 32 rows (Re rows from
-// the per-site weight image by bulk copies, Im rows derived by converter warps), two of them zero, arranged so
-// that every slab's targets are consecutive rows:
+// values, 64-byte swizzle), each one TMA box of the planar 16-bit copy of x ([rhs][site][16 Re | 16 Im], kept up
+// to date by the kernels that write x, rows past nrhs filled with zeros by the copy engine), and the weight
+// windows: 22 sub-tiles of 32 rows (Re rows from the per-site weight image by bulk copies, Im rows derived by
+// converter warps), two of them zero, arranged so that every slab's targets are consecutive rows:
 //   slab s00: [W(s00,self) W(s01,-x) W(s10,-t)]            N =  96, columns  0..95
 //   slab s01: [W(s00,+x) W(s01,self) 0 W(s11,-t)]          N = 128, columns  0..127
 //   slab s10: [W(s00,+t) 0 W(s10,self) W(s11,-x)]          N = 128, columns  0..127
