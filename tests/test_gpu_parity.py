@@ -245,7 +245,7 @@ def test_block_and_site_stencil_kernels(api, ctx, fmt):
                     err = relerr(out[variant, l, nrhs], (H.D[l] @ x.T).T)
                     assert err < tol, (variant, l, nrhs, err)
             sap = omg.SAP(H.D[1], H.side[1], H.dof[1], 2)
-            for nrhs in (3, 40):
+            for nrhs in (3, 40, 130):  # one 32-row tile, one 64-row tile, three 64-row tiles (ragged)
                 fv, x0 = rand_vecs(H.n[1], nrhs, 80 + nrhs), rand_vecs(H.n[1], nrhs, 90 + nrhs)
                 ref = sap.sweep(fv.T.copy(), sap.sweep(fv.T.copy(), x0.T.copy())).T
                 xd = cuda(x0.astype(np.complex64))
