@@ -672,8 +672,11 @@ __global__ void k_zero_colour_blocks(float2* __restrict__ res, int Ls, int color
 }
 
 // res = f - D x on the sites of the colour-0 blocks and 0 on the colour-1 blocks: the V-cycle residual after
-// a SAP sweep whose last half sweep solved the colour-1 blocks, where it vanishes (the blocks of one colour do
-// not couple to each other, so their solves leave f - D x = 0 on them)
+// a SAP sweep whose last half sweep solved the colour-1 blocks.  The blocks of one colour do not couple to each
+// other, so with exact block solves f - D x would vanish on them; here the block inverses, the residual feeding
+// them and the stored x are TF32/BF16/FP16-accurate, so the residual that is set to zero is of the order of that
+// format's rounding times |f - D x|.  Dropping it perturbs the preconditioner only: the outer flexible Krylov
+// iteration and the FP64 true-residual refinement still converge to the requested residual.
 void tc_residual_after_sap(cudaStream_t st, const void* Wst, int bf, int Ls, const float2* x, const void* x16,
                            float2* res, const float2* f, int nrhs, const int* active, int* err) {
   if (nrhs <= 0) return;
