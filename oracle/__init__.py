@@ -15,4 +15,10 @@ Modules
               operators, the level hierarchy.
   estimators  plain Hutchinson (Algorithm 1), the MG-MLMC level differences,
               MG-MLMC++ (Algorithm 2) with direct solves.
+  deflation   exactly deflated Hutchinson (Section 2): smallest singular
+              triplets from the Hermitian gamma5 D, subspace iteration.
+  nn          the learned gauge-covariant preconditioner (not in the paper):
+              forward, backward, the tensor-core number format.
+  tune_mass   bare-mass tuning of the benchmark fields (input preparation:
+              m0 from the leftmost eigenvalue of D(0)).
 """

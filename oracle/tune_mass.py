@@ -25,10 +25,21 @@ from . import schwinger
 OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden", "masses.json")
 
 
-def leftmost_real(L: int, beta: float, seed: int = 0, shift: float = -0.3, k: int = 16) -> complex:
-    D = schwinger.dirac_sparse(gauge.links(gauge.field(L, beta, seed)), 0.0)
+def leftmost_of_links(U: np.ndarray, shift: float = -0.3, k: int = 16) -> complex:
+    """The eigenvalue of smallest real part of D(m0 = 0) on the links U: the k eigenvalues nearest to `shift`
+    (shift-invert Arnoldi), of which the leftmost."""
+    D = schwinger.dirac_sparse(U, 0.0)
     ev = spla.eigs(D, k=k, sigma=shift, return_eigenvectors=False, tol=1e-10)
     return complex(ev[np.argmin(ev.real)])
+
+
+def leftmost_real(L: int, beta: float, seed: int = 0, shift: float = -0.3, k: int = 16) -> complex:
+    return leftmost_of_links(gauge.links(gauge.field(L, beta, seed)), shift, k)
+
+
+def mass_for_target(lam_c: complex, target: float = 1e-3) -> float:
+    """m0 that moves the leftmost eigenvalue lam_c of D(0) to real part `target` (D(m0) = D(0) + m0 I)."""
+    return target - lam_c.real
 
 
 def main(specs, target: float = 1e-3):
@@ -38,7 +49,7 @@ def main(specs, target: float = 1e-3):
         L, beta = int(L), float(beta)
         t = time.time()
         lam = leftmost_real(L, beta)
-        m0 = target - lam.real
+        m0 = mass_for_target(lam, target)
         data["L%d_beta%g_seed0" % (L, beta)] = dict(
             L=L, beta=beta, seed=0, sweeps=500 if L <= 64 else 100, lambda_c=[lam.real, lam.imag],
             target=target, m0=round(m0, 6),
