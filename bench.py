@@ -140,6 +140,22 @@ def dist_env():
     return rank, world, local
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Gauge-field seed of one replica: every rank estimates its own field (no data-path collective)."""
+    return base + rank
+
+
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest x over the ranks of the default process group: the slowest replica sets the job's time."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ CPU oracle (reference arm / cpu_baseline)
 # Sample counts N_l of the L = 512 GPU estimate (bench default), used by the reference arm, which runs no GPU
 N_WORKLOAD_L512 = [8, 7, 58]
@@ -451,7 +467,7 @@ def main():
     if args.tensor_cores is not None:
         W["tensor_cores"] = args.tensor_cores
     L = W["L"]
-    seed = W["seed"] + rank
+    seed = replica_seed(W["seed"], rank)
     m0 = mass_for(L, W["beta"], W["seed"])
     U_host = gauge.links(gauge.field(L, W["beta"], seed))
     U = torch.from_numpy(U_host).cuda()
@@ -487,11 +503,7 @@ def main():
     launches = ctx.launches - launches0
     ms = e0.elapsed_time(e1) / args.steps
     rpt = ctx.timing_report()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     value = ms / 1e3
 
     # dominant kernel -> roofline (CUDA-core FMA peaks measured on this GPU by the library)
