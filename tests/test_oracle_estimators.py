@@ -3,7 +3,8 @@ variance 1/2 ||offdiag(A + A^T)||_F^2 (Section 2) for Hutchinson, for the
 MG-MLMC level differences (both forms) and for the Hutch++-deflated samples;
 the Hutch++ trace split; CholeskyQR2 against Householder QR; the stop rule of
 Algorithm 2 on hand-computed numbers; Algorithm 2 end to end against the
-exact trace."""
+exact trace, statistically and in the full-sketch special case (d = n), where
+it is exact."""
 import math
 
 import numpy as np
@@ -121,8 +122,28 @@ def test_stop_rule_hand_computed():
     # uniform: rho^2 = 1 / 2
     act = update_active([True, True], [9.0, 1.0], [10, 10], [1.0, 1.0], 0.1, 10.0, "uniform")
     assert act == [True, False]
+    # the uniform split is over the L - 1 = 2 stochastic level differences, not over L = 3 levels:
+    # V_0 / N_0 = 0.45 <= 1/2 stops level 0 (it would stay active against 1/3)
+    act = update_active([True, True], [4.5, 1.0], [10, 10], [1.0, 1.0], 0.1, 10.0, "uniform")
+    assert act == [False, False]
     # no decision before every level has a variance
     assert update_active([True, True], [0.0, 1.0], [1, 10], [1, 1], 0.1, 10.0) == [True, True]
+
+
+@pytest.mark.parametrize("form", ["accumulated", "reduced"])
+@pytest.mark.parametrize("noise", [rng.NOISE_RADEMACHER, rng.NOISE_Z4])
+def test_full_sketch_gives_the_exact_trace(small, form, noise):
+    """Special case of Algorithm 2 fixed by the mathematics: with a sketch as wide as the space (d = n), Q is
+    unitary, every projected sample z^H A zeta has z = (I - QQ^H) zeta = 0, the low-rank part tr(Q^H A Q) is
+    tr(A), and the estimate is the exact trace tr(D^{-1}) (dense inverse) with zero variance."""
+    D, H = small
+    ld = LevelDifference(H, form)
+    n = ld.vec_size(0)
+    r = mgmlmc_pp(ld, 1e-3, n, 1, seed=6, noise=noise)
+    exact = trace_inverse_dense(D.toarray())
+    assert abs(r["tau"] - exact) < 1e-10 * abs(exact)
+    assert r["N"] == [2] and max(abs(t) for t in r["samples"][0]) < 1e-10 * abs(exact)
+    assert abs(r["tau_lr"][0] - (exact - r["tau_L"])) < 1e-10 * abs(exact)
 
 
 @pytest.mark.parametrize("d", [0, 8])
