@@ -15,6 +15,7 @@ import test_oracle_multigrid as t_mg
 import test_oracle_nn as t_nn
 import test_oracle_operator as t_op
 import test_oracle_rng as t_rng
+import test_oracle_tune_mass as t_tm
 from oracle import multigrid as mg
 from oracle import schwinger as osch
 from synthetic import gauge
@@ -145,6 +146,28 @@ CASES = [
      lambda mp, m: (mp.setattr(t_df, "odf", m), t_df.test_singular_values_and_trace_split(deflation_op()))),
     ("deflation_largest_not_smallest", "deflation", "idx = np.argsort(np.abs(mu))[:k]", "idx = np.argsort(mu)[:k]",
      lambda mp, m: (mp.setattr(t_df, "odf", m), t_df.test_singular_values_and_trace_split(deflation_op()))),
+    ("z4_table_not_zero_mean", "rng", "np.array([1.0, 1j, -1.0, -1j])[q]", "np.array([1.0, 1j, 1.0, -1j])[q]",
+     lambda mp, m: (mp.setattr(t_rng, "rng", m), t_rng.test_z4_values_isotropy_and_second_moment())),
+    ("stream_counter_fields_overlap", "rng", "ctr = np.uint64((level << 56) | (phase << 48) | sample)",
+     "ctr = np.uint64((level << 48) | (phase << 48) | sample)",
+     lambda mp, m: (mp.setattr(t_rng, "rng", m), t_rng.test_streams_are_distinct())),
+    ("sigma_without_division_by_N", "estimators", "sigma = math.sqrt(sum(V[l] / N[l] for l in range(nd) if N[l] >= 2))",
+     "sigma = math.sqrt(sum(V[l] for l in range(nd) if N[l] >= 2))",
+     lambda mp, m: (mp.setattr(t_est, "LevelDifference", m.LevelDifference), mp.setattr(t_est, "mgmlmc_pp", m.mgmlmc_pp),
+                    t_est.test_algorithm2_end_to_end(small(), 0))),
+    ("sap_block_inverse_transposed", "multigrid", "inv = np.stack([np.linalg.inv(Dd[i][:, i].toarray()) for i in I])",
+     "inv = np.stack([np.linalg.inv(Dd[i][:, i].toarray()).T for i in I])",
+     lambda mp, m: (mp.setattr(t_mg, "mg", m), t_mg.test_sap_residual_vanishes_on_updated_colour())),
+    ("mass_shift_sign", "tune_mass", "    return target - lam_c.real", "    return target + lam_c.real",
+     lambda mp, m: (mp.setattr(t_tm, "otm", m), t_tm.test_interacting_field_matches_dense_spectrum_and_target())),
+    ("deflated_sample_sign", "deflation", "taus.append(complex(np.vdot(z, y) - np.vdot(c, g)))",
+     "taus.append(complex(np.vdot(z, y) + np.vdot(c, g)))",
+     lambda mp, m: (mp.setattr(t_df, "odf", m), t_df.test_deflated_hutchinson_unbiased_with_smaller_variance(
+         deflation_op()))),
+    ("subspace_iteration_without_gamma5", "deflation", "V, _ = qr_positive(solve(g5[:, None] * V))",
+     "V, _ = qr_positive(solve(V))",
+     lambda mp, m: (mp.setattr(t_df, "odf", m), t_df.test_subspace_iteration_converges_to_the_exact_subspace(
+         deflation_op()))),
     # ---- learned preconditioner: backward pass against finite differences
     ("nn_input_gradient_not_conjugated", "nn", 'gu = np.einsum("dkc,rxk->rxdc", np.conj(self.W[l]), gz)',
      'gu = np.einsum("dkc,rxk->rxdc", self.W[l], gz)',
@@ -155,6 +178,15 @@ CASES = [
     ("nn_activation_radial_term_dropped", "nn", "gz = np.where(on, rad * ph + scale * (g - rad * ph), 0)",
      "gz = np.where(on, scale * (g - rad * ph), 0)",
      lambda mp, m: (mp.setattr(t_nn, "onn", m), t_nn.test_backward_matches_finite_differences())),
+    ("nn_activation_bias_outside", "nn",
+     "s = np.where(mag > 0, np.maximum(0.0, mag + self.b[l][None, None, :]) / np.where(mag > 0, mag, 1), 0)",
+     "s = np.where(mag > 0, (np.maximum(0.0, mag) + self.b[l][None, None, :]) / np.where(mag > 0, mag, 1), 0)",
+     lambda mp, m: (mp.setattr(t_nn, "onn", m), t_nn.test_backward_matches_finite_differences())),
+    ("nn_diagonal_single_path", "nn", "T = 0.5 * (Tx[dx] * sh(Tt[dt], dx, 0) + Tt[dt] * sh(Tx[dx], 0, dt))",
+     "T = Tx[dx] * sh(Tt[dt], dx, 0)",
+     lambda mp, m: (mp.setattr(t_nn, "onn", m), t_nn.test_reversed_path_identity())),
+    ("nn_transport_periodic_t", "nn", "sgn_f = np.where(t == L - 1, -1.0, 1.0)", "sgn_f = np.ones((L, L))",
+     lambda mp, m: (mp.setattr(t_nn, "onn", m), t_nn.test_transport_of_constant_field_is_trivial())),
 ]
 
 

@@ -31,15 +31,18 @@ def test_rademacher_isotropy():
 
 
 def test_streams_are_distinct():
-    a = rng.rademacher(1, 0, rng.PHASE_STOCH, 0, 256)
-    for other in (rng.rademacher(2, 0, rng.PHASE_STOCH, 0, 256),
-                  rng.rademacher(1, 1, rng.PHASE_STOCH, 0, 256),
-                  rng.rademacher(1, 0, rng.PHASE_SKETCH, 0, 256),
-                  rng.rademacher(1, 0, rng.PHASE_STOCH, 1, 256)):
-        assert np.mean(a == other) < 0.7
-    assert np.array_equal(a, rng.rademacher(1, 0, rng.PHASE_STOCH, 0, 256))
+    """Streams that differ in any one counter field (seed, level, phase, sample) are different, pairwise: the
+    fields occupy disjoint bits of the counter, so e.g. (level 1, phase 0) and (level 0, phase 1) differ."""
+    keys = [(1, 0, rng.PHASE_STOCH, 0), (2, 0, rng.PHASE_STOCH, 0), (1, 1, rng.PHASE_STOCH, 0),
+            (1, 0, rng.PHASE_SKETCH, 0), (1, 0, rng.PHASE_STOCH, 1), (1, 1, rng.PHASE_SKETCH, 0),
+            (1, 0, rng.PHASE_STOCH, 1 << 40)]
+    vecs = [rng.rademacher(*k, 256) for k in keys]
+    for i in range(len(keys)):
+        for j in range(i):
+            assert np.mean(vecs[i] == vecs[j]) < 0.7, (keys[i], keys[j])
+    assert np.array_equal(vecs[0], rng.rademacher(1, 0, rng.PHASE_STOCH, 0, 256))
     # prefix property: component i does not depend on the vector length
-    assert np.array_equal(a[:100], rng.rademacher(1, 0, rng.PHASE_STOCH, 0, 100))
+    assert np.array_equal(vecs[0][:100], rng.rademacher(1, 0, rng.PHASE_STOCH, 0, 100))
 
 
 def test_z4_values_isotropy_and_second_moment():
