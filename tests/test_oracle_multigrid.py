@@ -203,6 +203,33 @@ def test_imported_prolongators_rebuild_the_hierarchy(hier):
     P[i, :] = rj
     P[j, :] = ri
     assert not mg.check_prolongator(P.tocsr(), 64, 2, 4)["support"]
+    # planted mistake: swap the two spin rows (chiralities) of fine site (0, 0): same aggregate, wrong chirality
+    P = hier.P[0].tolil()
+    r0, r1 = P.getrow(0).copy(), P.getrow(1).copy()
+    P[0, :] = r1
+    P[1, :] = r0
+    c = mg.check_prolongator(P.tocsr(), 64, 2, 4)
+    assert c["support"] and not c["chirality"]
+    # planted mistake: one column scaled by 1.1 is no longer orthonormal (|P^H P - I| = 0.21 on its diagonal)
+    P = hier.P[0].tocsc(copy=True)
+    P[:, 3] = P[:, 3] * 1.1
+    assert abs(mg.check_prolongator(P.tocsr(), 64, 2, 4)["orth"] - 0.21) < 1e-12
+
+
+def test_stencil_blocks_direction_convention():
+    """stencil_blocks on the fine operator gives the hop blocks of the Wilson formula: S[+x] = -1/2 (1 - sigma_1)
+    U_0(x), S[-x] = -1/2 (1 + sigma_1) conj(U_0(x - x^)), S[+t] with the antiperiodic sign on the last time slice."""
+    L = 8
+    U = gauge.links(gauge.field(L, 3.0, 2, sweeps=20))
+    S = mg.stencil_blocks(osch.dirac_sparse(U, 0.1), L, 2)
+    e, s1, s2 = np.eye(2), osch.SIGMA[0], osch.SIGMA[1]
+    T, X = 3, 5
+    assert np.abs(S[T, X, 0] - 2.1 * e).max() < 1e-15
+    assert np.abs(S[T, X, 1] + 0.5 * (e - s1) * U[T, X, 0]).max() < 1e-15
+    assert np.abs(S[T, X, 2] + 0.5 * (e + s1) * np.conj(U[T, X - 1, 0])).max() < 1e-15
+    assert np.abs(S[T, X, 3] + 0.5 * (e - s2) * U[T, X, 1]).max() < 1e-15
+    assert np.abs(S[T, X, 4] + 0.5 * (e + s2) * np.conj(U[T - 1, X, 1])).max() < 1e-15
+    assert np.abs(S[L - 1, X, 3] - 0.5 * (e - s2) * U[L - 1, X, 1]).max() < 1e-15
 
 
 def test_sparse_from_stencil_round_trip(hier):

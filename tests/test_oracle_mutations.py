@@ -127,6 +127,17 @@ CASES = [
     ("chirality_blocks_interleaved", "multigrid", "ks = np.arange(dc) + c * dc if d > 2 else np.array([c])",
      "ks = 2 * np.arange(dc) + c if d > 2 else np.array([c])",
      lambda mp, m: t_mg.test_orthonormal_and_aggregate_support(three_level_agg4(m))),
+    ("stencil_directions_swapped", "multigrid", "enumerate(((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)))",
+     "enumerate(((0, 0), (-1, 0), (1, 0), (0, 1), (0, -1)))",
+     lambda mp, m: (mp.setattr(t_mg, "mg", m), t_mg.test_stencil_blocks_direction_convention())),
+    ("check_prolongator_ignores_chirality", "multigrid",
+     "chiral = bool(np.all(chirality(fk, d) == chirality(ck, dc)))", "chiral = True",
+     lambda mp, m: (mp.setattr(t_mg, "mg", m),
+                    t_mg.test_imported_prolongators_rebuild_the_hierarchy(three_level_agg4(mg)))),
+    ("check_prolongator_ignores_orthonormality", "multigrid",
+     "orth = float(np.abs(G.data).max()) if G.nnz else 0.0", "orth = 0.0",
+     lambda mp, m: (mp.setattr(t_mg, "mg", m),
+                    t_mg.test_imported_prolongators_rebuild_the_hierarchy(three_level_agg4(mg)))),
     ("galerkin_transpose_not_adjoint", "multigrid", "Dc = (P.conj().T @ self.D[l] @ P).tocsr()",
      "Dc = (P.T @ self.D[l] @ P).tocsr()",
      lambda mp, m: t_mg.test_gamma5_coarse(small3(m))),
