@@ -33,6 +33,12 @@ def mutant(name, old, new):
     return m
 
 
+def use_estimators(mp, m):
+    """The estimator tests run Algorithm 2 with the mutant's level differences and estimator."""
+    mp.setattr(t_est, "LevelDifference", m.LevelDifference)
+    mp.setattr(t_est, "mgmlmc_pp", m.mgmlmc_pp)
+
+
 def small():
     """The estimator tests' L = 16 operator and two-level hierarchy."""
     D = osch.dirac_sparse(gauge.links(gauge.field(16, 3.0, 0)), -0.05)
@@ -69,7 +75,8 @@ CASES = [
      lambda mp, m: (mp.setattr(t_op, "osch", m), t_op.test_gamma5_hermiticity())),
     ("hop_factor_one", "schwinger", "vals.append(-0.5 * Pm[a, b] * Uf)", "vals.append(-1.0 * Pm[a, b] * Uf)",
      lambda mp, m: (mp.setattr(t_op, "osch", m), t_op.test_free_field_spectrum_and_trace(6, 0.3))),
-    ("backward_link_not_conjugated", "schwinger", "Ub = (np.conj(U[tb, xb, mu]) * eta_b)", "Ub = (U[tb, xb, mu] * eta_b)",
+    ("backward_link_not_conjugated", "schwinger", "Ub = (np.conj(U[tb, xb, mu]) * eta_b)",
+     "Ub = (U[tb, xb, mu] * eta_b)",
      lambda mp, m: (mp.setattr(t_op, "osch", m), t_op.test_gamma5_hermiticity())),
     ("backward_link_wrong_site", "schwinger", "Ub = (np.conj(U[tb, xb, mu]) * eta_b)",
      "Ub = (np.conj(U[t, x, mu]) * eta_b)",
@@ -111,14 +118,15 @@ CASES = [
                     t_est.test_level_difference_unbiased(small(), "reduced"))),
     ("projection_sign", "estimators", "z = zeta if Q[l] is None else zeta - Q[l] @ (Q[l].conj().T @ zeta)",
      "z = zeta if Q[l] is None else zeta + Q[l] @ (Q[l].conj().T @ zeta)",
-     lambda mp, m: (mp.setattr(t_est, "LevelDifference", m.LevelDifference), mp.setattr(t_est, "mgmlmc_pp", m.mgmlmc_pp),
+     lambda mp, m: (use_estimators(mp, m),
                     t_est.test_full_sketch_gives_the_exact_trace(small(), "accumulated", 0))),
     ("low_rank_trace_not_conjugated", "estimators", "tau_lr[l] = complex(np.sum(np.conj(S) * ld.apply(l, S)))",
      "tau_lr[l] = complex(np.sum(S * ld.apply(l, S)))",
-     lambda mp, m: (mp.setattr(t_est, "LevelDifference", m.LevelDifference), mp.setattr(t_est, "mgmlmc_pp", m.mgmlmc_pp),
+     lambda mp, m: (use_estimators(mp, m),
                     t_est.test_full_sketch_gives_the_exact_trace(small(), "reduced", 1))),
-    ("coarsest_term_not_conjugated", "estimators", "M = (Ph.conj().T @ W @ Ph).toarray()", "M = (Ph.T @ W @ Ph).toarray()",
-     lambda mp, m: (mp.setattr(t_est, "LevelDifference", m.LevelDifference), mp.setattr(t_est, "mgmlmc_pp", m.mgmlmc_pp),
+    ("coarsest_term_not_conjugated", "estimators", "M = (Ph.conj().T @ W @ Ph).toarray()",
+     "M = (Ph.T @ W @ Ph).toarray()",
+     lambda mp, m: (use_estimators(mp, m),
                     t_est.test_algorithm2_end_to_end(small(), 0))),
     # ---- multigrid (Section 3.1): orthonormal aggregation, Galerkin operator, SAP, V-cycle
     ("prolongator_not_orthonormalised", "multigrid", "                Q, _ = qr_positive(V[I, :])\n",
@@ -164,7 +172,7 @@ CASES = [
      lambda mp, m: (mp.setattr(t_rng, "rng", m), t_rng.test_streams_are_distinct())),
     ("sigma_without_division_by_N", "estimators", "sigma = math.sqrt(sum(V[l] / N[l] for l in range(nd) if N[l] >= 2))",
      "sigma = math.sqrt(sum(V[l] for l in range(nd) if N[l] >= 2))",
-     lambda mp, m: (mp.setattr(t_est, "LevelDifference", m.LevelDifference), mp.setattr(t_est, "mgmlmc_pp", m.mgmlmc_pp),
+     lambda mp, m: (use_estimators(mp, m),
                     t_est.test_algorithm2_end_to_end(small(), 0))),
     ("sap_block_inverse_transposed", "multigrid", "inv = np.stack([np.linalg.inv(Dd[i][:, i].toarray()) for i in I])",
      "inv = np.stack([np.linalg.inv(Dd[i][:, i].toarray()).T for i in I])",
