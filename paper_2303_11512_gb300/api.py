@@ -34,6 +34,51 @@ def _ptr(t: torch.Tensor, dtype=None) -> int:
     return t.data_ptr()
 
 
+# The C entry points receive bare device pointers and sizes and cannot see a tensor's shape or device, so every
+# wrapper checks both before the call: a vector tensor of the wrong size would become an out-of-bounds device
+# access, and one on another GPU a launch on the wrong device's memory.
+def _rows(name: str, t: torch.Tensor, n: int) -> int:
+    """Rows of the vector tensor t: [nrhs, n], or [n] as one row."""
+    if t.dim() == 1 and t.shape[0] == n:
+        return 1
+    if t.dim() != 2 or t.shape[1] != n:
+        raise ValueError("%s must be [nrhs, %d], got %s" % (name, n, tuple(t.shape)))
+    return int(t.shape[0])
+
+
+def check_vectors(device, *spec) -> int:
+    """spec: (name, tensor, n) triples, each tensor [nrhs, n] with one common nrhs and, unless device is None, on
+    `device`.  Returns nrhs; raises ValueError on a mismatch."""
+    nrhs = None
+    for name, t, n in spec:
+        r = _rows(name, t, n)
+        if nrhs is None:
+            nrhs = r
+        elif r != nrhs:
+            raise ValueError("%s has %d rows, %d expected" % (name, r, nrhs))
+        if device is not None and t.device != device:
+            raise ValueError("%s is on %s, the launches go to %s" % (name, t.device, device))
+    return nrhs
+
+
+def check_field(device, U: torch.Tensor, L: int):
+    """Gauge links U must be [L, L, 2] (on `device` unless it is None); raises ValueError."""
+    if tuple(U.shape) != (L, L, 2):
+        raise ValueError("U must be [%d, %d, 2], got %s" % (L, L, tuple(U.shape)))
+    if device is not None and U.device != device:
+        raise ValueError("U is on %s, the launches go to %s" % (U.device, device))
+
+
+def check_level(level: int, top: int):
+    if not 0 <= level < top:
+        raise ValueError("level %d outside 0 .. %d" % (level, top - 1))
+
+
+def _dev(ctx) -> torch.device:
+    """The device the context's launches go to: that of its stream."""
+    return ctx.stream.device
+
+
 def _vec_dtype(prec: int):
     return torch.complex64 if prec in (FP32, TF32, BF16, FP16) else torch.complex128
 
@@ -83,7 +128,8 @@ def schwinger_apply(ctx: Context, U: torch.Tensor, L: int, m0: float, x: torch.T
                     prec: int = FP64):
     """y = D x (fine Schwinger operator); x, y [nrhs, 2 L^2]."""
     dt = _vec_dtype(prec)
-    nrhs = x.shape[0] if x.dim() == 2 else 1
+    check_field(_dev(ctx), U, L)
+    nrhs = check_vectors(_dev(ctx), ("x", x, 2 * L * L), ("y", y, 2 * L * L))
     check(_lib.load().schwinger_apply(ctx.ptr, _ptr(U, torch.complex128), L, m0, _ptr(x, dt), _ptr(y, dt),
                                       nrhs, prec), ctx.ptr)
 
@@ -91,7 +137,9 @@ def schwinger_apply(ctx: Context, U: torch.Tensor, L: int, m0: float, x: torch.T
 def mgmlmc_rademacher(ctx: Context, seed: int, level: int, phase: int, sample0: int, n: int, nrhs: int,
                       out: torch.Tensor | None = None) -> torch.Tensor:
     if out is None:
-        out = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
+        out = torch.empty((nrhs, n), dtype=torch.complex128, device=_dev(ctx))
+    elif check_vectors(_dev(ctx), ("out", out, n)) != nrhs:
+        raise ValueError("out must be [%d, %d], got %s" % (nrhs, n, tuple(out.shape)))
     check(_lib.load().mgmlmc_rademacher(ctx.ptr, seed, level, phase, sample0, n, nrhs,
                                         _ptr(out, torch.complex128)), ctx.ptr)
     return out
@@ -101,7 +149,9 @@ def mgmlmc_noise(ctx: Context, kind: int, seed: int, level: int, phase: int, sam
                  out: torch.Tensor | None = None) -> torch.Tensor:
     """Rademacher (kind NOISE_RADEMACHER) or Z4 (NOISE_Z4) vectors of the counter-based streams."""
     if out is None:
-        out = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
+        out = torch.empty((nrhs, n), dtype=torch.complex128, device=_dev(ctx))
+    elif check_vectors(_dev(ctx), ("out", out, n)) != nrhs:
+        raise ValueError("out must be [%d, %d], got %s" % (nrhs, n, tuple(out.shape)))
     check(_lib.load().mgmlmc_noise(ctx.ptr, kind, seed, level, phase, sample0, n, nrhs,
                                    _ptr(out, torch.complex128)), ctx.ptr)
     return out
@@ -143,24 +193,32 @@ class Hierarchy:
 
     def apply(self, level: int, x: torch.Tensor, y: torch.Tensor, prec: int = FP64):
         dt = _vec_dtype(prec)
-        check(_lib.load().mg_apply(self.ctx.ptr, self.ptr, level, _ptr(x, dt), _ptr(y, dt), x.shape[0], prec),
+        check_level(level, self.levels)
+        nrhs = check_vectors(_dev(self.ctx), ("x", x, self.n[level]), ("y", y, self.n[level]))
+        check(_lib.load().mg_apply(self.ctx.ptr, self.ptr, level, _ptr(x, dt), _ptr(y, dt), nrhs, prec),
               self.ctx.ptr)
 
     def restrict(self, level: int, xf: torch.Tensor, xc: torch.Tensor, prec: int = FP64):
         dt = _vec_dtype(prec)
-        check(_lib.load().mg_restrict(self.ctx.ptr, self.ptr, level, _ptr(xf, dt), _ptr(xc, dt), xf.shape[0],
-                                      prec), self.ctx.ptr)
+        check_level(level, self.levels - 1)
+        nrhs = check_vectors(_dev(self.ctx), ("xf", xf, self.n[level]), ("xc", xc, self.n[level + 1]))
+        check(_lib.load().mg_restrict(self.ctx.ptr, self.ptr, level, _ptr(xf, dt), _ptr(xc, dt), nrhs, prec),
+              self.ctx.ptr)
 
     def prolong(self, level: int, xc: torch.Tensor, xf: torch.Tensor, prec: int = FP64):
         dt = _vec_dtype(prec)
-        check(_lib.load().mg_prolong(self.ctx.ptr, self.ptr, level, _ptr(xc, dt), _ptr(xf, dt), xc.shape[0],
-                                     prec), self.ctx.ptr)
+        check_level(level, self.levels - 1)
+        nrhs = check_vectors(_dev(self.ctx), ("xc", xc, self.n[level + 1]), ("xf", xf, self.n[level]))
+        check(_lib.load().mg_prolong(self.ctx.ptr, self.ptr, level, _ptr(xc, dt), _ptr(xf, dt), nrhs, prec),
+              self.ctx.ptr)
 
     def smooth(self, level: int, f: torch.Tensor, x: torch.Tensor, prec: int = FP64, sweeps: int = 1):
         """SAP sweeps for D_l x = f, x updated in place (prec FP64, FP32, or TF32 / BF16 on the tensor cores)."""
         dt = _vec_dtype(prec)
-        check(_lib.load().mg_smooth(self.ctx.ptr, self.ptr, level, _ptr(f, dt), _ptr(x, dt), f.shape[0], prec,
-                                    sweeps), self.ctx.ptr)
+        check_level(level, self.levels)
+        nrhs = check_vectors(_dev(self.ctx), ("f", f, self.n[level]), ("x", x, self.n[level]))
+        check(_lib.load().mg_smooth(self.ctx.ptr, self.ptr, level, _ptr(f, dt), _ptr(x, dt), nrhs, prec, sweeps),
+              self.ctx.ptr)
 
     def tc_status(self) -> int:
         return _lib.load().mg_tc_status(self.ctx.ptr, self.ptr)
@@ -172,7 +230,9 @@ class Hierarchy:
 
     def vcycle(self, level: int, b: torch.Tensor, x: torch.Tensor, prec: int = FP64):
         dt = _vec_dtype(prec)
-        check(_lib.load().mg_vcycle(self.ctx.ptr, self.ptr, level, _ptr(b, dt), _ptr(x, dt), b.shape[0], prec),
+        check_level(level, self.levels)
+        nrhs = check_vectors(_dev(self.ctx), ("b", b, self.n[level]), ("x", x, self.n[level]))
+        check(_lib.load().mg_vcycle(self.ctx.ptr, self.ptr, level, _ptr(b, dt), _ptr(x, dt), nrhs, prec),
               self.ctx.ptr)
 
     def get_prolongator(self, level: int, agg: int, ntv: int) -> np.ndarray:
@@ -234,6 +294,7 @@ def tune_clear():
 
 
 def mg_setup(ctx: Context, U: torch.Tensor, L: int, m0: float, **params) -> Hierarchy:
+    check_field(_dev(ctx), U, L)
     p = mg_params(**params)
     h = C.c_void_p()
     check(_lib.load().mg_setup(ctx.ptr, _ptr(U, torch.complex128), L, m0, C.byref(p), C.byref(h)), ctx.ptr)
@@ -247,10 +308,11 @@ def _stats(st: SolveStats) -> dict:
 
 def fgmres_batched(ctx: Context, h: Hierarchy, level: int, b: torch.Tensor, x: torch.Tensor,
                    raise_on_nonconvergence: bool = True, **solve) -> dict:
+    check_level(level, h.levels)
+    nrhs = check_vectors(_dev(ctx), ("b", b, h.n[level]), ("x", x, h.n[level]))
     sp = solve_params(**solve)
     dt = _vec_dtype(sp.prec)
     st = SolveStats()
-    nrhs = b.shape[0]
     its = np.zeros(nrhs, dtype=np.int32)
     rc = _lib.load().fgmres_batched(ctx.ptr, h.ptr, level, _ptr(b, dt), _ptr(x, dt), nrhs, C.byref(sp),
                                     C.byref(st), its.ctypes.data)
@@ -265,23 +327,26 @@ def mlmc_level_sample(ctx: Context, h: Hierarchy, level: int, zeta: torch.Tensor
                       form: int = REDUCED, **solve) -> dict:
     """Level difference `level` applied to zeta: level-size vectors (REDUCED) or fine-size vectors
     (ACCUMULATED, y = Phat A Rhat zeta)."""
+    check_level(level, h.levels - 1)
     n = h.n[0] if form == ACCUMULATED else h.n[level]
-    if zeta.shape[-1] != n or y.shape != zeta.shape:
-        raise ValueError("zeta and y must be [nrhs, %d] for this form" % n)
+    nrhs = check_vectors(_dev(ctx), ("zeta", zeta, n), ("y", y, n))
     sp = solve_params(**solve)
     st = SolveStats()
     check(_lib.load().mlmc_level_sample(ctx.ptr, h.ptr, level, form, _ptr(zeta, torch.complex128),
-                                        _ptr(y, torch.complex128), zeta.shape[0], C.byref(sp), C.byref(st)),
+                                        _ptr(y, torch.complex128), nrhs, C.byref(sp), C.byref(st)),
           ctx.ptr)
     return _stats(st)
 
 
 def mg_restrict_to_level(ctx: Context, h: Hierarchy, level: int, zeta_fine: torch.Tensor,
                          out: torch.Tensor | None = None) -> torch.Tensor:
+    check_level(level, h.levels)
+    nrhs = check_vectors(_dev(ctx), ("zeta_fine", zeta_fine, h.n[0]))
     if out is None:
-        out = torch.empty((zeta_fine.shape[0], h.n[level]), dtype=torch.complex128, device="cuda")
+        out = torch.empty((nrhs, h.n[level]), dtype=torch.complex128, device=_dev(ctx))
+    check_vectors(_dev(ctx), ("zeta_fine", zeta_fine, h.n[0]), ("out", out, h.n[level]))
     check(_lib.load().mg_restrict_to_level(ctx.ptr, h.ptr, level, _ptr(zeta_fine, torch.complex128),
-                                           _ptr(out, torch.complex128), zeta_fine.shape[0]), ctx.ptr)
+                                           _ptr(out, torch.complex128), nrhs), ctx.ptr)
     return out
 
 
@@ -293,7 +358,7 @@ class Sketch:
         self.d, self.n = d.value, n.value
 
     def Q(self) -> torch.Tensor:
-        q = torch.empty((self.d, self.n), dtype=torch.complex128, device="cuda")
+        q = torch.empty((self.d, self.n), dtype=torch.complex128, device=_dev(self.ctx))
         check(_lib.load().hutchpp_sketch_get_q(self.ctx.ptr, self.ptr, _ptr(q), None, None), self.ctx.ptr)
         torch.cuda.synchronize()
         return q
@@ -324,6 +389,7 @@ def mg_dense_inverse(ctx: Context, A: torch.Tensor, prec: int = FP64, barrier_po
     """In-place inverse of the square device matrix A (complex128 for FP64, complex64 for FP32)."""
     if A.dim() != 2 or A.shape[0] != A.shape[1]:
         raise ValueError("A must be square")
+    check_vectors(_dev(ctx), ("A", A, A.shape[1]))
     check(_lib.load().mg_dense_inverse(ctx.ptr, _ptr(A, _vec_dtype(prec)), A.shape[0], prec, barrier_polls),
           ctx.ptr)
 
@@ -332,11 +398,17 @@ def hutchpp_cholqr2(ctx: Context, Y: torch.Tensor):
     """In-place CholeskyQR2 of the basis Y [d, n] (rows are the vectors), complex128."""
     if Y.dim() != 2:
         raise ValueError("Y must be [d, n]")
+    check_vectors(_dev(ctx), ("Y", Y, Y.shape[1]))
     check(_lib.load().hutchpp_cholqr2(ctx.ptr, _ptr(Y, torch.complex128), Y.shape[0], Y.shape[1]), ctx.ptr)
 
 
 def hutchpp_project(ctx: Context, sketch: Sketch | None, zeta: torch.Tensor, y: torch.Tensor) -> np.ndarray:
-    nrhs, n = zeta.shape
+    if zeta.dim() != 2:
+        raise ValueError("zeta must be [nrhs, n], got %s" % (tuple(zeta.shape),))
+    n = int(zeta.shape[1])
+    if sketch is not None and sketch.d > 0 and sketch.n != n:
+        raise ValueError("the sketch's basis has vectors of %d entries, zeta of %d" % (sketch.n, n))
+    nrhs = check_vectors(_dev(ctx), ("zeta", zeta, n), ("y", y, n))
     out = np.empty(nrhs, dtype=np.complex128)
     check(_lib.load().hutchpp_project(ctx.ptr, sketch.ptr if sketch else None, _ptr(zeta, torch.complex128),
                                       _ptr(y, torch.complex128), n, nrhs,
@@ -351,6 +423,7 @@ class Net:
                  tensor_cores: bool | None = None):
         """tensor_cores: True = BF16 tcgen05 layers, False = FP32 CUDA-core layers, None = the library's
         default (tensor cores where L is a multiple of 16)."""
+        check_field(_dev(ctx), U, L)
         self.ctx, self.L = ctx, L
         h = C.c_void_p()
         check(_lib.load().nn_create(ctx.ptr, _ptr(U, torch.complex128), L, layers, channels, seed, C.byref(h)),
@@ -369,6 +442,7 @@ class Net:
 
     def set_field(self, U: torch.Tensor, L: int):
         """Rebind to another gauge field (weights and Adam state kept)."""
+        check_field(_dev(self.ctx), U, L)
         check(_lib.load().nn_set_field(self.ctx.ptr, self.ptr, _ptr(U, torch.complex128), L), self.ctx.ptr)
         self.L = L
 
@@ -384,21 +458,27 @@ class Net:
 
     def forward(self, r: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
         y = torch.empty_like(r) if y is None else y
+        n = 2 * self.L * self.L
+        nrhs = check_vectors(_dev(self.ctx), ("r", r, n), ("y", y, n))
         check(_lib.load().nn_forward(self.ctx.ptr, self.ptr, _ptr(r, torch.complex64), _ptr(y, torch.complex64),
-                                     r.shape[0]), self.ctx.ptr)
+                                     nrhs), self.ctx.ptr)
         return y
 
     def loss_grad(self, r: torch.Tensor, e: torch.Tensor):
+        n = 2 * self.L * self.L
+        nrhs = check_vectors(_dev(self.ctx), ("r", r, n), ("e", e, n))
         loss = C.c_double()
         g = np.empty(self.nparams, dtype=np.float32)
         check(_lib.load().nn_loss_grad(self.ctx.ptr, self.ptr, _ptr(r, torch.complex64), _ptr(e, torch.complex64),
-                                       r.shape[0], C.byref(loss), g.ctypes.data), self.ctx.ptr)
+                                       nrhs, C.byref(loss), g.ctypes.data), self.ctx.ptr)
         return loss.value, g
 
     def train_step(self, r: torch.Tensor, e: torch.Tensor, lr: float = 1e-3) -> float:
+        n = 2 * self.L * self.L
+        nrhs = check_vectors(_dev(self.ctx), ("r", r, n), ("e", e, n))
         loss = C.c_double()
         check(_lib.load().nn_train_step(self.ctx.ptr, self.ptr, _ptr(r, torch.complex64), _ptr(e, torch.complex64),
-                                        r.shape[0], lr, C.byref(loss)), self.ctx.ptr)
+                                        nrhs, lr, C.byref(loss)), self.ctx.ptr)
         return loss.value
 
     def attach(self, h: "Hierarchy"):
@@ -421,7 +501,7 @@ def nn_harvest_pairs(ctx: Context, h: "Hierarchy", count: int, seed: int = 3, sa
     """Training pairs (R, E) [count, n_0] complex64 from the hierarchy's own V-cycle and FP32 solves
     (R = (zeta - D V zeta)/|.|, E = (D^{-1} zeta - V zeta)/|.|; see nn_harvest_pairs in the header)."""
     n = h.n[0]
-    R = torch.empty((count, n), dtype=torch.complex64, device="cuda")
+    R = torch.empty((count, n), dtype=torch.complex64, device=_dev(ctx))
     E = torch.empty_like(R)
     check(_lib.load().nn_harvest_pairs(ctx.ptr, h.ptr, seed, sample0, count, tol, _ptr(R, torch.complex64),
                                        _ptr(E, torch.complex64)), ctx.ptr)
