@@ -4,6 +4,7 @@ window of the slab it multiplies (the site j + f) at the accumulator columns of 
 staged weight rows; the sub-tiles of a window that hold no weight block are the zero ones, which no copy
 writes; and the first MMA of each site's columns overwrites them.  These are the invariants the kernel's
 layout comment states; the GPU parity tests check the results, this checks the tables without a GPU."""
+import ast
 import os
 import re
 
@@ -23,7 +24,7 @@ def tables():
         m = re.search(r"__constant__\s+(?:short|signed char)\s+%s(?:\[[^\]]*\])+\s*=\s*(\{.*?\});" % name, src,
                       re.S)
         assert m, name
-        out[name] = eval(m.group(1).replace("{", "[").replace("}", "]"))
+        out[name] = ast.literal_eval(m.group(1).replace("{", "[").replace("}", "]"))
     m = re.search(r"constexpr int TB_BROWS = (\d+);", src)
     out["rows"] = int(m.group(1))
     m = re.search(r"\(z \? (\d+) : (\d+)\) \* 64", src)       # the rows the kernel clears once
