@@ -44,11 +44,10 @@ FALLBACK_M0 = {512: -0.07, 128: -0.1199}
 
 # DRAM bytes per algorithmic byte of the tensor-core coarse kernels, from one ncu capture each of a level-1 launch
 # with 32 rhs of the L = 512 hierarchy (dram__bytes_read + _write against the launch's algorithmic bytes); the
-# benchmark scales them to its average launch.  Per-site TF32 stencil: 235.99 + 48.96 MB against 301.99 MB
-# (profiles/k_tc_stencil_level1_32rhs_L512.md).  2x2-block FP16 stencil, SAP residual of one colour: 109.31 +
-# 5.99 MB against 109.05 MB (8192 sites x 32 rhs x 256 B + 41.94 MB of weights); SAP block update: 83.95 + 5.74
-# MB against 134.22 MB (its x and 16-bit copy writes stay in L2;
-# profiles/k_tcb_k_tcs_sap_level1_32rhs_L512.md).
+# benchmark scales them to its average launch.  Per-site TF32 stencil: 235.99 + 48.96 MB against 301.99 MB.
+# 2x2-block FP16 stencil, SAP residual of one colour: 109.31 + 5.99 MB against 109.05 MB (8192 sites x 32 rhs x
+# 256 B + 41.94 MB of weights); SAP block update: 83.95 + 5.74 MB against 134.22 MB (its x and 16-bit copy
+# writes stay in L2).
 TRAFFIC_PER_ALG_BYTE = {
     "MODE = 0; int BF = 0": ((235.987 + 48.964) / 301.990, "ncu capture of one launch (level 1, 32 rhs): 284.95 MB "
                             "DRAM / 301.99 MB algorithmic, scaled to the average launch"),
