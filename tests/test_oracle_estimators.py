@@ -205,6 +205,20 @@ def test_gamma5_trace_properties():
     assert abs(np.trace(g5 @ np.linalg.inv(D0))) < 1e-12
 
 
+def test_gamma5_weighted_hutchinson(small):
+    """Algorithm 1 for tr(gamma5 D^{-1}) (Section 1: traces after multiplication with a gamma matrix) with Z4
+    vectors lands within 4.5 sigma of the dense trace, which is real and far from tr(D^{-1})."""
+    D, _ = small
+    A = np.linalg.inv(D.toarray())
+    g5 = osch.gamma5(16).diagonal()
+    exact = np.sum(g5 * np.diag(A))
+    z = rng.noise(rng.NOISE_Z4, 3, 0, rng.PHASE_HUTCH, 0, 64)
+    assert set(np.round(z, 12).tolist()) == {1, 1j, -1, -1j}       # kind Z4 draws fourth roots of unity
+    tau, V, s, _ = hutchinson(lambda b: A @ b, A.shape[0], 0.5, seed=8, smax=600, noise=rng.NOISE_Z4, weight=g5)
+    assert abs(tau - exact) < 4.5 * math.sqrt(V / s)
+    assert abs(exact - np.trace(A)) > 20 * math.sqrt(V / s)
+
+
 @pytest.mark.parametrize("form", ["accumulated", "reduced"])
 def test_gamma5_telescoping_and_unbiased(small3_g5, form):
     """With gamma5 weighting the exact level traces telescope to tr(gamma5 D^{-1}) (the gamma5 signs of the

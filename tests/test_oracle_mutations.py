@@ -46,7 +46,7 @@ def small():
 
 
 def small3(mgm=mg):
-    """The multigrid tests' three-level L = 32 hierarchy (2x2 aggregates), built by module mgm."""
+    """The three-level L = 32 hierarchy (2x2 aggregates) of the multigrid and gamma5-trace tests, built by mgm."""
     U = gauge.links(gauge.field(32, 3.0, 3, sweeps=40))
     return mgm.Hierarchy(osch.dirac_sparse(U, -0.05), 32, levels=3, agg=2, ntv=2, setup_sweeps=2, seed=1)
 
@@ -108,6 +108,10 @@ CASES = [
     ("hutchinson_stop_without_s", "estimators", "if s >= min_samples and V / s <= (abs(tau) * eps) ** 2:",
      "if s >= min_samples and V <= (abs(tau) * eps) ** 2:",
      lambda mp, m: (mp.setattr(t_est, "hutchinson", m.hutchinson), t_est.test_hutchinson_algorithm1_stop(small()))),
+    ("hutchinson_weight_dropped", "estimators", "            x = weight * x\n", "            x = x\n",
+     lambda mp, m: (mp.setattr(t_est, "hutchinson", m.hutchinson), t_est.test_gamma5_weighted_hutchinson(small()))),
+    ("noise_kind_ignored", "rng", "    if kind == NOISE_Z4:\n", "    if kind == -1:\n",
+     lambda mp, m: (mp.setattr(t_est, "rng", m), t_est.test_gamma5_weighted_hutchinson(small()))),
     # ---- level differences (eqs. mlmc_decomp_matrix / mlmc_dec_trace_reduced) and Algorithm 2's samples
     ("accumulated_difference_sign", "estimators", "            Y = a - b\n", "            Y = a + b\n",
      lambda mp, m: (mp.setattr(t_est, "LevelDifference", m.LevelDifference),
@@ -128,6 +132,9 @@ CASES = [
      "M = (Ph.T @ W @ Ph).toarray()",
      lambda mp, m: (use_estimators(mp, m),
                     t_est.test_algorithm2_end_to_end(small(), 0))),
+    ("level_weight_dropped", "estimators", "        return Y if W is None else W @ Y\n", "        return Y\n",
+     lambda mp, m: (mp.setattr(t_est, "LevelDifference", m.LevelDifference),
+                    t_est.test_gamma5_telescoping_and_unbiased(small3(), "reduced"))),
     # ---- multigrid (Section 3.1): orthonormal aggregation, Galerkin operator, SAP, V-cycle
     ("prolongator_not_orthonormalised", "multigrid", "                Q, _ = qr_positive(V[I, :])\n",
      "                Q = V[I, :]\n",
