@@ -38,3 +38,48 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[cname, "sizeof"] == ctypes.sizeof(cls), cname
         for field in cls._fields_:
             assert got[cname, field[0]] == getattr(cls, field[0]).offset, (cname, field[0])
+
+
+def _prototypes():
+    """name -> (return type, [argument types]) of every function the header declares (comments removed)."""
+    import re
+    src = open(os.path.join(ROOT, "include", "mgmlmc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = {}
+    for m in re.finditer(r"^\s*((?:const\s+)?[A-Za-z_]\w*\s*\**)\s*([A-Za-z_]\w*)\s*\(([^)]*)\)\s*;", src, re.M):
+        ret, name, args = m.group(1), m.group(2), m.group(3).strip()
+        params = [] if args in ("", "void") else [a.strip() for a in args.split(",")]
+        out[name] = (ret.strip(), params)
+    return out
+
+
+def _kind_of_c(decl: str) -> str:
+    """Calling-convention class of a C parameter or return type: pointer, double, int64, uint64, int, void."""
+    if "*" in decl:
+        return "pointer"
+    words = decl.replace("const", "").split()
+    base = words[0] if words else ""
+    return {"double": "double", "int64_t": "int64", "uint64_t": "uint64", "int": "int", "void": "void"}[base]
+
+
+def _kind_of_ctypes(t) -> str:
+    import ctypes as C
+    if t is None:
+        return "void"
+    if t in (C.c_void_p, C.c_char_p) or hasattr(t, "contents") or t.__name__.startswith("LP_"):
+        return "pointer"
+    return {C.c_double: "double", C.c_int64: "int64", C.c_uint64: "uint64", C.c_int: "int"}[t]
+
+
+def test_ctypes_signatures_match_the_prototypes():
+    """Every entry point's ctypes argument and return types have the C prototype's calling-convention classes
+    (pointer, double, 64-bit or 32-bit integer), in the same number and order."""
+    protos = _prototypes()
+    assert set(protos) == set(_lib.SIGNATURES)
+    for name, (res, args) in _lib.SIGNATURES.items():
+        cret, cargs = protos[name]
+        assert _kind_of_ctypes(res) == _kind_of_c(cret), name
+        assert len(args) == len(cargs), (name, len(args), len(cargs))
+        for i, (a, c) in enumerate(zip(args, cargs)):
+            assert _kind_of_ctypes(a) == _kind_of_c(c.rsplit(" ", 1)[0] if "*" not in c else c), (name, i, c)
