@@ -83,3 +83,29 @@ def test_ctypes_signatures_match_the_prototypes():
         assert len(args) == len(cargs), (name, len(args), len(cargs))
         for i, (a, c) in enumerate(zip(args, cargs)):
             assert _kind_of_ctypes(a) == _kind_of_c(c.rsplit(" ", 1)[0] if "*" not in c else c), (name, i, c)
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Status codes, precisions, forms, policies, noise kinds, trace weights, stream phases and the level limit
+    of the binding have the header's values (printed by a C program compiled on the host)."""
+    import re
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    hdr = open(os.path.join(ROOT, "include", "mgmlmc.h")).read()
+    names = sorted(set(re.findall(r"\bMGMLMC_([A-Z0-9_]+)\s*=", hdr)))
+    assert len(names) > 20
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "mgmlmc.h"\nint main(void) {\n'
+                   + "".join('printf("%s %%d\\n", (int)MGMLMC_%s);\n' % (n, n) for n in names + ["MAX_LEVELS"])
+                   + "return 0;\n}\n")
+    exe = tmp_path / "consts"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    values = dict((a, int(b)) for a, b in (line.split() for line in subprocess.run(
+        [str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()))
+    checked = 0
+    for name, value in values.items():
+        if hasattr(_lib, name):
+            assert getattr(_lib, name) == value, name
+            checked += 1
+    assert checked >= 25
