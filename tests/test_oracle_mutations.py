@@ -174,6 +174,8 @@ CASES = [
      lambda mp, m: (mp.setattr(t_df, "odf", m), t_df.test_singular_values_and_trace_split(deflation_op()))),
     ("z4_table_not_zero_mean", "rng", "np.array([1.0, 1j, -1.0, -1j])[q]", "np.array([1.0, 1j, 1.0, -1j])[q]",
      lambda mp, m: (mp.setattr(t_rng, "rng", m), t_rng.test_z4_values_isotropy_and_second_moment())),
+    ("complex_test_vector_same_bit", "rng", "return s[0::2] + 1j * s[1::2]", "return s[0::2] + 1j * s[0::2]",
+     lambda mp, m: (mp.setattr(t_rng, "rng", m), t_rng.test_complex_rademacher_test_vectors())),
     ("stream_counter_fields_overlap", "rng", "ctr = np.uint64((level << 56) | (phase << 48) | sample)",
      "ctr = np.uint64((level << 48) | (phase << 48) | sample)",
      lambda mp, m: (mp.setattr(t_rng, "rng", m), t_rng.test_streams_are_distinct())),

@@ -63,3 +63,17 @@ def test_z4_values_isotropy_and_second_moment():
     z = rng.z4(11, 1, rng.PHASE_STOCH, 3, n)
     assert np.array_equal(np.where(np.isin(z, [1, 1j]), 1.0, -1.0), r)
     assert np.array_equal(rng.noise(rng.NOISE_Z4, 11, 1, 0, 3, n), z)
+
+
+def test_complex_rademacher_test_vectors():
+    """The set-up's complex test vectors have independent +-1 real and imaginary parts (E|z|^2 = 2, E Re z Im z = 0,
+    Re and Im uncorrelated across entries), drawn from consecutive words of the same counter stream."""
+    n, s = 4096, 32
+    Z = np.stack([rng.complex_rademacher(5, 1, rng.PHASE_TESTVEC, j, n) for j in range(s)])
+    assert set(np.unique(Z.real)) == {-1.0, 1.0} and set(np.unique(Z.imag)) == {-1.0, 1.0}
+    assert abs((Z.real * Z.imag).mean()) < 5 / np.sqrt(Z.size)
+    assert abs(Z.real.mean()) < 5 / np.sqrt(Z.size) and abs(Z.imag.mean()) < 5 / np.sqrt(Z.size)
+    w = rng.words(5, 1, rng.PHASE_TESTVEC, 0, 2 * n)
+    sign = np.where((w >> np.uint64(63)) == 0, 1.0, -1.0)
+    assert np.array_equal(Z[0], sign[0::2] + 1j * sign[1::2])
+
